@@ -1,0 +1,175 @@
+/*
+ * rsc.h -- C ABI of the GB300 library for convection in a rotating spherical
+ * shell with implicit Coriolis integration (Gonzalez Sembla, Rambert, Feudel,
+ * Tuckerman, "Convection in a Rapidly Rotating Spherical Shell: Newton's
+ * Method Using Implicit Coriolis Integration", Mathematics 13, 2113, 2025).
+ *
+ * Model (Sec. 2.1, Eqs. Navier-Stokes, temp, div, BCs): Boussinesq convection
+ * between r_in = eta/(1-eta) and r_out = 1/(1-eta), no-slip walls, T = 1 at
+ * r_in and T = 0 at r_out, gravity proportional to r, rotation about z.
+ *
+ * State layout (Sec. 3.1, Eq. expansion).  Every state or direction vector is
+ * a contiguous array of n = 3 * P * Nr * 2 doubles in DEVICE memory unless a
+ * name ends in _host:
+ *     v[((field * P + pair) * Nr + k) * 2 + part]
+ *   field 0 = toroidal potential e, 1 = poloidal potential f, 2 = total
+ *   temperature T (U = curl(e r_hat) + curl curl(f r_hat));
+ *   pair  = (m, l) with m = 0, Ms, 2Ms, ... <= L and, inside each m,
+ *           l = m .. L; P is the number of pairs;
+ *   k     = Chebyshev degree of x = 2r - r_in - r_out, k < Nr;
+ *   part  = 0 real, 1 imaginary.
+ * Spherical harmonics follow Eq. Ylm_norm (no Condon-Shortley phase) and a
+ * real field is sum_l a_l0 Y_l^0 + 2 Re sum_{m>0} a_lm Y_l^m.  The imaginary
+ * parts of m = 0 coefficients and the entries of e_00, f_00 are zero in every
+ * state the library writes.
+ *
+ * Ownership.  The caller owns every state / vector buffer (for example
+ * torch tensors).  The library owns its tables, factorisations, Krylov basis
+ * and workspace: allocated by rsc_create (and by the first call with a new
+ * time step), released by rsc_destroy.
+ *
+ * Streams.  Device work is issued on the stream given to rsc_create.  Calls
+ * that return numbers to the host (rsc_newton_rw, rsc_norm2, *_host)
+ * synchronise that stream; the others are asynchronous.  A context must not be
+ * used from two threads at once.
+ *
+ * Errors.  Every call returns an rsc_status; none aborts or traps.  The text
+ * of the last error is available from rsc_last_error.
+ */
+#ifndef RSC_H
+#define RSC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSC_ABI_VERSION 1
+
+typedef struct rsc_ctx rsc_ctx;
+
+typedef enum {
+  RSC_OK = 0,
+  RSC_EINVAL = 1,      /* bad argument: null pointer, size out of range      */
+  RSC_ENOMEM = 2,      /* device or host allocation failed                    */
+  RSC_ECUDA = 3,       /* a CUDA runtime call failed                          */
+  RSC_ENOCONV = 4,     /* Newton or GMRES reached its iteration cap           */
+  RSC_ENAN = 5,        /* a non-finite residual or Krylov norm                */
+  RSC_ESINGULAR = 6,   /* zero pivot while factorising the implicit operator  */
+  RSC_ETIMEOUT = 7     /* a bounded device wait gave up                       */
+} rsc_status;
+
+typedef enum {
+  RSC_FP64 = 0,        /* every stage in FP64                                 */
+  RSC_MIXED = 1        /* transforms and products in FP32; RHS, block solves,
+                          GMRES and Newton update in FP64                      */
+} rsc_precision;
+
+/* Physical parameters and truncation (Sec. 2.1 parameters; Sec. 3.1 grids).
+ * Ra is the rotational Rayleigh number, Ek the Ekman number, Pr the Prandtl
+ * number, eta = r_in / r_out.  The triangular truncation keeps l <= L and
+ * m <= L with m a multiple of Ms (the azimuthal sector 0 <= phi < 2 pi/Ms).
+ * Nr Chebyshev coefficients per radial profile, 4 <= Nr <= 128, L <= 255.  */
+typedef struct {
+  double Ra, Ek, Pr, eta;
+  int L, Ms, Nr;
+  int precision;       /* rsc_precision */
+} rsc_params;
+
+/* Newton-GMRES controls (Sec. 3.3: GMRES relative tolerance 1e-10, Newton
+ * pseudo-timestep dt = 200).                                                 */
+typedef struct {
+  double tol;          /* stop when ||B(U) - U||_2 < tol                      */
+  int max_newton;      /* Newton iteration cap                                */
+  int kmax;            /* GMRES iteration cap (no restart), <= 512            */
+  double gmres_tol;    /* relative GMRES tolerance                            */
+  double dt_newton;    /* pseudo-timestep of the Stokes preconditioner        */
+} rsc_newton_opts;
+
+#define RSC_MAX_HISTORY 64
+typedef struct {
+  int iterations;                         /* Newton iterations taken          */
+  int gmres_total;                        /* Jacobian actions in all GMRES    */
+  double residual;                        /* final ||B(U) - U||_2             */
+  double C;                               /* final drift speed                */
+  double residual_history[RSC_MAX_HISTORY];
+  int gmres_history[RSC_MAX_HISTORY];
+  double seconds;                         /* wall time of the call            */
+} rsc_newton_report;
+
+/* Create a context for `params` on the CUDA stream `stream` (a cudaStream_t;
+ * NULL = legacy default stream) of the current device.  Builds the Gauss-
+ * Legendre, associated-Legendre and Chebyshev tables (Sec. 3.1) and uploads
+ * them.  Factorisations are built on first use of each time step.          */
+rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out);
+
+/* Release every resource of the context (waits for its stream).            */
+rsc_status rsc_destroy(rsc_ctx* ctx);
+
+/* Change the parameters.  A new Ra only changes the explicit part (Sec. 4.2
+ * notes that Ra appears only on the right-hand side); Ek, Pr or eta drop the
+ * cached factorisations; L, Ms, Nr and precision cannot change.            */
+rsc_status rsc_set_params(rsc_ctx* ctx, const rsc_params* params);
+
+/* Number of doubles n in a state vector, and the number of pairs P.        */
+rsc_status rsc_state_size(const rsc_ctx* ctx, size_t* n_real, int* n_pairs);
+
+/* Write the conductive state U = 0, T = r_out r_in / r - r_in (Sec. 2.1) as
+ * the steady solution of the discrete temperature equation.                */
+rsc_status rsc_conductive_state(rsc_ctx* ctx, double* U);
+
+/* nsteps IMEX Euler steps in place, U <- B(U) (Eq. discrete), with the drift
+ * term C d/dphi in the explicit part (Sec. 3.4; C = 0 for plain time
+ * stepping).  The implicit operator holds diffusion and Coriolis
+ * (Eqs. impcor_e_final, impcor_f_final); it is factorised once per dt.     */
+rsc_status rsc_step(rsc_ctx* ctx, double* U, double C, double dt, int nsteps);
+
+/* Same as rsc_step on a HOST buffer: copies to the device, steps, copies
+ * back (synchronous).  For end-to-end timing.                              */
+rsc_status rsc_step_host(rsc_ctx* ctx, double* U_host, double C, double dt, int nsteps);
+
+/* Explicit terms N(U) at the collocation radii, layout of a state vector:
+ * e-rows e_r.curl F, f-rows e_r.curl curl F (F = Ek U x omega + Ra T r/r_out),
+ * T-rows -U.grad T (Sec. 3.2, Eq. defineFimp).  Boundary rows hold the
+ * unprojected values.  A diagnostic of the transform pipeline.             */
+rsc_status rsc_explicit_terms(rsc_ctx* ctx, const double* U, double* N);
+
+/* Jacobian action of Sec. 3.3-3.4 for `count` directions:
+ *   out_i = (B_U - I) u_i with the drift unknown c = u_i[J] (Sec. 3.4):
+ *   c is read, u_i[J] set to zero in a private copy, c i m M U added to the
+ *   explicit part, homogeneous boundary conditions applied.
+ * J < 0 gives the steady-state action (no drift unknown).  u and out hold
+ * `count` vectors of n doubles back to back; U is the base state.          */
+rsc_status rsc_apply_jacobian(rsc_ctx* ctx, const double* U, double C, long J,
+                              const double* u, double* out, int count, double dt);
+
+/* Newton-GMRES for a rotating wave (Secs. 3.3-3.4, Eq. twNewton): solves
+ * (B_U - I)(u, c) = B(U) - U with matrix-free GMRES, then U <- U - u,
+ * C <- C - c, until ||B(U) - U||_2 < opts->tol.  J >= 0 is the frozen phase
+ * slot; J < 0 solves for a steady state (C unchanged).  U and *C are updated
+ * in place.  Returns RSC_ENOCONV when max_newton is reached.               */
+rsc_status rsc_newton_rw(rsc_ctx* ctx, double* U, double* C, long J,
+                         const rsc_newton_opts* opts, rsc_newton_report* report);
+
+/* Newton-GMRES on a HOST state (copies in and out inside the call).        */
+rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
+                              const rsc_newton_opts* opts, rsc_newton_report* report);
+
+/* Euclidean norm of a device vector of n doubles (synchronous).            */
+rsc_status rsc_norm2(rsc_ctx* ctx, const double* v, size_t n, double* out);
+
+/* Text of the last error on this context (never NULL).                     */
+const char* rsc_last_error(const rsc_ctx* ctx);
+
+/* Name of a status code.                                                   */
+const char* rsc_status_string(int status);
+
+/* ABI version of the loaded library (RSC_ABI_VERSION).                     */
+int rsc_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSC_H */

@@ -1,0 +1,754 @@
+// C ABI and host orchestration of the rotating-shell library (see rsc.h).
+//
+// One context = one problem (parameters + truncation) on one CUDA stream.
+// A time step (Eq. discrete) and a Jacobian action (Secs. 3.3-3.4) are a
+// fixed sequence of kernel launches on that stream; Newton-GMRES (Eq.
+// precond, Eq. twNewton) drives them from the host with one small
+// device-to-host read per GMRES iteration for the Hessenberg column.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+
+#include "kernels.cuh"
+#include "rsc_internal.h"
+
+using namespace rsc;
+
+namespace {
+
+constexpr int kTT = 4;            // latitudes per block in k_products
+constexpr int kMaxKrylov = 512;
+
+struct DevFactor {
+  double dt = std::nan("");
+  long* chain_off = nullptr;
+  double2* G = nullptr;
+  double2* H = nullptr;
+  double2* W = nullptr;
+  double* Tinv = nullptr;
+  bool valid = false;
+};
+
+template <typename R>
+struct LegDev {
+  R* buf[8] = {nullptr};  // P dP Ps Pw dPw Psw twc tws
+  DevLegendre<R> view() const {
+    return DevLegendre<R>{buf[0], buf[1], buf[2], buf[3], buf[4], buf[5], buf[6], buf[7]};
+  }
+};
+
+}  // namespace
+
+struct rsc_ctx {
+  rsc_params p{};
+  Dims d;
+  HostTables t;
+  cudaStream_t s = nullptr;
+  int device = 0;
+  // geometry
+  int *d_m_of = nullptr, *d_pstart = nullptr, *d_pair_l = nullptr, *d_pair_m = nullptr;
+  long* d_leg_off = nullptr;
+  double *d_rc = nullptr, *d_rd = nullptr, *d_EcT0 = nullptr, *d_EcT2 = nullptr;
+  double *d_EdT0 = nullptr, *d_EdT1 = nullptr, *d_EdT2 = nullptr, *d_R0T = nullptr, *d_R1T = nullptr;
+  LegDev<double> leg64;
+  LegDev<float> leg32;
+  // workspace (sized for FP64; the FP32 path uses the front part)
+  void *SR = nullptr, *FC = nullptr, *FCU = nullptr, *FA = nullptr, *AR = nullptr;
+  double2* rhs = nullptr;
+  double* xtmp = nullptr;
+  double* vtmp = nullptr;
+  double* rtmp = nullptr;
+  // factorisations, two slots (time stepping dt and Newton dt)
+  DevFactor fac[2];
+  int fac_next = 0;
+  // Krylov
+  double* V = nullptr;
+  int V_cols = 0;
+  double* partial = nullptr;
+  double* dots = nullptr;
+  double* h_pinned = nullptr;
+  int nblk_dot = 0;
+  std::string err;
+  DevGeom geom() const {
+    DevGeom g;
+    g.L = d.L; g.Ms = d.Ms; g.Nr = d.Nr; g.Nd = d.Nd; g.nlat = d.nlat; g.nlat2 = d.nlat2;
+    g.nphi = d.nphi; g.nm = d.nm; g.K = d.K; g.P = d.P; g.r_in = d.r_in; g.r_out = d.r_out;
+    g.m_of = d_m_of; g.pstart = d_pstart; g.leg_off = d_leg_off; g.pair_l = d_pair_l;
+    g.pair_m = d_pair_m; g.rc = d_rc; g.rd = d_rd; g.EcT0 = d_EcT0; g.EcT2 = d_EcT2;
+    g.EdT0 = d_EdT0; g.EdT1 = d_EdT1; g.EdT2 = d_EdT2; g.R0T = d_R0T; g.R1T = d_R1T;
+    return g;
+  }
+};
+
+namespace {
+
+template <typename R> const LegDev<R>& leg(const rsc_ctx* ctx);
+template <> const LegDev<double>& leg<double>(const rsc_ctx* ctx) { return ctx->leg64; }
+template <> const LegDev<float>& leg<float>(const rsc_ctx* ctx) { return ctx->leg32; }
+
+#define CK(call)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+      return RSC_ECUDA;                                                       \
+    }                                                                         \
+  } while (0)
+
+#define CKS(expr)                                                             \
+  do {                                                                        \
+    rsc_status s_ = (expr);                                                   \
+    if (s_ != RSC_OK) return s_;                                              \
+  } while (0)
+
+int round32(int v) { return ((v + 31) / 32) * 32; }
+
+template <typename T>
+rsc_status upload(rsc_ctx* ctx, T** dst, const T* src, size_t count) {
+  CK(cudaMalloc((void**)dst, std::max<size_t>(1, count) * sizeof(T)));
+  if (count) CK(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+  return RSC_OK;
+}
+
+std::vector<double> transpose(const std::vector<double>& a, int rows, int cols) {
+  std::vector<double> o((size_t)rows * cols);
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) o[(size_t)c * rows + r] = a[(size_t)r * cols + c];
+  return o;
+}
+
+rsc_status check_params(const rsc_params* p) {
+  if (!p) return RSC_EINVAL;
+  if (p->L < 1 || p->L > 255 || p->Ms < 1 || p->Ms > p->L || p->Nr < 6 || p->Nr > 128)
+    return RSC_EINVAL;
+  if (!(p->eta > 0 && p->eta < 1) || !(p->Ek > 0) || !(p->Pr > 0) || !std::isfinite(p->Ra))
+    return RSC_EINVAL;
+  if (p->precision != RSC_FP64 && p->precision != RSC_MIXED) return RSC_EINVAL;
+  return RSC_OK;
+}
+
+void free_factor(DevFactor& f) {
+  cudaFree(f.chain_off);
+  cudaFree(f.G);
+  cudaFree(f.H);
+  cudaFree(f.W);
+  cudaFree(f.Tinv);
+  f = DevFactor();
+}
+
+template <typename R>
+rsc_status upload_legendre(rsc_ctx* ctx, LegDev<R>& L) {
+  const HostTables& t = ctx->t;
+  const std::vector<double>* src[6] = {&t.P, &t.dP, &t.Ps, &t.Pw, &t.dPw, &t.Psw};
+  for (int q = 0; q < 6; ++q) {
+    std::vector<R> v(src[q]->begin(), src[q]->end());
+    CKS(upload(ctx, &L.buf[q], v.data(), v.size()));
+  }
+  const int K1 = ctx->d.K + 1, nphi = ctx->d.nphi;
+  std::vector<R> c((size_t)K1 * nphi), s((size_t)K1 * nphi);
+  for (int a = 0; a < K1; ++a)
+    for (int j = 0; j < nphi; ++j) {
+      // exact reduction of the angle to [0, nphi) before the trig call
+      const long q = ((long)a * j) % nphi;
+      const double ang = 2.0 * 3.14159265358979323846 * (double)q / nphi;
+      c[(size_t)a * nphi + j] = (R)std::cos(ang);
+      s[(size_t)a * nphi + j] = (R)std::sin(ang);
+    }
+  CKS(upload(ctx, &L.buf[6], c.data(), c.size()));
+  CKS(upload(ctx, &L.buf[7], s.data(), s.size()));
+  return RSC_OK;
+}
+
+rsc_status set_smem_limits(rsc_ctx* ctx) {
+  const int big = 200 * 1024;
+  CK(cudaFuncSetAttribute(k_products<double, false, kTT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_products<double, true, kTT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_products<float, false, kTT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_products<float, true, kTT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_synth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_synth<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_analysis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_analysis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_rhs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_rhs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  return RSC_OK;
+}
+
+rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
+  for (auto& f : ctx->fac)
+    if (f.valid && f.dt == dt) {
+      *out = &f;
+      return RSC_OK;
+    }
+  DevFactor& f = ctx->fac[ctx->fac_next];
+  ctx->fac_next ^= 1;
+  CK(cudaStreamSynchronize(ctx->s));
+  free_factor(f);
+  HostFactor hf;
+  const int bad = build_factor(ctx->p, ctx->d, ctx->t, dt, hf);
+  if (bad) {
+    ctx->err = "singular block in the implicit operator (chain " + std::to_string(bad - 1) + ")";
+    return RSC_ESINGULAR;
+  }
+  CKS(upload(ctx, &f.chain_off, hf.chain_off.data(), hf.chain_off.size()));
+  static_assert(sizeof(cplx) == sizeof(double2), "complex layout");
+  CKS(upload(ctx, &f.G, reinterpret_cast<const double2*>(hf.G.data()), hf.G.size()));
+  CKS(upload(ctx, &f.H, reinterpret_cast<const double2*>(hf.H.data()), hf.H.size()));
+  CKS(upload(ctx, &f.W, reinterpret_cast<const double2*>(hf.W.data()), hf.W.size()));
+  CKS(upload(ctx, &f.Tinv, hf.Tinv.data(), hf.Tinv.size()));
+  f.dt = dt;
+  f.valid = true;
+  *out = &f;
+  return RSC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pipeline stages.
+template <typename R>
+rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
+  using V = typename C2<R>::T;
+  const Dims& d = ctx->d;
+  const DevGeom g = ctx->geom();
+  k_radial<R><<<d.P, round32(std::max(d.Nd, 32)), 3 * d.Nr * sizeof(double2), ctx->s>>>(
+      g, reinterpret_cast<const double2*>(x), reinterpret_cast<V*>(ctx->SR));
+  CK(cudaGetLastError());
+  const LegDev<R>& L = leg<R>(ctx);
+  k_synth<R><<<dim3(d.nm, d.Nd), round32(d.nlat2), (size_t)(d.L + 1) * 8 * sizeof(V), ctx->s>>>(
+      g, L.view(), reinterpret_cast<const V*>(ctx->SR), reinterpret_cast<V*>(FCout));
+  CK(cudaGetLastError());
+  return RSC_OK;
+}
+
+template <typename R>
+rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
+  using V = typename C2<R>::T;
+  const Dims& d = ctx->d;
+  const DevGeom g = ctx->geom();
+  const LegDev<R>& L = leg<R>(ctx);
+  const int K1 = d.K + 1;
+  const int NF = lin ? 18 : 9;
+  const size_t smem = (size_t)NF * kTT * K1 * sizeof(V) + 2 * (size_t)K1 * d.nphi * sizeof(R) +
+                      4 * (size_t)kTT * d.nphi * sizeof(R);
+  dim3 grid(d.Nd, (d.nlat + kTT - 1) / kTT);
+  if (lin)
+    k_products<R, true, kTT><<<grid, 128, smem, ctx->s>>>(
+        g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC),
+        reinterpret_cast<const V*>(ctx->FCU), reinterpret_cast<V*>(ctx->FA));
+  else
+    k_products<R, false, kTT><<<grid, 128, smem, ctx->s>>>(
+        g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC), nullptr,
+        reinterpret_cast<V*>(ctx->FA));
+  CK(cudaGetLastError());
+  k_analysis<R><<<dim3(d.nm, d.Nd), round32(d.L + 1), 8 * (size_t)d.nlat2 * sizeof(V), ctx->s>>>(
+      g, L.view(), reinterpret_cast<const V*>(ctx->FA), reinterpret_cast<V*>(ctx->AR));
+  CK(cudaGetLastError());
+  return RSC_OK;
+}
+
+template <typename R>
+rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const double* U,
+                     double2* out) {
+  using V = typename C2<R>::T;
+  const Dims& d = ctx->d;
+  const size_t smem = (4 * (size_t)d.Nd + 6 * (size_t)d.Nr) * sizeof(double2);
+  k_rhs<R><<<d.P, round32(d.Nr), smem, ctx->s>>>(
+      ctx->geom(), rp, reinterpret_cast<const V*>(ctx->AR), reinterpret_cast<const double2*>(x),
+      reinterpret_cast<const double2*>(U), out);
+  CK(cudaGetLastError());
+  return RSC_OK;
+}
+
+rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
+  const Dims& d = ctx->d;
+  k_chain_solve<<<2 * d.nm, 256, 3 * (size_t)d.Nr * sizeof(double2), ctx->s>>>(
+      ctx->geom(), f->chain_off, f->G, f->H, f->W, ctx->rhs, reinterpret_cast<double2*>(out));
+  CK(cudaGetLastError());
+  k_temp_solve<<<d.P, round32(d.Nr), (size_t)d.Nr * sizeof(double2), ctx->s>>>(
+      ctx->geom(), f->Tinv, ctx->rhs, reinterpret_cast<double2*>(out));
+  CK(cudaGetLastError());
+  return RSC_OK;
+}
+
+RhsParams make_rp(rsc_ctx* ctx, double dt, double C, int mode) {
+  RhsParams rp;
+  rp.inv_dt = std::isfinite(dt) ? 1.0 / dt : 0.0;
+  rp.C = C;
+  rp.c = 0.0;
+  rp.Ek = ctx->p.Ek;
+  rp.Ra = ctx->p.Ra;
+  rp.r_out = ctx->d.r_out;
+  rp.mode = mode;
+  rp.has_c = 0;
+  return rp;
+}
+
+// One IMEX step in place, transforms in precision R.
+template <typename R>
+rsc_status do_step(rsc_ctx* ctx, double* U, double C, double dt) {
+  DevFactor* f = nullptr;
+  CKS(get_factor(ctx, dt, &f));
+  CKS(stage_synth<R>(ctx, U, ctx->FC));
+  CKS(stage_products_analysis<R>(ctx, false));
+  CKS(stage_rhs<R>(ctx, make_rp(ctx, dt, C, 0), U, nullptr, ctx->rhs));
+  CKS(stage_solve(ctx, f, U));
+  return RSC_OK;
+}
+
+rsc_status step_any(rsc_ctx* ctx, double* U, double C, double dt, bool fp32) {
+  return fp32 ? do_step<float>(ctx, U, C, dt) : do_step<double>(ctx, U, C, dt);
+}
+
+// Base-state grid coefficients for Jacobian actions.
+rsc_status cache_base(rsc_ctx* ctx, const double* U, bool fp32) {
+  return fp32 ? stage_synth<float>(ctx, U, ctx->FCU) : stage_synth<double>(ctx, U, ctx->FCU);
+}
+
+rsc_status launch_1d_grid(long n, int* blocks) {
+  *blocks = (int)std::min<long>((n + 255) / 256, 152L * 8);
+  return RSC_OK;
+}
+
+// out = (B_U - I) u with the drift unknown in slot J (Sec. 3.4); base cached.
+template <typename R>
+rsc_status do_jvp(rsc_ctx* ctx, const double* U, double C, long J, const double* u, double* out,
+                  double dt) {
+  DevFactor* f = nullptr;
+  CKS(get_factor(ctx, dt, &f));
+  const long n = ctx->d.n();
+  int nb;
+  launch_1d_grid(n, &nb);
+  double c = 0.0;
+  k_copy_zero_slot<<<nb, 256, 0, ctx->s>>>(u, J, ctx->xtmp, n);
+  CK(cudaGetLastError());
+  if (J >= 0) {
+    CK(cudaMemcpyAsync(ctx->h_pinned, u + J, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    c = ctx->h_pinned[0];
+  }
+  CKS(stage_synth<R>(ctx, ctx->xtmp, ctx->FC));
+  CKS(stage_products_analysis<R>(ctx, true));
+  RhsParams rp = make_rp(ctx, dt, C, 1);
+  rp.c = c;
+  rp.has_c = (J >= 0 && c != 0.0) ? 1 : 0;
+  CKS(stage_rhs<R>(ctx, rp, ctx->xtmp, U, ctx->rhs));
+  CKS(stage_solve(ctx, f, out));
+  k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, ctx->xtmp, 1.0, out, n);
+  CK(cudaGetLastError());
+  return RSC_OK;
+}
+
+rsc_status jvp_any(rsc_ctx* ctx, const double* U, double C, long J, const double* u, double* out,
+                   double dt, bool fp32) {
+  return fp32 ? do_jvp<float>(ctx, U, C, J, u, out, dt) : do_jvp<double>(ctx, U, C, J, u, out, dt);
+}
+
+// dots[j] = V_j . w for j < nv (written to ctx->dots on the device)
+rsc_status dots(rsc_ctx* ctx, const double* V, long ld, int nv, const double* w, long n,
+                double* dst) {
+  k_dots<<<dim3(ctx->nblk_dot, nv), 256, 0, ctx->s>>>(V, ld, nv, w, n, ctx->partial);
+  CK(cudaGetLastError());
+  k_reduce_rows<<<nv, 256, 0, ctx->s>>>(ctx->partial, ctx->nblk_dot, dst);
+  CK(cudaGetLastError());
+  return RSC_OK;
+}
+
+rsc_status ensure_krylov(rsc_ctx* ctx, int kmax) {
+  if (ctx->V_cols >= kmax + 1) return RSC_OK;
+  CK(cudaStreamSynchronize(ctx->s));
+  cudaFree(ctx->V);
+  ctx->V = nullptr;
+  const long n = ctx->d.n();
+  CK(cudaMalloc(&ctx->V, (size_t)(kmax + 1) * n * sizeof(double)));
+  ctx->V_cols = kmax + 1;
+  return RSC_OK;
+}
+
+rsc_status norm2(rsc_ctx* ctx, const double* v, long n, double* out) {
+  CKS(dots(ctx, v, n, 1, v, n, ctx->dots));
+  CK(cudaMemcpyAsync(ctx->h_pinned, ctx->dots, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  *out = std::sqrt(ctx->h_pinned[0]);
+  return RSC_OK;
+}
+
+// GMRES (Saad-Schultz) with classical Gram-Schmidt and one re-orthogonalisation
+// (CGS2), zero initial guess, no restart.  Solves (B_U - I) x = b; x returned
+// in `x`.  Each iteration reads k + 3 doubles back for the Hessenberg column.
+rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* b, double* x,
+                 double dt, int kmax, double tol, bool fp32, int* iters, double* relres) {
+  const long n = ctx->d.n();
+  CKS(ensure_krylov(ctx, kmax));
+  int nb;
+  launch_1d_grid(n, &nb);
+  double beta;
+  CKS(norm2(ctx, b, n, &beta));
+  if (!std::isfinite(beta)) {
+    ctx->err = "non-finite right-hand side in GMRES";
+    return RSC_ENAN;
+  }
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), ctx->s));
+  *iters = 0;
+  *relres = 0.0;
+  if (beta == 0.0) return RSC_OK;
+  double* V = ctx->V;
+  k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / beta, b, 0.0, V, n);
+  CK(cudaGetLastError());
+  std::vector<double> H((size_t)(kmax + 1) * kmax, 0.0), cs(kmax), sn(kmax), gvec(kmax + 1, 0.0);
+  gvec[0] = beta;
+  int k = 0;
+  double res = beta;
+  for (k = 0; k < kmax; ++k) {
+    double* w = V + (long)(k + 1) * n;
+    CKS(jvp_any(ctx, U, C, J, V + (long)k * n, w, dt, fp32));
+    // CGS2
+    CKS(dots(ctx, V, n, k + 1, w, n, ctx->dots));
+    k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots, -1.0, w, n);
+    CK(cudaGetLastError());
+    CKS(dots(ctx, V, n, k + 1, w, n, ctx->dots + (k + 1)));
+    k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots + (k + 1), -1.0, w, n);
+    CK(cudaGetLastError());
+    CKS(dots(ctx, w, n, 1, w, n, ctx->dots + 2 * (k + 1)));
+    CK(cudaMemcpyAsync(ctx->h_pinned, ctx->dots, (2 * (k + 1) + 1) * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    const double* hh = ctx->h_pinned;
+    for (int i = 0; i <= k; ++i) H[(size_t)i * kmax + k] = hh[i] + hh[k + 1 + i];
+    const double hn = std::sqrt(std::max(0.0, hh[2 * (k + 1)]));
+    if (!std::isfinite(hn)) {
+      ctx->err = "non-finite Krylov vector";
+      return RSC_ENAN;
+    }
+    H[(size_t)(k + 1) * kmax + k] = hn;
+    // Givens rotations
+    for (int i = 0; i < k; ++i) {
+      const double a = H[(size_t)i * kmax + k], bb = H[(size_t)(i + 1) * kmax + k];
+      H[(size_t)i * kmax + k] = cs[i] * a + sn[i] * bb;
+      H[(size_t)(i + 1) * kmax + k] = -sn[i] * a + cs[i] * bb;
+    }
+    const double a = H[(size_t)k * kmax + k], bb = H[(size_t)(k + 1) * kmax + k];
+    const double rr = std::hypot(a, bb);
+    cs[k] = (rr == 0.0) ? 1.0 : a / rr;
+    sn[k] = (rr == 0.0) ? 0.0 : bb / rr;
+    H[(size_t)k * kmax + k] = rr;
+    H[(size_t)(k + 1) * kmax + k] = 0.0;
+    gvec[k + 1] = -sn[k] * gvec[k];
+    gvec[k] = cs[k] * gvec[k];
+    res = std::fabs(gvec[k + 1]);
+    if (res <= tol * beta || hn == 0.0) {
+      ++k;
+      break;
+    }
+    k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / hn, w, 0.0, w, n);
+    CK(cudaGetLastError());
+  }
+  const int kk = std::min(k, kmax);
+  std::vector<double> y(kk, 0.0);
+  for (int i = kk - 1; i >= 0; --i) {
+    double s = gvec[i];
+    for (int q = i + 1; q < kk; ++q) s -= H[(size_t)i * kmax + q] * y[q];
+    y[i] = s / H[(size_t)i * kmax + i];
+  }
+  CK(cudaMemcpyAsync(ctx->dots, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+  k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, kk, ctx->dots, 1.0, x, n);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->s));
+  *iters = kk;
+  *relres = res / beta;
+  return RSC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int rsc_abi_version(void) { return RSC_ABI_VERSION; }
+
+const char* rsc_status_string(int s) {
+  switch (s) {
+    case RSC_OK: return "RSC_OK";
+    case RSC_EINVAL: return "RSC_EINVAL";
+    case RSC_ENOMEM: return "RSC_ENOMEM";
+    case RSC_ECUDA: return "RSC_ECUDA";
+    case RSC_ENOCONV: return "RSC_ENOCONV";
+    case RSC_ENAN: return "RSC_ENAN";
+    case RSC_ESINGULAR: return "RSC_ESINGULAR";
+    case RSC_ETIMEOUT: return "RSC_ETIMEOUT";
+    default: return "unknown status";
+  }
+}
+
+const char* rsc_last_error(const rsc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
+  if (!out) return RSC_EINVAL;
+  *out = nullptr;
+  CKS(check_params(params));
+  rsc_ctx* ctx = new (std::nothrow) rsc_ctx();
+  if (!ctx) return RSC_ENOMEM;
+  ctx->p = *params;
+  ctx->s = reinterpret_cast<cudaStream_t>(stream);
+  build_dims(ctx->p, ctx->d);
+  build_tables(ctx->p, ctx->d, ctx->t);
+  rsc_status st = RSC_OK;
+  auto fail = [&](rsc_status s) {
+    *out = ctx;  // keep the context so that rsc_last_error works; caller destroys
+    return s;
+  };
+  const Dims& d = ctx->d;
+  const HostTables& t = ctx->t;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    ctx->err = "no CUDA device";
+    return fail(RSC_ECUDA);
+  }
+#define UP(dst, vec) \
+  if ((st = upload(ctx, &dst, vec.data(), vec.size())) != RSC_OK) return fail(st)
+  UP(ctx->d_m_of, t.m_of);
+  UP(ctx->d_pstart, t.pstart);
+  UP(ctx->d_pair_l, t.pair_l);
+  UP(ctx->d_pair_m, t.pair_m);
+  UP(ctx->d_leg_off, t.leg_off);
+  UP(ctx->d_rc, t.rc);
+  UP(ctx->d_rd, t.rd);
+  {
+    auto e0 = transpose(t.Ec[0], d.Nr, d.Nr), e2 = transpose(t.Ec[2], d.Nr, d.Nr);
+    auto d0 = transpose(t.Ed[0], d.Nd, d.Nr), d1 = transpose(t.Ed[1], d.Nd, d.Nr),
+         d2 = transpose(t.Ed[2], d.Nd, d.Nr);
+    auto r0 = transpose(t.R0, d.Nr, d.Nd), r1 = transpose(t.R1, d.Nr, d.Nd);
+    UP(ctx->d_EcT0, e0);
+    UP(ctx->d_EcT2, e2);
+    UP(ctx->d_EdT0, d0);
+    UP(ctx->d_EdT1, d1);
+    UP(ctx->d_EdT2, d2);
+    UP(ctx->d_R0T, r0);
+    UP(ctx->d_R1T, r1);
+  }
+#undef UP
+  if ((st = upload_legendre(ctx, ctx->leg64)) != RSC_OK) return fail(st);
+  if ((st = upload_legendre(ctx, ctx->leg32)) != RSC_OK) return fail(st);
+  if ((st = set_smem_limits(ctx)) != RSC_OK) return fail(st);
+  const size_t c16 = sizeof(double2);
+  const size_t K1 = d.K + 1;
+  auto alloc = [&](void** p, size_t bytes) -> rsc_status {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      ctx->err = "cudaMalloc of workspace failed";
+      return RSC_ENOMEM;
+    }
+    return RSC_OK;
+  };
+  const long n = d.n();
+  if ((st = alloc(&ctx->SR, (size_t)d.P * d.Nd * 8 * c16)) != RSC_OK) return fail(st);
+  if ((st = alloc(&ctx->FC, 9 * (size_t)d.Nd * K1 * d.nlat * c16)) != RSC_OK) return fail(st);
+  if ((st = alloc(&ctx->FCU, 9 * (size_t)d.Nd * K1 * d.nlat * c16)) != RSC_OK) return fail(st);
+  if ((st = alloc(&ctx->FA, 4 * (size_t)d.Nd * K1 * d.nlat * c16)) != RSC_OK) return fail(st);
+  if ((st = alloc(&ctx->AR, (size_t)d.P * d.Nd * 4 * c16)) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->rhs, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->xtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->vtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->rtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
+  ctx->nblk_dot = (int)std::min<long>((n + 255) / 256, 304);
+  if ((st = alloc((void**)&ctx->partial, (size_t)ctx->nblk_dot * (kMaxKrylov + 2) * sizeof(double))) != RSC_OK)
+    return fail(st);
+  if ((st = alloc((void**)&ctx->dots, (size_t)(3 * kMaxKrylov + 8) * sizeof(double))) != RSC_OK)
+    return fail(st);
+  if (cudaMallocHost((void**)&ctx->h_pinned, (size_t)(3 * kMaxKrylov + 8) * sizeof(double)) != cudaSuccess) {
+    ctx->err = "cudaMallocHost failed";
+    return fail(RSC_ENOMEM);
+  }
+  *out = ctx;
+  return RSC_OK;
+}
+
+rsc_status rsc_destroy(rsc_ctx* ctx) {
+  if (!ctx) return RSC_EINVAL;
+  if (ctx->s) cudaStreamSynchronize(ctx->s);
+  else cudaDeviceSynchronize();
+  void* bufs[] = {ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
+                  ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
+                  ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
+                  ctx->AR, ctx->rhs, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->partial,
+                  ctx->dots};
+  for (void* b : bufs) cudaFree(b);
+  for (int q = 0; q < 8; ++q) {
+    cudaFree(ctx->leg64.buf[q]);
+    cudaFree(ctx->leg32.buf[q]);
+  }
+  for (auto& f : ctx->fac) free_factor(f);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  delete ctx;
+  return RSC_OK;
+}
+
+rsc_status rsc_set_params(rsc_ctx* ctx, const rsc_params* params) {
+  if (!ctx) return RSC_EINVAL;
+  CKS(check_params(params));
+  if (params->L != ctx->p.L || params->Ms != ctx->p.Ms || params->Nr != ctx->p.Nr ||
+      params->precision != ctx->p.precision) {
+    ctx->err = "L, Ms, Nr and precision are fixed for a context";
+    return RSC_EINVAL;
+  }
+  const bool refactor = params->Ek != ctx->p.Ek || params->Pr != ctx->p.Pr || params->eta != ctx->p.eta;
+  if (params->eta != ctx->p.eta) {
+    ctx->err = "eta is fixed for a context (it defines the radial grid)";
+    return RSC_EINVAL;
+  }
+  CK(cudaStreamSynchronize(ctx->s));
+  ctx->p = *params;
+  if (refactor)
+    for (auto& f : ctx->fac) free_factor(f);
+  return RSC_OK;
+}
+
+rsc_status rsc_state_size(const rsc_ctx* ctx, size_t* n_real, int* n_pairs) {
+  if (!ctx) return RSC_EINVAL;
+  if (n_real) *n_real = (size_t)ctx->d.n();
+  if (n_pairs) *n_pairs = ctx->d.P;
+  return RSC_OK;
+}
+
+rsc_status rsc_conductive_state(rsc_ctx* ctx, double* U) {
+  if (!ctx || !U) return RSC_EINVAL;
+  std::vector<double> coef;
+  conductive_T00(ctx->p, ctx->d, ctx->t, coef);
+  const long n = ctx->d.n();
+  CK(cudaMemsetAsync(U, 0, n * sizeof(double), ctx->s));
+  // T_00 is pair 0 (m = 0, l = 0) of field 2; real parts at stride 2.
+  std::vector<double> row(2 * ctx->d.Nr, 0.0);
+  for (int k = 0; k < ctx->d.Nr; ++k) row[2 * k] = coef[k];
+  double* dst = U + (long)2 * ctx->d.P * ctx->d.Nr * 2;
+  CK(cudaMemcpyAsync(dst, row.data(), row.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  return RSC_OK;
+}
+
+rsc_status rsc_step(rsc_ctx* ctx, double* U, double C, double dt, int nsteps) {
+  if (!ctx || !U || nsteps < 0 || !(dt > 0)) return RSC_EINVAL;
+  const bool fp32 = ctx->p.precision == RSC_MIXED;
+  for (int s = 0; s < nsteps; ++s) CKS(step_any(ctx, U, C, dt, fp32));
+  return RSC_OK;
+}
+
+rsc_status rsc_step_host(rsc_ctx* ctx, double* U_host, double C, double dt, int nsteps) {
+  if (!ctx || !U_host) return RSC_EINVAL;
+  const long n = ctx->d.n();
+  CK(cudaMemcpyAsync(ctx->vtmp, U_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+  CKS(rsc_step(ctx, ctx->vtmp, C, dt, nsteps));
+  CK(cudaMemcpyAsync(U_host, ctx->vtmp, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  return RSC_OK;
+}
+
+rsc_status rsc_explicit_terms(rsc_ctx* ctx, const double* U, double* N) {
+  if (!ctx || !U || !N) return RSC_EINVAL;
+  if (ctx->p.precision == RSC_MIXED) {
+    CKS(stage_synth<float>(ctx, U, ctx->FC));
+    CKS(stage_products_analysis<float>(ctx, false));
+    CKS(stage_rhs<float>(ctx, make_rp(ctx, 1.0, 0.0, 2), U, nullptr, reinterpret_cast<double2*>(N)));
+  } else {
+    CKS(stage_synth<double>(ctx, U, ctx->FC));
+    CKS(stage_products_analysis<double>(ctx, false));
+    CKS(stage_rhs<double>(ctx, make_rp(ctx, 1.0, 0.0, 2), U, nullptr, reinterpret_cast<double2*>(N)));
+  }
+  return RSC_OK;
+}
+
+rsc_status rsc_apply_jacobian(rsc_ctx* ctx, const double* U, double C, long J, const double* u,
+                              double* out, int count, double dt) {
+  if (!ctx || !U || !u || !out || count < 0 || !(dt > 0)) return RSC_EINVAL;
+  const long n = ctx->d.n();
+  if (J >= n) return RSC_EINVAL;
+  const bool fp32 = ctx->p.precision == RSC_MIXED;
+  CKS(cache_base(ctx, U, fp32));
+  for (int q = 0; q < count; ++q)
+    CKS(jvp_any(ctx, U, C, J < 0 ? -1 : J, u + (long)q * n, out + (long)q * n, dt, fp32));
+  return RSC_OK;
+}
+
+rsc_status rsc_norm2(rsc_ctx* ctx, const double* v, size_t n, double* out) {
+  if (!ctx || !v || !out) return RSC_EINVAL;
+  return norm2(ctx, v, (long)n, out);
+}
+
+rsc_status rsc_newton_rw(rsc_ctx* ctx, double* U, double* C, long J, const rsc_newton_opts* o,
+                         rsc_newton_report* rep) {
+  if (!ctx || !U || !C || !o) return RSC_EINVAL;
+  if (o->kmax < 1 || o->kmax > kMaxKrylov || o->max_newton < 0 || !(o->dt_newton > 0))
+    return RSC_EINVAL;
+  const long n = ctx->d.n();
+  if (J >= n) return RSC_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  rsc_newton_report local{};
+  rsc_newton_report* r = rep ? rep : &local;
+  std::memset(r, 0, sizeof(*r));
+  const bool fp32 = ctx->p.precision == RSC_MIXED;
+  int nb;
+  launch_1d_grid(n, &nb);
+  double Cv = *C;
+  rsc_status result = RSC_ENOCONV;
+  for (int it = 0; it <= o->max_newton; ++it) {
+    // residual B(U) - U in FP64 (the refinement step of the mixed path)
+    CK(cudaMemcpyAsync(ctx->rtmp, U, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+    CKS(step_any(ctx, ctx->rtmp, Cv, o->dt_newton, false));
+    k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, U, 1.0, ctx->rtmp, n);
+    CK(cudaGetLastError());
+    double rn;
+    CKS(norm2(ctx, ctx->rtmp, n, &rn));
+    if (it < RSC_MAX_HISTORY) r->residual_history[it] = rn;
+    r->residual = rn;
+    r->iterations = it;
+    if (!std::isfinite(rn)) {
+      ctx->err = "non-finite Newton residual";
+      result = RSC_ENAN;
+      break;
+    }
+    if (rn < o->tol) {
+      result = RSC_OK;
+      break;
+    }
+    if (it == o->max_newton) break;
+    CKS(cache_base(ctx, U, fp32));
+    int its = 0;
+    double rel = 0;
+    CKS(gmres(ctx, U, Cv, J < 0 ? -1 : J, ctx->rtmp, ctx->vtmp, o->dt_newton, o->kmax,
+              o->gmres_tol, fp32, &its, &rel));
+    if (it < RSC_MAX_HISTORY) r->gmres_history[it] = its;
+    r->gmres_total += its;
+    double c = 0.0;
+    if (J >= 0) {
+      CK(cudaMemcpyAsync(ctx->h_pinned, ctx->vtmp + J, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+      CK(cudaStreamSynchronize(ctx->s));
+      c = ctx->h_pinned[0];
+      CK(cudaMemsetAsync(ctx->vtmp + J, 0, sizeof(double), ctx->s));
+    }
+    k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, ctx->vtmp, 1.0, U, n);
+    CK(cudaGetLastError());
+    Cv -= c;
+  }
+  CK(cudaStreamSynchronize(ctx->s));
+  *C = Cv;
+  r->C = Cv;
+  r->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (result == RSC_ENOCONV) ctx->err = "Newton iteration cap reached";
+  return result;
+}
+
+rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
+                              const rsc_newton_opts* o, rsc_newton_report* rep) {
+  if (!ctx || !U_host) return RSC_EINVAL;
+  const long n = ctx->d.n();
+  double* Ud = nullptr;
+  CK(cudaMalloc(&Ud, n * sizeof(double)));
+  cudaMemcpyAsync(Ud, U_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->s);
+  rsc_status st = rsc_newton_rw(ctx, Ud, C, J, o, rep);
+  cudaMemcpyAsync(U_host, Ud, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
+  cudaStreamSynchronize(ctx->s);
+  cudaFree(Ud);
+  return st;
+}
+
+}  // extern "C"

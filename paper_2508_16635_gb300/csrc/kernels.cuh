@@ -1,0 +1,628 @@
+// Device kernels of one IMEX step / Jacobian action (Sec. 3.1-3.4).
+//
+// Data flow of a step (rows of the hot path):
+//   k_radial    Chebyshev coefficients -> spectral values on the de-aliased
+//               radii (u_r, S_u, T_u, omega_r, S_w, T_w, d_r T, T/r)   [a1]
+//   k_synth     per (m, r): Legendre sums over l, parity split     [a2]
+//   k_products  per (r, theta tile): inverse DFT in phi, U x omega and
+//               U.grad T (or their linearisation), forward DFT     [a3-a5]
+//   k_analysis  per (m, r): Gauss-weighted Legendre projection      [a6]
+//   k_rhs       per (l, m): radial projection, curl / double curl,
+//               mass, drift and boundary rows (FP64)               [a7]
+//   k_chain_solve / k_temp_solve: block-tridiagonal Coriolis chains
+//               and per-l temperature solves (FP64)                [a8]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsc {
+
+template <typename R> struct C2;
+template <> struct C2<double> { using T = double2; };
+template <> struct C2<float> { using T = float2; };
+
+template <typename R>
+__device__ __forceinline__ typename C2<R>::T mk(R x, R y) {
+  typename C2<R>::T v;
+  v.x = x;
+  v.y = y;
+  return v;
+}
+
+// Device view of the tables.
+template <typename R>
+struct DevLegendre {
+  const R* P;      // synthesis layout [off_m + q * nlat2 + t]
+  const R* dP;
+  const R* Ps;
+  const R* Pw;     // analysis layout [off_m + t * nl + q]
+  const R* dPw;
+  const R* Psw;
+  const R* twc;    // cos(2 pi a j / nphi) [a][j]
+  const R* tws;    // sin(2 pi a j / nphi) [a][j]
+};
+
+struct DevGeom {
+  int L, Ms, Nr, Nd, nlat, nlat2, nphi, nm, K, P;
+  double r_in, r_out;
+  const int* m_of;      // [nm]
+  const int* pstart;    // [nm + 1]
+  const long* leg_off;  // [nm + 1]
+  const int* pair_l;    // [P]
+  const int* pair_m;    // [P]
+  const double* rc;     // [Nr]
+  const double* rd;     // [Nd]
+  const double* EcT0;   // [k][j] T_k(r_j)
+  const double* EcT2;   // [k][j] d2 T_k / dr2 (r_j)
+  const double* EdT0;   // [k][i] at the de-aliased radii
+  const double* EdT1;
+  const double* EdT2;
+  const double* R0T;    // [i][j]
+  const double* R1T;    // [i][j]
+};
+
+// ---------------------------------------------------------------------------
+// a1: radial evaluation.  grid = P, block >= Nd.
+// SR[(p * Nd + i) * 8 + q], q = ur, Su, Tu, wr, Sw, Tw, dT, ST.
+template <typename R>
+__global__ void k_radial(DevGeom g, const double2* __restrict__ x,
+                         typename C2<R>::T* __restrict__ SR) {
+  using V = typename C2<R>::T;
+  extern __shared__ double2 sh_coef[];  // [3][Nr]
+  const int p = blockIdx.x;
+  const int Nr = g.Nr, Nd = g.Nd;
+  for (int idx = threadIdx.x; idx < 3 * Nr; idx += blockDim.x) {
+    const int f = idx / Nr, k = idx % Nr;
+    sh_coef[idx] = x[((long)f * g.P + p) * Nr + k];
+  }
+  __syncthreads();
+  const int i = threadIdx.x;
+  if (i >= Nd) return;
+  double2 fv = {0, 0}, f1 = {0, 0}, f2 = {0, 0}, ev = {0, 0}, e1 = {0, 0}, Tv = {0, 0}, T1 = {0, 0};
+  for (int k = 0; k < Nr; ++k) {
+    const double a0 = g.EdT0[k * Nd + i], a1 = g.EdT1[k * Nd + i], a2 = g.EdT2[k * Nd + i];
+    const double2 e = sh_coef[k], f = sh_coef[Nr + k], T = sh_coef[2 * Nr + k];
+    fv.x += a0 * f.x; fv.y += a0 * f.y;
+    f1.x += a1 * f.x; f1.y += a1 * f.y;
+    f2.x += a2 * f.x; f2.y += a2 * f.y;
+    ev.x += a0 * e.x; ev.y += a0 * e.y;
+    e1.x += a1 * e.x; e1.y += a1 * e.y;
+    Tv.x += a0 * T.x; Tv.y += a0 * T.y;
+    T1.x += a1 * T.x; T1.y += a1 * T.y;
+  }
+  const int l = g.pair_l[p];
+  const double lam = l * (l + 1.0);
+  const double r = g.rd[i], ir = 1.0 / r, ir2 = ir * ir;
+  V* o = SR + ((long)p * Nd + i) * 8;
+  o[0] = mk<R>((R)(lam * fv.x * ir2), (R)(lam * fv.y * ir2));              // u_r
+  o[1] = mk<R>((R)(f1.x * ir), (R)(f1.y * ir));                            // S_u
+  o[2] = mk<R>((R)(ev.x * ir), (R)(ev.y * ir));                            // T_u
+  o[3] = mk<R>((R)(lam * ev.x * ir2), (R)(lam * ev.y * ir2));              // omega_r
+  o[4] = mk<R>((R)(e1.x * ir), (R)(e1.y * ir));                            // S_w
+  o[5] = mk<R>((R)(-(f2.x - lam * fv.x * ir2) * ir), (R)(-(f2.y - lam * fv.y * ir2) * ir));  // T_w
+  o[6] = mk<R>((R)T1.x, (R)T1.y);                                          // d_r T
+  o[7] = mk<R>((R)(Tv.x * ir), (R)(Tv.y * ir));                            // S_T
+}
+
+// ---------------------------------------------------------------------------
+// a2: Legendre synthesis.  grid = (nm, Nd), block >= nlat2 (multiple of 32).
+// FC[((fld * Nd + i) * (K+1) + a) * nlat + th], fld = ur, ut, up, wr, wt, wp, Tr, Tt, Tp.
+template <typename R>
+__global__ void k_synth(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __restrict__ SR,
+                        typename C2<R>::T* __restrict__ FC) {
+  using V = typename C2<R>::T;
+  extern __shared__ unsigned char sh_raw[];
+  V* sh = reinterpret_cast<V*>(sh_raw);  // [nl][8]
+  const int a = blockIdx.x, i = blockIdx.y;
+  const int m = g.m_of[a];
+  const int p0 = g.pstart[a];
+  const int nl = g.L - m + 1;
+  const int Nd = g.Nd;
+  for (int idx = threadIdx.x; idx < nl * 8; idx += blockDim.x) {
+    const int q = idx >> 3, c = idx & 7;
+    sh[idx] = SR[((long)(p0 + q) * Nd + i) * 8 + c];
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t >= g.nlat2) return;
+  const long off = g.leg_off[a];
+  const int n2 = g.nlat2;
+  // accumulators: [parity][...]
+  R sPr[2][3], sPi[2][3];   // P-sums of ur, wr, dT
+  R dRr[2][5], dRi[2][5];   // dP-sums of Su, Tu, Sw, Tw, ST
+  R qRr[2][5], qRi[2][5];   // Ps-sums of Su, Tu, Sw, Tw, ST
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sPr[s][c] = sPi[s][c] = 0;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) dRr[s][c] = dRi[s][c] = qRr[s][c] = qRi[s][c] = 0;
+  }
+  for (int q0 = 0; q0 < nl; q0 += 2) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int q = q0 + s;
+      if (q < nl) {
+        const R pv = T.P[off + (long)q * n2 + t];
+        const R dv = T.dP[off + (long)q * n2 + t];
+        const R sv = T.Ps[off + (long)q * n2 + t];
+        const V* c = sh + q * 8;
+        sPr[s][0] += pv * c[0].x; sPi[s][0] += pv * c[0].y;
+        sPr[s][1] += pv * c[3].x; sPi[s][1] += pv * c[3].y;
+        sPr[s][2] += pv * c[6].x; sPi[s][2] += pv * c[6].y;
+        const int vi[5] = {1, 2, 4, 5, 7};
+#pragma unroll
+        for (int u = 0; u < 5; ++u) {
+          dRr[s][u] += dv * c[vi[u]].x; dRi[s][u] += dv * c[vi[u]].y;
+          qRr[s][u] += sv * c[vi[u]].x; qRi[s][u] += sv * c[vi[u]].y;
+        }
+      }
+    }
+  }
+  const R mm = (R)m;
+  const int K1 = g.K + 1, nlat = g.nlat;
+#pragma unroll
+  for (int hemi = 0; hemi < 2; ++hemi) {
+    // north: E + O for P-type and dP-type; south: E - O (P-type), -E + O (dP-type)
+    const R sP = hemi ? (R)-1 : (R)1;
+    const R sD = hemi ? (R)-1 : (R)1;
+    const int th = hemi ? (nlat - 1 - t) : t;
+    R Pr[3], Pi[3], Dr[5], Di[5], Sr[5], Si[5];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Pr[c] = sPr[0][c] + sP * sPr[1][c];
+      Pi[c] = sPi[0][c] + sP * sPi[1][c];
+    }
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+      Dr[u] = sD * dRr[0][u] + dRr[1][u];
+      Di[u] = sD * dRi[0][u] + dRi[1][u];
+      Sr[u] = qRr[0][u] + sP * qRr[1][u];
+      Si[u] = qRi[0][u] + sP * qRi[1][u];
+    }
+    // i m X = (-m X.y, m X.x)
+    V out[9];
+    out[0] = mk<R>(Pr[0], Pi[0]);                                        // u_r
+    out[1] = mk<R>(Dr[0] - mm * Si[1], Di[0] + mm * Sr[1]);               // u_th = dS_u + i m T_u/s
+    out[2] = mk<R>(-mm * Si[0] - Dr[1], mm * Sr[0] - Di[1]);              // u_ph = i m S_u/s - dT_u
+    out[3] = mk<R>(Pr[1], Pi[1]);                                        // omega_r
+    out[4] = mk<R>(Dr[2] - mm * Si[3], Di[2] + mm * Sr[3]);               // omega_th
+    out[5] = mk<R>(-mm * Si[2] - Dr[3], mm * Sr[2] - Di[3]);              // omega_ph
+    out[6] = mk<R>(Pr[2], Pi[2]);                                        // d_r T
+    out[7] = mk<R>(Dr[4], Di[4]);                                        // (1/r) d_th T
+    out[8] = mk<R>(-mm * Si[4], mm * Sr[4]);                              // (1/(r s)) d_ph T
+#pragma unroll
+    for (int fld = 0; fld < 9; ++fld)
+      FC[(((long)fld * Nd + i) * K1 + a) * nlat + th] = out[fld];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a3-a5: inverse DFT, products, forward DFT.  grid = (Nd, ceil(nlat / TT)).
+// LIN = false: F = Ek U x omega, N = U.grad T from FC.
+// LIN = true : F = Ek (U x omega_u + u x omega_U), N = U.grad tau + u.grad T
+//              with U from FCU and u from FC.
+template <typename R, bool LIN, int TT>
+__global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
+                           const typename C2<R>::T* __restrict__ FC,
+                           const typename C2<R>::T* __restrict__ FCU,
+                           typename C2<R>::T* __restrict__ FA) {
+  using V = typename C2<R>::T;
+  constexpr int NF = LIN ? 18 : 9;
+  extern __shared__ unsigned char sh_raw[];
+  const int K1 = g.K + 1, nphi = g.nphi, nlat = g.nlat, Nd = g.Nd;
+  V* coef = reinterpret_cast<V*>(sh_raw);                 // [NF][TT][K1]
+  R* twc = reinterpret_cast<R*>(coef + NF * TT * K1);     // [K1][nphi]
+  R* tws = twc + K1 * nphi;
+  R* prod = tws + K1 * nphi;                              // [4][TT][nphi]
+  const int i = blockIdx.x;
+  const int th0 = blockIdx.y * TT;
+  for (int idx = threadIdx.x; idx < K1 * nphi; idx += blockDim.x) {
+    twc[idx] = T.twc[idx];
+    tws[idx] = T.tws[idx];
+  }
+  for (int idx = threadIdx.x; idx < NF * TT * K1; idx += blockDim.x) {
+    const int tt = idx % TT;
+    const int rest = idx / TT;
+    const int a = rest % K1;
+    const int f = rest / K1;
+    const int th = th0 + tt;
+    V v = mk<R>(0, 0);
+    if (th < nlat) {
+      const V* src = (f < 9) ? FC : FCU;
+      const int ff = (f < 9) ? f : f - 9;
+      v = src[(((long)ff * Nd + i) * K1 + a) * nlat + th];
+    }
+    coef[(f * TT + tt) * K1 + a] = v;
+  }
+  __syncthreads();
+  for (int pt = threadIdx.x; pt < TT * nphi; pt += blockDim.x) {
+    const int tt = pt / nphi, j = pt % nphi;
+    R val[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const V* c = coef + (f * TT + tt) * K1;
+      R s = c[0].x;
+      R acc = 0;
+      for (int a = 1; a < K1; ++a) acc += c[a].x * twc[a * nphi + j] - c[a].y * tws[a * nphi + j];
+      val[f] = s + (R)2 * acc;
+    }
+    R Fr, Ft, Fp, N;
+    if (!LIN) {
+      // val: 0 ur 1 ut 2 up 3 wr 4 wt 5 wp 6 Tr 7 Tt 8 Tp
+      Fr = Ek * (val[1] * val[5] - val[2] * val[4]);
+      Ft = Ek * (val[2] * val[3] - val[0] * val[5]);
+      Fp = Ek * (val[0] * val[4] - val[1] * val[3]);
+      N = val[0] * val[6] + val[1] * val[7] + val[2] * val[8];
+    } else {
+      const R* u = val;      // perturbation
+      const R* U = val + 9;  // base state
+      Fr = Ek * ((U[1] * u[5] - U[2] * u[4]) + (u[1] * U[5] - u[2] * U[4]));
+      Ft = Ek * ((U[2] * u[3] - U[0] * u[5]) + (u[2] * U[3] - u[0] * U[5]));
+      Fp = Ek * ((U[0] * u[4] - U[1] * u[3]) + (u[0] * U[4] - u[1] * U[3]));
+      N = U[0] * u[6] + U[1] * u[7] + U[2] * u[8] + u[0] * U[6] + u[1] * U[7] + u[2] * U[8];
+    }
+    prod[(0 * TT + tt) * nphi + j] = Fr;
+    prod[(1 * TT + tt) * nphi + j] = Ft;
+    prod[(2 * TT + tt) * nphi + j] = Fp;
+    prod[(3 * TT + tt) * nphi + j] = N;
+  }
+  __syncthreads();
+  const R inv = (R)1 / (R)nphi;
+  for (int idx = threadIdx.x; idx < 4 * TT * K1; idx += blockDim.x) {
+    const int tt = idx % TT;
+    const int rest = idx / TT;
+    const int a = rest % K1;
+    const int q = rest / K1;
+    const int th = th0 + tt;
+    if (th >= nlat) continue;
+    const R* pr = prod + (q * TT + tt) * nphi;
+    R sr = 0, si = 0;
+    for (int j = 0; j < nphi; ++j) {
+      sr += pr[j] * twc[a * nphi + j];
+      si -= pr[j] * tws[a * nphi + j];
+    }
+    FA[(((long)q * Nd + i) * K1 + a) * nlat + th] = mk<R>(sr * inv, si * inv);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a6: Legendre analysis.  grid = (nm, Nd), block >= L + 1 (multiple of 32).
+// AR[((p * Nd) + i) * 4 + c], c = Q (F_r), S_F, T_F, (U.grad T).
+template <typename R>
+__global__ void k_analysis(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __restrict__ FA,
+                           typename C2<R>::T* __restrict__ AR) {
+  using V = typename C2<R>::T;
+  extern __shared__ unsigned char sh_raw[];
+  const int n2 = g.nlat2, nlat = g.nlat, K1 = g.K + 1, Nd = g.Nd;
+  V* sym = reinterpret_cast<V*>(sh_raw);   // [4][n2]
+  V* ant = sym + 4 * n2;                   // [4][n2]
+  const int a = blockIdx.x, i = blockIdx.y;
+  const int m = g.m_of[a];
+  const int nl = g.L - m + 1;
+  for (int idx = threadIdx.x; idx < 4 * n2; idx += blockDim.x) {
+    const int q = idx / n2, t = idx % n2;
+    const V* base = FA + (((long)q * Nd + i) * K1 + a) * nlat;
+    const V n = base[t], s = base[nlat - 1 - t];
+    sym[idx] = mk<R>(n.x + s.x, n.y + s.y);
+    ant[idx] = mk<R>(n.x - s.x, n.y - s.y);
+  }
+  __syncthreads();
+  const int ql = threadIdx.x;
+  if (ql >= nl) return;
+  const bool even = (ql & 1) == 0;
+  const V* CP = even ? sym : ant;   // parity of P and P/sin
+  const V* CD = even ? ant : sym;   // parity of dP/dtheta
+  const long off = g.leg_off[a];
+  R Qr = 0, Qi = 0, Nr_ = 0, Ni = 0, Sr = 0, Si = 0, Tr = 0, Ti = 0;
+  const R mm = (R)m;
+  for (int t = 0; t < n2; ++t) {
+    const R pw = T.Pw[off + (long)t * nl + ql];
+    const R dw = T.dPw[off + (long)t * nl + ql];
+    const R sw = T.Psw[off + (long)t * nl + ql];
+    const V fr = CP[0 * n2 + t], nt = CP[3 * n2 + t];
+    const V ftD = CD[1 * n2 + t], fpD = CD[2 * n2 + t];
+    const V ftP = CP[1 * n2 + t], fpP = CP[2 * n2 + t];
+    Qr += pw * fr.x; Qi += pw * fr.y;
+    Nr_ += pw * nt.x; Ni += pw * nt.y;
+    // S = dP F_th - i m P/s F_ph ;  -i m (x + i y) = (m y, -m x)
+    Sr += dw * ftD.x + mm * sw * fpP.y;
+    Si += dw * ftD.y - mm * sw * fpP.x;
+    // T = -i m P/s F_th - dP F_ph
+    Tr += mm * sw * ftP.y - dw * fpD.x;
+    Ti += -mm * sw * ftP.x - dw * fpD.y;
+  }
+  const int l = m + ql;
+  const R il = (l > 0) ? (R)1 / ((R)l * (R)(l + 1)) : (R)0;
+  V* o = AR + ((long)(g.pstart[a] + ql) * Nd + i) * 4;
+  o[0] = mk<R>(Qr, Qi);
+  o[1] = mk<R>(Sr * il, Si * il);
+  o[2] = mk<R>(Tr * il, Ti * il);
+  o[3] = mk<R>(Nr_, Ni);
+}
+
+// ---------------------------------------------------------------------------
+// a7: right-hand side at the collocation radii (FP64).  grid = P, block >= Nr.
+// mode 0: time step (inhomogeneous T_00 wall values)
+// mode 1: Jacobian action (homogeneous rows), c * i m M U added when has_c
+// mode 2: explicit terms only (no mass, drift or boundary rows)
+struct RhsParams {
+  double inv_dt, C, c, Ek, Ra, r_out;
+  int mode, has_c;
+};
+
+template <typename R>
+__global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restrict__ AR,
+                      const double2* __restrict__ x, const double2* __restrict__ U,
+                      double2* __restrict__ rhs) {
+  extern __shared__ double2 sh2[];
+  const int Nr = g.Nr, Nd = g.Nd, P = g.P;
+  double2* ar = sh2;               // [Nd][4]
+  double2* xs = ar + 4 * Nd;       // [3][Nr]
+  double2* us = xs + 3 * Nr;       // [3][Nr]
+  const int p = blockIdx.x;
+  for (int idx = threadIdx.x; idx < 4 * Nd; idx += blockDim.x) {
+    const auto v = AR[(long)p * Nd * 4 + idx];
+    ar[idx] = make_double2((double)v.x, (double)v.y);
+  }
+  for (int idx = threadIdx.x; idx < 3 * Nr; idx += blockDim.x) {
+    const int f = idx / Nr, k = idx % Nr;
+    xs[idx] = x[((long)f * P + p) * Nr + k];
+    if (rp.has_c) us[idx] = U[((long)f * P + p) * Nr + k];
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j >= Nr) return;
+  const int l = g.pair_l[p], m = g.pair_m[p];
+  const double lam = l * (l + 1.0);
+  const double r = g.rc[j], ir = 1.0 / r, ir2 = ir * ir;
+  double2 Tc = {0, 0}, Qc = {0, 0}, dS = {0, 0}, Nc = {0, 0};
+  for (int i = 0; i < Nd; ++i) {
+    const double w0 = g.R0T[i * Nr + j], w1 = g.R1T[i * Nr + j] * g.rd[i];
+    const double2 q = ar[i * 4 + 0], s = ar[i * 4 + 1], t = ar[i * 4 + 2], n = ar[i * 4 + 3];
+    Qc.x += w0 * q.x; Qc.y += w0 * q.y;
+    Tc.x += w0 * t.x; Tc.y += w0 * t.y;
+    Nc.x += w0 * n.x; Nc.y += w0 * n.y;
+    dS.x += w1 * s.x; dS.y += w1 * s.y;
+  }
+  auto mass = [&](const double2* v, double2& me, double2& mf, double2& mt) {
+    double2 e0 = {0, 0}, f0 = {0, 0}, f2 = {0, 0}, t0 = {0, 0};
+    for (int k = 0; k < Nr; ++k) {
+      const double c0 = g.EcT0[k * Nr + j], c2 = g.EcT2[k * Nr + j];
+      const double2 e = v[k], f = v[Nr + k], t = v[2 * Nr + k];
+      e0.x += c0 * e.x; e0.y += c0 * e.y;
+      f0.x += c0 * f.x; f0.y += c0 * f.y;
+      f2.x += c2 * f.x; f2.y += c2 * f.y;
+      t0.x += c0 * t.x; t0.y += c0 * t.y;
+    }
+    const double ce = lam * rp.Ek * ir2;
+    me = make_double2(ce * e0.x, ce * e0.y);
+    mf = make_double2(-ce * (f2.x - lam * ir2 * f0.x), -ce * (f2.y - lam * ir2 * f0.y));
+    mt = t0;
+  };
+  double2 Me, Mf, MT;
+  mass(xs, Me, Mf, MT);
+  // explicit terms (curl projections and buoyancy)
+  double2 Ne = make_double2(lam * ir * Tc.x, lam * ir * Tc.y);
+  const double cb = lam * rp.Ra * ir / rp.r_out;
+  double2 Nf = make_double2(lam * ir2 * (Qc.x - dS.x) + cb * MT.x, lam * ir2 * (Qc.y - dS.y) + cb * MT.y);
+  double2 NT = make_double2(-Nc.x, -Nc.y);
+  double2 out[3];
+  if (rp.mode == 2) {
+    out[0] = Ne; out[1] = Nf; out[2] = NT;
+  } else {
+    const double fr = rp.inv_dt, fi = rp.C * m;  // (1/dt + i C m)
+    auto cm = [&](double2 v, double2 n) {
+      return make_double2(fr * v.x - fi * v.y + n.x, fr * v.y + fi * v.x + n.y);
+    };
+    out[0] = cm(Me, Ne);
+    out[1] = cm(Mf, Nf);
+    out[2] = cm(MT, NT);
+    if (rp.has_c) {
+      double2 ue, uf, ut;
+      mass(us, ue, uf, ut);
+      const double cmv = rp.c * m;  // c * i m * v = (-cm v.y, cm v.x)
+      out[0].x -= cmv * ue.y; out[0].y += cmv * ue.x;
+      out[1].x -= cmv * uf.y; out[1].y += cmv * uf.x;
+      out[2].x -= cmv * ut.y; out[2].y += cmv * ut.x;
+    }
+    // boundary rows (Sec. 3.1) and identity rows of e_00, f_00
+    if (j == 0 || j == Nr - 1) { out[0] = make_double2(0, 0); out[2] = make_double2(0, 0); }
+    if (j == 0 || j == 1 || j == Nr - 2 || j == Nr - 1) out[1] = make_double2(0, 0);
+    if (rp.mode == 0 && l == 0 && j == Nr - 1) out[2] = make_double2(1.0, 0.0);  // T(r_in) = 1
+    if (l == 0) { out[0] = make_double2(0, 0); out[1] = make_double2(0, 0); }
+    if (m == 0) { out[0].y = 0; out[1].y = 0; out[2].y = 0; }
+  }
+#pragma unroll
+  for (int f = 0; f < 3; ++f) rhs[((long)f * P + p) * Nr + j] = out[f];
+}
+
+// ---------------------------------------------------------------------------
+// a8: block-tridiagonal chain solve (block Thomas with stored
+// G = D'^{-1}, H = D'^{-1} A, W = D'^{-1} C).  grid = 2 nm chains, block = 256.
+//   forward  y_i = G_i b_i - H_i y_{i-1}
+//   backward x_i = y_i - W_i x_{i+1}
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double2 cmac(double2 acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+  return acc;
+}
+
+__global__ void k_chain_solve(DevGeom g, const long* __restrict__ chain_off,
+                              const double2* __restrict__ G, const double2* __restrict__ H,
+                              const double2* __restrict__ W, const double2* __restrict__ rhs,
+                              double2* __restrict__ out) {
+  extern __shared__ double2 sv[];
+  const int Nr = g.Nr, P = g.P;
+  double2* b = sv;           // [Nr]
+  double2* yp = sv + Nr;     // [Nr] previous y / next x
+  double2* yn = sv + 2 * Nr; // [Nr]
+  const int c = blockIdx.x;
+  const int a = c >> 1, cls = c & 1;
+  const int m = g.m_of[a];
+  const int p0 = g.pstart[a];
+  const int nb = g.L - m + 1;
+  const long boff = chain_off[c];
+  const long blk = (long)Nr * Nr;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = 0; i < nb; ++i) {
+    const int fld = ((i + cls) & 1) ? 1 : 0;
+    const long row0 = ((long)fld * P + p0 + i) * Nr;
+    for (int k = threadIdx.x; k < Nr; k += blockDim.x) b[k] = rhs[row0 + k];
+    __syncthreads();
+    const double2* Gi = G + (boff + i) * blk;
+    const double2* Hi = H + (boff + i) * blk;
+    for (int r = warp; r < Nr; r += nw) {
+      double2 acc = {0, 0};
+      for (int k = lane; k < Nr; k += 32) {
+        acc = cmac(acc, Gi[(long)r * Nr + k], b[k]);
+        if (i > 0) {
+          const double2 h = Hi[(long)r * Nr + k];
+          acc = cmac(acc, make_double2(-h.x, -h.y), yp[k]);
+        }
+      }
+      acc = warp_sum2(acc);
+      if (lane == 0) {
+        yn[r] = acc;
+        out[row0 + r] = acc;
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < Nr; k += blockDim.x) yp[k] = yn[k];
+    __syncthreads();
+  }
+  // yp holds x_{nb-1} = y_{nb-1}
+  for (int i = nb - 2; i >= 0; --i) {
+    const int fld = ((i + cls) & 1) ? 1 : 0;
+    const long row0 = ((long)fld * P + p0 + i) * Nr;
+    const double2* Wi = W + (boff + i) * blk;
+    for (int r = warp; r < Nr; r += nw) {
+      double2 acc = {0, 0};
+      for (int k = lane; k < Nr; k += 32) {
+        const double2 w = Wi[(long)r * Nr + k];
+        acc = cmac(acc, make_double2(-w.x, -w.y), yp[k]);
+      }
+      acc = warp_sum2(acc);
+      if (lane == 0) {
+        const double2 y = out[row0 + r];
+        const double2 v = make_double2(y.x + acc.x, y.y + acc.y);
+        yn[r] = v;
+        out[row0 + r] = v;
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < Nr; k += blockDim.x) yp[k] = yn[k];
+    __syncthreads();
+  }
+}
+
+// Temperature: y = Tinv_l rhs per pair.  grid = P, block >= Nr.
+__global__ void k_temp_solve(DevGeom g, const double* __restrict__ Tinv,
+                             const double2* __restrict__ rhs, double2* __restrict__ out) {
+  extern __shared__ double2 sv[];
+  const int Nr = g.Nr, P = g.P;
+  const int p = blockIdx.x;
+  const long row0 = ((long)2 * P + p) * Nr;
+  for (int k = threadIdx.x; k < Nr; k += blockDim.x) sv[k] = rhs[row0 + k];
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j >= Nr) return;
+  const double* Ti = Tinv + (long)g.pair_l[p] * Nr * Nr + (long)j * Nr;
+  double2 acc = {0, 0};
+  for (int k = 0; k < Nr; ++k) {
+    acc.x = fma(Ti[k], sv[k].x, acc.x);
+    acc.y = fma(Ti[k], sv[k].y, acc.y);
+  }
+  out[row0 + j] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// GMRES / Newton BLAS-1 (FP64).
+// partial[j * nblk + b] = sum over block b's chunk of V_j . w
+__global__ void k_dots(const double* __restrict__ V, long ld, int nv, const double* __restrict__ w,
+                       long n, double* __restrict__ partial) {
+  __shared__ double red[32];
+  const int j = blockIdx.y;
+  const double* v = V + (long)j * ld;
+  double s = 0.0;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x)
+    s = fma(v[idx], w[idx], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) partial[(long)j * gridDim.x + blockIdx.x] = s;
+  }
+  (void)nv;
+}
+
+// out[j] = sum_b partial[j * nblk + b].  grid = nv, block = 256.
+__global__ void k_reduce_rows(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[(long)j * nblk + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[j] = s;
+  }
+}
+
+// w += sign * sum_j coef[j] V_j
+__global__ void k_multi_axpy(const double* __restrict__ V, long ld, int nv,
+                             const double* __restrict__ coef, double sign, double* __restrict__ w,
+                             long n) {
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < nv; ++j) s = fma(coef[j], V[(long)j * ld + idx], s);
+    w[idx] = fma(sign, s, w[idx]);
+  }
+}
+
+// y = a * x + b * y
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y,
+                        long n) {
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x)
+    y[idx] = a * x[idx] + b * y[idx];
+}
+
+// out = y - u, except out[J] = y[J] (u_J is the drift unknown, Sec. 3.4)
+__global__ void k_sub_frozen(const double* __restrict__ y, const double* __restrict__ u, long J,
+                             double* __restrict__ out, long n) {
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x)
+    out[idx] = (idx == J) ? y[idx] : y[idx] - u[idx];
+}
+
+// copy with u_J zeroed (x holds the canonical layout)
+__global__ void k_copy_zero_slot(const double* __restrict__ u, long J, double* __restrict__ x,
+                                 long n) {
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x)
+    x[idx] = (idx == J) ? 0.0 : u[idx];
+}
+
+}  // namespace rsc

@@ -1,0 +1,84 @@
+// Internal declarations of the rotating-shell GB300 library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "rsc.h"
+
+namespace rsc {
+
+using cplx = std::complex<double>;
+
+// Problem sizes (Sec. 3.1).  Pairs (m, l) are ordered by m then l, as in the
+// canonical state layout.
+struct Dims {
+  int L = 0, Ms = 0, Nr = 0;
+  int Nd = 0;        // de-aliased radial points, ceil(3 Nr / 2)
+  int nlat = 0;      // Gauss-Legendre latitudes (even)
+  int nlat2 = 0;     // nlat / 2 (one hemisphere)
+  int nphi = 0;      // longitudes per sector
+  int nm = 0;        // active m values
+  int K = 0;         // nm - 1
+  int P = 0;         // (l, m) pairs
+  double r_in = 0, r_out = 0;
+  long n() const { return 6L * P * Nr; }
+};
+
+// Host-side tables, all FP64.
+struct HostTables {
+  std::vector<double> rc, rd;          // collocation radii (Nr), de-aliased radii (Nd)
+  std::vector<double> Ec[5];           // [j][k] d^o T_k / dr^o at rc, o = 0..4
+  std::vector<double> Ed[3];           // [i][k] d^o T_k / dr^o at rd, o = 0..2
+  std::vector<double> R0, R1;          // [j][i]: N_d values -> value / d_r at rc of
+                                       // the N_r-truncated interpolant
+  std::vector<double> xlat, wlat;      // Gauss-Legendre nodes (north first), weights
+  std::vector<int> m_of, pstart;       // per m index: m, first pair
+  std::vector<int> pair_l, pair_m;     // per pair
+  std::vector<long> leg_off;           // per m index: offset into Legendre tables
+  // synthesis layout [m block][l - m][t], t < nlat2 (north hemisphere)
+  std::vector<double> P, dP, Ps;
+  // analysis layout [m block][t][l - m], weighted by w_t / (2 (2 - delta_m0))
+  std::vector<double> Pw, dPw, Psw;
+};
+
+// Factorisation of the implicit operator for one dt (Sec. 3.2, block Thomas).
+// Chain c = 2 * m_index + class; block i of a chain is l = m + i.
+struct HostFactor {
+  double dt = 0;
+  std::vector<long> chain_off;        // first block of each chain
+  std::vector<cplx> G, H, W;          // per block Nr x Nr, row-major
+  std::vector<double> Tinv;           // per l: Nr x Nr inverse of the T operator
+};
+
+void build_dims(const rsc_params& p, Dims& d);
+void build_tables(const rsc_params& p, const Dims& d, HostTables& t);
+// Returns 0 on success, or 1 + chain index of a singular block.
+int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double dt,
+                 HostFactor& f);
+void conductive_T00(const rsc_params& p, const Dims& d, const HostTables& t,
+                    std::vector<double>& coef);
+
+// ---------------------------------------------------------------------------
+// Device kernels (launch wrappers).  Real = double (FP64 path) or float
+// (transforms of the mixed path).
+struct DevTables;
+
+template <typename Real>
+struct Work {
+  // SR: spectral values on the de-aliased radii [P][Nd][8]
+  // FC: Fourier coefficients of 9 grid fields [9][Nd][K+1][nlat]
+  // FCU: the same for the base state of a Jacobian action
+  // FA: Fourier coefficients of the 4 products [4][Nd][K+1][nlat]
+  // AR: analysed products on the de-aliased radii [P][Nd][4]
+  void* SR = nullptr;
+  void* FC = nullptr;
+  void* FCU = nullptr;
+  void* FA = nullptr;
+  void* AR = nullptr;
+};
+
+}  // namespace rsc

@@ -1,0 +1,484 @@
+// Host-side FP64 construction of the tables and of the block-tridiagonal
+// factorisation of the implicit operator.
+//
+// Radial: Chebyshev polynomials of x = 2r - r_in - r_out on Gauss-Lobatto
+// points (Sec. 3.1, Eq. expansion; 3/2-rule de-aliasing).  Derivatives are
+// taken exactly in coefficient space and evaluated with cos(k theta_j).
+// Angular: Gauss-Legendre nodes by Newton's method on P_n; normalised
+// associated Legendre functions of Eq. Ylm_norm by the three-term recursion in
+// l, with d/dtheta from the recursion Eq. recu1.
+// Implicit operator: Eqs. impcor_e_final and impcor_f_final (diffusion and
+// Coriolis on the left-hand side), the temperature equation Eq. temp, with
+// boundary rows replacing the rows at the walls (Sec. 3.1).
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <stdexcept>
+#include <thread>
+
+#include "rsc_internal.h"
+
+namespace rsc {
+
+static const double kPi = 3.14159265358979323846;
+
+static int nlat_for(int L) { return 2 * ((3 * (L + 1) + 3) / 4); }
+
+static int nphi_for(int L, int Ms) {
+  const long need = 3L * (L / Ms) + 1;
+  long best = LONG_MAX;
+  for (long a = 1; a < 4 * need; a *= 2)
+    for (long b = a; b < 4 * need; b *= 3)
+      if (b >= need && b < best) best = b;
+  return (int)best;
+}
+
+void build_dims(const rsc_params& p, Dims& d) {
+  d.L = p.L;
+  d.Ms = p.Ms;
+  d.Nr = p.Nr;
+  d.Nd = (3 * p.Nr + 1) / 2;
+  d.nlat = nlat_for(p.L);
+  d.nlat2 = d.nlat / 2;
+  d.nphi = nphi_for(p.L, p.Ms);
+  d.nm = p.L / p.Ms + 1;
+  d.K = d.nm - 1;
+  d.P = 0;
+  for (int a = 0; a < d.nm; ++a) d.P += p.L - a * p.Ms + 1;
+  d.r_out = 1.0 / (1.0 - p.eta);
+  d.r_in = p.eta / (1.0 - p.eta);
+}
+
+// Coefficients of d/dx of a Chebyshev series a[0..n-1].
+static void cheb_derivative(const std::vector<double>& a, std::vector<double>& b) {
+  const int n = (int)a.size();
+  b.assign(n, 0.0);
+  if (n < 2) return;
+  std::vector<double> c(n + 1, 0.0);
+  for (int k = n - 1; k >= 1; --k) c[k - 1] = c[k + 1] + 2.0 * k * a[k];
+  for (int k = 0; k < n; ++k) b[k] = c[k];
+  b[0] *= 0.5;
+}
+
+// out[j][k] = d^order T_k / dr^order at x_j = cos(pi j / (npts - 1)), k < nk.
+static void cheb_table(int npts, int nk, int order, double r_in, double r_out,
+                       std::vector<double>& out) {
+  out.assign((size_t)npts * nk, 0.0);
+  const double scale = std::pow(2.0 / (r_out - r_in), order);
+  std::vector<double> a(nk), b;
+  for (int k = 0; k < nk; ++k) {
+    std::fill(a.begin(), a.end(), 0.0);
+    a[k] = 1.0;
+    for (int o = 0; o < order; ++o) {
+      cheb_derivative(a, b);
+      a = b;
+    }
+    for (int j = 0; j < npts; ++j) {
+      const double th = kPi * j / (npts - 1);
+      double s = 0.0;
+      for (int q = 0; q < nk; ++q)
+        if (a[q] != 0.0) s += a[q] * std::cos(q * th);
+      out[(size_t)j * nk + k] = s * scale;
+    }
+  }
+}
+
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));  // i = 0 nearest x = +1
+    double dp = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Normalised P_l^m (Eq. Ylm_norm, no Condon-Shortley phase) for l = m..lmax at
+// one node, with an extended exponent so that high m near the poles underflow
+// gracefully instead of zeroing the whole recursion.
+static void legendre_column(int lmax, int m, double x, std::vector<double>& out) {
+  out.assign(lmax - m + 1, 0.0);
+  const double s = std::sqrt(std::max(0.0, 1.0 - x * x));
+  double lg = 0.0;  // log2 of pbar_m^m
+  for (int k = 1; k <= m; ++k) lg += 0.5 * std::log2((2.0 * k + 1.0) / (2.0 * k));
+  lg += m * std::log2(s);
+  long E = (long)std::floor(lg);
+  double v0 = 0.0, v1 = std::exp2(lg - (double)E);
+  const double norm = (m > 0) ? std::sqrt(2.0) : 1.0;
+  out[0] = norm * std::ldexp(v1, (int)E);
+  if (lmax == m) return;
+  double v2 = x * std::sqrt(2.0 * m + 3.0) * v1;
+  v0 = v1;
+  v1 = v2;
+  out[1] = norm * std::ldexp(v1, (int)E);
+  for (int l = m + 2; l <= lmax; ++l) {
+    const double a = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+    const double b = std::sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) /
+                               (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+    v2 = a * (x * v1 - b * v0);
+    v0 = v1;
+    v1 = v2;
+    if (std::fabs(v1) > 0x1p500) {
+      v0 = std::ldexp(v0, -500);
+      v1 = std::ldexp(v1, -500);
+      E += 500;
+    }
+    out[l - m] = norm * std::ldexp(v1, (int)std::min<long>(E, INT_MAX));
+  }
+}
+
+void build_tables(const rsc_params& p, const Dims& d, HostTables& t) {
+  const int Nr = d.Nr, Nd = d.Nd;
+  t.rc.resize(Nr);
+  t.rd.resize(Nd);
+  for (int j = 0; j < Nr; ++j)
+    t.rc[j] = d.r_in + 0.5 * (std::cos(kPi * j / (Nr - 1)) + 1.0) * (d.r_out - d.r_in);
+  for (int i = 0; i < Nd; ++i)
+    t.rd[i] = d.r_in + 0.5 * (std::cos(kPi * i / (Nd - 1)) + 1.0) * (d.r_out - d.r_in);
+  for (int o = 0; o < 5; ++o) cheb_table(Nr, Nr, o, d.r_in, d.r_out, t.Ec[o]);
+  for (int o = 0; o < 3; ++o) cheb_table(Nd, Nr, o, d.r_in, d.r_out, t.Ed[o]);
+  // Interpolation on the N_d Gauss-Lobatto radii (DCT-I), truncated to k < Nr.
+  const int N = Nd - 1;
+  std::vector<double> Cm((size_t)Nr * Nd);
+  for (int k = 0; k < Nr; ++k) {
+    const double gk = (k == 0 || k == N) ? 2.0 : 1.0;
+    for (int i = 0; i < Nd; ++i) {
+      const double gi = (i == 0 || i == N) ? 2.0 : 1.0;
+      Cm[(size_t)k * Nd + i] = 2.0 / (N * gk * gi) * std::cos(kPi * (double)k * i / N);
+    }
+  }
+  t.R0.assign((size_t)Nr * Nd, 0.0);
+  t.R1.assign((size_t)Nr * Nd, 0.0);
+  for (int j = 0; j < Nr; ++j)
+    for (int i = 0; i < Nd; ++i) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int k = 0; k < Nr; ++k) {
+        s0 += t.Ec[0][(size_t)j * Nr + k] * Cm[(size_t)k * Nd + i];
+        s1 += t.Ec[1][(size_t)j * Nr + k] * Cm[(size_t)k * Nd + i];
+      }
+      t.R0[(size_t)j * Nd + i] = s0;
+      t.R1[(size_t)j * Nd + i] = s1;
+    }
+  // Angular tables.
+  gauss_legendre(d.nlat, t.xlat, t.wlat);
+  t.m_of.resize(d.nm);
+  t.pstart.resize(d.nm + 1);
+  t.pair_l.clear();
+  t.pair_m.clear();
+  t.leg_off.resize(d.nm + 1);
+  long off = 0;
+  for (int a = 0; a < d.nm; ++a) {
+    const int m = a * d.Ms;
+    t.m_of[a] = m;
+    t.pstart[a] = (int)t.pair_l.size();
+    for (int l = m; l <= d.L; ++l) {
+      t.pair_l.push_back(l);
+      t.pair_m.push_back(m);
+    }
+    t.leg_off[a] = off;
+    off += (long)(d.L - m + 1) * d.nlat2;
+  }
+  t.pstart[d.nm] = d.P;
+  t.leg_off[d.nm] = off;
+  t.P.assign(off, 0.0);
+  t.dP.assign(off, 0.0);
+  t.Ps.assign(off, 0.0);
+  t.Pw.assign(off, 0.0);
+  t.dPw.assign(off, 0.0);
+  t.Psw.assign(off, 0.0);
+  std::vector<double> col;
+  for (int a = 0; a < d.nm; ++a) {
+    const int m = t.m_of[a];
+    const int nl = d.L - m + 1;
+    const double nrm = 2.0 * (m > 0 ? 2.0 : 1.0);  // int P^2 dx with Eq. Ylm_norm
+    for (int tt = 0; tt < d.nlat2; ++tt) {
+      const double x = t.xlat[tt];
+      const double s = std::sqrt(1.0 - x * x);
+      legendre_column(d.L + 1, m, x, col);  // rows l = m..L+1
+      for (int q = 0; q < nl; ++q) {
+        const int l = m + q;
+        const double cl = std::sqrt(((double)l * l - (double)m * m) / (4.0 * l * l - 1.0));
+        const double cl1 = std::sqrt(((l + 1.0) * (l + 1.0) - (double)m * m) /
+                                     (4.0 * (l + 1.0) * (l + 1.0) - 1.0));
+        const double pm1 = (q > 0) ? col[q - 1] : 0.0;
+        // Eq. recu1 in normalised form: sin th dP_l = l c_{l+1} P_{l+1} - (l+1) c_l P_{l-1}
+        const double dpv = (l * cl1 * col[q + 1] - (l + 1.0) * cl * pm1) / s;
+        const double pv = col[q];
+        const size_t is = t.leg_off[a] + (size_t)q * d.nlat2 + tt;
+        t.P[is] = pv;
+        t.dP[is] = dpv;
+        t.Ps[is] = pv / s;
+        const size_t ia = t.leg_off[a] + (size_t)tt * nl + q;
+        const double wn = t.wlat[tt] / nrm;
+        t.Pw[ia] = wn * pv;
+        t.dPw[ia] = wn * dpv;
+        t.Psw[ia] = wn * pv / s;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Implicit operator blocks (rows at the collocation radii).
+namespace {
+
+struct Ops {
+  const Dims& d;
+  const HostTables& t;
+  double Ek, Pr, inv_dt;
+  int Nr;
+  double E(int o, int j, int k) const { return t.Ec[o][(size_t)j * Nr + k]; }
+
+  // field 0 = e, 1 = f
+  void diag(int field, int l, int m, std::vector<cplx>& D) const {
+    D.assign((size_t)Nr * Nr, cplx(0.0));
+    if (l == 0) {
+      for (int j = 0; j < Nr; ++j) D[(size_t)j * Nr + j] = 1.0;
+      return;
+    }
+    const double lam = l * (l + 1.0);
+    for (int j = 0; j < Nr; ++j) {
+      const double r = t.rc[j];
+      const double r2 = r * r;
+      for (int k = 0; k < Nr; ++k) {
+        const double e0 = E(0, j, k), e1 = E(1, j, k), e2 = E(2, j, k), e4 = E(4, j, k);
+        cplx v;
+        if (field == 0) {
+          const double Ll = e2 - lam / r2 * e0;
+          v = cplx(lam * Ek / r2 * inv_dt * e0 - lam * Ek / r2 * Ll, -2.0 * m / r2 * e0);
+        } else {
+          const double Ll = e2 - lam / r2 * e0;
+          const double LL = e4 - 2.0 * lam / r2 * e2 + 4.0 * lam / (r2 * r) * e1 +
+                            (lam * lam - 6.0 * lam) / (r2 * r2) * e0;
+          v = cplx(-lam * Ek / r2 * inv_dt * Ll + lam * Ek / r2 * LL, 2.0 * m / r2 * Ll);
+        }
+        D[(size_t)j * Nr + k] = v;
+      }
+    }
+    bc_rows(field, D);
+  }
+
+  void bc_rows(int field, std::vector<cplx>& D) const {
+    auto setrow = [&](int j, int o, int src) {
+      for (int k = 0; k < Nr; ++k) D[(size_t)j * Nr + k] = E(o, src, k);
+    };
+    setrow(0, 0, 0);
+    setrow(Nr - 1, 0, Nr - 1);
+    if (field == 1) {
+      setrow(1, 1, 0);
+      setrow(Nr - 2, 1, Nr - 1);
+    }
+  }
+
+  // Coupling of the equation at l to the other potential at l + side (Coriolis).
+  void coupling(int field, int l, int m, int side, std::vector<cplx>& B) const {
+    B.assign((size_t)Nr * Nr, cplx(0.0));
+    if (l == 0) return;
+    double coef;
+    if (side < 0) {
+      coef = ((double)l * l - 1.0) * std::sqrt(((double)l * l - (double)m * m) / (4.0 * l * l - 1.0));
+    } else {
+      const double l1 = l + 1.0;
+      coef = l * (l + 2.0) * std::sqrt((l1 * l1 - (double)m * m) / (4.0 * l1 * l1 - 1.0));
+    }
+    const int j0 = (field == 1) ? 2 : 1;
+    const int j1 = (field == 1) ? Nr - 3 : Nr - 2;
+    for (int j = j0; j <= j1; ++j) {
+      const double r = t.rc[j];
+      const double a = (side < 0) ? (double)l / r : -(l + 1.0) / r;
+      for (int k = 0; k < Nr; ++k)
+        B[(size_t)j * Nr + k] = 2.0 / (r * r) * coef * (a * E(0, j, k) - E(1, j, k));
+    }
+  }
+
+  void temp(int l, std::vector<double>& D) const {
+    D.assign((size_t)Nr * Nr, 0.0);
+    const double lam = l * (l + 1.0);
+    for (int j = 0; j < Nr; ++j) {
+      const double r = t.rc[j];
+      for (int k = 0; k < Nr; ++k)
+        D[(size_t)j * Nr + k] = inv_dt * E(0, j, k) -
+                                (1.0 / Pr) * (E(2, j, k) + 2.0 / r * E(1, j, k) - lam / (r * r) * E(0, j, k));
+    }
+    for (int k = 0; k < Nr; ++k) {
+      D[k] = E(0, 0, k);
+      D[(size_t)(Nr - 1) * Nr + k] = E(0, Nr - 1, k);
+    }
+  }
+};
+
+// LU with partial pivoting, in place (row-major n x n).  Returns false if singular.
+template <typename T>
+bool lu_factor(int n, std::vector<T>& A, std::vector<int>& piv) {
+  piv.resize(n);
+  for (int c = 0; c < n; ++c) {
+    int best = c;
+    double bv = std::abs(A[(size_t)c * n + c]);
+    for (int r = c + 1; r < n; ++r) {
+      const double v = std::abs(A[(size_t)r * n + c]);
+      if (v > bv) {
+        bv = v;
+        best = r;
+      }
+    }
+    if (bv == 0.0 || !std::isfinite(bv)) return false;
+    piv[c] = best;
+    if (best != c)
+      for (int k = 0; k < n; ++k) std::swap(A[(size_t)c * n + k], A[(size_t)best * n + k]);
+    const T inv = T(1.0) / A[(size_t)c * n + c];
+    for (int r = c + 1; r < n; ++r) {
+      const T f = A[(size_t)r * n + c] * inv;
+      A[(size_t)r * n + c] = f;
+      if (f != T(0.0))
+        for (int k = c + 1; k < n; ++k) A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+    }
+  }
+  return true;
+}
+
+// Solve LU X = B for nrhs columns of B (row-major n x nrhs), in place.
+template <typename T>
+void lu_solve(int n, const std::vector<T>& LU, const std::vector<int>& piv, int nrhs,
+              std::vector<T>& B) {
+  for (int c = 0; c < n; ++c)
+    if (piv[c] != c)
+      for (int q = 0; q < nrhs; ++q)
+        std::swap(B[(size_t)c * nrhs + q], B[(size_t)piv[c] * nrhs + q]);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < r; ++c) {
+      const T f = LU[(size_t)r * n + c];
+      if (f != T(0.0))
+        for (int q = 0; q < nrhs; ++q) B[(size_t)r * nrhs + q] -= f * B[(size_t)c * nrhs + q];
+    }
+  for (int r = n - 1; r >= 0; --r) {
+    for (int c = r + 1; c < n; ++c) {
+      const T f = LU[(size_t)r * n + c];
+      if (f != T(0.0))
+        for (int q = 0; q < nrhs; ++q) B[(size_t)r * nrhs + q] -= f * B[(size_t)c * nrhs + q];
+    }
+    const T inv = T(1.0) / LU[(size_t)r * n + r];
+    for (int q = 0; q < nrhs; ++q) B[(size_t)r * nrhs + q] *= inv;
+  }
+}
+
+}  // namespace
+
+int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double dt,
+                 HostFactor& f) {
+  const int Nr = d.Nr;
+  const size_t blk = (size_t)Nr * Nr;
+  Ops ops{d, t, p.Ek, p.Pr, std::isfinite(dt) ? 1.0 / dt : 0.0, Nr};
+  f.dt = dt;
+  const int nchains = 2 * d.nm;
+  f.chain_off.resize(nchains + 1);
+  long off = 0;
+  for (int c = 0; c < nchains; ++c) {
+    f.chain_off[c] = off;
+    off += d.L - t.m_of[c / 2] + 1;
+  }
+  f.chain_off[nchains] = off;
+  f.G.assign(off * blk, cplx(0.0));
+  f.H.assign(off * blk, cplx(0.0));
+  f.W.assign(off * blk, cplx(0.0));
+  std::vector<int> bad(nchains, 0);
+
+  auto work = [&](int c) {
+    const int a = c / 2, cls = c % 2;
+    const int m = t.m_of[a];
+    const int nb = d.L - m + 1;
+    std::vector<cplx> D, A, C, tmp;
+    std::vector<int> piv;
+    for (int i = 0; i < nb; ++i) {
+      const int l = m + i;
+      const int field = ((i + cls) % 2 == 0) ? 0 : 1;
+      ops.diag(field, l, m, D);
+      cplx* Gi = &f.G[(f.chain_off[c] + i) * blk];
+      cplx* Hi = &f.H[(f.chain_off[c] + i) * blk];
+      cplx* Wi = &f.W[(f.chain_off[c] + i) * blk];
+      if (i > 0) {
+        ops.coupling(field, l, m, -1, A);
+        const cplx* Wp = &f.W[(f.chain_off[c] + i - 1) * blk];
+        for (int r = 0; r < Nr; ++r)
+          for (int q = 0; q < Nr; ++q) {
+            const cplx arq = A[(size_t)r * Nr + q];
+            if (arq == cplx(0.0)) continue;
+            for (int k = 0; k < Nr; ++k) D[(size_t)r * Nr + k] -= arq * Wp[(size_t)q * Nr + k];
+          }
+      }
+      if (!lu_factor(Nr, D, piv)) {
+        bad[c] = 1;
+        return;
+      }
+      tmp.assign(blk, cplx(0.0));
+      for (int r = 0; r < Nr; ++r) tmp[(size_t)r * Nr + r] = 1.0;
+      lu_solve(Nr, D, piv, Nr, tmp);
+      std::copy(tmp.begin(), tmp.end(), Gi);
+      if (i > 0) {
+        lu_solve(Nr, D, piv, Nr, A);
+        std::copy(A.begin(), A.end(), Hi);
+      }
+      if (i < nb - 1) {
+        ops.coupling(field, l, m, +1, C);
+        lu_solve(Nr, D, piv, Nr, C);
+        std::copy(C.begin(), C.end(), Wi);
+      }
+    }
+  };
+  const int nth = std::max(1, std::min<int>(nchains, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nth; ++w)
+    pool.emplace_back([&, w]() {
+      for (int c = w; c < nchains; c += nth) work(c);
+    });
+  for (auto& th : pool) th.join();
+  for (int c = 0; c < nchains; ++c)
+    if (bad[c]) return 1 + c;
+  // Temperature: real inverse per l.
+  f.Tinv.assign((size_t)(d.L + 1) * blk, 0.0);
+  std::vector<double> D, I;
+  std::vector<int> piv;
+  for (int l = 0; l <= d.L; ++l) {
+    ops.temp(l, D);
+    if (!lu_factor(Nr, D, piv)) return 1 + nchains;
+    I.assign(blk, 0.0);
+    for (int r = 0; r < Nr; ++r) I[(size_t)r * Nr + r] = 1.0;
+    lu_solve(Nr, D, piv, Nr, I);
+    std::copy(I.begin(), I.end(), f.Tinv.begin() + (size_t)l * blk);
+  }
+  return 0;
+}
+
+void conductive_T00(const rsc_params& p, const Dims& d, const HostTables& t,
+                    std::vector<double>& coef) {
+  const int Nr = d.Nr;
+  Ops ops{d, t, p.Ek, p.Pr, 0.0, Nr};
+  std::vector<double> D;
+  ops.temp(0, D);
+  std::vector<int> piv;
+  lu_factor(Nr, D, piv);
+  coef.assign(Nr, 0.0);
+  coef[Nr - 1] = 1.0;  // row Nr-1 is x = -1, r = r_in, where T = 1 (Eq. BCtemp)
+  lu_solve(Nr, D, piv, 1, coef);
+}
+
+}  // namespace rsc

@@ -1,0 +1,218 @@
+"""ctypes binding of librsc.so (the C ABI declared in include/rsc.h).
+
+Argument marshalling only: every stage of the step, the Jacobian action and
+Newton-GMRES runs in the library's CUDA kernels.  Device buffers are torch
+tensors (float64, contiguous, on the context's device); the CUDA stream is
+torch's current stream when the context is created.  There is no CPU
+fallback: a missing library raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librsc.so")
+
+RSC_FP64, RSC_MIXED = 0, 1
+STATUS = {0: "RSC_OK", 1: "RSC_EINVAL", 2: "RSC_ENOMEM", 3: "RSC_ECUDA", 4: "RSC_ENOCONV",
+          5: "RSC_ENAN", 6: "RSC_ESINGULAR", 7: "RSC_ETIMEOUT"}
+MAX_HISTORY = 64
+
+# Every symbol of include/rsc.h.
+EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
+           "rsc_conductive_state", "rsc_step", "rsc_step_host", "rsc_explicit_terms",
+           "rsc_apply_jacobian", "rsc_newton_rw", "rsc_newton_rw_host", "rsc_norm2",
+           "rsc_last_error", "rsc_status_string", "rsc_abi_version")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("Ra", ctypes.c_double), ("Ek", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("eta", ctypes.c_double), ("L", ctypes.c_int), ("Ms", ctypes.c_int),
+                ("Nr", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class NewtonOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_newton", ctypes.c_int), ("kmax", ctypes.c_int),
+                ("gmres_tol", ctypes.c_double), ("dt_newton", ctypes.c_double)]
+
+
+class NewtonReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("gmres_total", ctypes.c_int),
+                ("residual", ctypes.c_double), ("C", ctypes.c_double),
+                ("residual_history", ctypes.c_double * MAX_HISTORY),
+                ("gmres_history", ctypes.c_int * MAX_HISTORY), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        it = self.iterations
+        return {"iterations": it, "gmres_total": self.gmres_total, "residual": self.residual,
+                "C": self.C, "residual_history": list(self.residual_history[: it + 1]),
+                "gmres_history": list(self.gmres_history[:it]), "seconds": self.seconds}
+
+
+class RscError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load librsc.so (build it with paper_2508_16635_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librsc.so not found at {path}: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    sig = {
+        "rsc_create": ([ctypes.POINTER(Params), P, ctypes.POINTER(P)], I),
+        "rsc_destroy": ([P], I),
+        "rsc_set_params": ([P, ctypes.POINTER(Params)], I),
+        "rsc_state_size": ([P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(I)], I),
+        "rsc_conductive_state": ([P, P], I),
+        "rsc_step": ([P, P, D, D, I], I),
+        "rsc_step_host": ([P, P, D, D, I], I),
+        "rsc_explicit_terms": ([P, P, P], I),
+        "rsc_apply_jacobian": ([P, P, D, ctypes.c_long, P, P, I, D], I),
+        "rsc_newton_rw": ([P, P, ctypes.POINTER(D), ctypes.c_long, ctypes.POINTER(NewtonOpts),
+                           ctypes.POINTER(NewtonReport)], I),
+        "rsc_newton_rw_host": ([P, P, ctypes.POINTER(D), ctypes.c_long,
+                                ctypes.POINTER(NewtonOpts), ctypes.POINTER(NewtonReport)], I),
+        "rsc_norm2": ([P, P, ctypes.c_size_t, ctypes.POINTER(D)], I),
+        "rsc_last_error": ([P], ctypes.c_char_p),
+        "rsc_status_string": ([I], ctypes.c_char_p),
+        "rsc_abi_version": ([], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class RotatingShell:
+    """One problem on the GPU: parameters, truncation, tables and factorisations."""
+
+    def __init__(self, L, Ms, Nr, Ek, Ra, Pr=1.0, eta=0.35, precision="fp64", device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("RotatingShell needs a CUDA device")
+        self.torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        self.lib = load_library()
+        self.params = Params(Ra, Ek, Pr, eta, L, Ms, Nr,
+                             RSC_MIXED if precision == "mixed" else RSC_FP64)
+        self.L, self.Ms, self.Nr = L, Ms, Nr
+        self._ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            st = self.lib.rsc_create(ctypes.byref(self.params), ctypes.c_void_p(stream),
+                                     ctypes.byref(self._ctx))
+        self._check(st)
+        n = ctypes.c_size_t()
+        P = ctypes.c_int()
+        self._check(self.lib.rsc_state_size(self._ctx, ctypes.byref(n), ctypes.byref(P)))
+        self.n, self.P = n.value, P.value
+
+    # ---- helpers -----------------------------------------------------------
+    def _check(self, st):
+        if st != 0:
+            msg = self.lib.rsc_last_error(self._ctx).decode() if self._ctx else ""
+            raise RscError(st, msg)
+
+    def _vec(self, t, count=1):
+        torch = self.torch
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("expected a contiguous float64 CUDA tensor")
+        if t.numel() != self.n * count:
+            raise ValueError(f"expected {self.n * count} doubles, got {t.numel()}")
+        return _ptr(t)
+
+    def new_state(self):
+        return self.torch.zeros(self.n, dtype=self.torch.float64, device=self.device)
+
+    def close(self):
+        if self._ctx:
+            self.lib.rsc_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- the C ABI -----------------------------------------------------------
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            setattr(self.params, k, v)
+        self._check(self.lib.rsc_set_params(self._ctx, ctypes.byref(self.params)))
+
+    def conductive_state(self):
+        U = self.new_state()
+        self._check(self.lib.rsc_conductive_state(self._ctx, _ptr(U)))
+        return U
+
+    def step(self, U, C=0.0, dt=1e-4, nsteps=1):
+        self._check(self.lib.rsc_step(self._ctx, self._vec(U), C, dt, nsteps))
+        return U
+
+    def step_host(self, U_host, C=0.0, dt=1e-4, nsteps=1):
+        """U_host: contiguous float64 numpy array or pinned CPU tensor (updated in place)."""
+        ptr = U_host.ctypes.data if hasattr(U_host, "ctypes") else U_host.data_ptr()
+        self._check(self.lib.rsc_step_host(self._ctx, ctypes.c_void_p(ptr), C, dt, nsteps))
+        return U_host
+
+    def explicit_terms(self, U):
+        N = self.new_state()
+        self._check(self.lib.rsc_explicit_terms(self._ctx, self._vec(U), _ptr(N)))
+        return N
+
+    def apply_jacobian(self, U, C, J, u, dt, out=None):
+        count = u.numel() // self.n
+        if out is None:
+            out = self.torch.empty_like(u)
+        self._check(self.lib.rsc_apply_jacobian(
+            self._ctx, self._vec(U), C, -1 if J is None else int(J), self._vec(u, count),
+            self._vec(out, count), count, dt))
+        return out
+
+    def newton_rw(self, U, C, J, tol=1e-10, max_newton=10, kmax=100, gmres_tol=1e-10,
+                  dt_newton=200.0):
+        """Newton-GMRES in place on U; returns (C, report dict, status)."""
+        opts = NewtonOpts(tol, max_newton, kmax, gmres_tol, dt_newton)
+        rep = NewtonReport()
+        Cv = ctypes.c_double(C)
+        st = self.lib.rsc_newton_rw(self._ctx, self._vec(U), ctypes.byref(Cv),
+                                    -1 if J is None else int(J), ctypes.byref(opts),
+                                    ctypes.byref(rep))
+        if st not in (0, 4):
+            self._check(st)
+        return Cv.value, rep.as_dict(), st
+
+    def newton_rw_host(self, U_host, C, J, tol=1e-10, max_newton=10, kmax=100,
+                       gmres_tol=1e-10, dt_newton=200.0):
+        opts = NewtonOpts(tol, max_newton, kmax, gmres_tol, dt_newton)
+        rep = NewtonReport()
+        Cv = ctypes.c_double(C)
+        ptr = U_host.ctypes.data if hasattr(U_host, "ctypes") else U_host.data_ptr()
+        st = self.lib.rsc_newton_rw_host(self._ctx, ctypes.c_void_p(ptr), ctypes.byref(Cv),
+                                         -1 if J is None else int(J), ctypes.byref(opts),
+                                         ctypes.byref(rep))
+        if st not in (0, 4):
+            self._check(st)
+        return Cv.value, rep.as_dict(), st
+
+    def norm2(self, v):
+        out = ctypes.c_double()
+        self._check(self.lib.rsc_norm2(self._ctx, _ptr(v), v.numel(), ctypes.byref(out)))
+        return out.value

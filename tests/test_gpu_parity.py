@@ -1,0 +1,167 @@
+"""GPU (CUDA, through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: FP64 path, relative 2-norm per field 1e-11 per step and 1e-10 on
+Jacobian actions and converged rotating waves (the accuracy targets of the
+FP64 path); mixed path (FP32 transforms) 1e-5 per step.
+"""
+import numpy as np
+import pytest
+
+import seeded_inputs as si
+from oracle.shell import Shell
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return _t
+
+
+def _rel_fields(s, got, want):
+    g = s.to_complex(got)
+    w = s.to_complex(want)
+    return [float(np.linalg.norm(g[i] - w[i]) / max(np.linalg.norm(w[i]), 1e-300)) for i in range(3)]
+
+
+def _rel(got, want):
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+
+CASES = [
+    # name, L, Ms, Nr, Ek, Ra
+    ("tiny", 7, 4, 10, 1e-3, 80.0),
+    ("ragged", 13, 3, 17, 3e-3, 95.0),      # odd Nr, m not dividing L, nlat2 not a warp multiple
+    ("one_m", 9, 9, 12, 1e-3, 60.0),        # m in {0, L}
+    ("C1", 31, 4, 24, 1e-3, 120.0),
+]
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES)
+def test_explicit_terms_parity(torch, name, L, Ms, Nr, Ek, Ra):
+    from paper_2508_16635_gb300 import RotatingShell
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra)
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=21, amp=3e-2)
+    got = gpu.explicit_terms(torch.tensor(x, device="cuda")).cpu().numpy()
+    want = s.to_real(s.explicit_terms(s.to_complex(x)))
+    errs = _rel_fields(s, got, want)
+    assert max(errs) < 1e-12, errs
+    gpu.close()
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES)
+@pytest.mark.parametrize("dt,C", [(1e-4, 0.0), (2e-3, -2.7), (200.0, 1.3)])
+def test_step_parity(torch, name, L, Ms, Nr, Ek, Ra, dt, C):
+    from paper_2508_16635_gb300 import RotatingShell
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra)
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=22, amp=1e-2)
+    U = torch.tensor(x, device="cuda")
+    gpu.step(U, C, dt, nsteps=2)
+    want = s.step(x, C, dt, nsteps=2)
+    errs = _rel_fields(s, U.cpu().numpy(), want)
+    assert max(errs) < 1e-11, errs
+    gpu.close()
+
+
+def test_step_host_buffer_matches_device_step(torch):
+    from paper_2508_16635_gb300 import RotatingShell
+    L, Ms, Nr = 15, 4, 16
+    gpu = RotatingShell(L, Ms, Nr, 1e-3, 100.0)
+    x = np.ascontiguousarray(gpu.conductive_state().cpu().numpy() + si.perturbation(L, Ms, Nr, 5))
+    U = torch.tensor(x, device="cuda")
+    gpu.step(U, 0.5, 1e-3, nsteps=3)
+    h = x.copy()
+    gpu.step_host(h, 0.5, 1e-3, nsteps=3)
+    assert np.array_equal(h, U.cpu().numpy())
+    gpu.close()
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES)
+@pytest.mark.parametrize("with_drift", [False, True])
+def test_jacobian_parity(torch, name, L, Ms, Nr, Ek, Ra, with_drift):
+    from paper_2508_16635_gb300 import RotatingShell
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra)
+    U = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=23, amp=3e-2)
+    u = si.random_vector(L, Ms, Nr, seed=24)
+    J = s.real_index("T", Ms, Ms, 1, 1) if with_drift else None
+    if with_drift:
+        u[J] = 0.7
+    C, dt = -1.1, 200.0
+    got = gpu.apply_jacobian(torch.tensor(U, device="cuda"), C, J,
+                             torch.tensor(u, device="cuda"), dt).cpu().numpy()
+    want = s.jvp(U, C, J, u, dt)
+    assert _rel(got, want) < 1e-10
+    gpu.close()
+
+
+def test_jacobian_batch_of_directions(torch):
+    from paper_2508_16635_gb300 import RotatingShell
+    L, Ms, Nr = 15, 4, 16
+    s = Shell(L, Ms, Nr, 1e-3, 120.0)
+    gpu = RotatingShell(L, Ms, Nr, 1e-3, 120.0)
+    U = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=31, amp=3e-2)
+    us = np.stack([si.random_vector(L, Ms, Nr, seed=40 + q) for q in range(3)])
+    got = gpu.apply_jacobian(torch.tensor(U, device="cuda"), 0.2, None,
+                             torch.tensor(us.reshape(-1), device="cuda"), 200.0).cpu().numpy()
+    for q in range(3):
+        assert _rel(got[q * s.n:(q + 1) * s.n], s.jvp(U, 0.2, None, us[q], 200.0)) < 1e-10
+    gpu.close()
+
+
+def test_mixed_precision_step_error(torch):
+    from paper_2508_16635_gb300 import RotatingShell
+    L, Ms, Nr, Ek, Ra = 31, 4, 24, 1e-3, 120.0
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=25, amp=1e-2)
+    U = torch.tensor(x, device="cuda")
+    gpu.step(U, 0.0, 1e-3)
+    want = s.step(x, 0.0, 1e-3)
+    # only the explicit part is FP32: compare the change of the state
+    err = np.linalg.norm(U.cpu().numpy() - want) / np.linalg.norm(want - x)
+    assert err < 1e-4
+    gpu.close()
+
+
+def _rw_initial_guess(s, M, nsteps=400, dt=2e-3):
+    """Oracle time stepping from an m = M temperature seed (the paper starts from cos(M phi))."""
+    x = s.to_complex(s.conductive_state())
+    prof = 1e-2 * np.sin(np.pi * (s.rc - s.r_in))
+    x[2, s.pair_index(M, M)] += np.linalg.solve(s.E[0], prof)
+    U = s.step(s.to_real(x), 0.0, dt, nsteps=nsteps)
+    U1 = s.step(U, 0.0, dt, nsteps=5)
+    from oracle import krylov
+    return U, krylov.drift_estimate(s, U, U1, 5 * dt, M), krylov.phase_index(s, U, M)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_newton_rotating_wave_parity(torch, precision):
+    """RW4 at Ek = 1e-3, Ra = 120 (Table 1 row 1) on a reduced truncation: the GPU Newton-GMRES
+    solution matches the oracle's to 1e-10 (FP64) and the drift to 1e-8 (mixed)."""
+    from oracle import krylov
+    from paper_2508_16635_gb300 import RotatingShell
+    L, Ms, Nr, Ek, Ra = 23, 4, 20, 1e-3, 120.0
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    U0, C0, J = _rw_initial_guess(s, 4)
+    Uo, Co, hist = krylov.newton(s, U0, C0, J, dt=200.0, tol=1e-11, max_newton=12, kmax=120)
+    assert hist[-1]["residual"] < 1e-11
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision=precision)
+    U = torch.tensor(U0, device="cuda")
+    C, rep, st = gpu.newton_rw(U, C0, J, tol=1e-11, max_newton=14, kmax=120, gmres_tol=1e-10)
+    assert st == 0, rep
+    Ug = U.cpu().numpy()
+    if precision == "fp64":
+        assert _rel(Ug, Uo) < 1e-10
+        assert abs(C - Co) < 1e-10 * abs(Co)
+    else:
+        assert _rel(Ug, Uo) < 1e-9
+        assert abs(C - Co) < 1e-8 * abs(Co)
+    gpu.close()
