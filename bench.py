@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the Newton-GMRES hot path on one or more GB300s (one process per GPU).
+
+Workload: the RW12 problem of Table 1 row 3 (Ek = 1e-5, Ra = 140, Pr = 1,
+r_in/r_out = 0.35, 12-fold azimuthal symmetry) at truncation L = 127,
+N_r = 64 (the low-Ekman configuration).  One bench step is one Newton
+iteration of the rotating-wave solver (Secs. 3.3-3.4): the FP64 residual
+B(U) - U at the pseudo-timestep dt = 200, a GMRES solve with a fixed number
+of Jacobian actions (every row of the hot path: radial evaluation, Legendre
+synthesis, azimuthal DFT, grid products, analysis, right-hand side, the
+implicit-Coriolis chain solves, CGS2 orthogonalisation), the Newton update and
+the new residual.  The metric is Jacobian actions per second.
+
+Inputs are synthetic and seeded: the conductive state plus a decaying
+Gaussian perturbation; the state is reset from a device copy before every
+step and L2 is flushed (a 256 MB write) between steps, outside the timed
+interval of each step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference   # the FP64 CPU oracle on the host cores
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import seeded_inputs as si  # noqa: E402
+
+WORKLOAD = dict(name="RW12 Ek=1e-5 Ra=140 (Table 1 row 3), L=127, Ms=12, Nr=64",
+                L=127, Ms=12, Nr=64, Ek=1e-5, Ra=140.0, Pr=1.0, eta=0.35)
+METRIC = "Jacobian actions/s in Newton-GMRES (timesteps/s, JVPs/s, Newton time at Ek=1e-5)"
+UNIT = "JVP/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--krylov", type=int, default=20, help="Jacobian actions per Newton iteration")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(krylov, budget_s=25.0):
+    """Time the FP64 oracle on a bounded sample of the same Newton iteration.
+
+    Factorisation (done once per dt, as on the GPU) is excluded; one residual
+    step and as many Jacobian actions as fit in the budget are timed, and the
+    iteration time is 2 t_step + krylov t_jvp.
+    """
+    import numpy as np
+    from oracle.shell import Shell
+    w = WORKLOAD
+    s = Shell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"])
+    x = s.conductive_state() + si.perturbation(w["L"], w["Ms"], w["Nr"], seed=3000)
+    u = si.random_vector(w["L"], w["Ms"], w["Nr"], seed=3001)
+    s.factor(200.0)
+    t0 = time.perf_counter()
+    s.step(x, 0.0, 200.0)
+    t_step = time.perf_counter() - t0
+    gU = s.grid_fields(s.to_complex(x))
+    n_jvp = 0
+    t0 = time.perf_counter()
+    while True:
+        s.jvp(x, 0.0, None, u, 200.0, gU)
+        n_jvp += 1
+        if time.perf_counter() - t0 > budget_s - t_step or n_jvp >= krylov:
+            break
+    t_jvp = (time.perf_counter() - t0) / n_jvp
+    t_iter = 2 * t_step + krylov * t_jvp
+    return {"value": krylov / t_iter, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 FP64 step + {n_jvp} Jacobian actions of the same workload on the host "
+                      f"(numpy/LAPACK, all cores); iteration time = 2 t_step + {krylov} t_jvp",
+            "t_step_s": t_step, "t_jvp_s": t_jvp}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    times = []
+    for _ in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(args.krylov, budget_s=8.0)
+        times.append(args.krylov / r["value"])
+    t = sum(times[args.warmup:]) / args.steps
+    v = args.krylov / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded perturbation of the conductive state)",
+            "config": {"workload": WORKLOAD["name"], "krylov_per_iteration": args.krylov,
+                       "l2": "not applicable (CPU)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "per step: 1 FP64 step + up to "
+                                       f"{args.krylov} Jacobian actions (8 s budget), "
+                                       f"iteration time = 2 t_step + {args.krylov} t_jvp"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks(torch):
+    """Peaks for the roofline: HBM and bf16 from MEASURED_PEAKS.json; FP64 / FP32 ALU from
+    a cuBLAS DGEMM / SGEMM timed here on the same GPU."""
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        peaks["hbm_gbs"] = float(mp["hbm_gbs"])
+        peaks["hbm_source"] = "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        peaks["hbm_gbs"] = 6800.0
+        peaks["hbm_source"] = "fallback"
+    for dt, key, N in ((torch.float64, "fp64_tflops", 4096), (torch.float32, "fp32_tflops", 8192)):
+        a = torch.randn(N, N, dtype=dt, device="cuda")
+        b = torch.randn(N, N, dtype=dt, device="cuda")
+        for _ in range(2):
+            a @ b
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(4):
+            a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        peaks[key] = 2 * N ** 3 * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        del a, b
+    torch.cuda.empty_cache()
+    return peaks
+
+
+# kernels whose arithmetic is FP64 on both paths; the transforms follow the path's precision
+FP64_KERNELS = {"radial_eval", "rhs_assemble", "chain_solve", "temp_solve", "gmres_dots",
+                "gmres_axpy", "blas1"}
+
+
+def roofline(prof, peaks, precision):
+    name = max(prof, key=lambda k: prof[k]["ms"])
+    p = prof[name]
+    t = p["ms"] / max(1, p["launches"]) * 1e-3
+    gbs = p["bytes"] / max(1, p["launches"]) / t / 1e9
+    fp64 = name in FP64_KERNELS or precision == "fp64"
+    alu_peak = peaks["fp64_tflops"] if fp64 else peaks["fp32_tflops"]
+    tfs = p["flops"] / max(1, p["launches"]) / t / 1e12
+    f_hbm = gbs / peaks["hbm_gbs"]
+    f_alu = tfs / alu_peak
+    if f_alu >= f_hbm:
+        out = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s",
+               "frac": f_alu, "peak_source": ("FP64" if fp64 else "FP32") +
+               " cuBLAS GEMM timed in this run on this GPU (measured)"}
+    else:
+        out = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": f_hbm, "peak_source": peaks["hbm_source"]}
+    out.update(kernel=name, traffic=None, avg_launch_ms=t * 1e3, launches=p["launches"],
+               algorithmic_bytes_per_launch=p["bytes"] / max(1, p["launches"]),
+               algorithmic_flops_per_launch=p["flops"] / max(1, p["launches"]))
+    return out
+
+
+def run_gpu(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_2508_16635_gb300 import RotatingShell
+    from paper_2508_16635_gb300.rsc import KERNELS
+
+    w = WORKLOAD
+    peaks = measured_peaks(torch)
+    sh = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
+                       precision=args.precision)
+    U0 = sh.conductive_state() + torch.tensor(
+        si.perturbation(w["L"], w["Ms"], w["Nr"], seed=3000 + rank), device="cuda")
+    # phase slot: Im of the T coefficient (l = m = 12, k*) with k* = argmax |Re|
+    x = U0.view(3, sh.P, w["Nr"], 2)
+    p12 = (w["L"] + 1)  # first pair of m = 12
+    kstar = int(torch.argmax(torch.abs(x[2, p12, :, 0])).item())
+    J = (((2 * sh.P + p12) * w["Nr"] + kstar) * 2 + 1)
+    U = U0.clone()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    K = args.krylov
+
+    def one_step():
+        return sh.newton_rw(U, 0.5, J, tol=0.0, max_newton=1, kmax=K, gmres_tol=0.0)
+
+    for _ in range(args.warmup):
+        U.copy_(U0)
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = sh.launch_count()
+    gmres_total = 0
+    sh.profile(True)
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            U.copy_(U0)
+            flush.zero_()
+            ev[i][0].record()
+            _, rep, _ = one_step()
+            ev[i][1].record()
+            gmres_total += rep["gmres_total"]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    prof = sh.profile_report()
+    sh.profile(False)
+    launches = sh.launch_count() - launches0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    jvps_per_step = gmres_total / args.steps
+    value = world * jvps_per_step / (ms * 1e-3)
+
+    # plain time stepping (timesteps/s) on the same workload
+    Us = U0.clone()
+    sh.step(Us, 0.0, 5e-6, nsteps=3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sh.step(Us, 0.0, 5e-6, nsteps=20)
+    e1.record()
+    torch.cuda.synchronize()
+    steps_per_s = 20 / (e0.elapsed_time(e1) * 1e-3)
+
+    # end to end through the C ABI with host buffers (copies inside the call)
+    import numpy as np
+    host = np.ascontiguousarray(U0.cpu().numpy())
+    e2e_times = []
+    for i in range(max(2, min(3, args.steps))):
+        h = host.copy()
+        t0 = time.perf_counter()
+        _, rep2, _ = sh.newton_rw_host(h, 0.5, J, tol=0.0, max_newton=1, kmax=K, gmres_tol=0.0)
+        e2e_times.append((time.perf_counter() - t0, rep2["gmres_total"]))
+    e2e_t = sum(t for t, _ in e2e_times) / len(e2e_times)
+    e2e_v = world * sum(g for _, g in e2e_times) / len(e2e_times) / e2e_t
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 transforms + f64 solves" if args.precision == "mixed" else "f64",
+            "data": "synthetic (seeded perturbation of the conductive state)",
+            "config": {"workload": w["name"], "precision": args.precision,
+                       "step": f"1 Newton iteration: FP64 residual, GMRES with {K} Jacobian "
+                               f"actions (CGS2), update, FP64 residual",
+                       "krylov_per_iteration": K, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MB write, outside the timed interval)"},
+            "timesteps_per_s": steps_per_s,
+            "jvps_per_step": jvps_per_step,
+            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 8 * sh.n,
+                    "d2h_bytes_per_step": 8 * sh.n, "ms_per_step": e2e_t * 1e3},
+            "gpu_launches": int(launches),
+            "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items()},
+            "roofline": roofline(prof, peaks, args.precision),
+            "peaks": {k: v for k, v in peaks.items()},
+            "clocks": clk.summary(),
+            "wall_s_timed_region": wall,
+        }
+        if not args.no_baseline:
+            line["cpu_baseline"] = cpu_oracle_sample(K)
+        print(json.dumps(line), flush=True)
+    sh.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

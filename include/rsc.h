@@ -156,6 +156,36 @@ rsc_status rsc_newton_rw(rsc_ctx* ctx, double* U, double* C, long J,
 rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
                               const rsc_newton_opts* opts, rsc_newton_report* report);
 
+/* Tracing.  Kernel identifiers of rsc_profile_query / rsc_kernel_name.     */
+enum {
+  RSC_K_RADIAL = 0,    /* Chebyshev evaluation on the de-aliased radii        */
+  RSC_K_SYNTH = 1,     /* Legendre synthesis                                  */
+  RSC_K_PRODUCTS = 2,  /* inverse DFT, grid products, forward DFT             */
+  RSC_K_ANALYSIS = 3,  /* Legendre analysis                                   */
+  RSC_K_RHS = 4,       /* curl projections, mass, drift and boundary rows     */
+  RSC_K_CHAIN = 5,     /* block-tridiagonal Coriolis chain solve              */
+  RSC_K_TEMP = 6,      /* per-l temperature solve                             */
+  RSC_K_DOTS = 7,      /* GMRES dot products and their reduction              */
+  RSC_K_AXPY = 8,      /* GMRES multi-vector updates                          */
+  RSC_K_BLAS = 9,      /* other vector operations                             */
+  RSC_NUM_KERNELS = 10
+};
+
+/* Start (on != 0) or stop collecting per-kernel timings: CUDA events are
+ * recorded around every launch on the context stream.  Clears the counters. */
+rsc_status rsc_profile_enable(rsc_ctx* ctx, int on);
+
+/* Accumulated device time (ms), launches, algorithmic bytes and flops of one
+ * kernel since rsc_profile_enable (synchronises the stream).                */
+rsc_status rsc_profile_query(rsc_ctx* ctx, int kernel_id, double* ms, long* launches,
+                             double* bytes, double* flops);
+
+/* Name of a kernel identifier.                                              */
+const char* rsc_kernel_name(int kernel_id);
+
+/* Number of kernel launches issued by this context since rsc_create.        */
+rsc_status rsc_launch_count(const rsc_ctx* ctx, long* count);
+
 /* Euclidean norm of a device vector of n doubles (synchronous).            */
 rsc_status rsc_norm2(rsc_ctx* ctx, const double* v, size_t n, double* out);
 

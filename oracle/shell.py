@@ -51,10 +51,10 @@ FIELDS = ("e", "f", "T")
 BC_ROWS = {"e": (0, -1), "T": (0, -1), "f": (0, 1, -2, -1)}
 
 
-def ylm_n(l, m):
-    """N_l^m of Eq. Ylm_norm: sqrt((2 - delta_m0)(2l+1)(l-m)!/(l+m)!)."""
-    return math.sqrt((2.0 - (m == 0)) * (2 * l + 1)
-                     * math.exp(math.lgamma(l - m + 1) - math.lgamma(l + m + 1)))
+def ylm_log_n(l, m):
+    """log N_l^m of Eq. Ylm_norm: N = sqrt((2 - delta_m0)(2l+1)(l-m)!/(l+m)!) (log avoids underflow)."""
+    return 0.5 * (math.log(2.0 - (m == 0)) + math.log(2 * l + 1)
+                  + math.lgamma(l - m + 1) - math.lgamma(l + m + 1))
 
 
 def coriolis_coefficients(l, m):
@@ -66,9 +66,9 @@ def coriolis_coefficients(l, m):
     alpha = 0.0
     if l - 1 >= m and l >= 1:
         alpha = ((l - 1) * (l + 1) * (l - m) / (2 * l - 1)
-                 * ylm_n(l - 1, m) / ylm_n(l, m))
+                 * math.exp(ylm_log_n(l - 1, m) - ylm_log_n(l, m)))
     beta = (l * (l + 2) * (l + 1 + m) / (2 * l + 3)
-            * ylm_n(l + 1, m) / ylm_n(l, m))
+            * math.exp(ylm_log_n(l + 1, m) - ylm_log_n(l, m)))
     return alpha, beta
 
 

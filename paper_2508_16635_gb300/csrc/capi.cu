@@ -73,6 +73,15 @@ struct rsc_ctx {
   double* dots = nullptr;
   double* h_pinned = nullptr;
   int nblk_dot = 0;
+  // tracing: launch counter, per-kernel CUDA-event timing and algorithmic traffic
+  long launches = 0;
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double prof_ms[RSC_NUM_KERNELS] = {0};
+  long prof_launches[RSC_NUM_KERNELS] = {0};
+  double prof_bytes[RSC_NUM_KERNELS] = {0};
+  double prof_flops[RSC_NUM_KERNELS] = {0};
   std::string err;
   DevGeom geom() const {
     DevGeom g;
@@ -107,6 +116,55 @@ template <> const LegDev<float>& leg<float>(const rsc_ctx* ctx) { return ctx->le
   } while (0)
 
 int round32(int v) { return ((v + 31) / 32) * 32; }
+
+cudaEvent_t take_event(rsc_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one kernel launch: counts it, adds its algorithmic bytes / flops
+// and, when tracing is on, records CUDA events around it on the context stream.
+struct KSpan {
+  rsc_ctx* ctx;
+  int id;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KSpan(rsc_ctx* c, int kid, double bytes, double flops) : ctx(c), id(kid) {
+    ctx->launches++;
+    if (ctx->prof_on) {
+      ctx->prof_launches[id]++;
+      ctx->prof_bytes[id] += bytes;
+      ctx->prof_flops[id] += flops;
+      e0 = take_event(ctx);
+      e1 = take_event(ctx);
+      cudaEventRecord(e0, ctx->s);
+    }
+  }
+  ~KSpan() {
+    if (e0) {
+      cudaEventRecord(e1, ctx->s);
+      ctx->ev_pending.push_back({id, {e0, e1}});
+    }
+  }
+};
+
+void drain_events(rsc_ctx* ctx) {
+  if (ctx->ev_pending.empty()) return;
+  cudaStreamSynchronize(ctx->s);
+  for (auto& pe : ctx->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess)
+      ctx->prof_ms[pe.first] += ms;
+    ctx->ev_pool.push_back(pe.second.first);
+    ctx->ev_pool.push_back(pe.second.second);
+  }
+  ctx->ev_pending.clear();
+}
 
 template <typename T>
 rsc_status upload(rsc_ctx* ctx, T** dst, const T* src, size_t count) {
@@ -214,13 +272,23 @@ rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
   using V = typename C2<R>::T;
   const Dims& d = ctx->d;
   const DevGeom g = ctx->geom();
+  {
+  KSpan sp(ctx, RSC_K_RADIAL, 48.0 * d.P * d.Nr + 8.0 * d.P * d.Nd * sizeof(V),
+           28.0 * d.P * d.Nd * d.Nr);
   k_radial<R><<<d.P, round32(std::max(d.Nd, 32)), 3 * d.Nr * sizeof(double2), ctx->s>>>(
       g, reinterpret_cast<const double2*>(x), reinterpret_cast<V*>(ctx->SR));
   CK(cudaGetLastError());
+  }
   const LegDev<R>& L = leg<R>(ctx);
+  {
+  KSpan sp(ctx, RSC_K_SYNTH,
+           8.0 * d.P * d.Nd * sizeof(V) + 9.0 * d.Nd * (d.K + 1) * d.nlat * sizeof(V) +
+               3.0 * d.P * d.nlat2 * sizeof(R),
+           52.0 * d.P * d.nlat2 * d.Nd);
   k_synth<R><<<dim3(d.nm, d.Nd), round32(d.nlat2), (size_t)(d.L + 1) * 8 * sizeof(V), ctx->s>>>(
       g, L.view(), reinterpret_cast<const V*>(ctx->SR), reinterpret_cast<V*>(FCout));
   CK(cudaGetLastError());
+  }
   return RSC_OK;
 }
 
@@ -235,6 +303,10 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
   const size_t smem = (size_t)NF * kTT * K1 * sizeof(V) + 2 * (size_t)K1 * d.nphi * sizeof(R) +
                       4 * (size_t)kTT * d.nphi * sizeof(R);
   dim3 grid(d.Nd, (d.nlat + kTT - 1) / kTT);
+  const double npts = (double)d.Nd * d.nlat * d.nphi;
+  {
+  KSpan sp(ctx, RSC_K_PRODUCTS, (double)(NF + 4) * d.Nd * K1 * d.nlat * sizeof(V),
+           npts * (4.0 * NF * d.K + (lin ? 60.0 : 30.0) + 16.0 * K1));
   if (lin)
     k_products<R, true, kTT><<<grid, 128, smem, ctx->s>>>(
         g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC),
@@ -244,9 +316,16 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
         g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC), nullptr,
         reinterpret_cast<V*>(ctx->FA));
   CK(cudaGetLastError());
+  }
+  {
+  KSpan sp(ctx, RSC_K_ANALYSIS,
+           4.0 * d.Nd * K1 * d.nlat * sizeof(V) + 4.0 * d.P * d.Nd * sizeof(V) +
+               3.0 * d.P * d.nlat2 * sizeof(R),
+           24.0 * d.P * d.nlat2 * d.Nd);
   k_analysis<R><<<dim3(d.nm, d.Nd), round32(d.L + 1), 8 * (size_t)d.nlat2 * sizeof(V), ctx->s>>>(
       g, L.view(), reinterpret_cast<const V*>(ctx->FA), reinterpret_cast<V*>(ctx->AR));
   CK(cudaGetLastError());
+  }
   return RSC_OK;
 }
 
@@ -256,6 +335,9 @@ rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const d
   using V = typename C2<R>::T;
   const Dims& d = ctx->d;
   const size_t smem = (4 * (size_t)d.Nd + 6 * (size_t)d.Nr) * sizeof(double2);
+  KSpan sp(ctx, RSC_K_RHS,
+           4.0 * d.P * d.Nd * sizeof(V) + (rp.has_c ? 144.0 : 96.0) * d.P * d.Nr,
+           d.P * (double)d.Nr * (16.0 * d.Nd + 32.0 * d.Nr));
   k_rhs<R><<<d.P, round32(d.Nr), smem, ctx->s>>>(
       ctx->geom(), rp, reinterpret_cast<const V*>(ctx->AR), reinterpret_cast<const double2*>(x),
       reinterpret_cast<const double2*>(U), out);
@@ -265,9 +347,15 @@ rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const d
 
 rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
   const Dims& d = ctx->d;
+  {
+  KSpan sp(ctx, RSC_K_CHAIN, 3.0 * 2 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
+           3.0 * 2 * d.P * d.Nr * d.Nr * 8.0);
   k_chain_solve<<<2 * d.nm, 256, 3 * (size_t)d.Nr * sizeof(double2), ctx->s>>>(
       ctx->geom(), f->chain_off, f->G, f->H, f->W, ctx->rhs, reinterpret_cast<double2*>(out));
   CK(cudaGetLastError());
+  }
+  KSpan sp(ctx, RSC_K_TEMP, (double)(d.L + 1) * d.Nr * d.Nr * 8.0 + 2.0 * d.P * d.Nr * 16.0,
+           4.0 * d.P * d.Nr * d.Nr);
   k_temp_solve<<<d.P, round32(d.Nr), (size_t)d.Nr * sizeof(double2), ctx->s>>>(
       ctx->geom(), f->Tinv, ctx->rhs, reinterpret_cast<double2*>(out));
   CK(cudaGetLastError());
@@ -323,8 +411,11 @@ rsc_status do_jvp(rsc_ctx* ctx, const double* U, double C, long J, const double*
   int nb;
   launch_1d_grid(n, &nb);
   double c = 0.0;
-  k_copy_zero_slot<<<nb, 256, 0, ctx->s>>>(u, J, ctx->xtmp, n);
-  CK(cudaGetLastError());
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 0.0);
+    k_copy_zero_slot<<<nb, 256, 0, ctx->s>>>(u, J, ctx->xtmp, n);
+    CK(cudaGetLastError());
+  }
   if (J >= 0) {
     CK(cudaMemcpyAsync(ctx->h_pinned, u + J, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
@@ -337,8 +428,11 @@ rsc_status do_jvp(rsc_ctx* ctx, const double* U, double C, long J, const double*
   rp.has_c = (J >= 0 && c != 0.0) ? 1 : 0;
   CKS(stage_rhs<R>(ctx, rp, ctx->xtmp, U, ctx->rhs));
   CKS(stage_solve(ctx, f, out));
-  k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, ctx->xtmp, 1.0, out, n);
-  CK(cudaGetLastError());
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
+    k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, ctx->xtmp, 1.0, out, n);
+    CK(cudaGetLastError());
+  }
   return RSC_OK;
 }
 
@@ -350,10 +444,16 @@ rsc_status jvp_any(rsc_ctx* ctx, const double* U, double C, long J, const double
 // dots[j] = V_j . w for j < nv (written to ctx->dots on the device)
 rsc_status dots(rsc_ctx* ctx, const double* V, long ld, int nv, const double* w, long n,
                 double* dst) {
-  k_dots<<<dim3(ctx->nblk_dot, nv), 256, 0, ctx->s>>>(V, ld, nv, w, n, ctx->partial);
-  CK(cudaGetLastError());
-  k_reduce_rows<<<nv, 256, 0, ctx->s>>>(ctx->partial, ctx->nblk_dot, dst);
-  CK(cudaGetLastError());
+  {
+    KSpan sp(ctx, RSC_K_DOTS, 8.0 * n * (nv + 1), 2.0 * n * nv);
+    k_dots<<<dim3(ctx->nblk_dot, nv), 256, 0, ctx->s>>>(V, ld, nv, w, n, ctx->partial);
+    CK(cudaGetLastError());
+  }
+  {
+    KSpan sp(ctx, RSC_K_DOTS, 8.0 * nv * ctx->nblk_dot, (double)nv * ctx->nblk_dot);
+    k_reduce_rows<<<nv, 256, 0, ctx->s>>>(ctx->partial, ctx->nblk_dot, dst);
+    CK(cudaGetLastError());
+  }
   return RSC_OK;
 }
 
@@ -396,8 +496,11 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
   *relres = 0.0;
   if (beta == 0.0) return RSC_OK;
   double* V = ctx->V;
-  k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / beta, b, 0.0, V, n);
-  CK(cudaGetLastError());
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 1.0 * n);
+    k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / beta, b, 0.0, V, n);
+    CK(cudaGetLastError());
+  }
   std::vector<double> H((size_t)(kmax + 1) * kmax, 0.0), cs(kmax), sn(kmax), gvec(kmax + 1, 0.0);
   gvec[0] = beta;
   int k = 0;
@@ -407,11 +510,17 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
     CKS(jvp_any(ctx, U, C, J, V + (long)k * n, w, dt, fp32));
     // CGS2
     CKS(dots(ctx, V, n, k + 1, w, n, ctx->dots));
-    k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots, -1.0, w, n);
-    CK(cudaGetLastError());
+    {
+      KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (k + 3), 2.0 * n * (k + 1));
+      k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots, -1.0, w, n);
+      CK(cudaGetLastError());
+    }
     CKS(dots(ctx, V, n, k + 1, w, n, ctx->dots + (k + 1)));
-    k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots + (k + 1), -1.0, w, n);
-    CK(cudaGetLastError());
+    {
+      KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (k + 3), 2.0 * n * (k + 1));
+      k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots + (k + 1), -1.0, w, n);
+      CK(cudaGetLastError());
+    }
     CKS(dots(ctx, w, n, 1, w, n, ctx->dots + 2 * (k + 1)));
     CK(cudaMemcpyAsync(ctx->h_pinned, ctx->dots, (2 * (k + 1) + 1) * sizeof(double),
                        cudaMemcpyDeviceToHost, ctx->s));
@@ -443,8 +552,11 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
       ++k;
       break;
     }
-    k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / hn, w, 0.0, w, n);
-    CK(cudaGetLastError());
+    {
+      KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 1.0 * n);
+      k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / hn, w, 0.0, w, n);
+      CK(cudaGetLastError());
+    }
   }
   const int kk = std::min(k, kmax);
   std::vector<double> y(kk, 0.0);
@@ -454,8 +566,11 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
     y[i] = s / H[(size_t)i * kmax + i];
   }
   CK(cudaMemcpyAsync(ctx->dots, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
-  k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, kk, ctx->dots, 1.0, x, n);
-  CK(cudaGetLastError());
+  {
+    KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (kk + 2), 2.0 * n * kk);
+    k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, kk, ctx->dots, 1.0, x, n);
+    CK(cudaGetLastError());
+  }
   CK(cudaStreamSynchronize(ctx->s));
   *iters = kk;
   *relres = res / beta;
@@ -580,6 +695,8 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
   }
   for (auto& f : ctx->fac) free_factor(f);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  drain_events(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
   return RSC_OK;
 }
@@ -669,6 +786,44 @@ rsc_status rsc_apply_jacobian(rsc_ctx* ctx, const double* U, double C, long J, c
   return RSC_OK;
 }
 
+static const char* kKernelNames[RSC_NUM_KERNELS] = {
+    "radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
+    "chain_solve", "temp_solve", "gmres_dots", "gmres_axpy", "blas1"};
+
+const char* rsc_kernel_name(int id) {
+  return (id >= 0 && id < RSC_NUM_KERNELS) ? kKernelNames[id] : "unknown";
+}
+
+rsc_status rsc_profile_enable(rsc_ctx* ctx, int on) {
+  if (!ctx) return RSC_EINVAL;
+  drain_events(ctx);
+  for (int k = 0; k < RSC_NUM_KERNELS; ++k) {
+    ctx->prof_ms[k] = 0.0;
+    ctx->prof_launches[k] = 0;
+    ctx->prof_bytes[k] = 0.0;
+    ctx->prof_flops[k] = 0.0;
+  }
+  ctx->prof_on = on != 0;
+  return RSC_OK;
+}
+
+rsc_status rsc_profile_query(rsc_ctx* ctx, int id, double* ms, long* launches, double* bytes,
+                             double* flops) {
+  if (!ctx || id < 0 || id >= RSC_NUM_KERNELS) return RSC_EINVAL;
+  drain_events(ctx);
+  if (ms) *ms = ctx->prof_ms[id];
+  if (launches) *launches = ctx->prof_launches[id];
+  if (bytes) *bytes = ctx->prof_bytes[id];
+  if (flops) *flops = ctx->prof_flops[id];
+  return RSC_OK;
+}
+
+rsc_status rsc_launch_count(const rsc_ctx* ctx, long* count) {
+  if (!ctx || !count) return RSC_EINVAL;
+  *count = ctx->launches;
+  return RSC_OK;
+}
+
 rsc_status rsc_norm2(rsc_ctx* ctx, const double* v, size_t n, double* out) {
   if (!ctx || !v || !out) return RSC_EINVAL;
   return norm2(ctx, v, (long)n, out);
@@ -694,8 +849,11 @@ rsc_status rsc_newton_rw(rsc_ctx* ctx, double* U, double* C, long J, const rsc_n
     // residual B(U) - U in FP64 (the refinement step of the mixed path)
     CK(cudaMemcpyAsync(ctx->rtmp, U, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
     CKS(step_any(ctx, ctx->rtmp, Cv, o->dt_newton, false));
-    k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, U, 1.0, ctx->rtmp, n);
-    CK(cudaGetLastError());
+    {
+      KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
+      k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, U, 1.0, ctx->rtmp, n);
+      CK(cudaGetLastError());
+    }
     double rn;
     CKS(norm2(ctx, ctx->rtmp, n, &rn));
     if (it < RSC_MAX_HISTORY) r->residual_history[it] = rn;
@@ -725,8 +883,11 @@ rsc_status rsc_newton_rw(rsc_ctx* ctx, double* U, double* C, long J, const rsc_n
       c = ctx->h_pinned[0];
       CK(cudaMemsetAsync(ctx->vtmp + J, 0, sizeof(double), ctx->s));
     }
-    k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, ctx->vtmp, 1.0, U, n);
-    CK(cudaGetLastError());
+    {
+      KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
+      k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, ctx->vtmp, 1.0, U, n);
+      CK(cudaGetLastError());
+    }
     Cv -= c;
   }
   CK(cudaStreamSynchronize(ctx->s));

@@ -21,7 +21,10 @@ MAX_HISTORY = 64
 EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_conductive_state", "rsc_step", "rsc_step_host", "rsc_explicit_terms",
            "rsc_apply_jacobian", "rsc_newton_rw", "rsc_newton_rw_host", "rsc_norm2",
-           "rsc_last_error", "rsc_status_string", "rsc_abi_version")
+           "rsc_last_error", "rsc_status_string", "rsc_abi_version", "rsc_profile_enable",
+           "rsc_profile_query", "rsc_kernel_name", "rsc_launch_count")
+KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
+           "chain_solve", "temp_solve", "gmres_dots", "gmres_axpy", "blas1")
 
 
 class Params(ctypes.Structure):
@@ -86,6 +89,11 @@ def load_library(path=LIB_PATH):
         "rsc_last_error": ([P], ctypes.c_char_p),
         "rsc_status_string": ([I], ctypes.c_char_p),
         "rsc_abi_version": ([], I),
+        "rsc_profile_enable": ([P, I], I),
+        "rsc_profile_query": ([P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long),
+                               ctypes.POINTER(D), ctypes.POINTER(D)], I),
+        "rsc_kernel_name": ([I], ctypes.c_char_p),
+        "rsc_launch_count": ([P, ctypes.POINTER(ctypes.c_long)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -211,6 +219,25 @@ class RotatingShell:
         if st not in (0, 4):
             self._check(st)
         return Cv.value, rep.as_dict(), st
+
+    def profile(self, on=True):
+        """Start / stop per-kernel CUDA-event timing inside the library (clears counters)."""
+        self._check(self.lib.rsc_profile_enable(self._ctx, 1 if on else 0))
+
+    def profile_report(self):
+        """{kernel: {ms, launches, bytes, flops}} accumulated since profile(True)."""
+        out = {}
+        for k, name in enumerate(KERNELS):
+            ms, n, b, f = ctypes.c_double(), ctypes.c_long(), ctypes.c_double(), ctypes.c_double()
+            self._check(self.lib.rsc_profile_query(self._ctx, k, ctypes.byref(ms), ctypes.byref(n),
+                                                   ctypes.byref(b), ctypes.byref(f)))
+            out[name] = {"ms": ms.value, "launches": n.value, "bytes": b.value, "flops": f.value}
+        return out
+
+    def launch_count(self):
+        c = ctypes.c_long()
+        self._check(self.lib.rsc_launch_count(self._ctx, ctypes.byref(c)))
+        return c.value
 
     def norm2(self, v):
         out = ctypes.c_double()
