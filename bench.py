@@ -198,8 +198,8 @@ def measured_peaks(torch):
 
 
 # kernels whose arithmetic is FP64 on both paths; the transforms follow the path's precision
-FP64_KERNELS = {"radial_eval", "rhs_assemble", "chain_solve", "temp_solve", "gmres_dots",
-                "gmres_axpy", "blas1"}
+FP64_KERNELS = {"radial_eval", "rhs_assemble", "chain_gemv", "chain_sweep", "temp_solve",
+                "gmres_dots", "gmres_axpy", "blas1"}
 
 
 def roofline(prof, peaks, precision):

@@ -163,12 +163,13 @@ enum {
   RSC_K_PRODUCTS = 2,  /* inverse DFT, grid products, forward DFT             */
   RSC_K_ANALYSIS = 3,  /* Legendre analysis                                   */
   RSC_K_RHS = 4,       /* curl projections, mass, drift and boundary rows     */
-  RSC_K_CHAIN = 5,     /* block-tridiagonal Coriolis chain solve              */
+  RSC_K_CHAIN = 5,     /* chain solve, parallel part g = D'^{-1} b per block  */
   RSC_K_TEMP = 6,      /* per-l temperature solve                             */
   RSC_K_DOTS = 7,      /* GMRES dot products and their reduction              */
   RSC_K_AXPY = 8,      /* GMRES multi-vector updates                          */
   RSC_K_BLAS = 9,      /* other vector operations                             */
-  RSC_NUM_KERNELS = 10
+  RSC_K_CHAIN_SEQ = 10,/* chain solve, forward / backward sweeps (clusters)   */
+  RSC_NUM_KERNELS = 11
 };
 
 /* Start (on != 0) or stop collecting per-kernel timings: CUDA events are

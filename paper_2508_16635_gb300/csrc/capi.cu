@@ -73,6 +73,7 @@ struct rsc_ctx {
   double* dots = nullptr;
   double* h_pinned = nullptr;
   int nblk_dot = 0;
+  int cluster = 8;  // CTAs per chain in the cluster chain solve
   // tracing: launch counter, per-kernel CUDA-event timing and algorithmic traffic
   long launches = 0;
   bool prof_on = false;
@@ -345,14 +346,46 @@ rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const d
   return RSC_OK;
 }
 
+template <int Q>
+cudaError_t launch_chain(rsc_ctx* ctx, const DevFactor* f, double* out) {
+  const Dims& d = ctx->d;
+  const int CS = ctx->cluster;
+  const int RPC = (d.Nr + CS - 1) / CS;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * d.nm * CS);
+  cfg.blockDim = dim3(32 * RPC);
+  cfg.dynamicSmemBytes = 2 * (size_t)d.Nr * sizeof(double2);
+  cfg.stream = ctx->s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_chain_cluster<Q>, ctx->geom(), (const long*)f->chain_off,
+                            (const double2*)f->H, (const double2*)f->W,
+                            reinterpret_cast<double2*>(out), CS);
+}
+
 rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
   const Dims& d = ctx->d;
   {
-  KSpan sp(ctx, RSC_K_CHAIN, 3.0 * 2 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
-           3.0 * 2 * d.P * d.Nr * d.Nr * 8.0);
-  k_chain_solve<<<2 * d.nm, 256, 3 * (size_t)d.Nr * sizeof(double2), ctx->s>>>(
-      ctx->geom(), f->chain_off, f->G, f->H, f->W, ctx->rhs, reinterpret_cast<double2*>(out));
-  CK(cudaGetLastError());
+    KSpan sp(ctx, RSC_K_CHAIN, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
+             2.0 * d.P * d.Nr * d.Nr * 8.0);
+    k_block_gemv<<<2 * d.P, 256, (size_t)d.Nr * sizeof(double2), ctx->s>>>(
+        ctx->geom(), f->chain_off, f->G, ctx->rhs, reinterpret_cast<double2*>(out));
+    CK(cudaGetLastError());
+  }
+  {
+    KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * 2 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
+             2.0 * 2 * d.P * d.Nr * d.Nr * 8.0);
+    const int Q = (d.Nr + 31) / 32;
+    cudaError_t e = Q == 1 ? launch_chain<1>(ctx, f, out)
+                  : Q == 2 ? launch_chain<2>(ctx, f, out)
+                  : Q == 3 ? launch_chain<3>(ctx, f, out)
+                           : launch_chain<4>(ctx, f, out);
+    CK(e);
   }
   KSpan sp(ctx, RSC_K_TEMP, (double)(d.L + 1) * d.Nr * d.Nr * 8.0 + 2.0 * d.P * d.Nr * 16.0,
            4.0 * d.P * d.Nr * d.Nr);
@@ -360,6 +393,41 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
       ctx->geom(), f->Tinv, ctx->rhs, reinterpret_cast<double2*>(out));
   CK(cudaGetLastError());
   return RSC_OK;
+}
+
+// Largest cluster (16, else 8, 4, 2) that the device can co-schedule for the chain solve.
+rsc_status choose_cluster(rsc_ctx* ctx) {
+  const Dims& d = ctx->d;
+  const int Q = (d.Nr + 31) / 32;
+  const void* fn = Q == 1 ? (const void*)k_chain_cluster<1>
+                 : Q == 2 ? (const void*)k_chain_cluster<2>
+                 : Q == 3 ? (const void*)k_chain_cluster<3>
+                          : (const void*)k_chain_cluster<4>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaGetLastError();
+  for (int CS : {16, 8, 4, 2}) {
+    if (CS > d.Nr) continue;
+    const int RPC = (d.Nr + CS - 1) / CS;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * d.nm * CS);
+    cfg.blockDim = dim3(32 * RPC);
+    cfg.dynamicSmemBytes = 2 * (size_t)d.Nr * sizeof(double2);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters > 0) {
+      ctx->cluster = CS;
+      return RSC_OK;
+    }
+    cudaGetLastError();
+  }
+  ctx->err = "no thread-block cluster configuration available for the chain solve";
+  return RSC_ECUDA;
 }
 
 RhsParams make_rp(rsc_ctx* ctx, double dt, double C, int mode) {
@@ -647,6 +715,7 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = upload_legendre(ctx, ctx->leg64)) != RSC_OK) return fail(st);
   if ((st = upload_legendre(ctx, ctx->leg32)) != RSC_OK) return fail(st);
   if ((st = set_smem_limits(ctx)) != RSC_OK) return fail(st);
+  if ((st = choose_cluster(ctx)) != RSC_OK) return fail(st);
   const size_t c16 = sizeof(double2);
   const size_t K1 = d.K + 1;
   auto alloc = [&](void** p, size_t bytes) -> rsc_status {

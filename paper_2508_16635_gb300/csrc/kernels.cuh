@@ -9,10 +9,11 @@
 //   k_analysis  per (m, r): Gauss-weighted Legendre projection      [a6]
 //   k_rhs       per (l, m): radial projection, curl / double curl,
 //               mass, drift and boundary rows (FP64)               [a7]
-//   k_chain_solve / k_temp_solve: block-tridiagonal Coriolis chains
-//               and per-l temperature solves (FP64)                [a8]
+//   k_block_gemv, k_chain_cluster, k_temp_solve: block-tridiagonal
+//               Coriolis chains and per-l temperature solves (FP64) [a8]
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -440,9 +441,7 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
 
 // ---------------------------------------------------------------------------
 // a8: block-tridiagonal chain solve (block Thomas with stored
-// G = D'^{-1}, H = D'^{-1} A, W = D'^{-1} C).  grid = 2 nm chains, block = 256.
-//   forward  y_i = G_i b_i - H_i y_{i-1}
-//   backward x_i = y_i - W_i x_{i+1}
+// G = D'^{-1}, H = D'^{-1} A, W = D'^{-1} C from the factorisation).
 __device__ __forceinline__ double2 warp_sum2(double2 v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -458,71 +457,133 @@ __device__ __forceinline__ double2 cmac(double2 acc, double2 a, double2 b) {
   return acc;
 }
 
-__global__ void k_chain_solve(DevGeom g, const long* __restrict__ chain_off,
-                              const double2* __restrict__ G, const double2* __restrict__ H,
-                              const double2* __restrict__ W, const double2* __restrict__ rhs,
-                              double2* __restrict__ out) {
+// a8, parallel part: g = G b for every diagonal block of every chain (the
+// part of the forward sweep that does not depend on earlier blocks).
+// grid = 2 P (blockIdx.x = 2 p + field), block = 256.  g is written to out.
+__global__ void k_block_gemv(DevGeom g, const long* __restrict__ chain_off,
+                             const double2* __restrict__ G, const double2* __restrict__ rhs,
+                             double2* __restrict__ out) {
   extern __shared__ double2 sv[];
   const int Nr = g.Nr, P = g.P;
-  double2* b = sv;           // [Nr]
-  double2* yp = sv + Nr;     // [Nr] previous y / next x
-  double2* yn = sv + 2 * Nr; // [Nr]
-  const int c = blockIdx.x;
+  const int p = blockIdx.x >> 1, fld = blockIdx.x & 1;
+  const int m = g.pair_m[p], a = m / g.Ms, i = g.pair_l[p] - m;
+  const int cls = (fld == 0) ? (i & 1) : 1 - (i & 1);
+  const double2* Gi = G + (chain_off[2 * a + cls] + i) * (long)Nr * Nr;
+  const long row0 = ((long)fld * P + p) * Nr;
+  for (int k = threadIdx.x; k < Nr; k += blockDim.x) sv[k] = rhs[row0 + k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < Nr; r += nw) {
+    double2 acc = {0, 0};
+    for (int k = lane; k < Nr; k += 32) acc = cmac(acc, Gi[(long)r * Nr + k], sv[k]);
+    acc = warp_sum2(acc);
+    if (lane == 0) out[row0 + r] = acc;
+  }
+}
+
+// a8, sequential part on a thread-block cluster of CS CTAs per chain.
+//   forward  y_i = g_i - H_i y_{i-1}      backward x_i = y_i - W_i x_{i+1}
+// CTA `rank` owns rows [rank * RPC, rank * RPC + RPC), one warp per row; the
+// full vector of the previous block lives in every CTA's shared memory and
+// each new slice is broadcast through distributed shared memory, followed by
+// one cluster barrier per block.  H / W rows of the next block are loaded
+// into registers before the barrier.  The barrier is the hardware cluster
+// barrier (no spin loop); every CTA runs the same number of iterations.
+template <int MAXQ>
+__global__ void k_chain_cluster(DevGeom g, const long* __restrict__ chain_off,
+                                const double2* __restrict__ H, const double2* __restrict__ W,
+                                double2* __restrict__ out, int CS) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double2 sv[];  // [2][Nr] double-buffered vector
+  const int Nr = g.Nr, P = g.P;
+  const int rank = (int)cluster.block_rank();
+  const int c = blockIdx.x / CS;
   const int a = c >> 1, cls = c & 1;
   const int m = g.m_of[a];
   const int p0 = g.pstart[a];
   const int nb = g.L - m + 1;
   const long boff = chain_off[c];
   const long blk = (long)Nr * Nr;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = 0; i < nb; ++i) {
+  const int RPC = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = rank * RPC + warp;
+  const bool active = r < Nr;
+  auto rowptr = [&](int i) {
     const int fld = ((i + cls) & 1) ? 1 : 0;
-    const long row0 = ((long)fld * P + p0 + i) * Nr;
-    for (int k = threadIdx.x; k < Nr; k += blockDim.x) b[k] = rhs[row0 + k];
-    __syncthreads();
-    const double2* Gi = G + (boff + i) * blk;
-    const double2* Hi = H + (boff + i) * blk;
-    for (int r = warp; r < Nr; r += nw) {
-      double2 acc = {0, 0};
-      for (int k = lane; k < Nr; k += 32) {
-        acc = cmac(acc, Gi[(long)r * Nr + k], b[k]);
-        if (i > 0) {
-          const double2 h = Hi[(long)r * Nr + k];
-          acc = cmac(acc, make_double2(-h.x, -h.y), yp[k]);
-        }
-      }
-      acc = warp_sum2(acc);
-      if (lane == 0) {
-        yn[r] = acc;
-        out[row0 + r] = acc;
-      }
+    return ((long)fld * P + p0 + i) * Nr;
+  };
+  auto broadcast = [&](int buf, double2 v) {
+    // lanes 0..CS-1 each write the new value into one CTA of the cluster
+    if (active && lane < CS) {
+      double2* dst = cluster.map_shared_rank(sv + buf * Nr, lane);
+      dst[r] = v;
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < Nr; k += blockDim.x) yp[k] = yn[k];
-    __syncthreads();
+  };
+  double2 hc[MAXQ], hn[MAXQ];
+  // block 0: y_0 = g_0
+  double2 y0 = active ? out[rowptr(0) + r] : make_double2(0, 0);
+  broadcast(0, y0);
+#pragma unroll
+  for (int q = 0; q < MAXQ; ++q) {
+    const int k = lane + 32 * q;
+    hn[q] = (active && nb > 1 && k < Nr) ? H[(boff + 1) * blk + (long)r * Nr + k] : make_double2(0, 0);
   }
-  // yp holds x_{nb-1} = y_{nb-1}
-  for (int i = nb - 2; i >= 0; --i) {
-    const int fld = ((i + cls) & 1) ? 1 : 0;
-    const long row0 = ((long)fld * P + p0 + i) * Nr;
-    const double2* Wi = W + (boff + i) * blk;
-    for (int r = warp; r < Nr; r += nw) {
-      double2 acc = {0, 0};
-      for (int k = lane; k < Nr; k += 32) {
-        const double2 w = Wi[(long)r * Nr + k];
-        acc = cmac(acc, make_double2(-w.x, -w.y), yp[k]);
-      }
-      acc = warp_sum2(acc);
-      if (lane == 0) {
-        const double2 y = out[row0 + r];
-        const double2 v = make_double2(y.x + acc.x, y.y + acc.y);
-        yn[r] = v;
-        out[row0 + r] = v;
-      }
+  cluster.sync();
+  for (int i = 1; i < nb; ++i) {
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) hc[q] = hn[q];
+    double2 gi = active ? out[rowptr(i) + r] : make_double2(0, 0);
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+      const int k = lane + 32 * q;
+      hn[q] = (active && i + 1 < nb && k < Nr) ? H[(boff + i + 1) * blk + (long)r * Nr + k]
+                                               : make_double2(0, 0);
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < Nr; k += blockDim.x) yp[k] = yn[k];
-    __syncthreads();
+    const double2* yprev = sv + ((i - 1) & 1) * Nr;
+    double2 acc = {0, 0};
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+      const int k = lane + 32 * q;
+      if (k < Nr) acc = cmac(acc, hc[q], yprev[k]);
+    }
+    acc = warp_sum2(acc);
+    const double2 yi = make_double2(gi.x - acc.x, gi.y - acc.y);
+    if (active && lane == 0) out[rowptr(i) + r] = yi;
+    broadcast(i & 1, yi);
+    cluster.sync();
+  }
+  // backward sweep; the vector of block nb-1 is in buffer (nb-1) & 1
+#pragma unroll
+  for (int q = 0; q < MAXQ; ++q) {
+    const int k = lane + 32 * q;
+    hn[q] = (active && nb > 1 && k < Nr) ? W[(boff + nb - 2) * blk + (long)r * Nr + k]
+                                         : make_double2(0, 0);
+  }
+  int cur = (nb - 1) & 1;
+  for (int i = nb - 2; i >= 0; --i) {
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) hc[q] = hn[q];
+    double2 yi = active ? out[rowptr(i) + r] : make_double2(0, 0);
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+      const int k = lane + 32 * q;
+      hn[q] = (active && i >= 1 && k < Nr) ? W[(boff + i - 1) * blk + (long)r * Nr + k]
+                                           : make_double2(0, 0);
+    }
+    const double2* xnext = sv + cur * Nr;
+    double2 acc = {0, 0};
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+      const int k = lane + 32 * q;
+      if (k < Nr) acc = cmac(acc, hc[q], xnext[k]);
+    }
+    acc = warp_sum2(acc);
+    const double2 xi = make_double2(yi.x - acc.x, yi.y - acc.y);
+    if (active && lane == 0) out[rowptr(i) + r] = xi;
+    cur ^= 1;
+    broadcast(cur, xi);
+    cluster.sync();
   }
 }
 

@@ -24,7 +24,7 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_last_error", "rsc_status_string", "rsc_abi_version", "rsc_profile_enable",
            "rsc_profile_query", "rsc_kernel_name", "rsc_launch_count")
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
-           "chain_solve", "temp_solve", "gmres_dots", "gmres_axpy", "blas1")
+           "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
 
 
 class Params(ctypes.Structure):
