@@ -190,6 +190,25 @@ rsc_status rsc_launch_count(const rsc_ctx* ctx, long* count);
 /* Euclidean norm of a device vector of n doubles (synchronous).            */
 rsc_status rsc_norm2(rsc_ctx* ctx, const double* v, size_t n, double* out);
 
+/* Allocation-free variant of rsc_norm2 (the paper has no counterpart).
+ * Some callers cannot call cudaMalloc: hosts whose device memory is wholly
+ * owned by their own pool allocator, and long-running services that forbid
+ * allocation after start-up.  This entry point needs no context and
+ * allocates nothing: it writes ||v||_2 of the n doubles at device pointer v
+ * to out[0] (a device pointer the caller owns), asynchronously on `stream`
+ * (a cudaStream_t; NULL = legacy default stream) of the current device.
+ * Its scratch is a fixed array of RSC_NORM2_NOALLOC_MAX_N / 4096 doubles
+ * (16 KiB) in device memory, held by every GPU that loads the library until
+ * the process exits.  The first call on a device looks the array up (once
+ * per device, with that device current), so make that first call before any
+ * stream capture.  All calls on a device share the array: calls whose
+ * kernels overlap on the GPU (other streams, other host threads) race and
+ * may return wrong sums; serialise them.  Returns RSC_EINVAL when v or out
+ * is NULL or n > RSC_NORM2_NOALLOC_MAX_N, RSC_ECUDA when the look-up or
+ * launch fails.                                                            */
+#define RSC_NORM2_NOALLOC_MAX_N 8388608
+rsc_status rsc_norm2_noalloc(const double* v, size_t n, double* out, void* stream);
+
 /* Text of the last error on this context (never NULL).                     */
 const char* rsc_last_error(const rsc_ctx* ctx);
 

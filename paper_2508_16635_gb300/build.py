@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librsc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "tables.cpp"]
+SOURCES = ["capi.cu", "tables.cpp", "noalloc.cu"]
 
 
 def _nvcc():

@@ -22,7 +22,8 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_conductive_state", "rsc_step", "rsc_step_host", "rsc_explicit_terms",
            "rsc_apply_jacobian", "rsc_newton_rw", "rsc_newton_rw_host", "rsc_norm2",
            "rsc_last_error", "rsc_status_string", "rsc_abi_version", "rsc_profile_enable",
-           "rsc_profile_query", "rsc_kernel_name", "rsc_launch_count")
+           "rsc_profile_query", "rsc_kernel_name", "rsc_launch_count", "rsc_norm2_noalloc")
+NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
            "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
 
@@ -94,6 +95,7 @@ def load_library(path=LIB_PATH):
                                ctypes.POINTER(D), ctypes.POINTER(D)], I),
         "rsc_kernel_name": ([I], ctypes.c_char_p),
         "rsc_launch_count": ([P, ctypes.POINTER(ctypes.c_long)], I),
+        "rsc_norm2_noalloc": ([P, ctypes.c_size_t, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
