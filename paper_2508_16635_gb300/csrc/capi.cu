@@ -55,11 +55,14 @@ struct rsc_ctx {
   long* d_leg_off = nullptr;
   double *d_rc = nullptr, *d_rd = nullptr, *d_EcT0 = nullptr, *d_EcT2 = nullptr;
   double *d_EdT0 = nullptr, *d_EdT1 = nullptr, *d_EdT2 = nullptr, *d_R0T = nullptr, *d_R1T = nullptr;
+  float *f_EdT0 = nullptr, *f_EdT1 = nullptr, *f_EdT2 = nullptr, *f_R0T = nullptr, *f_R1T = nullptr;
+  float* f_rd = nullptr;
   LegDev<double> leg64;
   LegDev<float> leg32;
   // workspace (sized for FP64; the FP32 path uses the front part)
   void *SR = nullptr, *FC = nullptr, *FCU = nullptr, *FA = nullptr, *AR = nullptr;
   double2* rhs = nullptr;
+  double2* mid = nullptr;   // chain sweep staging, [2 nm][3][Nr]
   double* xtmp = nullptr;
   double* vtmp = nullptr;
   double* rtmp = nullptr;
@@ -91,6 +94,8 @@ struct rsc_ctx {
     g.m_of = d_m_of; g.pstart = d_pstart; g.leg_off = d_leg_off; g.pair_l = d_pair_l;
     g.pair_m = d_pair_m; g.rc = d_rc; g.rd = d_rd; g.EcT0 = d_EcT0; g.EcT2 = d_EcT2;
     g.EdT0 = d_EdT0; g.EdT1 = d_EdT1; g.EdT2 = d_EdT2; g.R0T = d_R0T; g.R1T = d_R1T;
+    g.EdT0f = f_EdT0; g.EdT1f = f_EdT1; g.EdT2f = f_EdT2; g.R0Tf = f_R0T; g.R1Tf = f_R1T;
+    g.rdf = f_rd;
     return g;
   }
 };
@@ -276,7 +281,7 @@ rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
   {
   KSpan sp(ctx, RSC_K_RADIAL, 48.0 * d.P * d.Nr + 8.0 * d.P * d.Nd * sizeof(V),
            28.0 * d.P * d.Nd * d.Nr);
-  k_radial<R><<<d.P, round32(std::max(d.Nd, 32)), 3 * d.Nr * sizeof(double2), ctx->s>>>(
+  k_radial<R><<<d.P, round32(std::max(d.Nd, 32)), 3 * d.Nr * sizeof(V), ctx->s>>>(
       g, reinterpret_cast<const double2*>(x), reinterpret_cast<V*>(ctx->SR));
   CK(cudaGetLastError());
   }
@@ -332,29 +337,35 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
 
 template <typename R>
 rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const double* U,
-                     double2* out) {
+                     const double* u_orig, double2* out) {
   using V = typename C2<R>::T;
   const Dims& d = ctx->d;
   const size_t smem = (4 * (size_t)d.Nd + 6 * (size_t)d.Nr) * sizeof(double2);
   KSpan sp(ctx, RSC_K_RHS,
-           4.0 * d.P * d.Nd * sizeof(V) + (rp.has_c ? 144.0 : 96.0) * d.P * d.Nr,
+           4.0 * d.P * d.Nd * sizeof(V) + (rp.J >= 0 ? 144.0 : 96.0) * d.P * d.Nr,
            d.P * (double)d.Nr * (16.0 * d.Nd + 32.0 * d.Nr));
   k_rhs<R><<<d.P, round32(d.Nr), smem, ctx->s>>>(
       ctx->geom(), rp, reinterpret_cast<const V*>(ctx->AR), reinterpret_cast<const double2*>(x),
-      reinterpret_cast<const double2*>(U), out);
+      reinterpret_cast<const double2*>(U), u_orig, out);
   CK(cudaGetLastError());
   return RSC_OK;
 }
 
+// MAXQ (columns per lane, 8 lanes per row) rounded up to an instantiated size.
+int chain_maxq(int Nr) {
+  const int q = (Nr + 7) / 8;
+  return q <= 2 ? 2 : q <= 4 ? 4 : q <= 8 ? 8 : q <= 12 ? 12 : 16;
+}
+
 template <int Q>
-cudaError_t launch_chain(rsc_ctx* ctx, const DevFactor* f, double* out) {
+cudaError_t launch_chain_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
   const Dims& d = ctx->d;
   const int CS = ctx->cluster;
   const int RPC = (d.Nr + CS - 1) / CS;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * d.nm * CS);
-  cfg.blockDim = dim3(32 * RPC);
-  cfg.dynamicSmemBytes = 2 * (size_t)d.Nr * sizeof(double2);
+  cfg.gridDim = dim3(2 * 2 * d.nm * CS);
+  cfg.blockDim = dim3(32 * ((RPC + 3) / 4));
+  cfg.dynamicSmemBytes = (outward ? 4 : 2) * (size_t)d.Nr * sizeof(double2);
   cfg.stream = ctx->s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -363,9 +374,22 @@ cudaError_t launch_chain(rsc_ctx* ctx, const DevFactor* f, double* out) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_chain_cluster<Q>, ctx->geom(), (const long*)f->chain_off,
-                            (const double2*)f->H, (const double2*)f->W,
-                            reinterpret_cast<double2*>(out), CS);
+  if (outward)
+    return cudaLaunchKernelEx(&cfg, k_chain_out<Q>, ctx->geom(), (const long*)f->chain_off,
+                              (const double2*)f->H, (const double2*)f->W,
+                              reinterpret_cast<double2*>(out), (const double2*)ctx->mid, CS);
+  return cudaLaunchKernelEx(&cfg, k_chain_half<Q>, ctx->geom(), (const long*)f->chain_off,
+                            (const double2*)f->H, reinterpret_cast<double2*>(out), ctx->mid, CS);
+}
+
+cudaError_t launch_chain(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
+  switch (chain_maxq(ctx->d.Nr)) {
+    case 2: return launch_chain_q<2>(ctx, f, out, outward);
+    case 4: return launch_chain_q<4>(ctx, f, out, outward);
+    case 8: return launch_chain_q<8>(ctx, f, out, outward);
+    case 12: return launch_chain_q<12>(ctx, f, out, outward);
+    default: return launch_chain_q<16>(ctx, f, out, outward);
+  }
 }
 
 rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
@@ -378,14 +402,15 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
     CK(cudaGetLastError());
   }
   {
-    KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * 2 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
-             2.0 * 2 * d.P * d.Nr * d.Nr * 8.0);
-    const int Q = (d.Nr + 31) / 32;
-    cudaError_t e = Q == 1 ? launch_chain<1>(ctx, f, out)
-                  : Q == 2 ? launch_chain<2>(ctx, f, out)
-                  : Q == 3 ? launch_chain<3>(ctx, f, out)
-                           : launch_chain<4>(ctx, f, out);
-    CK(e);
+    // forward half-sweeps read H of about half the blocks each way, outward sweeps W
+    KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
+             2.0 * d.P * d.Nr * d.Nr * 8.0);
+    CK(launch_chain(ctx, f, out, false));
+  }
+  {
+    KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
+             2.0 * d.P * d.Nr * d.Nr * 8.0);
+    CK(launch_chain(ctx, f, out, true));
   }
   KSpan sp(ctx, RSC_K_TEMP, (double)(d.L + 1) * d.Nr * d.Nr * 8.0 + 2.0 * d.P * d.Nr * 16.0,
            4.0 * d.P * d.Nr * d.Nr);
@@ -395,23 +420,18 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
   return RSC_OK;
 }
 
-// Largest cluster (16, else 8, 4, 2) that the device can co-schedule for the chain solve.
-rsc_status choose_cluster(rsc_ctx* ctx) {
-  const Dims& d = ctx->d;
-  const int Q = (d.Nr + 31) / 32;
-  const void* fn = Q == 1 ? (const void*)k_chain_cluster<1>
-                 : Q == 2 ? (const void*)k_chain_cluster<2>
-                 : Q == 3 ? (const void*)k_chain_cluster<3>
-                          : (const void*)k_chain_cluster<4>;
-  cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaGetLastError();
-  for (int CS : {16, 8, 4, 2}) {
-    if (CS > d.Nr) continue;
+// Largest cluster (16, else 8, 4, 2) that the device can co-schedule for the chain sweeps.
+template <int Q>
+bool cluster_ok(const Dims& d, int CS) {
+  const void* fns[2] = {(const void*)k_chain_half<Q>, (const void*)k_chain_out<Q>};
+  for (int w = 0; w < 2; ++w) {
+    cudaFuncSetAttribute(fns[w], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaGetLastError();
     const int RPC = (d.Nr + CS - 1) / CS;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * d.nm * CS);
-    cfg.blockDim = dim3(32 * RPC);
-    cfg.dynamicSmemBytes = 2 * (size_t)d.Nr * sizeof(double2);
+    cfg.gridDim = dim3(2 * 2 * d.nm * CS);
+    cfg.blockDim = dim3(32 * ((RPC + 3) / 4));
+    cfg.dynamicSmemBytes = (w ? 4 : 2) * (size_t)d.Nr * sizeof(double2);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CS;
@@ -419,12 +439,31 @@ rsc_status choose_cluster(rsc_ctx* ctx) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters > 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fns[w], &cfg) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  return true;
+}
+
+rsc_status choose_cluster(rsc_ctx* ctx) {
+  const Dims& d = ctx->d;
+  for (int CS : {16, 8, 4, 2}) {
+    if (CS > d.Nr) continue;
+    bool ok = false;
+    switch (chain_maxq(d.Nr)) {
+      case 2: ok = cluster_ok<2>(d, CS); break;
+      case 4: ok = cluster_ok<4>(d, CS); break;
+      case 8: ok = cluster_ok<8>(d, CS); break;
+      case 12: ok = cluster_ok<12>(d, CS); break;
+      default: ok = cluster_ok<16>(d, CS); break;
+    }
+    if (ok) {
       ctx->cluster = CS;
       return RSC_OK;
     }
-    cudaGetLastError();
   }
   ctx->err = "no thread-block cluster configuration available for the chain solve";
   return RSC_ECUDA;
@@ -434,12 +473,11 @@ RhsParams make_rp(rsc_ctx* ctx, double dt, double C, int mode) {
   RhsParams rp;
   rp.inv_dt = std::isfinite(dt) ? 1.0 / dt : 0.0;
   rp.C = C;
-  rp.c = 0.0;
+  rp.J = -1;
   rp.Ek = ctx->p.Ek;
   rp.Ra = ctx->p.Ra;
   rp.r_out = ctx->d.r_out;
   rp.mode = mode;
-  rp.has_c = 0;
   return rp;
 }
 
@@ -450,7 +488,7 @@ rsc_status do_step(rsc_ctx* ctx, double* U, double C, double dt) {
   CKS(get_factor(ctx, dt, &f));
   CKS(stage_synth<R>(ctx, U, ctx->FC));
   CKS(stage_products_analysis<R>(ctx, false));
-  CKS(stage_rhs<R>(ctx, make_rp(ctx, dt, C, 0), U, nullptr, ctx->rhs));
+  CKS(stage_rhs<R>(ctx, make_rp(ctx, dt, C, 0), U, nullptr, nullptr, ctx->rhs));
   CKS(stage_solve(ctx, f, U));
   return RSC_OK;
 }
@@ -478,23 +516,16 @@ rsc_status do_jvp(rsc_ctx* ctx, const double* U, double C, long J, const double*
   const long n = ctx->d.n();
   int nb;
   launch_1d_grid(n, &nb);
-  double c = 0.0;
   {
     KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 0.0);
     k_copy_zero_slot<<<nb, 256, 0, ctx->s>>>(u, J, ctx->xtmp, n);
     CK(cudaGetLastError());
   }
-  if (J >= 0) {
-    CK(cudaMemcpyAsync(ctx->h_pinned, u + J, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
-    CK(cudaStreamSynchronize(ctx->s));
-    c = ctx->h_pinned[0];
-  }
   CKS(stage_synth<R>(ctx, ctx->xtmp, ctx->FC));
   CKS(stage_products_analysis<R>(ctx, true));
   RhsParams rp = make_rp(ctx, dt, C, 1);
-  rp.c = c;
-  rp.has_c = (J >= 0 && c != 0.0) ? 1 : 0;
-  CKS(stage_rhs<R>(ctx, rp, ctx->xtmp, U, ctx->rhs));
+  rp.J = J;  // c = u[J] is read on the device
+  CKS(stage_rhs<R>(ctx, rp, ctx->xtmp, U, u, ctx->rhs));
   CKS(stage_solve(ctx, f, out));
   {
     KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
@@ -710,6 +741,14 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
     UP(ctx->d_EdT2, d2);
     UP(ctx->d_R0T, r0);
     UP(ctx->d_R1T, r1);
+    auto tof = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+    auto d0f = tof(d0), d1f = tof(d1), d2f = tof(d2), r0f = tof(r0), r1f = tof(r1), rdf = tof(t.rd);
+    UP(ctx->f_EdT0, d0f);
+    UP(ctx->f_EdT1, d1f);
+    UP(ctx->f_EdT2, d2f);
+    UP(ctx->f_R0T, r0f);
+    UP(ctx->f_R1T, r1f);
+    UP(ctx->f_rd, rdf);
   }
 #undef UP
   if ((st = upload_legendre(ctx, ctx->leg64)) != RSC_OK) return fail(st);
@@ -732,6 +771,7 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = alloc(&ctx->FA, 4 * (size_t)d.Nd * K1 * d.nlat * c16)) != RSC_OK) return fail(st);
   if ((st = alloc(&ctx->AR, (size_t)d.P * d.Nd * 4 * c16)) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->rhs, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->mid, (size_t)2 * d.nm * 3 * d.Nr * c16)) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->xtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->vtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->rtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
@@ -754,8 +794,9 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
   else cudaDeviceSynchronize();
   void* bufs[] = {ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
-                  ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
-                  ctx->AR, ctx->rhs, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->partial,
+                  ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
+                  ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
+                  ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->partial,
                   ctx->dots};
   for (void* b : bufs) cudaFree(b);
   for (int q = 0; q < 8; ++q) {
@@ -834,11 +875,13 @@ rsc_status rsc_explicit_terms(rsc_ctx* ctx, const double* U, double* N) {
   if (ctx->p.precision == RSC_MIXED) {
     CKS(stage_synth<float>(ctx, U, ctx->FC));
     CKS(stage_products_analysis<float>(ctx, false));
-    CKS(stage_rhs<float>(ctx, make_rp(ctx, 1.0, 0.0, 2), U, nullptr, reinterpret_cast<double2*>(N)));
+    CKS(stage_rhs<float>(ctx, make_rp(ctx, 1.0, 0.0, 2), U, nullptr, nullptr,
+                         reinterpret_cast<double2*>(N)));
   } else {
     CKS(stage_synth<double>(ctx, U, ctx->FC));
     CKS(stage_products_analysis<double>(ctx, false));
-    CKS(stage_rhs<double>(ctx, make_rp(ctx, 1.0, 0.0, 2), U, nullptr, reinterpret_cast<double2*>(N)));
+    CKS(stage_rhs<double>(ctx, make_rp(ctx, 1.0, 0.0, 2), U, nullptr, nullptr,
+                          reinterpret_cast<double2*>(N)));
   }
   return RSC_OK;
 }

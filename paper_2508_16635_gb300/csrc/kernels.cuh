@@ -9,7 +9,7 @@
 //   k_analysis  per (m, r): Gauss-weighted Legendre projection      [a6]
 //   k_rhs       per (l, m): radial projection, curl / double curl,
 //               mass, drift and boundary rows (FP64)               [a7]
-//   k_block_gemv, k_chain_cluster, k_temp_solve: block-tridiagonal
+//   k_block_gemv, k_chain_half, k_chain_out, k_temp_solve: block-tridiagonal
 //               Coriolis chains and per-l temperature solves (FP64) [a8]
 #pragma once
 
@@ -61,6 +61,31 @@ struct DevGeom {
   const double* EdT2;
   const double* R0T;    // [i][j]
   const double* R1T;    // [i][j]
+  // FP32 copies for the transforms of the mixed path
+  const float* EdT0f;
+  const float* EdT1f;
+  const float* EdT2f;
+  const float* R0Tf;
+  const float* R1Tf;
+  const float* rdf;
+};
+
+template <typename R> struct Tab;
+template <> struct Tab<double> {
+  static __device__ __forceinline__ const double* Ed0(const DevGeom& g) { return g.EdT0; }
+  static __device__ __forceinline__ const double* Ed1(const DevGeom& g) { return g.EdT1; }
+  static __device__ __forceinline__ const double* Ed2(const DevGeom& g) { return g.EdT2; }
+  static __device__ __forceinline__ const double* R0(const DevGeom& g) { return g.R0T; }
+  static __device__ __forceinline__ const double* R1(const DevGeom& g) { return g.R1T; }
+  static __device__ __forceinline__ const double* rd(const DevGeom& g) { return g.rd; }
+};
+template <> struct Tab<float> {
+  static __device__ __forceinline__ const float* Ed0(const DevGeom& g) { return g.EdT0f; }
+  static __device__ __forceinline__ const float* Ed1(const DevGeom& g) { return g.EdT1f; }
+  static __device__ __forceinline__ const float* Ed2(const DevGeom& g) { return g.EdT2f; }
+  static __device__ __forceinline__ const float* R0(const DevGeom& g) { return g.R0Tf; }
+  static __device__ __forceinline__ const float* R1(const DevGeom& g) { return g.R1Tf; }
+  static __device__ __forceinline__ const float* rd(const DevGeom& g) { return g.rdf; }
 };
 
 // ---------------------------------------------------------------------------
@@ -70,40 +95,46 @@ template <typename R>
 __global__ void k_radial(DevGeom g, const double2* __restrict__ x,
                          typename C2<R>::T* __restrict__ SR) {
   using V = typename C2<R>::T;
-  extern __shared__ double2 sh_coef[];  // [3][Nr]
+  extern __shared__ unsigned char sh_raw[];
+  V* sc = reinterpret_cast<V*>(sh_raw);  // [3][Nr] coefficients in precision R
   const int p = blockIdx.x;
   const int Nr = g.Nr, Nd = g.Nd;
   for (int idx = threadIdx.x; idx < 3 * Nr; idx += blockDim.x) {
     const int f = idx / Nr, k = idx % Nr;
-    sh_coef[idx] = x[((long)f * g.P + p) * Nr + k];
+    const double2 v = x[((long)f * g.P + p) * Nr + k];
+    sc[idx] = mk<R>((R)v.x, (R)v.y);
   }
   __syncthreads();
   const int i = threadIdx.x;
   if (i >= Nd) return;
-  double2 fv = {0, 0}, f1 = {0, 0}, f2 = {0, 0}, ev = {0, 0}, e1 = {0, 0}, Tv = {0, 0}, T1 = {0, 0};
+  const R* E0 = Tab<R>::Ed0(g);
+  const R* E1 = Tab<R>::Ed1(g);
+  const R* E2 = Tab<R>::Ed2(g);
+  R fvx = 0, fvy = 0, f1x = 0, f1y = 0, f2x = 0, f2y = 0, evx = 0, evy = 0, e1x = 0, e1y = 0;
+  R Tvx = 0, Tvy = 0, T1x = 0, T1y = 0;
   for (int k = 0; k < Nr; ++k) {
-    const double a0 = g.EdT0[k * Nd + i], a1 = g.EdT1[k * Nd + i], a2 = g.EdT2[k * Nd + i];
-    const double2 e = sh_coef[k], f = sh_coef[Nr + k], T = sh_coef[2 * Nr + k];
-    fv.x += a0 * f.x; fv.y += a0 * f.y;
-    f1.x += a1 * f.x; f1.y += a1 * f.y;
-    f2.x += a2 * f.x; f2.y += a2 * f.y;
-    ev.x += a0 * e.x; ev.y += a0 * e.y;
-    e1.x += a1 * e.x; e1.y += a1 * e.y;
-    Tv.x += a0 * T.x; Tv.y += a0 * T.y;
-    T1.x += a1 * T.x; T1.y += a1 * T.y;
+    const R a0 = E0[k * Nd + i], a1 = E1[k * Nd + i], a2 = E2[k * Nd + i];
+    const V e = sc[k], f = sc[Nr + k], T = sc[2 * Nr + k];
+    fvx += a0 * f.x; fvy += a0 * f.y;
+    f1x += a1 * f.x; f1y += a1 * f.y;
+    f2x += a2 * f.x; f2y += a2 * f.y;
+    evx += a0 * e.x; evy += a0 * e.y;
+    e1x += a1 * e.x; e1y += a1 * e.y;
+    Tvx += a0 * T.x; Tvy += a0 * T.y;
+    T1x += a1 * T.x; T1y += a1 * T.y;
   }
   const int l = g.pair_l[p];
-  const double lam = l * (l + 1.0);
-  const double r = g.rd[i], ir = 1.0 / r, ir2 = ir * ir;
+  const R lam = (R)(l * (l + 1.0));
+  const R ir = (R)1 / Tab<R>::rd(g)[i], ir2 = ir * ir;
   V* o = SR + ((long)p * Nd + i) * 8;
-  o[0] = mk<R>((R)(lam * fv.x * ir2), (R)(lam * fv.y * ir2));              // u_r
-  o[1] = mk<R>((R)(f1.x * ir), (R)(f1.y * ir));                            // S_u
-  o[2] = mk<R>((R)(ev.x * ir), (R)(ev.y * ir));                            // T_u
-  o[3] = mk<R>((R)(lam * ev.x * ir2), (R)(lam * ev.y * ir2));              // omega_r
-  o[4] = mk<R>((R)(e1.x * ir), (R)(e1.y * ir));                            // S_w
-  o[5] = mk<R>((R)(-(f2.x - lam * fv.x * ir2) * ir), (R)(-(f2.y - lam * fv.y * ir2) * ir));  // T_w
-  o[6] = mk<R>((R)T1.x, (R)T1.y);                                          // d_r T
-  o[7] = mk<R>((R)(Tv.x * ir), (R)(Tv.y * ir));                            // S_T
+  o[0] = mk<R>(lam * fvx * ir2, lam * fvy * ir2);                                // u_r
+  o[1] = mk<R>(f1x * ir, f1y * ir);                                              // S_u
+  o[2] = mk<R>(evx * ir, evy * ir);                                              // T_u
+  o[3] = mk<R>(lam * evx * ir2, lam * evy * ir2);                                // omega_r
+  o[4] = mk<R>(e1x * ir, e1y * ir);                                              // S_w
+  o[5] = mk<R>(-(f2x - lam * fvx * ir2) * ir, -(f2y - lam * fvy * ir2) * ir);    // T_w
+  o[6] = mk<R>(T1x, T1y);                                                        // d_r T
+  o[7] = mk<R>(Tvx * ir, Tvy * ir);                                              // S_T
 }
 
 // ---------------------------------------------------------------------------
@@ -349,14 +380,16 @@ __global__ void k_analysis(DevGeom g, DevLegendre<R> T, const typename C2<R>::T*
 // mode 1: Jacobian action (homogeneous rows), c * i m M U added when has_c
 // mode 2: explicit terms only (no mass, drift or boundary rows)
 struct RhsParams {
-  double inv_dt, C, c, Ek, Ra, r_out;
-  int mode, has_c;
+  double inv_dt, C, Ek, Ra, r_out;
+  long J;        // drift slot (Sec. 3.4), < 0 for none; c is read from u_orig[J]
+  int mode;
 };
 
 template <typename R>
 __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restrict__ AR,
                       const double2* __restrict__ x, const double2* __restrict__ U,
-                      double2* __restrict__ rhs) {
+                      const double* __restrict__ u_orig, double2* __restrict__ rhs) {
+  const int has_c = rp.J >= 0;
   extern __shared__ double2 sh2[];
   const int Nr = g.Nr, Nd = g.Nd, P = g.P;
   double2* ar = sh2;               // [Nd][4]
@@ -370,7 +403,7 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   for (int idx = threadIdx.x; idx < 3 * Nr; idx += blockDim.x) {
     const int f = idx / Nr, k = idx % Nr;
     xs[idx] = x[((long)f * P + p) * Nr + k];
-    if (rp.has_c) us[idx] = U[((long)f * P + p) * Nr + k];
+    if (has_c) us[idx] = U[((long)f * P + p) * Nr + k];
   }
   __syncthreads();
   const int j = threadIdx.x;
@@ -378,15 +411,23 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   const int l = g.pair_l[p], m = g.pair_m[p];
   const double lam = l * (l + 1.0);
   const double r = g.rc[j], ir = 1.0 / r, ir2 = ir * ir;
-  double2 Tc = {0, 0}, Qc = {0, 0}, dS = {0, 0}, Nc = {0, 0};
-  for (int i = 0; i < Nd; ++i) {
-    const double w0 = g.R0T[i * Nr + j], w1 = g.R1T[i * Nr + j] * g.rd[i];
-    const double2 q = ar[i * 4 + 0], s = ar[i * 4 + 1], t = ar[i * 4 + 2], n = ar[i * 4 + 3];
-    Qc.x += w0 * q.x; Qc.y += w0 * q.y;
-    Tc.x += w0 * t.x; Tc.y += w0 * t.y;
-    Nc.x += w0 * n.x; Nc.y += w0 * n.y;
-    dS.x += w1 * s.x; dS.y += w1 * s.y;
+  // radial projection of the analysed products (precision of the transforms)
+  R Tcx = 0, Tcy = 0, Qcx = 0, Qcy = 0, dSx = 0, dSy = 0, Ncx = 0, Ncy = 0;
+  {
+    const R* R0 = Tab<R>::R0(g);
+    const R* R1 = Tab<R>::R1(g);
+    const R* rdv = Tab<R>::rd(g);
+    for (int i = 0; i < Nd; ++i) {
+      const R w0 = R0[i * Nr + j], w1 = R1[i * Nr + j] * rdv[i];
+      const double2 q = ar[i * 4 + 0], s = ar[i * 4 + 1], t = ar[i * 4 + 2], n = ar[i * 4 + 3];
+      Qcx += w0 * (R)q.x; Qcy += w0 * (R)q.y;
+      Tcx += w0 * (R)t.x; Tcy += w0 * (R)t.y;
+      Ncx += w0 * (R)n.x; Ncy += w0 * (R)n.y;
+      dSx += w1 * (R)s.x; dSy += w1 * (R)s.y;
+    }
   }
+  const double2 Tc = make_double2(Tcx, Tcy), Qc = make_double2(Qcx, Qcy);
+  const double2 dS = make_double2(dSx, dSy), Nc = make_double2(Ncx, Ncy);
   auto mass = [&](const double2* v, double2& me, double2& mf, double2& mt) {
     double2 e0 = {0, 0}, f0 = {0, 0}, f2 = {0, 0}, t0 = {0, 0};
     for (int k = 0; k < Nr; ++k) {
@@ -420,10 +461,10 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
     out[0] = cm(Me, Ne);
     out[1] = cm(Mf, Nf);
     out[2] = cm(MT, NT);
-    if (rp.has_c) {
+    if (has_c) {
       double2 ue, uf, ut;
       mass(us, ue, uf, ut);
-      const double cmv = rp.c * m;  // c * i m * v = (-cm v.y, cm v.x)
+      const double cmv = u_orig[rp.J] * m;  // c * i m * v = (-cm v.y, cm v.x)
       out[0].x -= cmv * ue.y; out[0].y += cmv * ue.x;
       out[1].x -= cmv * uf.y; out[1].y += cmv * uf.x;
       out[2].x -= cmv * ut.y; out[2].y += cmv * ut.x;
@@ -481,108 +522,207 @@ __global__ void k_block_gemv(DevGeom g, const long* __restrict__ chain_off,
   }
 }
 
-// a8, sequential part on a thread-block cluster of CS CTAs per chain.
-//   forward  y_i = g_i - H_i y_{i-1}      backward x_i = y_i - W_i x_{i+1}
-// CTA `rank` owns rows [rank * RPC, rank * RPC + RPC), one warp per row; the
-// full vector of the previous block lives in every CTA's shared memory and
-// each new slice is broadcast through distributed shared memory, followed by
-// one cluster barrier per block.  H / W rows of the next block are loaded
-// into registers before the barrier.  The barrier is the hardware cluster
-// barrier (no spin loop); every CTA runs the same number of iterations.
+// a8, sequential part: the twisted sweeps of each chain, on thread-block
+// clusters.  Cluster (c, dir) handles chain c from the top (dir 0: blocks
+// 1..k-1, y_i = g_i - H_i y_{i-1}) or from the bottom (dir 1: blocks
+// n-2..k+1, z_i = g_i - H_i z_{i+1}), k = (n-1)/2, concurrently.  In
+// k_chain_out both clusters of a chain form the middle block
+// x_k = g_k - H_k y_{k-1} - W_k z_{k+1} and then run outward:
+// x_i = y_i - W_i x_{i+1} (top) and x_i = z_i - W_i x_{i-1} (bottom).
+//
+// CTA `rank` of a cluster of CS CTAs owns rows [rank*RPC, rank*RPC + RPC);
+// 8 lanes share one row (lane s takes columns s, s+8, ...), 4 rows per warp.
+// The vector of the previous block is held in every CTA's shared memory; each
+// new slice is broadcast through distributed shared memory, then one cluster
+// barrier (hardware, no spin loop; every CTA runs the same iterations).  The
+// next block's matrix rows and g value are loaded before the current product.
 template <int MAXQ>
-__global__ void k_chain_cluster(DevGeom g, const long* __restrict__ chain_off,
-                                const double2* __restrict__ H, const double2* __restrict__ W,
-                                double2* __restrict__ out, int CS) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ double2 sv[];  // [2][Nr] double-buffered vector
-  const int Nr = g.Nr, P = g.P;
-  const int rank = (int)cluster.block_rank();
-  const int c = blockIdx.x / CS;
-  const int a = c >> 1, cls = c & 1;
-  const int m = g.m_of[a];
-  const int p0 = g.pstart[a];
-  const int nb = g.L - m + 1;
-  const long boff = chain_off[c];
-  const long blk = (long)Nr * Nr;
-  const int RPC = blockDim.x >> 5;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int r = rank * RPC + warp;
-  const bool active = r < Nr;
-  auto rowptr = [&](int i) {
+struct ChainLane {
+  int r, s;        // row and column phase of this lane
+  bool active;
+  __device__ __forceinline__ void load(const double2* __restrict__ M, int Nr, double2 (&reg)[MAXQ]) const {
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+      const int k = s + 8 * q;
+      reg[q] = (active && k < Nr) ? M[(long)r * Nr + k] : make_double2(0, 0);
+    }
+  }
+  __device__ __forceinline__ double2 dot(const double2 (&reg)[MAXQ], const double2* v, int Nr) const {
+    double2 acc = {0, 0};
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+      const int k = s + 8 * q;
+      if (k < Nr) acc = cmac(acc, reg[q], v[k]);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    return acc;
+  }
+};
+
+struct ChainInfo {
+  int c, dir, cls, p0, nb, km, P, Nr;
+  long boff, blk;
+  __device__ __forceinline__ long row(int i) const {
     const int fld = ((i + cls) & 1) ? 1 : 0;
     return ((long)fld * P + p0 + i) * Nr;
-  };
-  auto broadcast = [&](int buf, double2 v) {
-    // lanes 0..CS-1 each write the new value into one CTA of the cluster
-    if (active && lane < CS) {
-      double2* dst = cluster.map_shared_rank(sv + buf * Nr, lane);
-      dst[r] = v;
-    }
-  };
-  double2 hc[MAXQ], hn[MAXQ];
-  // block 0: y_0 = g_0
-  double2 y0 = active ? out[rowptr(0) + r] : make_double2(0, 0);
-  broadcast(0, y0);
-#pragma unroll
-  for (int q = 0; q < MAXQ; ++q) {
-    const int k = lane + 32 * q;
-    hn[q] = (active && nb > 1 && k < Nr) ? H[(boff + 1) * blk + (long)r * Nr + k] : make_double2(0, 0);
   }
-  cluster.sync();
-  for (int i = 1; i < nb; ++i) {
+};
+
+__device__ __forceinline__ ChainInfo chain_info(const DevGeom& g, const long* chain_off, int CS) {
+  ChainInfo ci;
+  const int cl = blockIdx.x / CS;
+  ci.c = cl >> 1;
+  ci.dir = cl & 1;
+  const int a = ci.c >> 1;
+  ci.cls = ci.c & 1;
+  const int m = g.m_of[a];
+  ci.p0 = g.pstart[a];
+  ci.nb = g.L - m + 1;
+  ci.km = (ci.nb - 1) / 2;
+  ci.P = g.P;
+  ci.Nr = g.Nr;
+  ci.boff = chain_off[ci.c];
+  ci.blk = (long)g.Nr * g.Nr;
+  return ci;
+}
+
+// mid[(c * 3 + q) * Nr + k]: q = 0 the last top vector y_{k-1}, q = 1 the
+// last bottom vector z_{k+1}, q = 2 the middle g_k.  Staging them lets the
+// two clusters of a chain run their outward sweeps without touching anything
+// the other cluster reads.
+template <int MAXQ>
+__global__ void k_chain_half(DevGeom g, const long* __restrict__ chain_off,
+                             const double2* __restrict__ H, double2* __restrict__ out,
+                             double2* __restrict__ mid, int CS) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double2 sv[];  // [2][Nr]
+  const ChainInfo ci = chain_info(g, chain_off, CS);
+  const int Nr = ci.Nr;
+  const int rank = (int)cluster.block_rank();
+  const int RPC = (Nr + CS - 1) / CS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ChainLane<MAXQ> ln;
+  ln.r = rank * RPC + warp * 4 + (lane >> 3);
+  ln.s = lane & 7;
+  ln.active = (warp * 4 + (lane >> 3)) < RPC && ln.r < Nr;
+  // top: start at block 0, sweep 1 .. km-1; bottom: start at nb-1, sweep nb-2 .. km+1
+  const bool has = ci.dir == 0 ? (ci.km >= 1) : (ci.km <= ci.nb - 2);
+  const int first = ci.dir == 0 ? 0 : ci.nb - 1;
+  const int step = ci.dir == 0 ? 1 : -1;
+  const int count = ci.dir == 0 ? ci.km - 1 : ci.nb - 2 - ci.km;
+  for (int k = threadIdx.x; k < Nr; k += blockDim.x)
+    sv[k] = has ? out[ci.row(first) + k] : make_double2(0, 0);
+  double2 mc[MAXQ], mn[MAXQ];
+  double2 gn = {0, 0};
+  if (count > 0) {
+    ln.load(H + (ci.boff + first + step) * ci.blk, Nr, mn);
+    if (ln.active) gn = out[ci.row(first + step) + ln.r];
+  }
+  cluster.sync();  // every CTA of the cluster has started before any DSMEM store
+  for (int t = 1; t <= count; ++t) {
+    const int i = first + t * step;
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) hc[q] = hn[q];
-    double2 gi = active ? out[rowptr(i) + r] : make_double2(0, 0);
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-      const int k = lane + 32 * q;
-      hn[q] = (active && i + 1 < nb && k < Nr) ? H[(boff + i + 1) * blk + (long)r * Nr + k]
-                                               : make_double2(0, 0);
+    for (int q = 0; q < MAXQ; ++q) mc[q] = mn[q];
+    const double2 gc = gn;
+    if (t < count) {
+      ln.load(H + (ci.boff + i + step) * ci.blk, Nr, mn);
+      if (ln.active) gn = out[ci.row(i + step) + ln.r];
     }
-    const double2* yprev = sv + ((i - 1) & 1) * Nr;
-    double2 acc = {0, 0};
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-      const int k = lane + 32 * q;
-      if (k < Nr) acc = cmac(acc, hc[q], yprev[k]);
+    const double2 acc = ln.dot(mc, sv + ((t - 1) & 1) * Nr, Nr);
+    const double2 v = make_double2(gc.x - acc.x, gc.y - acc.y);
+    if (ln.active) {
+      if (ln.s == 0) out[ci.row(i) + ln.r] = v;
+      for (int dst = ln.s; dst < CS; dst += 8)
+        cluster.map_shared_rank(sv + (t & 1) * Nr, dst)[ln.r] = v;
     }
-    acc = warp_sum2(acc);
-    const double2 yi = make_double2(gi.x - acc.x, gi.y - acc.y);
-    if (active && lane == 0) out[rowptr(i) + r] = yi;
-    broadcast(i & 1, yi);
     cluster.sync();
   }
-  // backward sweep; the vector of block nb-1 is in buffer (nb-1) & 1
-#pragma unroll
-  for (int q = 0; q < MAXQ; ++q) {
-    const int k = lane + 32 * q;
-    hn[q] = (active && nb > 1 && k < Nr) ? W[(boff + nb - 2) * blk + (long)r * Nr + k]
-                                         : make_double2(0, 0);
+  if (rank == 0) {
+    const double2* last = sv + ((count > 0 ? count : 0) & 1) * Nr;
+    double2* dst = mid + ((long)ci.c * 3 + ci.dir) * Nr;
+    for (int k = threadIdx.x; k < Nr; k += blockDim.x) dst[k] = has ? last[k] : make_double2(0, 0);
+    if (ci.dir == 0) {
+      double2* gm = mid + ((long)ci.c * 3 + 2) * Nr;
+      for (int k = threadIdx.x; k < Nr; k += blockDim.x) gm[k] = out[ci.row(ci.km) + k];
+    }
   }
-  int cur = (nb - 1) & 1;
-  for (int i = nb - 2; i >= 0; --i) {
+}
+
+template <int MAXQ>
+__global__ void k_chain_out(DevGeom g, const long* __restrict__ chain_off,
+                            const double2* __restrict__ H, const double2* __restrict__ W,
+                            double2* __restrict__ out, const double2* __restrict__ mid, int CS) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double2 sv[];  // [2][Nr] ping-pong, [2][Nr] middle inputs
+  const ChainInfo ci = chain_info(g, chain_off, CS);
+  const int Nr = ci.Nr;
+  const int rank = (int)cluster.block_rank();
+  const int RPC = (Nr + CS - 1) / CS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ChainLane<MAXQ> ln;
+  ln.r = rank * RPC + warp * 4 + (lane >> 3);
+  ln.s = lane & 7;
+  ln.active = (warp * 4 + (lane >> 3)) < RPC && ln.r < Nr;
+  const int km = ci.km, nb = ci.nb;
+  double2* yup = sv + 2 * Nr;   // y_{k-1}
+  double2* zdn = sv + 3 * Nr;   // z_{k+1}
+  const double2* mc0 = mid + (long)ci.c * 3 * Nr;
+  for (int k = threadIdx.x; k < Nr; k += blockDim.x) {
+    yup[k] = mc0[k];
+    zdn[k] = mc0[Nr + k];
+  }
+  __syncthreads();
+  double2 mc[MAXQ], mn[MAXQ];
+  // middle block: x_k = g_k - H_k y_{k-1} - W_k z_{k+1} (both clusters, same arithmetic)
+  double2 acc = {0, 0};
+  if (km > 0) {
+    ln.load(H + (ci.boff + km) * ci.blk, Nr, mc);
+    const double2 a1 = ln.dot(mc, yup, Nr);
+    acc.x += a1.x; acc.y += a1.y;
+  }
+  if (km < nb - 1) {
+    ln.load(W + (ci.boff + km) * ci.blk, Nr, mc);
+    const double2 a2 = ln.dot(mc, zdn, Nr);
+    acc.x += a2.x; acc.y += a2.y;
+  }
+  const double2 gk = ln.active ? mc0[2 * Nr + ln.r] : make_double2(0, 0);
+  const double2 xk = make_double2(gk.x - acc.x, gk.y - acc.y);
+  const int step = ci.dir == 0 ? -1 : 1;
+  const int count = ci.dir == 0 ? km : nb - 1 - km;
+  double2 yn = {0, 0};
+  if (count > 0) {
+    ln.load(W + (ci.boff + km + step) * ci.blk, Nr, mn);
+    if (ln.active) yn = out[ci.row(km + step) + ln.r];
+  }
+  cluster.sync();  // every CTA of the cluster has started before any DSMEM store
+  if (ln.active) {
+    if (ln.s == 0 && ci.dir == 0) out[ci.row(km) + ln.r] = xk;
+    for (int dst = ln.s; dst < CS; dst += 8) cluster.map_shared_rank(sv, dst)[ln.r] = xk;
+  }
+  cluster.sync();
+  // outward: top i = km-1 .. 0 with W_i x_{i+1}; bottom i = km+1 .. nb-1 with W_i x_{i-1}
+  for (int t = 1; t <= count; ++t) {
+    const int i = km + t * step;
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) hc[q] = hn[q];
-    double2 yi = active ? out[rowptr(i) + r] : make_double2(0, 0);
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-      const int k = lane + 32 * q;
-      hn[q] = (active && i >= 1 && k < Nr) ? W[(boff + i - 1) * blk + (long)r * Nr + k]
-                                           : make_double2(0, 0);
+    for (int q = 0; q < MAXQ; ++q) mc[q] = mn[q];
+    const double2 yc = yn;
+    if (t < count) {
+      ln.load(W + (ci.boff + i + step) * ci.blk, Nr, mn);
+      if (ln.active) yn = out[ci.row(i + step) + ln.r];
     }
-    const double2* xnext = sv + cur * Nr;
-    double2 acc = {0, 0};
-#pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-      const int k = lane + 32 * q;
-      if (k < Nr) acc = cmac(acc, hc[q], xnext[k]);
+    const double2 a3 = ln.dot(mc, sv + ((t - 1) & 1) * Nr, Nr);
+    const double2 v = make_double2(yc.x - a3.x, yc.y - a3.y);
+    if (ln.active) {
+      if (ln.s == 0) out[ci.row(i) + ln.r] = v;
+      for (int dst = ln.s; dst < CS; dst += 8)
+        cluster.map_shared_rank(sv + (t & 1) * Nr, dst)[ln.r] = v;
     }
-    acc = warp_sum2(acc);
-    const double2 xi = make_double2(yi.x - acc.x, yi.y - acc.y);
-    if (active && lane == 0) out[rowptr(i) + r] = xi;
-    cur ^= 1;
-    broadcast(cur, xi);
     cluster.sync();
   }
 }

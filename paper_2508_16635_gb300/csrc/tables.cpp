@@ -402,45 +402,91 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
   f.W.assign(off * blk, cplx(0.0));
   std::vector<int> bad(nchains, 0);
 
+  // Twisted block factorisation of each chain: blocks 0..k-1 are eliminated
+  // top-down (block Thomas), blocks k+1..n-1 bottom-up, and the middle block
+  // k = (n-1)/2 closes the system, so the forward sweeps run from both ends at
+  // once and meet in the middle.  Per block three matrices are stored:
+  //   top    i < k : G = D'^-1, H = D'^-1 A, W = D'^-1 C
+  //   bottom i > k : G = E'^-1, H = E'^-1 C, W = E'^-1 A
+  //   middle i = k : G = Z, H = Z A, W = Z C,  Z = (D - A W_{k-1} - C W_{k+1})^-1
+  // with A (C) the Coriolis coupling to block i-1 (i+1).
+  auto sub_prod = [&](std::vector<cplx>& Dm, const std::vector<cplx>& X, const cplx* Y) {
+    for (int r = 0; r < Nr; ++r)
+      for (int q = 0; q < Nr; ++q) {
+        const cplx x = X[(size_t)r * Nr + q];
+        if (x == cplx(0.0)) continue;
+        for (int k = 0; k < Nr; ++k) Dm[(size_t)r * Nr + k] -= x * Y[(size_t)q * Nr + k];
+      }
+  };
   auto work = [&](int c) {
     const int a = c / 2, cls = c % 2;
     const int m = t.m_of[a];
     const int nb = d.L - m + 1;
+    const int km = (nb - 1) / 2;
+    auto field_of = [&](int i) { return ((i + cls) % 2 == 0) ? 0 : 1; };
+    auto slot = [&](std::vector<cplx>& v, int i) { return &v[(f.chain_off[c] + i) * blk]; };
     std::vector<cplx> D, A, C, tmp;
     std::vector<int> piv;
-    for (int i = 0; i < nb; ++i) {
-      const int l = m + i;
-      const int field = ((i + cls) % 2 == 0) ? 0 : 1;
-      ops.diag(field, l, m, D);
-      cplx* Gi = &f.G[(f.chain_off[c] + i) * blk];
-      cplx* Hi = &f.H[(f.chain_off[c] + i) * blk];
-      cplx* Wi = &f.W[(f.chain_off[c] + i) * blk];
-      if (i > 0) {
-        ops.coupling(field, l, m, -1, A);
-        const cplx* Wp = &f.W[(f.chain_off[c] + i - 1) * blk];
-        for (int r = 0; r < Nr; ++r)
-          for (int q = 0; q < Nr; ++q) {
-            const cplx arq = A[(size_t)r * Nr + q];
-            if (arq == cplx(0.0)) continue;
-            for (int k = 0; k < Nr; ++k) D[(size_t)r * Nr + k] -= arq * Wp[(size_t)q * Nr + k];
-          }
-      }
-      if (!lu_factor(Nr, D, piv)) {
-        bad[c] = 1;
-        return;
-      }
+    auto invert_into = [&](int i) {
       tmp.assign(blk, cplx(0.0));
       for (int r = 0; r < Nr; ++r) tmp[(size_t)r * Nr + r] = 1.0;
       lu_solve(Nr, D, piv, Nr, tmp);
-      std::copy(tmp.begin(), tmp.end(), Gi);
+      std::copy(tmp.begin(), tmp.end(), slot(f.G, i));
+    };
+    for (int i = 0; i < km; ++i) {  // top-down
+      const int l = m + i, fld = field_of(i);
+      ops.diag(fld, l, m, D);
+      if (i > 0) {
+        ops.coupling(fld, l, m, -1, A);
+        sub_prod(D, A, slot(f.W, i - 1));
+      }
+      if (!lu_factor(Nr, D, piv)) { bad[c] = 1; return; }
+      invert_into(i);
       if (i > 0) {
         lu_solve(Nr, D, piv, Nr, A);
-        std::copy(A.begin(), A.end(), Hi);
+        std::copy(A.begin(), A.end(), slot(f.H, i));
+      }
+      ops.coupling(fld, l, m, +1, C);
+      lu_solve(Nr, D, piv, Nr, C);
+      std::copy(C.begin(), C.end(), slot(f.W, i));
+    }
+    for (int i = nb - 1; i > km; --i) {  // bottom-up
+      const int l = m + i, fld = field_of(i);
+      ops.diag(fld, l, m, D);
+      if (i < nb - 1) {
+        ops.coupling(fld, l, m, +1, C);
+        sub_prod(D, C, slot(f.W, i + 1));
+      }
+      if (!lu_factor(Nr, D, piv)) { bad[c] = 1; return; }
+      invert_into(i);
+      if (i < nb - 1) {
+        lu_solve(Nr, D, piv, Nr, C);
+        std::copy(C.begin(), C.end(), slot(f.H, i));
+      }
+      ops.coupling(fld, l, m, -1, A);
+      lu_solve(Nr, D, piv, Nr, A);
+      std::copy(A.begin(), A.end(), slot(f.W, i));
+    }
+    {  // middle
+      const int i = km, l = m + i, fld = field_of(i);
+      ops.diag(fld, l, m, D);
+      if (i > 0) {
+        ops.coupling(fld, l, m, -1, A);
+        sub_prod(D, A, slot(f.W, i - 1));
       }
       if (i < nb - 1) {
-        ops.coupling(field, l, m, +1, C);
+        ops.coupling(fld, l, m, +1, C);
+        sub_prod(D, C, slot(f.W, i + 1));
+      }
+      if (!lu_factor(Nr, D, piv)) { bad[c] = 1; return; }
+      invert_into(i);
+      if (i > 0) {
+        lu_solve(Nr, D, piv, Nr, A);
+        std::copy(A.begin(), A.end(), slot(f.H, i));
+      }
+      if (i < nb - 1) {
         lu_solve(Nr, D, piv, Nr, C);
-        std::copy(C.begin(), C.end(), Wi);
+        std::copy(C.begin(), C.end(), slot(f.W, i));
       }
     }
   };
