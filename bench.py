@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--krylov", type=int, default=20, help="Jacobian actions per Newton iteration")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-rw", action="store_true", help="skip the time-to-rotating-wave run")
     return ap.parse_args()
 
 
@@ -225,6 +226,74 @@ def roofline(prof, peaks, precision):
     return out
 
 
+def newton_rw_measure(torch, RotatingShell, w, max_steps=40000, dt=2e-5):
+    """Time-to-converged rotating wave at the workload's parameters (Table 1 row 3).
+
+    The initial guess comes from time stepping an m = M_s seed (the route of
+    Sec. 2.2) until the state stops changing relative to its drift; then
+    Newton-GMRES (dt = 200, Sec. 3.3) is run from that guess on the FP64 path
+    and on the mixed path, each timed end to end.
+    """
+    M = w["Ms"]
+    sh = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
+                       precision="mixed")
+    U = sh.conductive_state() + torch.tensor(
+        si.mode_seed(w["L"], w["Ms"], w["Nr"], M, seed=4000, amp=1e-2), device="cuda")
+    x = U.view(3, sh.P, w["Nr"], 2)
+    pM = w["L"] + 1   # first pair of m = M (l = M)
+    t0 = time.perf_counter()
+    chunk = 500
+    steps = 0
+    prev_amp = None
+    while steps < max_steps:
+        sh.step(U, 0.0, dt, nsteps=chunk)
+        steps += chunk
+        amp = float(torch.linalg.norm(x[2, pM]).item())
+        if prev_amp is not None and amp > 1e-3 and abs(amp - prev_amp) < 1e-3 * amp:
+            break
+        prev_amp = amp
+    torch.cuda.synchronize()
+    t_stepping = time.perf_counter() - t0
+    a0 = x[2, pM].clone()
+    sh.step(U, 0.0, dt, nsteps=10)
+    a1 = x[2, pM]
+    k = int(torch.argmax(a0[:, 0] ** 2 + a0[:, 1] ** 2).item())
+    z0 = complex(a0[k, 0].item(), a0[k, 1].item())
+    z1 = complex(a1[k, 0].item(), a1[k, 1].item())
+    import cmath
+    C0 = -cmath.phase(z1 / z0) / (M * 10 * dt)
+    kstar = int(torch.argmax(torch.abs(x[2, pM, :, 0])).item())
+    J = (((2 * sh.P + pM) * w["Nr"] + kstar) * 2 + 1)
+    guess = U.clone()
+    sh.close()
+    out = {"time_stepping": {"steps": steps, "dt": dt, "seconds": t_stepping,
+                             "precision": "mixed"}, "C0": C0, "phase_slot": J}
+    for prec in ("fp64", "mixed"):
+        s2 = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
+                           precision=prec)
+        s2.step(s2.new_state(), 0.0, 200.0, nsteps=1)   # factorise dt = 200 outside the timing
+        Ur = guess.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        C, rep, st = s2.newton_rw(Ur, C0, J, tol=1e-10, max_newton=20, kmax=300,
+                                  gmres_tol=1e-10, dt_newton=200.0)
+        torch.cuda.synchronize()
+        out[prec] = {"seconds": time.perf_counter() - t0, "status": st, "C": C,
+                     "residual": rep["residual"], "newton_iterations": rep["iterations"],
+                     "gmres_total": rep["gmres_total"], "gmres_per_newton": rep["gmres_history"],
+                     "residual_history": rep["residual_history"]}
+        out[prec + "_U"] = Ur
+        s2.close()
+    Uf, Um = out.pop("fp64_U"), out.pop("mixed_U")
+    out["mixed_vs_fp64"] = {
+        "drift_rel_diff": abs(out["mixed"]["C"] - out["fp64"]["C"]) / abs(out["fp64"]["C"]),
+        "state_rel_diff": float((torch.linalg.norm(Um - Uf) / torch.linalg.norm(Uf)).item()),
+        "speedup": out["fp64"]["seconds"] / out["mixed"]["seconds"]}
+    out["paper_C_exact"] = 51.2817
+    out["C_vs_paper_rel"] = abs(out["fp64"]["C"] - 51.2817) / 51.2817
+    return out
+
+
 def run_gpu(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -345,6 +414,8 @@ def run_gpu(args):
             "clocks": clk.summary(),
             "wall_s_timed_region": wall,
         }
+        if not args.no_rw:
+            line["newton_rw"] = newton_rw_measure(torch, RotatingShell, w)
         if not args.no_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(K)
         print(json.dumps(line), flush=True)

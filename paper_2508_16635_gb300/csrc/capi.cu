@@ -57,6 +57,7 @@ struct rsc_ctx {
   double *d_EdT0 = nullptr, *d_EdT1 = nullptr, *d_EdT2 = nullptr, *d_R0T = nullptr, *d_R1T = nullptr;
   float *f_EdT0 = nullptr, *f_EdT1 = nullptr, *f_EdT2 = nullptr, *f_R0T = nullptr, *f_R1T = nullptr;
   float* f_rd = nullptr;
+  float *f_EcT0 = nullptr, *f_EcT2 = nullptr;
   LegDev<double> leg64;
   LegDev<float> leg32;
   // workspace (sized for FP64; the FP32 path uses the front part)
@@ -96,6 +97,8 @@ struct rsc_ctx {
     g.EdT0 = d_EdT0; g.EdT1 = d_EdT1; g.EdT2 = d_EdT2; g.R0T = d_R0T; g.R1T = d_R1T;
     g.EdT0f = f_EdT0; g.EdT1f = f_EdT1; g.EdT2f = f_EdT2; g.R0Tf = f_R0T; g.R1Tf = f_R1T;
     g.rdf = f_rd;
+    g.EcT0f = f_EcT0;
+    g.EcT2f = f_EcT2;
     return g;
   }
 };
@@ -749,6 +752,9 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
     UP(ctx->f_R0T, r0f);
     UP(ctx->f_R1T, r1f);
     UP(ctx->f_rd, rdf);
+    auto e0f = tof(e0), e2f = tof(e2);
+    UP(ctx->f_EcT0, e0f);
+    UP(ctx->f_EcT2, e2f);
   }
 #undef UP
   if ((st = upload_legendre(ctx, ctx->leg64)) != RSC_OK) return fail(st);
@@ -795,7 +801,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
   void* bufs[] = {ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
-                  ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
+                  ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
                   ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->partial,
                   ctx->dots};
   for (void* b : bufs) cudaFree(b);

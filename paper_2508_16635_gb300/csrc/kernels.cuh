@@ -68,6 +68,8 @@ struct DevGeom {
   const float* R0Tf;
   const float* R1Tf;
   const float* rdf;
+  const float* EcT0f;
+  const float* EcT2f;
 };
 
 template <typename R> struct Tab;
@@ -428,15 +430,33 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   }
   const double2 Tc = make_double2(Tcx, Tcy), Qc = make_double2(Qcx, Qcy);
   const double2 dS = make_double2(dSx, dSy), Nc = make_double2(Ncx, Ncy);
+  // M x at the collocation radius r_j.  FP64 except in Jacobian actions of the
+  // mixed path (mode 1, R = float), whose other terms are FP32-accurate anyway;
+  // the time step keeps M x^n / dt in FP64 because it dominates small-dt steps.
+  const bool low = sizeof(R) == 4 && rp.mode == 1;
   auto mass = [&](const double2* v, double2& me, double2& mf, double2& mt) {
     double2 e0 = {0, 0}, f0 = {0, 0}, f2 = {0, 0}, t0 = {0, 0};
-    for (int k = 0; k < Nr; ++k) {
-      const double c0 = g.EcT0[k * Nr + j], c2 = g.EcT2[k * Nr + j];
-      const double2 e = v[k], f = v[Nr + k], t = v[2 * Nr + k];
-      e0.x += c0 * e.x; e0.y += c0 * e.y;
-      f0.x += c0 * f.x; f0.y += c0 * f.y;
-      f2.x += c2 * f.x; f2.y += c2 * f.y;
-      t0.x += c0 * t.x; t0.y += c0 * t.y;
+    if (low) {
+      float e0x = 0, e0y = 0, f0x = 0, f0y = 0, f2x = 0, f2y = 0, t0x = 0, t0y = 0;
+      for (int k = 0; k < Nr; ++k) {
+        const float c0 = g.EcT0f[k * Nr + j], c2 = g.EcT2f[k * Nr + j];
+        const double2 e = v[k], f = v[Nr + k], t = v[2 * Nr + k];
+        e0x += c0 * (float)e.x; e0y += c0 * (float)e.y;
+        f0x += c0 * (float)f.x; f0y += c0 * (float)f.y;
+        f2x += c2 * (float)f.x; f2y += c2 * (float)f.y;
+        t0x += c0 * (float)t.x; t0y += c0 * (float)t.y;
+      }
+      e0 = make_double2(e0x, e0y); f0 = make_double2(f0x, f0y);
+      f2 = make_double2(f2x, f2y); t0 = make_double2(t0x, t0y);
+    } else {
+      for (int k = 0; k < Nr; ++k) {
+        const double c0 = g.EcT0[k * Nr + j], c2 = g.EcT2[k * Nr + j];
+        const double2 e = v[k], f = v[Nr + k], t = v[2 * Nr + k];
+        e0.x += c0 * e.x; e0.y += c0 * e.y;
+        f0.x += c0 * f.x; f0.y += c0 * f.y;
+        f2.x += c2 * f.x; f2.y += c2 * f.y;
+        t0.x += c0 * t.x; t0.y += c0 * t.y;
+      }
     }
     const double ce = lam * rp.Ek * ir2;
     me = make_double2(ce * e0.x, ce * e0.y);
@@ -513,12 +533,20 @@ __global__ void k_block_gemv(DevGeom g, const long* __restrict__ chain_off,
   const long row0 = ((long)fld * P + p) * Nr;
   for (int k = threadIdx.x; k < Nr; k += blockDim.x) sv[k] = rhs[row0 + k];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < Nr; r += nw) {
+  // 8 lanes per row (lane s takes columns s, s+8, ...): few FP64 adds in the reduction
+  const int s8 = threadIdx.x & 7;
+  const int rows_per_pass = blockDim.x >> 3;
+  for (int r = threadIdx.x >> 3; r < Nr + ((rows_per_pass - Nr % rows_per_pass) % rows_per_pass);
+       r += rows_per_pass) {
     double2 acc = {0, 0};
-    for (int k = lane; k < Nr; k += 32) acc = cmac(acc, Gi[(long)r * Nr + k], sv[k]);
-    acc = warp_sum2(acc);
-    if (lane == 0) out[row0 + r] = acc;
+    if (r < Nr)
+      for (int k = s8; k < Nr; k += 8) acc = cmac(acc, Gi[(long)r * Nr + k], sv[k]);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (r < Nr && s8 == 0) out[row0 + r] = acc;
   }
 }
 

@@ -42,6 +42,15 @@ def perturbation(L, Ms, Nr, seed, amp=1e-3, l_decay=8.0, k_decay=6.0):
     return z.reshape(-1)
 
 
+def mode_seed(L, Ms, Nr, M, seed, amp=1e-2):
+    """The perturbation recipe restricted to the azimuthal wavenumber m = M (a cos(M phi)-like
+    seed for reaching a rotating wave by time stepping, as in Sec. 2.2)."""
+    pl, pm = layout(L, Ms, Nr)
+    z = perturbation(L, Ms, Nr, seed, amp=amp).reshape(3, len(pl), Nr, 2)
+    z[:, pm != M] = 0.0
+    return z.reshape(-1)
+
+
 def random_vector(L, Ms, Nr, seed, amp=1.0):
     """A Gaussian direction vector with the same decay and zero pattern (for Jacobian tests)."""
     return perturbation(L, Ms, Nr, seed, amp=amp)
