@@ -21,7 +21,6 @@ using namespace rsc;
 
 namespace {
 
-constexpr int kTT = 4;            // latitudes per block in k_products
 constexpr int kMaxKrylov = 512;
 
 struct DevFactor {
@@ -78,6 +77,7 @@ struct rsc_ctx {
   double* h_pinned = nullptr;
   int nblk_dot = 0;
   int cluster = 8;  // CTAs per chain in the cluster chain solve
+  int rt_synth[2] = {1, 1}, rt_anal[2] = {1, 1};  // radii per block, [fp64, fp32]
   // tracing: launch counter, per-kernel CUDA-event timing and algorithmic traffic
   long launches = 0;
   bool prof_on = false;
@@ -233,10 +233,25 @@ rsc_status upload_legendre(rsc_ctx* ctx, LegDev<R>& L) {
 
 rsc_status set_smem_limits(rsc_ctx* ctx) {
   const int big = 200 * 1024;
-  CK(cudaFuncSetAttribute(k_products<double, false, kTT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(k_products<double, true, kTT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(k_products<float, false, kTT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(k_products<float, true, kTT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_products<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_products<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_products<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_products<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_radial<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_radial<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  // radii per block of the Legendre kernels: as many as the register file allows (<= 4)
+  auto rt_for = [&](const void* fn, int threads_x) {
+    cudaFuncAttributes at{};
+    if (cudaFuncGetAttributes(&at, fn) != cudaSuccess) return 1;
+    int rt = 4;
+    while (rt > 1 && ((long)rt * threads_x * std::max(at.numRegs, 1) > 65536 || rt * threads_x > 1024))
+      --rt;
+    return rt;
+  };
+  ctx->rt_synth[0] = rt_for((const void*)k_synth<double>, round32(ctx->d.nlat2));
+  ctx->rt_synth[1] = rt_for((const void*)k_synth<float>, round32(ctx->d.nlat2));
+  ctx->rt_anal[0] = rt_for((const void*)k_analysis<double>, round32(ctx->d.L + 1));
+  ctx->rt_anal[1] = rt_for((const void*)k_analysis<float>, round32(ctx->d.L + 1));
   CK(cudaFuncSetAttribute(k_synth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_synth<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_analysis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -294,7 +309,9 @@ rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
            8.0 * d.P * d.Nd * sizeof(V) + 9.0 * d.Nd * (d.K + 1) * d.nlat * sizeof(V) +
                3.0 * d.P * d.nlat2 * sizeof(R),
            52.0 * d.P * d.nlat2 * d.Nd);
-  k_synth<R><<<dim3(d.nm, d.Nd), round32(d.nlat2), (size_t)(d.L + 1) * 8 * sizeof(V), ctx->s>>>(
+  const int RT = ctx->rt_synth[sizeof(R) == 4 ? 1 : 0];
+  k_synth<R><<<dim3(d.nm, (d.Nd + RT - 1) / RT), dim3(round32(d.nlat2), RT),
+               (size_t)RT * (d.L + 1) * 8 * sizeof(V), ctx->s>>>(
       g, L.view(), reinterpret_cast<const V*>(ctx->SR), reinterpret_cast<V*>(FCout));
   CK(cudaGetLastError());
   }
@@ -309,19 +326,24 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
   const LegDev<R>& L = leg<R>(ctx);
   const int K1 = d.K + 1;
   const int NF = lin ? 18 : 9;
-  const size_t smem = (size_t)NF * kTT * K1 * sizeof(V) + 2 * (size_t)K1 * d.nphi * sizeof(R) +
-                      4 * (size_t)kTT * d.nphi * sizeof(R);
-  dim3 grid(d.Nd, (d.nlat + kTT - 1) / kTT);
+  int WPB = 8;
+  auto smem_for = [&](int wpb) {
+    return (size_t)wpb * NF * K1 * sizeof(V) + 4 * (size_t)K1 * d.nphi * sizeof(R) +
+           (size_t)wpb * 4 * d.nphi * sizeof(R);
+  };
+  while (WPB > 1 && smem_for(WPB) > 190 * 1024) WPB /= 2;
+  const size_t smem = smem_for(WPB);
+  dim3 grid(d.Nd, (d.nlat + WPB - 1) / WPB);
   const double npts = (double)d.Nd * d.nlat * d.nphi;
   {
   KSpan sp(ctx, RSC_K_PRODUCTS, (double)(NF + 4) * d.Nd * K1 * d.nlat * sizeof(V),
            npts * (4.0 * NF * d.K + (lin ? 60.0 : 30.0) + 16.0 * K1));
   if (lin)
-    k_products<R, true, kTT><<<grid, 128, smem, ctx->s>>>(
+    k_products<R, true><<<grid, 32 * WPB, smem, ctx->s>>>(
         g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC),
         reinterpret_cast<const V*>(ctx->FCU), reinterpret_cast<V*>(ctx->FA));
   else
-    k_products<R, false, kTT><<<grid, 128, smem, ctx->s>>>(
+    k_products<R, false><<<grid, 32 * WPB, smem, ctx->s>>>(
         g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC), nullptr,
         reinterpret_cast<V*>(ctx->FA));
   CK(cudaGetLastError());
@@ -331,7 +353,9 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
            4.0 * d.Nd * K1 * d.nlat * sizeof(V) + 4.0 * d.P * d.Nd * sizeof(V) +
                3.0 * d.P * d.nlat2 * sizeof(R),
            24.0 * d.P * d.nlat2 * d.Nd);
-  k_analysis<R><<<dim3(d.nm, d.Nd), round32(d.L + 1), 8 * (size_t)d.nlat2 * sizeof(V), ctx->s>>>(
+  const int RTa = ctx->rt_anal[sizeof(R) == 4 ? 1 : 0];
+  k_analysis<R><<<dim3(d.nm, (d.Nd + RTa - 1) / RTa), dim3(round32(d.L + 1), RTa),
+                  (size_t)RTa * 8 * d.nlat2 * sizeof(V), ctx->s>>>(
       g, L.view(), reinterpret_cast<const V*>(ctx->FA), reinterpret_cast<V*>(ctx->AR));
   CK(cudaGetLastError());
   }
@@ -343,11 +367,12 @@ rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const d
                      const double* u_orig, double2* out) {
   using V = typename C2<R>::T;
   const Dims& d = ctx->d;
-  const size_t smem = (4 * (size_t)d.Nd + 6 * (size_t)d.Nr) * sizeof(double2);
+  const int PPB = std::max(1, 256 / round32(d.Nr));
+  const size_t smem = (size_t)PPB * (4 * (size_t)d.Nd + 6 * (size_t)d.Nr) * sizeof(double2);
   KSpan sp(ctx, RSC_K_RHS,
            4.0 * d.P * d.Nd * sizeof(V) + (rp.J >= 0 ? 144.0 : 96.0) * d.P * d.Nr,
            d.P * (double)d.Nr * (16.0 * d.Nd + 32.0 * d.Nr));
-  k_rhs<R><<<d.P, round32(d.Nr), smem, ctx->s>>>(
+  k_rhs<R><<<(d.P + PPB - 1) / PPB, dim3(round32(d.Nr), PPB), smem, ctx->s>>>(
       ctx->geom(), rp, reinterpret_cast<const V*>(ctx->AR), reinterpret_cast<const double2*>(x),
       reinterpret_cast<const double2*>(U), u_orig, out);
   CK(cudaGetLastError());

@@ -140,29 +140,38 @@ __global__ void k_radial(DevGeom g, const double2* __restrict__ x,
 }
 
 // ---------------------------------------------------------------------------
-// a2: Legendre synthesis.  grid = (nm, Nd), block >= nlat2 (multiple of 32).
+// a2: Legendre synthesis.  grid = (nm, ceil(Nd / blockDim.y)), block =
+// (>= nlat2, multiple of 32) x RT radii; the RT threads of one latitude read
+// the same table entries, so the table traffic is served from L1.
 // FC[((fld * Nd + i) * (K+1) + a) * nlat + th], fld = ur, ut, up, wr, wt, wp, Tr, Tt, Tp.
 template <typename R>
 __global__ void k_synth(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __restrict__ SR,
                         typename C2<R>::T* __restrict__ FC) {
   using V = typename C2<R>::T;
   extern __shared__ unsigned char sh_raw[];
-  V* sh = reinterpret_cast<V*>(sh_raw);  // [nl][8]
-  const int a = blockIdx.x, i = blockIdx.y;
+  const int RT = blockDim.y;
+  V* sh = reinterpret_cast<V*>(sh_raw);  // [RT][nl][8]
+  const int a = blockIdx.x;
   const int m = g.m_of[a];
   const int p0 = g.pstart[a];
   const int nl = g.L - m + 1;
   const int Nd = g.Nd;
-  for (int idx = threadIdx.x; idx < nl * 8; idx += blockDim.x) {
-    const int q = idx >> 3, c = idx & 7;
-    sh[idx] = SR[((long)(p0 + q) * Nd + i) * 8 + c];
+  const int i0 = blockIdx.y * RT;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int idx = tid; idx < RT * nl * 8; idx += blockDim.x * RT) {
+    const int rr = idx / (nl * 8);
+    const int rem = idx - rr * nl * 8;
+    const int q = rem >> 3, c = rem & 7;
+    const int i = i0 + rr;
+    sh[idx] = (i < Nd) ? SR[((long)(p0 + q) * Nd + i) * 8 + c] : mk<R>(0, 0);
   }
   __syncthreads();
   const int t = threadIdx.x;
-  if (t >= g.nlat2) return;
+  const int i = i0 + threadIdx.y;
+  if (t >= g.nlat2 || i >= Nd) return;
+  const V* shr = sh + threadIdx.y * nl * 8;
   const long off = g.leg_off[a];
   const int n2 = g.nlat2;
-  // accumulators: [parity][...]
   R sPr[2][3], sPi[2][3];   // P-sums of ur, wr, dT
   R dRr[2][5], dRi[2][5];   // dP-sums of Su, Tu, Sw, Tw, ST
   R qRr[2][5], qRi[2][5];   // Ps-sums of Su, Tu, Sw, Tw, ST
@@ -181,7 +190,7 @@ __global__ void k_synth(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __
         const R pv = T.P[off + (long)q * n2 + t];
         const R dv = T.dP[off + (long)q * n2 + t];
         const R sv = T.Ps[off + (long)q * n2 + t];
-        const V* c = sh + q * 8;
+        const V* c = shr + q * 8;
         sPr[s][0] += pv * c[0].x; sPi[s][0] += pv * c[0].y;
         sPr[s][1] += pv * c[3].x; sPi[s][1] += pv * c[3].y;
         sPr[s][2] += pv * c[6].x; sPi[s][2] += pv * c[6].y;
@@ -233,11 +242,15 @@ __global__ void k_synth(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __
 }
 
 // ---------------------------------------------------------------------------
-// a3-a5: inverse DFT, products, forward DFT.  grid = (Nd, ceil(nlat / TT)).
+// a3-a5: inverse DFT, products, forward DFT.  grid = (Nd, ceil(nlat / WPB)),
+// block = 32 x WPB: warp w handles latitude th0 + w.  Inverse DFT: lane j
+// sums the (K+1) coefficients of each field at its longitudes (coefficients
+// are warp broadcasts, twiddles [a][j] are bank-conflict free).  Forward DFT:
+// lane a sums its wavenumber over the nphi longitudes (twiddles stored [j][a]).
 // LIN = false: F = Ek U x omega, N = U.grad T from FC.
 // LIN = true : F = Ek (U x omega_u + u x omega_U), N = U.grad tau + u.grad T
 //              with U from FCU and u from FC.
-template <typename R, bool LIN, int TT>
+template <typename R, bool LIN>
 __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
                            const typename C2<R>::T* __restrict__ FC,
                            const typename C2<R>::T* __restrict__ FCU,
@@ -246,41 +259,56 @@ __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
   constexpr int NF = LIN ? 18 : 9;
   extern __shared__ unsigned char sh_raw[];
   const int K1 = g.K + 1, nphi = g.nphi, nlat = g.nlat, Nd = g.Nd;
-  V* coef = reinterpret_cast<V*>(sh_raw);                 // [NF][TT][K1]
-  R* twc = reinterpret_cast<R*>(coef + NF * TT * K1);     // [K1][nphi]
+  const int WPB = blockDim.x >> 5;
+  V* coef = reinterpret_cast<V*>(sh_raw);                 // [WPB][NF][K1]
+  R* twc = reinterpret_cast<R*>(coef + WPB * NF * K1);    // [K1][nphi] (x2 for a > 0)
   R* tws = twc + K1 * nphi;
-  R* prod = tws + K1 * nphi;                              // [4][TT][nphi]
+  R* twcT = tws + K1 * nphi;                              // [nphi][K1] / nphi
+  R* twsT = twcT + K1 * nphi;
+  R* prod = twsT + K1 * nphi;                             // [WPB][4][nphi]
   const int i = blockIdx.x;
-  const int th0 = blockIdx.y * TT;
+  const int th0 = blockIdx.y * WPB;
+  const R inv = (R)1 / (R)nphi;
   for (int idx = threadIdx.x; idx < K1 * nphi; idx += blockDim.x) {
-    twc[idx] = T.twc[idx];
-    tws[idx] = T.tws[idx];
+    const int a = idx / nphi, j = idx - a * nphi;
+    const R f = a ? (R)2 : (R)1;
+    const R c = T.twc[idx], sn = T.tws[idx];
+    twc[idx] = f * c;
+    tws[idx] = f * sn;
+    twcT[j * K1 + a] = c * inv;
+    twsT[j * K1 + a] = sn * inv;
   }
-  for (int idx = threadIdx.x; idx < NF * TT * K1; idx += blockDim.x) {
-    const int tt = idx % TT;
-    const int rest = idx / TT;
+  for (int idx = threadIdx.x; idx < WPB * NF * K1; idx += blockDim.x) {
+    const int w = idx % WPB;              // latitude fastest: coalesced reads of FC
+    const int rest = idx / WPB;
     const int a = rest % K1;
     const int f = rest / K1;
-    const int th = th0 + tt;
+    const int th = th0 + w;
     V v = mk<R>(0, 0);
     if (th < nlat) {
       const V* src = (f < 9) ? FC : FCU;
       const int ff = (f < 9) ? f : f - 9;
       v = src[(((long)ff * Nd + i) * K1 + a) * nlat + th];
     }
-    coef[(f * TT + tt) * K1 + a] = v;
+    if (a == 0) v.y = 0;                  // the m = 0 coefficient enters with its real part
+    coef[(w * NF + f) * K1 + a] = v;
   }
   __syncthreads();
-  for (int pt = threadIdx.x; pt < TT * nphi; pt += blockDim.x) {
-    const int tt = pt / nphi, j = pt % nphi;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int th = th0 + w;
+  const V* cw = coef + w * NF * K1;
+  R* pw = prod + w * 4 * nphi;
+  for (int j = lane; j < nphi; j += 32) {
     R val[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const V* c = coef + (f * TT + tt) * K1;
-      R s = c[0].x;
-      R acc = 0;
-      for (int a = 1; a < K1; ++a) acc += c[a].x * twc[a * nphi + j] - c[a].y * tws[a * nphi + j];
-      val[f] = s + (R)2 * acc;
+    for (int f = 0; f < NF; ++f) val[f] = 0;
+    for (int a = 0; a < K1; ++a) {
+      const R c = twc[a * nphi + j], sn = tws[a * nphi + j];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const V cf = cw[f * K1 + a];
+        val[f] += cf.x * c - cf.y * sn;
+      }
     }
     R Fr, Ft, Fp, N;
     if (!LIN) {
@@ -297,32 +325,33 @@ __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
       Fp = Ek * ((U[0] * u[4] - U[1] * u[3]) + (u[0] * U[4] - u[1] * U[3]));
       N = U[0] * u[6] + U[1] * u[7] + U[2] * u[8] + u[0] * U[6] + u[1] * U[7] + u[2] * U[8];
     }
-    prod[(0 * TT + tt) * nphi + j] = Fr;
-    prod[(1 * TT + tt) * nphi + j] = Ft;
-    prod[(2 * TT + tt) * nphi + j] = Fp;
-    prod[(3 * TT + tt) * nphi + j] = N;
+    pw[0 * nphi + j] = Fr;
+    pw[1 * nphi + j] = Ft;
+    pw[2 * nphi + j] = Fp;
+    pw[3 * nphi + j] = N;
   }
-  __syncthreads();
-  const R inv = (R)1 / (R)nphi;
-  for (int idx = threadIdx.x; idx < 4 * TT * K1; idx += blockDim.x) {
-    const int tt = idx % TT;
-    const int rest = idx / TT;
-    const int a = rest % K1;
-    const int q = rest / K1;
-    const int th = th0 + tt;
-    if (th >= nlat) continue;
-    const R* pr = prod + (q * TT + tt) * nphi;
-    R sr = 0, si = 0;
+  __syncwarp();
+  if (th >= nlat) return;
+  for (int a = lane; a < K1; a += 32) {
+    R sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0};
     for (int j = 0; j < nphi; ++j) {
-      sr += pr[j] * twc[a * nphi + j];
-      si -= pr[j] * tws[a * nphi + j];
+      const R c = twcT[j * K1 + a], sn = twsT[j * K1 + a];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const R v = pw[q * nphi + j];
+        sr[q] += v * c;
+        si[q] -= v * sn;
+      }
     }
-    FA[(((long)q * Nd + i) * K1 + a) * nlat + th] = mk<R>(sr * inv, si * inv);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      FA[(((long)q * Nd + i) * K1 + a) * nlat + th] = mk<R>(sr[q], si[q]);
   }
 }
 
 // ---------------------------------------------------------------------------
-// a6: Legendre analysis.  grid = (nm, Nd), block >= L + 1 (multiple of 32).
+// a6: Legendre analysis.  grid = (nm, ceil(Nd / blockDim.y)), block =
+// (>= L + 1, multiple of 32) x RT radii.
 // AR[((p * Nd) + i) * 4 + c], c = Q (F_r), S_F, T_F, (U.grad T).
 template <typename R>
 __global__ void k_analysis(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __restrict__ FA,
@@ -330,24 +359,36 @@ __global__ void k_analysis(DevGeom g, DevLegendre<R> T, const typename C2<R>::T*
   using V = typename C2<R>::T;
   extern __shared__ unsigned char sh_raw[];
   const int n2 = g.nlat2, nlat = g.nlat, K1 = g.K + 1, Nd = g.Nd;
-  V* sym = reinterpret_cast<V*>(sh_raw);   // [4][n2]
-  V* ant = sym + 4 * n2;                   // [4][n2]
-  const int a = blockIdx.x, i = blockIdx.y;
+  const int RT = blockDim.y;
+  V* sym = reinterpret_cast<V*>(sh_raw);   // [RT][4][n2]
+  V* ant = sym + RT * 4 * n2;              // [RT][4][n2]
+  const int a = blockIdx.x;
+  const int i0 = blockIdx.y * RT;
   const int m = g.m_of[a];
   const int nl = g.L - m + 1;
-  for (int idx = threadIdx.x; idx < 4 * n2; idx += blockDim.x) {
-    const int q = idx / n2, t = idx % n2;
-    const V* base = FA + (((long)q * Nd + i) * K1 + a) * nlat;
-    const V n = base[t], s = base[nlat - 1 - t];
-    sym[idx] = mk<R>(n.x + s.x, n.y + s.y);
-    ant[idx] = mk<R>(n.x - s.x, n.y - s.y);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int idx = tid; idx < RT * 4 * n2; idx += blockDim.x * RT) {
+    const int rr = idx / (4 * n2);
+    const int rem = idx - rr * 4 * n2;
+    const int q = rem / n2, t = rem % n2;
+    const int i = i0 + rr;
+    V sv = mk<R>(0, 0), av = mk<R>(0, 0);
+    if (i < Nd) {
+      const V* base = FA + (((long)q * Nd + i) * K1 + a) * nlat;
+      const V n = base[t], s = base[nlat - 1 - t];
+      sv = mk<R>(n.x + s.x, n.y + s.y);
+      av = mk<R>(n.x - s.x, n.y - s.y);
+    }
+    sym[idx] = sv;
+    ant[idx] = av;
   }
   __syncthreads();
   const int ql = threadIdx.x;
-  if (ql >= nl) return;
+  const int i = i0 + threadIdx.y;
+  if (ql >= nl || i >= Nd) return;
   const bool even = (ql & 1) == 0;
-  const V* CP = even ? sym : ant;   // parity of P and P/sin
-  const V* CD = even ? ant : sym;   // parity of dP/dtheta
+  const V* CP = (even ? sym : ant) + threadIdx.y * 4 * n2;   // parity of P and P/sin
+  const V* CD = (even ? ant : sym) + threadIdx.y * 4 * n2;   // parity of dP/dtheta
   const long off = g.leg_off[a];
   R Qr = 0, Qi = 0, Nr_ = 0, Ni = 0, Sr = 0, Si = 0, Tr = 0, Ti = 0;
   const R mm = (R)m;
@@ -377,7 +418,7 @@ __global__ void k_analysis(DevGeom g, DevLegendre<R> T, const typename C2<R>::T*
 }
 
 // ---------------------------------------------------------------------------
-// a7: right-hand side at the collocation radii (FP64).  grid = P, block >= Nr.
+// a7: right-hand side at the collocation radii.  grid = ceil(P / PPB), block = (>= Nr) x PPB.
 // mode 0: time step (inhomogeneous T_00 wall values)
 // mode 1: Jacobian action (homogeneous rows), c * i m M U added when has_c
 // mode 2: explicit terms only (no mass, drift or boundary rows)
@@ -394,22 +435,25 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   const int has_c = rp.J >= 0;
   extern __shared__ double2 sh2[];
   const int Nr = g.Nr, Nd = g.Nd, P = g.P;
-  double2* ar = sh2;               // [Nd][4]
+  // blockDim.y pairs per block, one per thread row
+  double2* ar = sh2 + (size_t)threadIdx.y * (4 * Nd + 6 * Nr);   // [Nd][4]
   double2* xs = ar + 4 * Nd;       // [3][Nr]
   double2* us = xs + 3 * Nr;       // [3][Nr]
-  const int p = blockIdx.x;
-  for (int idx = threadIdx.x; idx < 4 * Nd; idx += blockDim.x) {
-    const auto v = AR[(long)p * Nd * 4 + idx];
-    ar[idx] = make_double2((double)v.x, (double)v.y);
-  }
-  for (int idx = threadIdx.x; idx < 3 * Nr; idx += blockDim.x) {
-    const int f = idx / Nr, k = idx % Nr;
-    xs[idx] = x[((long)f * P + p) * Nr + k];
-    if (has_c) us[idx] = U[((long)f * P + p) * Nr + k];
+  const int p = blockIdx.x * blockDim.y + threadIdx.y;
+  if (p < P) {
+    for (int idx = threadIdx.x; idx < 4 * Nd; idx += blockDim.x) {
+      const auto v = AR[(long)p * Nd * 4 + idx];
+      ar[idx] = make_double2((double)v.x, (double)v.y);
+    }
+    for (int idx = threadIdx.x; idx < 3 * Nr; idx += blockDim.x) {
+      const int f = idx / Nr, k = idx % Nr;
+      xs[idx] = x[((long)f * P + p) * Nr + k];
+      if (has_c) us[idx] = U[((long)f * P + p) * Nr + k];
+    }
   }
   __syncthreads();
   const int j = threadIdx.x;
-  if (j >= Nr) return;
+  if (j >= Nr || p >= P) return;
   const int l = g.pair_l[p], m = g.pair_m[p];
   const double lam = l * (l + 1.0);
   const double r = g.rc[j], ir = 1.0 / r, ir2 = ir * ir;
