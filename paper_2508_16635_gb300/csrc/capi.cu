@@ -311,7 +311,8 @@ rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
            52.0 * d.P * d.nlat2 * d.Nd);
   const int RT = ctx->rt_synth[sizeof(R) == 4 ? 1 : 0];
   k_synth<R><<<dim3(d.nm, (d.Nd + RT - 1) / RT), dim3(round32(d.nlat2), RT),
-               (size_t)RT * (d.L + 1) * 8 * sizeof(V), ctx->s>>>(
+               (size_t)RT * (d.L + 1) * 8 * sizeof(V) + 16 * 3 * (size_t)d.nlat2 * sizeof(R),
+               ctx->s>>>(
       g, L.view(), reinterpret_cast<const V*>(ctx->SR), reinterpret_cast<V*>(FCout));
   CK(cudaGetLastError());
   }
@@ -355,7 +356,8 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
            24.0 * d.P * d.nlat2 * d.Nd);
   const int RTa = ctx->rt_anal[sizeof(R) == 4 ? 1 : 0];
   k_analysis<R><<<dim3(d.nm, (d.Nd + RTa - 1) / RTa), dim3(round32(d.L + 1), RTa),
-                  (size_t)RTa * 8 * d.nlat2 * sizeof(V), ctx->s>>>(
+                  (size_t)RTa * 8 * d.nlat2 * sizeof(V) + 16 * 3 * (size_t)(d.L + 1) * sizeof(R),
+                  ctx->s>>>(
       g, L.view(), reinterpret_cast<const V*>(ctx->FA), reinterpret_cast<V*>(ctx->AR));
   CK(cudaGetLastError());
   }
@@ -368,7 +370,8 @@ rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const d
   using V = typename C2<R>::T;
   const Dims& d = ctx->d;
   const int PPB = std::max(1, 256 / round32(d.Nr));
-  const size_t smem = (size_t)PPB * (4 * (size_t)d.Nd + 6 * (size_t)d.Nr) * sizeof(double2);
+  const size_t smem = (size_t)PPB * (6 * (size_t)d.Nr * sizeof(double2) +
+                                     6 * (size_t)d.Nr * sizeof(float2) + 4 * (size_t)d.Nd * sizeof(V));
   KSpan sp(ctx, RSC_K_RHS,
            4.0 * d.P * d.Nd * sizeof(V) + (rp.J >= 0 ? 144.0 : 96.0) * d.P * d.Nr,
            d.P * (double)d.Nr * (16.0 * d.Nd + 32.0 * d.Nr));

@@ -165,13 +165,15 @@ __global__ void k_synth(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __
     const int i = i0 + rr;
     sh[idx] = (i < Nd) ? SR[((long)(p0 + q) * Nd + i) * 8 + c] : mk<R>(0, 0);
   }
-  __syncthreads();
   const int t = threadIdx.x;
   const int i = i0 + threadIdx.y;
-  if (t >= g.nlat2 || i >= Nd) return;
+  const bool live = t < g.nlat2 && i < Nd;
   const V* shr = sh + threadIdx.y * nl * 8;
   const long off = g.leg_off[a];
   const int n2 = g.nlat2;
+  // table chunks of QC degrees staged in shared memory by the whole block
+  constexpr int QC = 16;
+  R* tab = reinterpret_cast<R*>(sh + RT * nl * 8);   // [QC][3][n2]
   R sPr[2][3], sPi[2][3];   // P-sums of ur, wr, dT
   R dRr[2][5], dRi[2][5];   // dP-sums of Su, Tu, Sw, Tw, ST
   R qRr[2][5], qRi[2][5];   // Ps-sums of Su, Tu, Sw, Tw, ST
@@ -182,27 +184,43 @@ __global__ void k_synth(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __
 #pragma unroll
     for (int c = 0; c < 5; ++c) dRr[s][c] = dRi[s][c] = qRr[s][c] = qRi[s][c] = 0;
   }
-  for (int q0 = 0; q0 < nl; q0 += 2) {
+  const int nthr = blockDim.x * RT;
+  for (int qc = 0; qc < nl; qc += QC) {
+    const int nq = min(QC, nl - qc);
+    __syncthreads();
+    for (int idx = tid; idx < nq * 3 * n2; idx += nthr) {
+      const int q = idx / (3 * n2);
+      const int rem = idx - q * 3 * n2;
+      const int w = rem / n2, tt = rem - w * n2;
+      const R* src = (w == 0) ? T.P : (w == 1) ? T.dP : T.Ps;
+      tab[idx] = src[off + (long)(qc + q) * n2 + tt];
+    }
+    __syncthreads();
+    if (live) {
+      for (int q0 = 0; q0 < nq; q0 += 2) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const int q = q0 + s;
-      if (q < nl) {
-        const R pv = T.P[off + (long)q * n2 + t];
-        const R dv = T.dP[off + (long)q * n2 + t];
-        const R sv = T.Ps[off + (long)q * n2 + t];
-        const V* c = shr + q * 8;
-        sPr[s][0] += pv * c[0].x; sPi[s][0] += pv * c[0].y;
-        sPr[s][1] += pv * c[3].x; sPi[s][1] += pv * c[3].y;
-        sPr[s][2] += pv * c[6].x; sPi[s][2] += pv * c[6].y;
-        const int vi[5] = {1, 2, 4, 5, 7};
+        for (int s = 0; s < 2; ++s) {
+          const int q = q0 + s;   // qc is even, so the parity of q is that of l - m
+          if (q < nq) {
+            const R pv = tab[(q * 3 + 0) * n2 + t];
+            const R dv = tab[(q * 3 + 1) * n2 + t];
+            const R sv = tab[(q * 3 + 2) * n2 + t];
+            const V* c = shr + (qc + q) * 8;
+            sPr[s][0] += pv * c[0].x; sPi[s][0] += pv * c[0].y;
+            sPr[s][1] += pv * c[3].x; sPi[s][1] += pv * c[3].y;
+            sPr[s][2] += pv * c[6].x; sPi[s][2] += pv * c[6].y;
+            const int vi[5] = {1, 2, 4, 5, 7};
 #pragma unroll
-        for (int u = 0; u < 5; ++u) {
-          dRr[s][u] += dv * c[vi[u]].x; dRi[s][u] += dv * c[vi[u]].y;
-          qRr[s][u] += sv * c[vi[u]].x; qRi[s][u] += sv * c[vi[u]].y;
+            for (int u = 0; u < 5; ++u) {
+              dRr[s][u] += dv * c[vi[u]].x; dRi[s][u] += dv * c[vi[u]].y;
+              qRr[s][u] += sv * c[vi[u]].x; qRi[s][u] += sv * c[vi[u]].y;
+            }
+          }
         }
       }
     }
   }
+  if (!live) return;
   const R mm = (R)m;
   const int K1 = g.K + 1, nlat = g.nlat;
 #pragma unroll
@@ -382,32 +400,50 @@ __global__ void k_analysis(DevGeom g, DevLegendre<R> T, const typename C2<R>::T*
     sym[idx] = sv;
     ant[idx] = av;
   }
-  __syncthreads();
   const int ql = threadIdx.x;
   const int i = i0 + threadIdx.y;
-  if (ql >= nl || i >= Nd) return;
+  const bool live = ql < nl && i < Nd;
   const bool even = (ql & 1) == 0;
   const V* CP = (even ? sym : ant) + threadIdx.y * 4 * n2;   // parity of P and P/sin
   const V* CD = (even ? ant : sym) + threadIdx.y * 4 * n2;   // parity of dP/dtheta
   const long off = g.leg_off[a];
   R Qr = 0, Qi = 0, Nr_ = 0, Ni = 0, Sr = 0, Si = 0, Tr = 0, Ti = 0;
   const R mm = (R)m;
-  for (int t = 0; t < n2; ++t) {
-    const R pw = T.Pw[off + (long)t * nl + ql];
-    const R dw = T.dPw[off + (long)t * nl + ql];
-    const R sw = T.Psw[off + (long)t * nl + ql];
-    const V fr = CP[0 * n2 + t], nt = CP[3 * n2 + t];
-    const V ftD = CD[1 * n2 + t], fpD = CD[2 * n2 + t];
-    const V ftP = CP[1 * n2 + t], fpP = CP[2 * n2 + t];
-    Qr += pw * fr.x; Qi += pw * fr.y;
-    Nr_ += pw * nt.x; Ni += pw * nt.y;
-    // S = dP F_th - i m P/s F_ph ;  -i m (x + i y) = (m y, -m x)
-    Sr += dw * ftD.x + mm * sw * fpP.y;
-    Si += dw * ftD.y - mm * sw * fpP.x;
-    // T = -i m P/s F_th - dP F_ph
-    Tr += mm * sw * ftP.y - dw * fpD.x;
-    Ti += -mm * sw * ftP.x - dw * fpD.y;
+  constexpr int TC = 16;
+  R* tab = reinterpret_cast<R*>(ant + RT * 4 * n2);   // [TC][3][nl]
+  const int nthr = blockDim.x * RT;
+  for (int tc = 0; tc < n2; tc += TC) {
+    const int nt = min(TC, n2 - tc);
+    __syncthreads();
+    for (int idx = tid; idx < nt * 3 * nl; idx += nthr) {
+      const int tt = idx / (3 * nl);
+      const int rem = idx - tt * 3 * nl;
+      const int w = rem / nl, q = rem - w * nl;
+      const R* src = (w == 0) ? T.Pw : (w == 1) ? T.dPw : T.Psw;
+      tab[idx] = src[off + (long)(tc + tt) * nl + q];
+    }
+    __syncthreads();
+    if (live) {
+      for (int tt = 0; tt < nt; ++tt) {
+        const int t = tc + tt;
+        const R pw = tab[(tt * 3 + 0) * nl + ql];
+        const R dw = tab[(tt * 3 + 1) * nl + ql];
+        const R sw = tab[(tt * 3 + 2) * nl + ql];
+        const V fr = CP[0 * n2 + t], nt4 = CP[3 * n2 + t];
+        const V ftD = CD[1 * n2 + t], fpD = CD[2 * n2 + t];
+        const V ftP = CP[1 * n2 + t], fpP = CP[2 * n2 + t];
+        Qr += pw * fr.x; Qi += pw * fr.y;
+        Nr_ += pw * nt4.x; Ni += pw * nt4.y;
+        // S = dP F_th - i m P/s F_ph ;  -i m (x + i y) = (m y, -m x)
+        Sr += dw * ftD.x + mm * sw * fpP.y;
+        Si += dw * ftD.y - mm * sw * fpP.x;
+        // T = -i m P/s F_th - dP F_ph
+        Tr += mm * sw * ftP.y - dw * fpD.x;
+        Ti += -mm * sw * ftP.x - dw * fpD.y;
+      }
+    }
   }
+  if (!live) return;
   const int l = m + ql;
   const R il = (l > 0) ? (R)1 / ((R)l * (R)(l + 1)) : (R)0;
   V* o = AR + ((long)(g.pstart[a] + ql) * Nd + i) * 4;
@@ -433,22 +469,33 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
                       const double2* __restrict__ x, const double2* __restrict__ U,
                       const double* __restrict__ u_orig, double2* __restrict__ rhs) {
   const int has_c = rp.J >= 0;
+  using V = typename C2<R>::T;
   extern __shared__ double2 sh2[];
   const int Nr = g.Nr, Nd = g.Nd, P = g.P;
-  // blockDim.y pairs per block, one per thread row
-  double2* ar = sh2 + (size_t)threadIdx.y * (4 * Nd + 6 * Nr);   // [Nd][4]
-  double2* xs = ar + 4 * Nd;       // [3][Nr]
-  double2* us = xs + 3 * Nr;       // [3][Nr]
+  const bool low = sizeof(R) == 4 && rp.mode == 1;
+  // blockDim.y pairs per block, one per thread row; per pair: xs, us (double2),
+  // xf, uf (float2 copies for the low-precision mass), ar ([Nd][4] in precision R)
+  const size_t per = 6 * (size_t)Nr * sizeof(double2) + 6 * (size_t)Nr * sizeof(float2) +
+                     4 * (size_t)Nd * sizeof(V);
+  unsigned char* base = reinterpret_cast<unsigned char*>(sh2) + threadIdx.y * per;
+  double2* xs = reinterpret_cast<double2*>(base);          // [3][Nr]
+  double2* us = xs + 3 * Nr;                                // [3][Nr]
+  float2* xf = reinterpret_cast<float2*>(us + 3 * Nr);      // [3][Nr]
+  float2* uf = xf + 3 * Nr;                                 // [3][Nr]
+  V* ar = reinterpret_cast<V*>(uf + 3 * Nr);                // [Nd][4]
   const int p = blockIdx.x * blockDim.y + threadIdx.y;
   if (p < P) {
-    for (int idx = threadIdx.x; idx < 4 * Nd; idx += blockDim.x) {
-      const auto v = AR[(long)p * Nd * 4 + idx];
-      ar[idx] = make_double2((double)v.x, (double)v.y);
-    }
+    for (int idx = threadIdx.x; idx < 4 * Nd; idx += blockDim.x) ar[idx] = AR[(long)p * Nd * 4 + idx];
     for (int idx = threadIdx.x; idx < 3 * Nr; idx += blockDim.x) {
       const int f = idx / Nr, k = idx % Nr;
-      xs[idx] = x[((long)f * P + p) * Nr + k];
-      if (has_c) us[idx] = U[((long)f * P + p) * Nr + k];
+      const double2 xv = x[((long)f * P + p) * Nr + k];
+      xs[idx] = xv;
+      if (low) xf[idx] = make_float2((float)xv.x, (float)xv.y);
+      if (has_c) {
+        const double2 uv = U[((long)f * P + p) * Nr + k];
+        us[idx] = uv;
+        if (low) uf[idx] = make_float2((float)uv.x, (float)uv.y);
+      }
     }
   }
   __syncthreads();
@@ -465,11 +512,11 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
     const R* rdv = Tab<R>::rd(g);
     for (int i = 0; i < Nd; ++i) {
       const R w0 = R0[i * Nr + j], w1 = R1[i * Nr + j] * rdv[i];
-      const double2 q = ar[i * 4 + 0], s = ar[i * 4 + 1], t = ar[i * 4 + 2], n = ar[i * 4 + 3];
-      Qcx += w0 * (R)q.x; Qcy += w0 * (R)q.y;
-      Tcx += w0 * (R)t.x; Tcy += w0 * (R)t.y;
-      Ncx += w0 * (R)n.x; Ncy += w0 * (R)n.y;
-      dSx += w1 * (R)s.x; dSy += w1 * (R)s.y;
+      const V q = ar[i * 4 + 0], s = ar[i * 4 + 1], t = ar[i * 4 + 2], n = ar[i * 4 + 3];
+      Qcx += w0 * q.x; Qcy += w0 * q.y;
+      Tcx += w0 * t.x; Tcy += w0 * t.y;
+      Ncx += w0 * n.x; Ncy += w0 * n.y;
+      dSx += w1 * s.x; dSy += w1 * s.y;
     }
   }
   const double2 Tc = make_double2(Tcx, Tcy), Qc = make_double2(Qcx, Qcy);
@@ -477,18 +524,17 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   // M x at the collocation radius r_j.  FP64 except in Jacobian actions of the
   // mixed path (mode 1, R = float), whose other terms are FP32-accurate anyway;
   // the time step keeps M x^n / dt in FP64 because it dominates small-dt steps.
-  const bool low = sizeof(R) == 4 && rp.mode == 1;
-  auto mass = [&](const double2* v, double2& me, double2& mf, double2& mt) {
+  auto mass = [&](const double2* v, const float2* vf, double2& me, double2& mf, double2& mt) {
     double2 e0 = {0, 0}, f0 = {0, 0}, f2 = {0, 0}, t0 = {0, 0};
     if (low) {
       float e0x = 0, e0y = 0, f0x = 0, f0y = 0, f2x = 0, f2y = 0, t0x = 0, t0y = 0;
       for (int k = 0; k < Nr; ++k) {
         const float c0 = g.EcT0f[k * Nr + j], c2 = g.EcT2f[k * Nr + j];
-        const double2 e = v[k], f = v[Nr + k], t = v[2 * Nr + k];
-        e0x += c0 * (float)e.x; e0y += c0 * (float)e.y;
-        f0x += c0 * (float)f.x; f0y += c0 * (float)f.y;
-        f2x += c2 * (float)f.x; f2y += c2 * (float)f.y;
-        t0x += c0 * (float)t.x; t0y += c0 * (float)t.y;
+        const float2 e = vf[k], f = vf[Nr + k], t = vf[2 * Nr + k];
+        e0x += c0 * e.x; e0y += c0 * e.y;
+        f0x += c0 * f.x; f0y += c0 * f.y;
+        f2x += c2 * f.x; f2y += c2 * f.y;
+        t0x += c0 * t.x; t0y += c0 * t.y;
       }
       e0 = make_double2(e0x, e0y); f0 = make_double2(f0x, f0y);
       f2 = make_double2(f2x, f2y); t0 = make_double2(t0x, t0y);
@@ -508,7 +554,7 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
     mt = t0;
   };
   double2 Me, Mf, MT;
-  mass(xs, Me, Mf, MT);
+  mass(xs, xf, Me, Mf, MT);
   // explicit terms (curl projections and buoyancy)
   double2 Ne = make_double2(lam * ir * Tc.x, lam * ir * Tc.y);
   const double cb = lam * rp.Ra * ir / rp.r_out;
@@ -526,11 +572,11 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
     out[1] = cm(Mf, Nf);
     out[2] = cm(MT, NT);
     if (has_c) {
-      double2 ue, uf, ut;
-      mass(us, ue, uf, ut);
+      double2 ue, uf_, ut;
+      mass(us, uf, ue, uf_, ut);
       const double cmv = u_orig[rp.J] * m;  // c * i m * v = (-cm v.y, cm v.x)
       out[0].x -= cmv * ue.y; out[0].y += cmv * ue.x;
-      out[1].x -= cmv * uf.y; out[1].y += cmv * uf.x;
+      out[1].x -= cmv * uf_.y; out[1].y += cmv * uf_.x;
       out[2].x -= cmv * ut.y; out[2].y += cmv * ut.x;
     }
     // boundary rows (Sec. 3.1) and identity rows of e_00, f_00
@@ -620,12 +666,15 @@ struct ChainLane {
     }
   }
   __device__ __forceinline__ double2 dot(const double2 (&reg)[MAXQ], const double2* v, int Nr) const {
-    double2 acc = {0, 0};
+    // two independent accumulators halve the dependent FP64 chain
+    double2 a0 = {0, 0}, a1 = {0, 0};
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) {
-      const int k = s + 8 * q;
-      if (k < Nr) acc = cmac(acc, reg[q], v[k]);
+    for (int q = 0; q < MAXQ; q += 2) {
+      const int k0 = s + 8 * q, k1 = k0 + 8;
+      if (k0 < Nr) a0 = cmac(a0, reg[q], v[k0]);
+      if (q + 1 < MAXQ && k1 < Nr) a1 = cmac(a1, reg[q + 1], v[k1]);
     }
+    double2 acc = make_double2(a0.x + a1.x, a0.y + a1.y);
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) {
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
