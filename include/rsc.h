@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RSC_ABI_VERSION 1
+#define RSC_ABI_VERSION 2
 
 typedef struct rsc_ctx rsc_ctx;
 
@@ -75,6 +75,9 @@ typedef struct {
   double Ra, Ek, Pr, eta;
   int L, Ms, Nr;
   int precision;       /* rsc_precision */
+  int explicit_coriolis; /* 0: Coriolis in the implicit operator (Sec. 3.2, the method);
+                            1: Coriolis in the explicit part with a block-diagonal implicit
+                            operator (Eqs. expcor_e/f), the comparison scheme of Sec. 5   */
 } rsc_params;
 
 /* Newton-GMRES controls (Sec. 3.3: GMRES relative tolerance 1e-10, Newton
@@ -109,7 +112,8 @@ rsc_status rsc_destroy(rsc_ctx* ctx);
 
 /* Change the parameters.  A new Ra only changes the explicit part (Sec. 4.2
  * notes that Ra appears only on the right-hand side); Ek, Pr or eta drop the
- * cached factorisations; L, Ms, Nr and precision cannot change.            */
+ * cached factorisations, as does a change of explicit_coriolis; L, Ms, Nr
+ * and precision cannot change.                                              */
 rsc_status rsc_set_params(rsc_ctx* ctx, const rsc_params* params);
 
 /* Number of doubles n in a state vector, and the number of pairs P.        */

@@ -75,7 +75,12 @@ def coriolis_coefficients(l, m):
 class Shell:
     """One rotating-shell problem at fixed truncation and parameters."""
 
-    def __init__(self, L, Ms, Nr, Ek, Ra, Pr=1.0, eta=0.35):
+    def __init__(self, L, Ms, Nr, Ek, Ra, Pr=1.0, eta=0.35, coriolis="implicit"):
+        """coriolis = "implicit" (Sec. 3.2, the method) or "explicit" (Eqs. expcor_e/f:
+        Coriolis in F, block-diagonal implicit operator), the comparison of Sec. 5."""
+        if coriolis not in ("implicit", "explicit"):
+            raise ValueError(coriolis)
+        self.coriolis = coriolis
         self.L, self.Ms, self.Nr = int(L), int(Ms), int(Nr)
         self.Ek, self.Ra, self.Pr, self.eta = float(Ek), float(Ra), float(Pr), float(eta)
         self.r_in, self.r_out = basis.shell_radii(eta)
@@ -293,7 +298,7 @@ class Shell:
             return np.eye(self.Nr, dtype=np.complex128)
         D = ((1.0 / dt) * self.mass_rows(field, l, self.E, r)
              + self.diffusion_rows(field, l, self.E, r)).astype(np.complex128)
-        if field != "T":
+        if field != "T" and self.coriolis == "implicit":
             D = D + self.coriolis_diag_rows(field, l, m, self.E, r)
         self._bc_rows(D, field)
         return D
@@ -306,7 +311,9 @@ class Shell:
             D[0], D[1], D[-2], D[-1] = E0[0], E1[0], E1[-1], E0[-1]
 
     def coupling_block(self, field, l, m, side):
-        """Off-diagonal block of the `field` equation at l (BC rows zero)."""
+        """Off-diagonal block of the `field` equation at l (BC rows zero; zero when explicit)."""
+        if self.coriolis == "explicit":
+            return np.zeros((self.Nr, self.Nr), dtype=np.complex128)
         B = np.array(self.coupling_rows(l, m, side, self.E, self._rows()), dtype=np.complex128)
         for j in BC_ROWS[field]:
             B[j] = 0.0
@@ -393,12 +400,33 @@ class Shell:
     def drift(self, C):
         return (1j * C * self.pair_m)[None, :, None]
 
+    def coriolis_terms(self, x):
+        """Coriolis rows of Eqs. impcor_e_final / impcor_f_final applied to x at the
+        collocation radii: e_r.curl(2 e_z x U) and e_r.curl curl(2 e_z x U), [3, P, N_r]."""
+        out = np.zeros_like(x)
+        r = self._rows()
+        for p in range(self.P):
+            l, m = int(self.pair_l[p]), int(self.pair_m[p])
+            if l == 0:
+                continue
+            for fi, fl in enumerate(("e", "f")):
+                other = 1 - fi
+                v = self.coriolis_diag_rows(fl, l, m, self.E, r) @ x[fi, p]
+                if l - 1 >= m:
+                    v = v + self.coupling_rows(l, m, -1, self.E, r) @ x[other, p - 1]
+                if l + 1 <= self.L:
+                    v = v + self.coupling_rows(l, m, +1, self.E, r) @ x[other, p + 1]
+                out[fi, p] = v
+        return out
+
     # ---- the step and the Jacobian action ---------------------------------------
     def step(self, vec, C=0.0, dt=1e-4, nsteps=1):
         """B(U): IMEX Euler steps with the drift C d_phi in the explicit part (Eq. discrete)."""
         x = self.to_complex(vec)
         for _ in range(nsteps):
             rhs = (1.0 / dt + self.drift(C)) * self.mass(x) + self.explicit_terms(x)
+            if self.coriolis == "explicit":
+                rhs = rhs - self.coriolis_terms(x)
             x = self.solve(self.apply_rows(rhs, homogeneous=False), dt)
         return self.to_real(x)
 
@@ -417,6 +445,8 @@ class Shell:
         rhs = ((1.0 / dt + self.drift(C)) * self.mass(x)
                + self.explicit_terms_linear(U, x, gU)
                + c * (1j * self.pair_m)[None, :, None] * self.mass(U))
+        if self.coriolis == "explicit":
+            rhs = rhs - self.coriolis_terms(x)
         y = self.solve(self.apply_rows(rhs, homogeneous=True), dt)
         return self.to_real(y) - u
 

@@ -53,6 +53,7 @@ struct rsc_ctx {
   int *d_m_of = nullptr, *d_pstart = nullptr, *d_pair_l = nullptr, *d_pair_m = nullptr;
   long* d_leg_off = nullptr;
   double *d_rc = nullptr, *d_rd = nullptr, *d_EcT0 = nullptr, *d_EcT2 = nullptr;
+  double* d_EcT1 = nullptr;
   double *d_EdT0 = nullptr, *d_EdT1 = nullptr, *d_EdT2 = nullptr, *d_R0T = nullptr, *d_R1T = nullptr;
   float *f_EdT0 = nullptr, *f_EdT1 = nullptr, *f_EdT2 = nullptr, *f_R0T = nullptr, *f_R1T = nullptr;
   float* f_rd = nullptr;
@@ -94,6 +95,7 @@ struct rsc_ctx {
     g.nphi = d.nphi; g.nm = d.nm; g.K = d.K; g.P = d.P; g.r_in = d.r_in; g.r_out = d.r_out;
     g.m_of = d_m_of; g.pstart = d_pstart; g.leg_off = d_leg_off; g.pair_l = d_pair_l;
     g.pair_m = d_pair_m; g.rc = d_rc; g.rd = d_rd; g.EcT0 = d_EcT0; g.EcT2 = d_EcT2;
+    g.EcT1 = d_EcT1;
     g.EdT0 = d_EdT0; g.EdT1 = d_EdT1; g.EdT2 = d_EdT2; g.R0T = d_R0T; g.R1T = d_R1T;
     g.EdT0f = f_EdT0; g.EdT1f = f_EdT1; g.EdT2f = f_EdT2; g.R0Tf = f_R0T; g.R1Tf = f_R1T;
     g.rdf = f_rd;
@@ -196,6 +198,7 @@ rsc_status check_params(const rsc_params* p) {
   if (!(p->eta > 0 && p->eta < 1) || !(p->Ek > 0) || !(p->Pr > 0) || !std::isfinite(p->Ra))
     return RSC_EINVAL;
   if (p->precision != RSC_FP64 && p->precision != RSC_MIXED) return RSC_EINVAL;
+  if (p->explicit_coriolis != 0 && p->explicit_coriolis != 1) return RSC_EINVAL;
   return RSC_OK;
 }
 
@@ -370,7 +373,7 @@ rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const d
   using V = typename C2<R>::T;
   const Dims& d = ctx->d;
   const int PPB = std::max(1, 256 / round32(d.Nr));
-  const size_t smem = (size_t)PPB * (6 * (size_t)d.Nr * sizeof(double2) +
+  const size_t smem = (size_t)PPB * (10 * (size_t)d.Nr * sizeof(double2) +
                                      6 * (size_t)d.Nr * sizeof(float2) + 4 * (size_t)d.Nd * sizeof(V));
   KSpan sp(ctx, RSC_K_RHS,
            4.0 * d.P * d.Nd * sizeof(V) + (rp.J >= 0 ? 144.0 : 96.0) * d.P * d.Nr,
@@ -432,13 +435,13 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
         ctx->geom(), f->chain_off, f->G, ctx->rhs, reinterpret_cast<double2*>(out));
     CK(cudaGetLastError());
   }
-  {
+  if (!ctx->p.explicit_coriolis) {
     // forward half-sweeps read H of about half the blocks each way, outward sweeps W
     KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
     CK(launch_chain(ctx, f, out, false));
   }
-  {
+  if (!ctx->p.explicit_coriolis) {
     KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
     CK(launch_chain(ctx, f, out, true));
@@ -509,6 +512,7 @@ RhsParams make_rp(rsc_ctx* ctx, double dt, double C, int mode) {
   rp.Ra = ctx->p.Ra;
   rp.r_out = ctx->d.r_out;
   rp.mode = mode;
+  rp.explicit_coriolis = ctx->p.explicit_coriolis ? 1 : 0;
   return rp;
 }
 
@@ -762,6 +766,8 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   UP(ctx->d_rd, t.rd);
   {
     auto e0 = transpose(t.Ec[0], d.Nr, d.Nr), e2 = transpose(t.Ec[2], d.Nr, d.Nr);
+    auto e1 = transpose(t.Ec[1], d.Nr, d.Nr);
+    UP(ctx->d_EcT1, e1);
     auto d0 = transpose(t.Ed[0], d.Nd, d.Nr), d1 = transpose(t.Ed[1], d.Nd, d.Nr),
          d2 = transpose(t.Ed[2], d.Nd, d.Nr);
     auto r0 = transpose(t.R0, d.Nr, d.Nd), r1 = transpose(t.R1, d.Nr, d.Nd);
@@ -826,7 +832,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
   if (!ctx) return RSC_EINVAL;
   if (ctx->s) cudaStreamSynchronize(ctx->s);
   else cudaDeviceSynchronize();
-  void* bufs[] = {ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
+  void* bufs[] = {ctx->d_EcT1, ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
@@ -853,7 +859,9 @@ rsc_status rsc_set_params(rsc_ctx* ctx, const rsc_params* params) {
     ctx->err = "L, Ms, Nr and precision are fixed for a context";
     return RSC_EINVAL;
   }
-  const bool refactor = params->Ek != ctx->p.Ek || params->Pr != ctx->p.Pr || params->eta != ctx->p.eta;
+  const bool refactor = params->Ek != ctx->p.Ek || params->Pr != ctx->p.Pr ||
+                        params->eta != ctx->p.eta ||
+                        params->explicit_coriolis != ctx->p.explicit_coriolis;
   if (params->eta != ctx->p.eta) {
     ctx->err = "eta is fixed for a context (it defines the radial grid)";
     return RSC_EINVAL;

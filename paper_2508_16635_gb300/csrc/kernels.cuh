@@ -56,6 +56,7 @@ struct DevGeom {
   const double* rd;     // [Nd]
   const double* EcT0;   // [k][j] T_k(r_j)
   const double* EcT2;   // [k][j] d2 T_k / dr2 (r_j)
+  const double* EcT1;   // [k][j] d T_k / dr (r_j)
   const double* EdT0;   // [k][i] at the de-aliased radii
   const double* EdT1;
   const double* EdT2;
@@ -462,6 +463,7 @@ struct RhsParams {
   double inv_dt, C, Ek, Ra, r_out;
   long J;        // drift slot (Sec. 3.4), < 0 for none; c is read from u_orig[J]
   int mode;
+  int explicit_coriolis;  // subtract the Coriolis rows of x (Eqs. expcor_e/f) in modes 0, 1
 };
 
 template <typename R>
@@ -475,7 +477,7 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   const bool low = sizeof(R) == 4 && rp.mode == 1;
   // blockDim.y pairs per block, one per thread row; per pair: xs, us (double2),
   // xf, uf (float2 copies for the low-precision mass), ar ([Nd][4] in precision R)
-  const size_t per = 6 * (size_t)Nr * sizeof(double2) + 6 * (size_t)Nr * sizeof(float2) +
+  const size_t per = 10 * (size_t)Nr * sizeof(double2) + 6 * (size_t)Nr * sizeof(float2) +
                      4 * (size_t)Nd * sizeof(V);
   unsigned char* base = reinterpret_cast<unsigned char*>(sh2) + threadIdx.y * per;
   double2* xs = reinterpret_cast<double2*>(base);          // [3][Nr]
@@ -483,7 +485,9 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   float2* xf = reinterpret_cast<float2*>(us + 3 * Nr);      // [3][Nr]
   float2* uf = xf + 3 * Nr;                                 // [3][Nr]
   V* ar = reinterpret_cast<V*>(uf + 3 * Nr);                // [Nd][4]
+  double2* nb = reinterpret_cast<double2*>(ar + 4 * Nd);    // [4][Nr]: f_{l-1}, f_{l+1}, e_{l-1}, e_{l+1}
   const int p = blockIdx.x * blockDim.y + threadIdx.y;
+  const bool coriolis_rhs = rp.explicit_coriolis && rp.mode != 2;
   if (p < P) {
     for (int idx = threadIdx.x; idx < 4 * Nd; idx += blockDim.x) ar[idx] = AR[(long)p * Nd * 4 + idx];
     for (int idx = threadIdx.x; idx < 3 * Nr; idx += blockDim.x) {
@@ -495,6 +499,18 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
         const double2 uv = U[((long)f * P + p) * Nr + k];
         us[idx] = uv;
         if (low) uf[idx] = make_float2((float)uv.x, (float)uv.y);
+      }
+    }
+    if (coriolis_rhs) {
+      const int lp = g.pair_l[p], mp = g.pair_m[p];
+      for (int idx = threadIdx.x; idx < 4 * Nr; idx += blockDim.x) {
+        const int w = idx / Nr, k = idx % Nr;
+        const int fld = (w < 2) ? 1 : 0;         // f neighbours for the e rows and vice versa
+        const int side = (w & 1) ? 1 : -1;
+        const int l2 = lp + side;
+        double2 v = make_double2(0, 0);
+        if (lp > 0 && l2 >= mp && l2 <= g.L) v = x[((long)fld * P + p + side) * Nr + k];
+        nb[idx] = v;
       }
     }
   }
@@ -524,6 +540,7 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   // M x at the collocation radius r_j.  FP64 except in Jacobian actions of the
   // mixed path (mode 1, R = float), whose other terms are FP32-accurate anyway;
   // the time step keeps M x^n / dt in FP64 because it dominates small-dt steps.
+  double2 e0v = {0, 0}, f0v = {0, 0}, f2v = {0, 0};   // raw e, f, d2f of the last mass() call
   auto mass = [&](const double2* v, const float2* vf, double2& me, double2& mf, double2& mt) {
     double2 e0 = {0, 0}, f0 = {0, 0}, f2 = {0, 0}, t0 = {0, 0};
     if (low) {
@@ -548,6 +565,9 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
         t0.x += c0 * t.x; t0.y += c0 * t.y;
       }
     }
+    e0v = e0;
+    f0v = f0;
+    f2v = f2;
     const double ce = lam * rp.Ek * ir2;
     me = make_double2(ce * e0.x, ce * e0.y);
     mf = make_double2(-ce * (f2.x - lam * ir2 * f0.x), -ce * (f2.y - lam * ir2 * f0.y));
@@ -555,6 +575,33 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   };
   double2 Me, Mf, MT;
   mass(xs, xf, Me, Mf, MT);
+  // explicit Coriolis rows (Eqs. impcor_e_final / impcor_f_final applied to x)
+  double2 Ce = {0, 0}, Cf = {0, 0};
+  if (coriolis_rhs && l > 0) {
+    double2 v0[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}}, v1[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int k = 0; k < Nr; ++k) {
+      const double c0 = g.EcT0[k * Nr + j], c1 = g.EcT1[k * Nr + j];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const double2 a = nb[w * Nr + k];
+        v0[w].x += c0 * a.x; v0[w].y += c0 * a.y;
+        v1[w].x += c1 * a.x; v1[w].y += c1 * a.y;
+      }
+    }
+    const double lm1 = (double)l * l - 1.0;
+    const double alpha = (l - 1 >= m) ? lm1 * sqrt(((double)l * l - (double)m * m) / (4.0 * l * l - 1.0)) : 0.0;
+    const double l1 = l + 1.0;
+    const double beta = (l + 1 <= g.L) ? l * (l + 2.0) * sqrt((l1 * l1 - (double)m * m) / (4.0 * l1 * l1 - 1.0)) : 0.0;
+    const double ca = 2.0 * ir2 * alpha, cb2 = 2.0 * ir2 * beta;
+    const double am = (double)l * ir, bp = -(l + 1.0) * ir;
+    // -2 i m / r^2 e  and  +2 i m / r^2 (f'' - l(l+1)/r^2 f)
+    const double dm = 2.0 * m * ir2;
+    const double2 Lf = make_double2(f2v.x - lam * ir2 * f0v.x, f2v.y - lam * ir2 * f0v.y);
+    Ce.x = dm * e0v.y + ca * (am * v0[0].x - v1[0].x) + cb2 * (bp * v0[1].x - v1[1].x);
+    Ce.y = -dm * e0v.x + ca * (am * v0[0].y - v1[0].y) + cb2 * (bp * v0[1].y - v1[1].y);
+    Cf.x = -dm * Lf.y + ca * (am * v0[2].x - v1[2].x) + cb2 * (bp * v0[3].x - v1[3].x);
+    Cf.y = dm * Lf.x + ca * (am * v0[2].y - v1[2].y) + cb2 * (bp * v0[3].y - v1[3].y);
+  }
   // explicit terms (curl projections and buoyancy)
   double2 Ne = make_double2(lam * ir * Tc.x, lam * ir * Tc.y);
   const double cb = lam * rp.Ra * ir / rp.r_out;
@@ -571,6 +618,8 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
     out[0] = cm(Me, Ne);
     out[1] = cm(Mf, Nf);
     out[2] = cm(MT, NT);
+    out[0].x -= Ce.x; out[0].y -= Ce.y;
+    out[1].x -= Cf.x; out[1].y -= Cf.y;
     if (has_c) {
       double2 ue, uf_, ut;
       mass(us, uf, ue, uf_, ut);

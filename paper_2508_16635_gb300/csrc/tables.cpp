@@ -247,6 +247,7 @@ struct Ops {
   const HostTables& t;
   double Ek, Pr, inv_dt;
   int Nr;
+  bool explicit_coriolis;  // Coriolis kept out of the implicit operator (Eqs. expcor_e/f)
   double E(int o, int j, int k) const { return t.Ec[o][(size_t)j * Nr + k]; }
 
   // field 0 = e, 1 = f
@@ -265,12 +266,14 @@ struct Ops {
         cplx v;
         if (field == 0) {
           const double Ll = e2 - lam / r2 * e0;
-          v = cplx(lam * Ek / r2 * inv_dt * e0 - lam * Ek / r2 * Ll, -2.0 * m / r2 * e0);
+          v = cplx(lam * Ek / r2 * inv_dt * e0 - lam * Ek / r2 * Ll,
+                   explicit_coriolis ? 0.0 : -2.0 * m / r2 * e0);
         } else {
           const double Ll = e2 - lam / r2 * e0;
           const double LL = e4 - 2.0 * lam / r2 * e2 + 4.0 * lam / (r2 * r) * e1 +
                             (lam * lam - 6.0 * lam) / (r2 * r2) * e0;
-          v = cplx(-lam * Ek / r2 * inv_dt * Ll + lam * Ek / r2 * LL, 2.0 * m / r2 * Ll);
+          v = cplx(-lam * Ek / r2 * inv_dt * Ll + lam * Ek / r2 * LL,
+                   explicit_coriolis ? 0.0 : 2.0 * m / r2 * Ll);
         }
         D[(size_t)j * Nr + k] = v;
       }
@@ -293,7 +296,7 @@ struct Ops {
   // Coupling of the equation at l to the other potential at l + side (Coriolis).
   void coupling(int field, int l, int m, int side, std::vector<cplx>& B) const {
     B.assign((size_t)Nr * Nr, cplx(0.0));
-    if (l == 0) return;
+    if (l == 0 || explicit_coriolis) return;
     double coef;
     if (side < 0) {
       coef = ((double)l * l - 1.0) * std::sqrt(((double)l * l - (double)m * m) / (4.0 * l * l - 1.0));
@@ -387,7 +390,7 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
                  HostFactor& f) {
   const int Nr = d.Nr;
   const size_t blk = (size_t)Nr * Nr;
-  Ops ops{d, t, p.Ek, p.Pr, std::isfinite(dt) ? 1.0 / dt : 0.0, Nr};
+  Ops ops{d, t, p.Ek, p.Pr, std::isfinite(dt) ? 1.0 / dt : 0.0, Nr, p.explicit_coriolis != 0};
   f.dt = dt;
   const int nchains = 2 * d.nm;
   f.chain_off.resize(nchains + 1);
@@ -517,7 +520,7 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
 void conductive_T00(const rsc_params& p, const Dims& d, const HostTables& t,
                     std::vector<double>& coef) {
   const int Nr = d.Nr;
-  Ops ops{d, t, p.Ek, p.Pr, 0.0, Nr};
+  Ops ops{d, t, p.Ek, p.Pr, 0.0, Nr, false};
   std::vector<double> D;
   ops.temp(0, D);
   std::vector<int> piv;

@@ -31,7 +31,8 @@ KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis",
 class Params(ctypes.Structure):
     _fields_ = [("Ra", ctypes.c_double), ("Ek", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("eta", ctypes.c_double), ("L", ctypes.c_int), ("Ms", ctypes.c_int),
-                ("Nr", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("Nr", ctypes.c_int), ("precision", ctypes.c_int),
+                ("explicit_coriolis", ctypes.c_int)]
 
 
 class NewtonOpts(ctypes.Structure):
@@ -112,15 +113,19 @@ def _ptr(t):
 class RotatingShell:
     """One problem on the GPU: parameters, truncation, tables and factorisations."""
 
-    def __init__(self, L, Ms, Nr, Ek, Ra, Pr=1.0, eta=0.35, precision="fp64", device=None):
+    def __init__(self, L, Ms, Nr, Ek, Ra, Pr=1.0, eta=0.35, precision="fp64", device=None,
+                 coriolis="implicit"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("RotatingShell needs a CUDA device")
         self.torch = torch
         self.device = torch.device(device if device is not None else "cuda")
         self.lib = load_library()
+        if coriolis not in ("implicit", "explicit"):
+            raise ValueError(coriolis)
         self.params = Params(Ra, Ek, Pr, eta, L, Ms, Nr,
-                             RSC_MIXED if precision == "mixed" else RSC_FP64)
+                             RSC_MIXED if precision == "mixed" else RSC_FP64,
+                             1 if coriolis == "explicit" else 0)
         self.L, self.Ms, self.Nr = L, Ms, Nr
         self._ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):

@@ -191,3 +191,50 @@ def test_newton_rotating_wave_parity(torch, precision):
         assert _rel(Ug, Uo) < 1e-9
         assert abs(C - Co) < 1e-8 * abs(Co)
     gpu.close()
+
+
+# ---- explicit-Coriolis variant (Eqs. expcor_e/f), the comparison scheme of Sec. 5 ----------
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES[:2] + CASES[3:])
+def test_explicit_coriolis_step_and_jacobian_parity(torch, name, L, Ms, Nr, Ek, Ra):
+    from paper_2508_16635_gb300 import RotatingShell
+    make = lambda: Shell(L, Ms, Nr, Ek, Ra, coriolis="explicit")
+    s = make()
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=26, amp=1e-2)
+    want, spread = _oracle_spread(make, lambda so: so.step(x, 0.7, 1e-3, nsteps=2))
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, coriolis="explicit")
+    U = torch.tensor(x, device="cuda")
+    gpu.step(U, 0.7, 1e-3, nsteps=2)
+    errs = _rel_fields(s, U.cpu().numpy(), want)
+    tol = _tolerances(spread)
+    assert all(e < t for e, t in zip(errs, tol)), (errs, tol, spread)
+    u = si.random_vector(L, Ms, Nr, seed=27)
+    J = s.real_index("T", Ms, Ms, 1, 1)
+    u[J] = -0.4
+    want, spread = _oracle_spread(make, lambda so: so.jvp(x, 0.7, J, u, 200.0))
+    got = gpu.apply_jacobian(torch.tensor(x, device="cuda"), 0.7, J,
+                             torch.tensor(u, device="cuda"), 200.0).cpu().numpy()
+    errs = _rel_fields(s, got, want)
+    tol = [max(1e-10, t) for t in _tolerances(spread)]
+    assert all(e < t for e, t in zip(errs, tol)), (errs, tol, spread)
+    gpu.close()
+
+
+def test_explicit_and_implicit_coriolis_reach_the_same_wave_on_the_gpu(torch):
+    """Eq. finalrhs: the root of B - I does not depend on how L is split, so both schemes
+    converge to the same rotating wave; the implicit one in fewer Jacobian actions (Sec. 5)."""
+    from paper_2508_16635_gb300 import RotatingShell
+    L, Ms, Nr, Ek, Ra = 23, 4, 20, 1e-3, 120.0
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    U0, C0, J = _rw_initial_guess(s, 4)
+    res = {}
+    for mode in ("implicit", "explicit"):
+        gpu = RotatingShell(L, Ms, Nr, Ek, Ra, coriolis=mode)
+        U = torch.tensor(U0, device="cuda")
+        C, rep, st = gpu.newton_rw(U, C0, J, tol=1e-11, max_newton=14, kmax=400, gmres_tol=1e-10)
+        assert st == 0, (mode, rep)
+        res[mode] = (U.cpu().numpy(), C, rep["gmres_total"])
+        gpu.close()
+    Ui, Ci, gi = res["implicit"]
+    Ue, Ce, ge = res["explicit"]
+    assert _rel(Ue, Ui) < 1e-8 and abs(Ce - Ci) < 1e-8 * abs(Ci)
+    assert ge > gi
