@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--krylov", type=int, default=20, help="Jacobian actions per Newton iteration")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-rw", action="store_true", help="skip the time-to-rotating-wave run")
+    ap.add_argument("--coriolis-study", action="store_true",
+                    help="only run the implicit vs explicit Coriolis comparison (Sec. 5)")
     return ap.parse_args()
 
 
@@ -294,6 +296,57 @@ def newton_rw_measure(torch, RotatingShell, w, max_steps=40000, dt=2e-5):
     return out
 
 
+def coriolis_study(torch, RotatingShell):
+    """Sec. 5 comparison: Jacobian actions needed by Newton-GMRES for the same rotating wave
+    with implicit Coriolis (the method) and explicit Coriolis (Eqs. expcor_e/f).
+
+    Cases: RW4 at Ek = 1e-3, Ra = 120 (L = 31, N_r = 24) and the RW12 workload at Ek = 1e-5.
+    Each case time-steps an m = M seed to the wave's basin, then solves with both schemes
+    from the same guess (FP64 path, GMRES relative 1e-10, Newton 1e-10).
+    """
+    cases = [dict(name="RW4 Ek=1e-3 Ra=120 L=31 Nr=24", L=31, Ms=4, Nr=24, Ek=1e-3, Ra=120.0,
+                  dt=2e-3, steps=2000),
+             dict(name=WORKLOAD["name"], L=127, Ms=12, Nr=64, Ek=1e-5, Ra=140.0, dt=2e-5,
+                  steps=8500)]
+    out = []
+    import cmath
+    for c in cases:
+        sh = RotatingShell(c["L"], c["Ms"], c["Nr"], c["Ek"], c["Ra"], precision="mixed")
+        M = c["Ms"]
+        U = sh.conductive_state() + torch.tensor(
+            si.mode_seed(c["L"], c["Ms"], c["Nr"], M, seed=4000, amp=1e-2), device="cuda")
+        sh.step(U, 0.0, c["dt"], nsteps=c["steps"])
+        x = U.view(3, sh.P, c["Nr"], 2)
+        pM = c["L"] + 1
+        a0 = x[2, pM].clone()
+        sh.step(U, 0.0, c["dt"], nsteps=10)
+        a1 = x[2, pM]
+        k = int(torch.argmax(a0[:, 0] ** 2 + a0[:, 1] ** 2).item())
+        C0 = -cmath.phase(complex(a1[k, 0].item(), a1[k, 1].item()) /
+                          complex(a0[k, 0].item(), a0[k, 1].item())) / (M * 10 * c["dt"])
+        kstar = int(torch.argmax(torch.abs(x[2, pM, :, 0])).item())
+        J = (((2 * sh.P + pM) * c["Nr"] + kstar) * 2 + 1)
+        guess = U.clone()
+        sh.close()
+        row = {"case": c["name"]}
+        for mode in ("implicit", "explicit"):
+            s2 = RotatingShell(c["L"], c["Ms"], c["Nr"], c["Ek"], c["Ra"], coriolis=mode)
+            Ur = guess.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            C, rep, st = s2.newton_rw(Ur, C0, J, tol=1e-10, max_newton=8, kmax=2048,
+                                      gmres_tol=1e-10, dt_newton=200.0)
+            torch.cuda.synchronize()
+            row[mode] = {"status": st, "seconds": time.perf_counter() - t0, "C": C,
+                         "newton_iterations": rep["iterations"], "jacobian_actions": rep["gmres_total"],
+                         "gmres_per_newton": rep["gmres_history"], "residual": rep["residual"]}
+            s2.close()
+        row["actions_explicit_over_implicit"] = (row["explicit"]["jacobian_actions"] /
+                                                 max(1, row["implicit"]["jacobian_actions"]))
+        out.append(row)
+    return out
+
+
 def run_gpu(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -314,6 +367,10 @@ def run_gpu(args):
     from paper_2508_16635_gb300.rsc import KERNELS
 
     w = WORKLOAD
+    if args.coriolis_study:
+        if rank == 0:
+            print(json.dumps({"coriolis_study": coriolis_study(torch, RotatingShell)}), flush=True)
+        return 0
     peaks = measured_peaks(torch)
     sh = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
                        precision=args.precision)

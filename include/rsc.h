@@ -85,7 +85,7 @@ typedef struct {
 typedef struct {
   double tol;          /* stop when ||B(U) - U||_2 < tol                      */
   int max_newton;      /* Newton iteration cap                                */
-  int kmax;            /* GMRES iteration cap (no restart), <= 512            */
+  int kmax;            /* GMRES iteration cap (no restart), <= 2048           */
   double gmres_tol;    /* relative GMRES tolerance                            */
   double dt_newton;    /* pseudo-timestep of the Stokes preconditioner        */
 } rsc_newton_opts;

@@ -21,7 +21,7 @@ using namespace rsc;
 
 namespace {
 
-constexpr int kMaxKrylov = 512;
+constexpr int kMaxKrylov = 2048;
 
 struct DevFactor {
   double dt = std::nan("");
