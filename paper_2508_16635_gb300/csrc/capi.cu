@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "legendre_tc.cuh"
 #include "rsc_internal.h"
 
 using namespace rsc;
@@ -79,6 +80,13 @@ struct rsc_ctx {
   int nblk_dot = 0;
   int cluster = 8;  // CTAs per chain in the cluster chain solve
   int rt_synth[2] = {1, 1}, rt_anal[2] = {1, 1};  // radii per block, [fp64, fp32]
+  // tensor-core Legendre synthesis (FP32 path): A tiles, offsets, padded K, status word
+  float* tc_tiles = nullptr;
+  long* tc_off = nullptr;
+  int* tc_kpad = nullptr;
+  int tc_nmt = 1;
+  size_t tc_smem = 0;
+  int* d_status = nullptr;
   // tracing: launch counter, per-kernel CUDA-event timing and algorithmic traffic
   long launches = 0;
   bool prof_on = false;
@@ -234,6 +242,61 @@ rsc_status upload_legendre(rsc_ctx* ctx, LegDev<R>& L) {
   return RSC_OK;
 }
 
+// A tiles of the tensor-core synthesis: for each (m, parity s, table w, latitude tile),
+// 128 latitudes x Kpad degrees of the class in the K-major core-matrix layout,
+// TF32 hi part then lo part.
+rsc_status build_tc_tables(rsc_ctx* ctx) {
+  const Dims& d = ctx->d;
+  const HostTables& t = ctx->t;
+  const int nmt = (d.nlat2 + 127) / 128;
+  std::vector<int> kpad(d.nm);
+  std::vector<long> off((size_t)d.nm * 2 * 3 * nmt);
+  long total = 0;
+  for (int a = 0; a < d.nm; ++a) {
+    const int nl = d.L - t.m_of[a] + 1;
+    kpad[a] = (((nl + 1) / 2) + 7) / 8 * 8;
+    for (int q = 0; q < 2 * 3 * nmt; ++q) {
+      off[(size_t)a * 2 * 3 * nmt + q] = total;
+      total += 2L * 128 * kpad[a];
+    }
+  }
+  std::vector<float> tiles((size_t)total, 0.0f);
+  const std::vector<double>* tab[3] = {&t.P, &t.dP, &t.Ps};
+  for (int a = 0; a < d.nm; ++a) {
+    const int nl = d.L - t.m_of[a] + 1;
+    const int Kp = kpad[a];
+    for (int s = 0; s < 2; ++s)
+      for (int w = 0; w < 3; ++w)
+        for (int mt = 0; mt < nmt; ++mt) {
+          float* hi = &tiles[(size_t)off[((size_t)(a * 2 + s) * 3 + w) * nmt + mt]];
+          float* lo = hi + 128 * Kp;
+          for (int row = 0; row < 128; ++row)
+            for (int k = 0; k < Kp; ++k) {
+              const int th = mt * 128 + row;
+              const int q = s + 2 * k;
+              float v = 0.0f;
+              if (th < d.nlat2 && q < nl) v = (float)(*tab[w])[t.leg_off[a] + (size_t)q * d.nlat2 + th];
+              uint32_t bits;
+              std::memcpy(&bits, &v, 4);
+              bits &= 0xFFFFE000u;
+              float h;
+              std::memcpy(&h, &bits, 4);
+              const size_t o = (size_t)(row >> 3) * (Kp / 4) * 32 + (size_t)(k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+              hi[o] = h;
+              lo[o] = v - h;
+            }
+        }
+  }
+  CKS(upload(ctx, &ctx->tc_tiles, tiles.data(), tiles.size()));
+  CKS(upload(ctx, &ctx->tc_off, off.data(), off.size()));
+  CKS(upload(ctx, &ctx->tc_kpad, kpad.data(), kpad.size()));
+  ctx->tc_nmt = nmt;
+  int kmax = 0;
+  for (int k : kpad) kmax = std::max(kmax, k);
+  ctx->tc_smem = (2 * 128 * (size_t)kmax + 2 * (size_t)kTcNV * kmax) * sizeof(float) + 64;
+  return RSC_OK;
+}
+
 rsc_status set_smem_limits(rsc_ctx* ctx) {
   const int big = 200 * 1024;
   CK(cudaFuncSetAttribute(k_products<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -261,6 +324,7 @@ rsc_status set_smem_limits(rsc_ctx* ctx) {
   CK(cudaFuncSetAttribute(k_analysis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_rhs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_rhs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
   return RSC_OK;
 }
 
@@ -312,12 +376,19 @@ rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
            8.0 * d.P * d.Nd * sizeof(V) + 9.0 * d.Nd * (d.K + 1) * d.nlat * sizeof(V) +
                3.0 * d.P * d.nlat2 * sizeof(R),
            52.0 * d.P * d.nlat2 * d.Nd);
-  const int RT = ctx->rt_synth[sizeof(R) == 4 ? 1 : 0];
-  k_synth<R><<<dim3(d.nm, (d.Nd + RT - 1) / RT), dim3(round32(d.nlat2), RT),
-               (size_t)RT * (d.L + 1) * 8 * sizeof(V) + 16 * 3 * (size_t)d.nlat2 * sizeof(R),
-               ctx->s>>>(
-      g, L.view(), reinterpret_cast<const V*>(ctx->SR), reinterpret_cast<V*>(FCout));
-  CK(cudaGetLastError());
+  if (sizeof(R) == 4) {
+    TcTables tt{ctx->tc_tiles, ctx->tc_off, ctx->tc_kpad, ctx->tc_nmt, ctx->d_status};
+    k_synth_tc<<<dim3(d.nm, (d.Nd + kTcRadii - 1) / kTcRadii, ctx->tc_nmt), 128, ctx->tc_smem,
+                 ctx->s>>>(g, tt, reinterpret_cast<const float2*>(ctx->SR),
+                           reinterpret_cast<float2*>(FCout));
+    CK(cudaGetLastError());
+  } else {
+    const int RT = ctx->rt_synth[0];
+    k_synth<R><<<dim3(d.nm, (d.Nd + RT - 1) / RT), dim3(round32(d.nlat2), RT),
+                 (size_t)RT * (d.L + 1) * 8 * sizeof(V) + 16 * 3 * (size_t)d.nlat2 * sizeof(R),
+                 ctx->s>>>(g, L.view(), reinterpret_cast<const V*>(ctx->SR), reinterpret_cast<V*>(FCout));
+    CK(cudaGetLastError());
+  }
   }
   return RSC_OK;
 }
@@ -602,6 +673,18 @@ rsc_status ensure_krylov(rsc_ctx* ctx, int kmax) {
   return RSC_OK;
 }
 
+// Device status word written by kernels whose bounded waits gave up.
+rsc_status check_status(rsc_ctx* ctx) {
+  int st = 0;
+  CK(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    ctx->err = "a bounded device wait gave up (tensor-core synthesis)";
+    cudaMemset(ctx->d_status, 0, sizeof(int));
+    return (rsc_status)st;
+  }
+  return RSC_OK;
+}
+
 rsc_status norm2(rsc_ctx* ctx, const double* v, long n, double* out) {
   CKS(dots(ctx, v, n, 1, v, n, ctx->dots));
   CK(cudaMemcpyAsync(ctx->h_pinned, ctx->dots, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
@@ -794,6 +877,12 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = upload_legendre(ctx, ctx->leg64)) != RSC_OK) return fail(st);
   if ((st = upload_legendre(ctx, ctx->leg32)) != RSC_OK) return fail(st);
   if ((st = set_smem_limits(ctx)) != RSC_OK) return fail(st);
+  if ((st = build_tc_tables(ctx)) != RSC_OK) return fail(st);
+  if (cudaMalloc((void**)&ctx->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+    ctx->err = "cudaMalloc of the status word failed";
+    return fail(RSC_ENOMEM);
+  }
   if ((st = choose_cluster(ctx)) != RSC_OK) return fail(st);
   const size_t c16 = sizeof(double2);
   const size_t K1 = d.K + 1;
@@ -832,7 +921,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
   if (!ctx) return RSC_EINVAL;
   if (ctx->s) cudaStreamSynchronize(ctx->s);
   else cudaDeviceSynchronize();
-  void* bufs[] = {ctx->d_EcT1, ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
+  void* bufs[] = {ctx->tc_tiles, ctx->tc_off, ctx->tc_kpad, ctx->d_status, ctx->d_EcT1, ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
@@ -1010,6 +1099,7 @@ rsc_status rsc_newton_rw(rsc_ctx* ctx, double* U, double* C, long J, const rsc_n
     }
     double rn;
     CKS(norm2(ctx, ctx->rtmp, n, &rn));
+    CKS(check_status(ctx));
     if (it < RSC_MAX_HISTORY) r->residual_history[it] = rn;
     r->residual = rn;
     r->iterations = it;

@@ -678,8 +678,17 @@ __global__ void k_block_gemv(DevGeom g, const long* __restrict__ chain_off,
   for (int r = threadIdx.x >> 3; r < Nr + ((rows_per_pass - Nr % rows_per_pass) % rows_per_pass);
        r += rows_per_pass) {
     double2 acc = {0, 0};
-    if (r < Nr)
-      for (int k = s8; k < Nr; k += 8) acc = cmac(acc, Gi[(long)r * Nr + k], sv[k]);
+    if (r < Nr) {
+      if (m == 0) {   // real factors at m = 0
+        for (int k = s8; k < Nr; k += 8) {
+          const double gr = Gi[(long)r * Nr + k].x;
+          acc.x = fma(gr, sv[k].x, acc.x);
+          acc.y = fma(gr, sv[k].y, acc.y);
+        }
+      } else {
+        for (int k = s8; k < Nr; k += 8) acc = cmac(acc, Gi[(long)r * Nr + k], sv[k]);
+      }
+    }
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) {
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -714,14 +723,28 @@ struct ChainLane {
       reg[q] = (active && k < Nr) ? M[(long)r * Nr + k] : make_double2(0, 0);
     }
   }
-  __device__ __forceinline__ double2 dot(const double2 (&reg)[MAXQ], const double2* v, int Nr) const {
+  // real_op: the m = 0 chains, whose factors are real (no 2im/r^2 terms): 2 FMA per entry
+  __device__ __forceinline__ double2 dot(const double2 (&reg)[MAXQ], const double2* v, int Nr,
+                                         bool real_op) const {
     // two independent accumulators halve the dependent FP64 chain
     double2 a0 = {0, 0}, a1 = {0, 0};
+    if (real_op) {
 #pragma unroll
-    for (int q = 0; q < MAXQ; q += 2) {
-      const int k0 = s + 8 * q, k1 = k0 + 8;
-      if (k0 < Nr) a0 = cmac(a0, reg[q], v[k0]);
-      if (q + 1 < MAXQ && k1 < Nr) a1 = cmac(a1, reg[q + 1], v[k1]);
+      for (int q = 0; q < MAXQ; q += 2) {
+        const int k0 = s + 8 * q, k1 = k0 + 8;
+        if (k0 < Nr) { a0.x = fma(reg[q].x, v[k0].x, a0.x); a0.y = fma(reg[q].x, v[k0].y, a0.y); }
+        if (q + 1 < MAXQ && k1 < Nr) {
+          a1.x = fma(reg[q + 1].x, v[k1].x, a1.x);
+          a1.y = fma(reg[q + 1].x, v[k1].y, a1.y);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < MAXQ; q += 2) {
+        const int k0 = s + 8 * q, k1 = k0 + 8;
+        if (k0 < Nr) a0 = cmac(a0, reg[q], v[k0]);
+        if (q + 1 < MAXQ && k1 < Nr) a1 = cmac(a1, reg[q + 1], v[k1]);
+      }
     }
     double2 acc = make_double2(a0.x + a1.x, a0.y + a1.y);
 #pragma unroll
@@ -734,7 +757,7 @@ struct ChainLane {
 };
 
 struct ChainInfo {
-  int c, dir, cls, p0, nb, km, P, Nr;
+  int c, dir, cls, p0, nb, km, P, Nr, m;
   long boff, blk;
   __device__ __forceinline__ long row(int i) const {
     const int fld = ((i + cls) & 1) ? 1 : 0;
@@ -750,6 +773,7 @@ __device__ __forceinline__ ChainInfo chain_info(const DevGeom& g, const long* ch
   const int a = ci.c >> 1;
   ci.cls = ci.c & 1;
   const int m = g.m_of[a];
+  ci.m = m;
   ci.p0 = g.pstart[a];
   ci.nb = g.L - m + 1;
   ci.km = (ci.nb - 1) / 2;
@@ -803,7 +827,7 @@ __global__ void k_chain_half(DevGeom g, const long* __restrict__ chain_off,
       ln.load(H + (ci.boff + i + step) * ci.blk, Nr, mn);
       if (ln.active) gn = out[ci.row(i + step) + ln.r];
     }
-    const double2 acc = ln.dot(mc, sv + ((t - 1) & 1) * Nr, Nr);
+    const double2 acc = ln.dot(mc, sv + ((t - 1) & 1) * Nr, Nr, ci.m == 0);
     const double2 v = make_double2(gc.x - acc.x, gc.y - acc.y);
     if (ln.active) {
       if (ln.s == 0) out[ci.row(i) + ln.r] = v;
@@ -853,12 +877,12 @@ __global__ void k_chain_out(DevGeom g, const long* __restrict__ chain_off,
   double2 acc = {0, 0};
   if (km > 0) {
     ln.load(H + (ci.boff + km) * ci.blk, Nr, mc);
-    const double2 a1 = ln.dot(mc, yup, Nr);
+    const double2 a1 = ln.dot(mc, yup, Nr, ci.m == 0);
     acc.x += a1.x; acc.y += a1.y;
   }
   if (km < nb - 1) {
     ln.load(W + (ci.boff + km) * ci.blk, Nr, mc);
-    const double2 a2 = ln.dot(mc, zdn, Nr);
+    const double2 a2 = ln.dot(mc, zdn, Nr, ci.m == 0);
     acc.x += a2.x; acc.y += a2.y;
   }
   const double2 gk = ln.active ? mc0[2 * Nr + ln.r] : make_double2(0, 0);
@@ -886,7 +910,7 @@ __global__ void k_chain_out(DevGeom g, const long* __restrict__ chain_off,
       ln.load(W + (ci.boff + i + step) * ci.blk, Nr, mn);
       if (ln.active) yn = out[ci.row(i + step) + ln.r];
     }
-    const double2 a3 = ln.dot(mc, sv + ((t - 1) & 1) * Nr, Nr);
+    const double2 a3 = ln.dot(mc, sv + ((t - 1) & 1) * Nr, Nr, ci.m == 0);
     const double2 v = make_double2(yc.x - a3.x, yc.y - a3.y);
     if (ln.active) {
       if (ln.s == 0) out[ci.row(i) + ln.r] = v;

@@ -142,6 +142,21 @@ def test_jacobian_batch_of_directions(torch):
     gpu.close()
 
 
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES + [("C3-ish", 127, 12, 24, 1e-5, 140.0)])
+def test_mixed_explicit_terms_accuracy(torch, name, L, Ms, Nr, Ek, Ra):
+    """Mixed path: FP32 radial evaluation, tensor-core (3xTF32) Legendre synthesis, FP32 DFT,
+    products and analysis; the explicit terms agree with the FP64 oracle to FP32 accuracy."""
+    from paper_2508_16635_gb300 import RotatingShell
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=28, amp=3e-2)
+    got = gpu.explicit_terms(torch.tensor(x, device="cuda")).cpu().numpy()
+    want = s.to_real(s.explicit_terms(s.to_complex(x)))
+    errs = _rel_fields(s, got, want)
+    assert max(errs) < 2e-5, errs
+    gpu.close()
+
+
 def test_mixed_precision_step_error(torch):
     from paper_2508_16635_gb300 import RotatingShell
     L, Ms, Nr, Ek, Ra = 31, 4, 24, 1e-3, 120.0
