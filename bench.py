@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--krylov", type=int, default=20, help="Jacobian actions per Newton iteration")
+    ap.add_argument("--krylov", type=int, default=200,
+                    help="Jacobian actions per Newton iteration (the RW12 solve takes 208-216)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-rw", action="store_true", help="skip the time-to-rotating-wave run")
     ap.add_argument("--coriolis-study", action="store_true",
@@ -425,6 +426,23 @@ def run_gpu(args):
     jvps_per_step = gmres_total / args.steps
     value = world * jvps_per_step / (ms * 1e-3)
 
+    # per-kernel cost of one Jacobian action and of one FP64 residual step
+    ub = torch.tensor(si.random_vector(w["L"], w["Ms"], w["Nr"], seed=3002), device="cuda")
+    ubatch = ub.repeat(10)
+    outb = torch.empty_like(ubatch)
+    sh.apply_jacobian(U0, 0.5, J, ubatch, 200.0, out=outb)
+    sh.profile(True)
+    sh.apply_jacobian(U0, 0.5, J, ubatch, 200.0, out=outb)
+    prof_jvp = {k: round(v["ms"] / 10, 5) for k, v in sh.profile_report().items() if v["launches"]}
+    sh.profile(False)
+    shf = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"])
+    Uf = U0.clone()
+    shf.step(Uf, 0.5, 200.0)
+    shf.profile(True)
+    shf.step(Uf, 0.5, 200.0, nsteps=2)
+    prof_step64 = {k: round(v["ms"] / 2, 5) for k, v in shf.profile_report().items() if v["launches"]}
+    shf.close()
+
     # plain time stepping (timesteps/s) on the same workload
     Us = U0.clone()
     sh.step(Us, 0.0, 5e-6, nsteps=3)
@@ -466,6 +484,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": 8 * sh.n, "ms_per_step": e2e_t * 1e3},
             "gpu_launches": int(launches),
             "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items()},
+            "kernel_ms_per_jacobian_action": prof_jvp,
+            "kernel_ms_per_fp64_step": prof_step64,
             "roofline": roofline(prof, peaks, args.precision),
             "peaks": {k: v for k, v in peaks.items()},
             "clocks": clk.summary(),
