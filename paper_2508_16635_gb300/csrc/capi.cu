@@ -325,6 +325,7 @@ rsc_status set_smem_limits(rsc_ctx* ctx) {
   CK(cudaFuncSetAttribute(k_rhs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_rhs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+  CK(cudaFuncSetAttribute(k_dots_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * (kMaxKrylov + 2) * 8));
   return RSC_OK;
 }
 
@@ -649,14 +650,16 @@ rsc_status jvp_any(rsc_ctx* ctx, const double* U, double C, long J, const double
 // dots[j] = V_j . w for j < nv (written to ctx->dots on the device)
 rsc_status dots(rsc_ctx* ctx, const double* V, long ld, int nv, const double* w, long n,
                 double* dst) {
+  const int nchunk = (int)((n + 2047) / 2048);
   {
     KSpan sp(ctx, RSC_K_DOTS, 8.0 * n * (nv + 1), 2.0 * n * nv);
-    k_dots<<<dim3(ctx->nblk_dot, nv), 256, 0, ctx->s>>>(V, ld, nv, w, n, ctx->partial);
+    k_dots_tiled<<<nchunk, 256, 8 * (size_t)nv * sizeof(double), ctx->s>>>(V, ld, nv, w, n,
+                                                                         ctx->partial);
     CK(cudaGetLastError());
   }
   {
-    KSpan sp(ctx, RSC_K_DOTS, 8.0 * nv * ctx->nblk_dot, (double)nv * ctx->nblk_dot);
-    k_reduce_rows<<<nv, 256, 0, ctx->s>>>(ctx->partial, ctx->nblk_dot, dst);
+    KSpan sp(ctx, RSC_K_DOTS, 8.0 * nv * nchunk, (double)nv * nchunk);
+    k_reduce_rows<<<nv, 256, 0, ctx->s>>>(ctx->partial, nchunk, dst);
     CK(cudaGetLastError());
   }
   return RSC_OK;
@@ -904,7 +907,7 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = alloc((void**)&ctx->xtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->vtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->rtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
-  ctx->nblk_dot = (int)std::min<long>((n + 255) / 256, 304);
+  ctx->nblk_dot = (int)std::max<long>((n + 2047) / 2048, 304);
   if ((st = alloc((void**)&ctx->partial, (size_t)ctx->nblk_dot * (kMaxKrylov + 2) * sizeof(double))) != RSC_OK)
     return fail(st);
   if ((st = alloc((void**)&ctx->dots, (size_t)(3 * kMaxKrylov + 8) * sizeof(double))) != RSC_OK)

@@ -966,6 +966,61 @@ __global__ void k_dots(const double* __restrict__ V, long ld, int nv, const doub
   (void)nv;
 }
 
+// Tiled V^T w: block b owns elements [b * 2048, (b+1) * 2048) (8 per thread),
+// keeps its slice of w in registers and streams every V_j over it; per-warp
+// sums go to shared memory, one cross-warp pass writes partial[j * nblk + b].
+// grid = ceil(n / 2048), block = 256, smem = 8 * nv doubles.
+__global__ void __launch_bounds__(256) k_dots_tiled(const double* __restrict__ V, long ld, int nv,
+                                                    const double* __restrict__ w, long n,
+                                                    double* __restrict__ partial) {
+  extern __shared__ double red2[];   // [8 warps][nv]
+  const long base = (long)blockIdx.x * 2048;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double wv[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const long i = base + threadIdx.x + 256 * e;
+    wv[e] = (i < n) ? w[i] : 0.0;
+  }
+  int j = 0;
+  for (; j + 4 <= nv; j += 4) {
+    double acc[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const long i = base + threadIdx.x + 256 * e;
+      if (i < n) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(V[(long)(j + u) * ld + i], wv[e], acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      double a = acc[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) red2[warp * nv + j + u] = a;
+    }
+  }
+  for (; j < nv; ++j) {
+    double a = 0.0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const long i = base + threadIdx.x + 256 * e;
+      if (i < n) a = fma(V[(long)j * ld + i], wv[e], a);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red2[warp * nv + j] = a;
+  }
+  __syncthreads();
+  for (int jj = threadIdx.x; jj < nv; jj += blockDim.x) {
+    double a = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a += red2[q * nv + jj];
+    partial[(long)jj * gridDim.x + blockIdx.x] = a;
+  }
+}
+
 // out[j] = sum_b partial[j * nblk + b].  grid = nv, block = 256.
 __global__ void k_reduce_rows(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
   __shared__ double red[32];
@@ -984,15 +1039,22 @@ __global__ void k_reduce_rows(const double* __restrict__ partial, int nblk, doub
   }
 }
 
-// w += sign * sum_j coef[j] V_j
+// w += sign * sum_j coef[j] V_j  (four independent accumulators for memory parallelism)
 __global__ void k_multi_axpy(const double* __restrict__ V, long ld, int nv,
                              const double* __restrict__ coef, double sign, double* __restrict__ w,
                              long n) {
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < nv; ++j) s = fma(coef[j], V[(long)j * ld + idx], s);
-    w[idx] = fma(sign, s, w[idx]);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = 0;
+    for (; j + 4 <= nv; j += 4) {
+      s0 = fma(coef[j], V[(long)j * ld + idx], s0);
+      s1 = fma(coef[j + 1], V[(long)(j + 1) * ld + idx], s1);
+      s2 = fma(coef[j + 2], V[(long)(j + 2) * ld + idx], s2);
+      s3 = fma(coef[j + 3], V[(long)(j + 3) * ld + idx], s3);
+    }
+    for (; j < nv; ++j) s0 = fma(coef[j], V[(long)j * ld + idx], s0);
+    w[idx] = fma(sign, (s0 + s1) + (s2 + s3), w[idx]);
   }
 }
 
