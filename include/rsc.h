@@ -176,9 +176,12 @@ enum {
   RSC_NUM_KERNELS = 11
 };
 
-/* Start (on != 0) or stop collecting per-kernel timings: CUDA events are
- * recorded around every launch on the context stream.  Clears the counters. */
-rsc_status rsc_profile_enable(rsc_ctx* ctx, int on);
+/* Start (mask != 0) or stop collecting per-kernel timings: CUDA events are
+ * recorded around the launches of the kernels whose bit (1 << kernel_id) is
+ * set in `mask`, on the context stream.  Clears the counters.  While tracing
+ * is on, Jacobian actions run as individual launches instead of a replayed
+ * CUDA graph.                                                               */
+rsc_status rsc_profile_enable(rsc_ctx* ctx, int mask);
 
 /* Accumulated device time (ms), launches, algorithmic bytes and flops of one
  * kernel since rsc_profile_enable (synchronises the stream).                */

@@ -90,6 +90,15 @@ struct rsc_ctx {
   // tracing: launch counter, per-kernel CUDA-event timing and algorithmic traffic
   long launches = 0;
   bool prof_on = false;
+  unsigned prof_mask = 0;      // kernel ids whose launches are bracketed by events
+  // CUDA graph of one Jacobian action (replayed inside GMRES)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t jvp_exec = nullptr;
+  long jvp_nodes = 0;
+  struct { int fp32; const double* U; double C; long J; double dt; } jvp_key{};
+  const double** d_slots = nullptr;   // [u, out] of the replayed action
+  double* d_cslot = nullptr;          // c = u_J of the replayed action
+  double* jvp_y = nullptr;            // solve output of the replayed action
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double prof_ms[RSC_NUM_KERNELS] = {0};
@@ -155,7 +164,7 @@ struct KSpan {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   KSpan(rsc_ctx* c, int kid, double bytes, double flops) : ctx(c), id(kid) {
     ctx->launches++;
-    if (ctx->prof_on) {
+    if (ctx->prof_on && ((ctx->prof_mask >> id) & 1u)) {
       ctx->prof_launches[id]++;
       ctx->prof_bytes[id] += bytes;
       ctx->prof_flops[id] += flops;
@@ -338,6 +347,10 @@ rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
   DevFactor& f = ctx->fac[ctx->fac_next];
   ctx->fac_next ^= 1;
   CK(cudaStreamSynchronize(ctx->s));
+  if (ctx->jvp_exec) {   // the captured Jacobian action may point into the slot being replaced
+    cudaGraphExecDestroy(ctx->jvp_exec);
+    ctx->jvp_exec = nullptr;
+  }
   free_factor(f);
   HostFactor hf;
   const int bad = build_factor(ctx->p, ctx->d, ctx->t, dt, hf);
@@ -616,10 +629,8 @@ rsc_status launch_1d_grid(long n, int* blocks) {
 
 // out = (B_U - I) u with the drift unknown in slot J (Sec. 3.4); base cached.
 template <typename R>
-rsc_status do_jvp(rsc_ctx* ctx, const double* U, double C, long J, const double* u, double* out,
-                  double dt) {
-  DevFactor* f = nullptr;
-  CKS(get_factor(ctx, dt, &f));
+rsc_status do_jvp_eager(rsc_ctx* ctx, const double* U, double C, long J, const double* u,
+                        double* out, DevFactor* f, double dt) {
   const long n = ctx->d.n();
   int nb;
   launch_1d_grid(n, &nb);
@@ -639,6 +650,74 @@ rsc_status do_jvp(rsc_ctx* ctx, const double* U, double C, long J, const double*
     k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, ctx->xtmp, 1.0, out, n);
     CK(cudaGetLastError());
   }
+  return RSC_OK;
+}
+
+// The same sequence with input / output through device pointer slots, for capture.
+template <typename R>
+rsc_status jvp_body_indirect(rsc_ctx* ctx, const double* U, double C, long J, DevFactor* f,
+                             double dt) {
+  const long n = ctx->d.n();
+  int nb;
+  launch_1d_grid(n, &nb);
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 0.0);
+    k_copy_zero_slot_ind<<<nb, 256, 0, ctx->s>>>(ctx->d_slots, J, ctx->xtmp, ctx->d_cslot, n);
+    CK(cudaGetLastError());
+  }
+  CKS(stage_synth<R>(ctx, ctx->xtmp, ctx->FC));
+  CKS(stage_products_analysis<R>(ctx, true));
+  RhsParams rp = make_rp(ctx, dt, C, 1);
+  rp.J = J >= 0 ? 0 : -1;  // c is read from d_cslot[0]
+  CKS(stage_rhs<R>(ctx, rp, ctx->xtmp, U, ctx->d_cslot, ctx->rhs));
+  CKS(stage_solve(ctx, f, ctx->jvp_y));
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
+    k_finish_ind<<<nb, 256, 0, ctx->s>>>(ctx->d_slots, ctx->jvp_y, ctx->xtmp, n);
+    CK(cudaGetLastError());
+  }
+  return RSC_OK;
+}
+
+template <typename R>
+rsc_status do_jvp(rsc_ctx* ctx, const double* U, double C, long J, const double* u, double* out,
+                  double dt) {
+  DevFactor* f = nullptr;
+  CKS(get_factor(ctx, dt, &f));
+  if (ctx->prof_on) return do_jvp_eager<R>(ctx, U, C, J, u, out, f, dt);
+  const int fp32 = sizeof(R) == 4;
+  const bool same = ctx->jvp_exec && ctx->jvp_key.fp32 == fp32 && ctx->jvp_key.U == U &&
+                    ctx->jvp_key.C == C && ctx->jvp_key.J == J && ctx->jvp_key.dt == dt;
+  if (!same) {
+    if (ctx->jvp_exec) {
+      cudaGraphExecDestroy(ctx->jvp_exec);
+      ctx->jvp_exec = nullptr;
+    }
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = ctx->s;
+    ctx->s = ctx->cap_stream;
+    const long before = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeThreadLocal));
+    const rsc_status st = jvp_body_indirect<R>(ctx, U, C, J, f, dt);
+    const cudaError_t ce = cudaStreamEndCapture(ctx->s, &graph);
+    ctx->s = user;
+    if (st != RSC_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    CK(ce);
+    const cudaError_t ie = cudaGraphInstantiate(&ctx->jvp_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie);
+    ctx->jvp_nodes = ctx->launches - before;
+    ctx->launches = before;
+    ctx->jvp_key = {fp32, U, C, J, dt};
+  }
+  k_set_ptrs<<<1, 1, 0, ctx->s>>>(ctx->d_slots, u, out);
+  CK(cudaGetLastError());
+  CK(cudaGraphLaunch(ctx->jvp_exec, ctx->s));
+  ctx->launches += ctx->jvp_nodes + 1;
   return RSC_OK;
 }
 
@@ -904,6 +983,9 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = alloc(&ctx->AR, (size_t)d.P * d.Nd * 4 * c16)) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->rhs, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->mid, (size_t)2 * d.nm * 3 * d.Nr * c16)) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->d_slots, 2 * sizeof(double*))) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->d_cslot, sizeof(double))) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->jvp_y, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->xtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->vtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->rtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
@@ -924,7 +1006,9 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
   if (!ctx) return RSC_EINVAL;
   if (ctx->s) cudaStreamSynchronize(ctx->s);
   else cudaDeviceSynchronize();
-  void* bufs[] = {ctx->tc_tiles, ctx->tc_off, ctx->tc_kpad, ctx->d_status, ctx->d_EcT1, ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
+  if (ctx->jvp_exec) cudaGraphExecDestroy(ctx->jvp_exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  void* bufs[] = {(void*)ctx->d_slots, ctx->d_cslot, ctx->jvp_y, ctx->tc_tiles, ctx->tc_off, ctx->tc_kpad, ctx->d_status, ctx->d_EcT1, ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
@@ -962,6 +1046,10 @@ rsc_status rsc_set_params(rsc_ctx* ctx, const rsc_params* params) {
   ctx->p = *params;
   if (refactor)
     for (auto& f : ctx->fac) free_factor(f);
+  if (ctx->jvp_exec) {   // captured launches embed parameters and factor pointers
+    cudaGraphExecDestroy(ctx->jvp_exec);
+    ctx->jvp_exec = nullptr;
+  }
   return RSC_OK;
 }
 
@@ -1050,6 +1138,7 @@ rsc_status rsc_profile_enable(rsc_ctx* ctx, int on) {
     ctx->prof_flops[k] = 0.0;
   }
   ctx->prof_on = on != 0;
+  ctx->prof_mask = (unsigned)on;
   return RSC_OK;
 }
 

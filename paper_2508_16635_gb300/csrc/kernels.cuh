@@ -1074,6 +1074,32 @@ __global__ void k_sub_frozen(const double* __restrict__ y, const double* __restr
     out[idx] = (idx == J) ? y[idx] : y[idx] - u[idx];
 }
 
+// Graph-replayed Jacobian action: the input and output vectors are reached
+// through pointers held in device memory (set by k_set_ptrs before each replay).
+__global__ void k_set_ptrs(const double** slots, const double* u, double* out) {
+  slots[0] = u;
+  slots[1] = out;
+}
+
+// x = u with u_J zeroed; c = u_J stored in cslot[0] (Sec. 3.4)
+__global__ void k_copy_zero_slot_ind(const double* const* slots, long J, double* __restrict__ x,
+                                     double* __restrict__ cslot, long n) {
+  const double* u = slots[0];
+  if (J >= 0 && blockIdx.x == 0 && threadIdx.x == 0) cslot[0] = u[J];
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x)
+    x[idx] = (idx == J) ? 0.0 : u[idx];
+}
+
+// out = y - x through the output pointer slot
+__global__ void k_finish_ind(const double* const* slots, const double* __restrict__ y,
+                             const double* __restrict__ x, long n) {
+  double* out = const_cast<double*>(slots[1]);
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x)
+    out[idx] = y[idx] - x[idx];
+}
+
 // copy with u_J zeroed (x holds the canonical layout)
 __global__ void k_copy_zero_slot(const double* __restrict__ u, long J, double* __restrict__ x,
                                  long n) {

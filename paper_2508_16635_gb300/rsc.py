@@ -227,9 +227,15 @@ class RotatingShell:
             self._check(st)
         return Cv.value, rep.as_dict(), st
 
-    def profile(self, on=True):
-        """Start / stop per-kernel CUDA-event timing inside the library (clears counters)."""
-        self._check(self.lib.rsc_profile_enable(self._ctx, 1 if on else 0))
+    def profile(self, on=True, kernels=None):
+        """Start / stop per-kernel CUDA-event timing inside the library (clears counters).
+
+        kernels: names to time (default all); events bracket only those launches.
+        """
+        mask = 0
+        if on:
+            mask = (1 << len(KERNELS)) - 1 if kernels is None else sum(1 << KERNELS.index(k) for k in kernels)
+        self._check(self.lib.rsc_profile_enable(self._ctx, mask))
 
     def profile_report(self):
         """{kernel: {ms, launches, bytes, flops}} accumulated since profile(True)."""
