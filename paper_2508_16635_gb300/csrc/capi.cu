@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <cstdint>
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -729,11 +730,17 @@ rsc_status jvp_any(rsc_ctx* ctx, const double* U, double C, long J, const double
 // dots[j] = V_j . w for j < nv (written to ctx->dots on the device)
 rsc_status dots(rsc_ctx* ctx, const double* V, long ld, int nv, const double* w, long n,
                 double* dst) {
-  const int nchunk = (int)((n + 2047) / 2048);
+  // the split kernel needs an even length and 16-byte aligned rows (n and ld even)
+  const bool split = (n % 2 == 0) && (ld % 2 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+  const int nchunk = split ? (int)((n + 4095) / 4096) : (int)((n + 2047) / 2048);
   {
     KSpan sp(ctx, RSC_K_DOTS, 8.0 * n * (nv + 1), 2.0 * n * nv);
-    k_dots_tiled<<<nchunk, 256, 8 * (size_t)nv * sizeof(double), ctx->s>>>(V, ld, nv, w, n,
-                                                                         ctx->partial);
+    if (split)
+      k_dots_split<<<dim3(nchunk, (nv + 7) / 8), 256, 0, ctx->s>>>(V, ld, nv, w, n, ctx->partial);
+    else
+      k_dots_tiled<<<nchunk, 256, 8 * (size_t)nv * sizeof(double), ctx->s>>>(V, ld, nv, w, n,
+                                                                           ctx->partial);
     CK(cudaGetLastError());
   }
   {
@@ -811,13 +818,13 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
     CKS(dots(ctx, V, n, k + 1, w, n, ctx->dots));
     {
       KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (k + 3), 2.0 * n * (k + 1));
-      k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots, -1.0, w, n);
+      k_multi_axpy2<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots, -1.0, w, n);
       CK(cudaGetLastError());
     }
     CKS(dots(ctx, V, n, k + 1, w, n, ctx->dots + (k + 1)));
     {
       KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (k + 3), 2.0 * n * (k + 1));
-      k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots + (k + 1), -1.0, w, n);
+      k_multi_axpy2<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots + (k + 1), -1.0, w, n);
       CK(cudaGetLastError());
     }
     CKS(dots(ctx, w, n, 1, w, n, ctx->dots + 2 * (k + 1)));
@@ -867,7 +874,7 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
   CK(cudaMemcpyAsync(ctx->dots, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
   {
     KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (kk + 2), 2.0 * n * kk);
-    k_multi_axpy<<<nb, 256, 0, ctx->s>>>(V, n, kk, ctx->dots, 1.0, x, n);
+    k_multi_axpy2<<<nb, 256, 0, ctx->s>>>(V, n, kk, ctx->dots, 1.0, x, n);
     CK(cudaGetLastError());
   }
   CK(cudaStreamSynchronize(ctx->s));

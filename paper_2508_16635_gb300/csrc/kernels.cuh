@@ -1021,6 +1021,93 @@ __global__ void __launch_bounds__(256) k_dots_tiled(const double* __restrict__ V
   }
 }
 
+// V^T w split over (element chunk, group of 8 basis vectors): block (c, gidx)
+// reads elements [c * 4096, (c+1) * 4096) of w and of V_j, j in [8 gidx, 8 gidx + 8),
+// as double2 (8 per thread), every load issued before the first FMA; one block
+// reduction of 8 values writes partial[j * nchunk + c].  grid = (nchunk, ceil(nv / 8)),
+// block = 256.  Requires n even and V, w 16-byte aligned (ld even).
+__global__ void __launch_bounds__(256) k_dots_split(const double* __restrict__ V, long ld, int nv,
+                                                    const double* __restrict__ w, long n,
+                                                    double* __restrict__ partial) {
+  __shared__ double red[8][8];
+  const long base = (long)blockIdx.x * 4096;
+  const int j0 = blockIdx.y * 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long n2 = n >> 1;
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  double2 wv[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const long i2 = (base >> 1) + threadIdx.x + 256 * e;
+    wv[e] = (i2 < n2) ? w2[i2] : make_double2(0, 0);
+  }
+  double acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    acc[u] = 0.0;
+    const int j = j0 + u;
+    if (j < nv) {
+      const double2* v2 = reinterpret_cast<const double2*>(V + (long)j * ld);
+      double2 vv[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const long i2 = (base >> 1) + threadIdx.x + 256 * e;
+        vv[e] = (i2 < n2) ? v2[i2] : make_double2(0, 0);
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[u] = fma(vv[e].x, wv[e].x, fma(vv[e].y, wv[e].y, acc[u]));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    double a = acc[u];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red[warp][u] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8 && j0 + threadIdx.x < nv) {
+    double a = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a += red[q][threadIdx.x];
+    partial[(long)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = a;
+  }
+}
+
+// w += sign * sum_j coef[j] V_j with double2 loads, eight vectors per iteration.
+// Requires n even and 16-byte aligned V, w (ld even).
+__global__ void k_multi_axpy2(const double* __restrict__ V, long ld, int nv,
+                              const double* __restrict__ coef, double sign, double* __restrict__ w,
+                              long n) {
+  const long n2 = n >> 1;
+  double2* w2 = reinterpret_cast<double2*>(w);
+  for (long i2 = (long)blockIdx.x * blockDim.x + threadIdx.x; i2 < n2;
+       i2 += (long)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0, tx = 0.0, ty = 0.0;
+    int j = 0;
+    for (; j + 8 <= nv; j += 8) {
+      double2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = reinterpret_cast<const double2*>(V + (long)(j + u) * ld)[i2];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const double c0 = coef[j + u], c1 = coef[j + u + 1];
+        sx = fma(c0, v[u].x, sx); sy = fma(c0, v[u].y, sy);
+        tx = fma(c1, v[u + 1].x, tx); ty = fma(c1, v[u + 1].y, ty);
+      }
+    }
+    for (; j < nv; ++j) {
+      const double2 v = reinterpret_cast<const double2*>(V + (long)j * ld)[i2];
+      sx = fma(coef[j], v.x, sx);
+      sy = fma(coef[j], v.y, sy);
+    }
+    double2 o = w2[i2];
+    o.x = fma(sign, sx + tx, o.x);
+    o.y = fma(sign, sy + ty, o.y);
+    w2[i2] = o;
+  }
+}
+
 // out[j] = sum_b partial[j * nblk + b].  grid = nv, block = 256.
 __global__ void k_reduce_rows(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
   __shared__ double red[32];
