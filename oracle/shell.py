@@ -461,20 +461,31 @@ class Shell:
 
     # ---- physical diagnostics (definitions stated in the design doc) ---------------------
     def kinetic_energy(self, vec, nquad=None):
-        """KE density (1/V) int |U|^2/2 dV by grid quadrature (Gauss-Legendre in r)."""
+        """KE density (1/V) int |U|^2/2 dV (the kinetic energy of the bifurcation diagrams,
+        Secs. 4-5; V = 4 pi (r_out^3 - r_in^3)/3).  The velocity of Sec. 2.1 is synthesised on
+        the transform grid at nquad Gauss-Legendre radii (default 2 N_r + 16, exact for the
+        polynomial part of r^2 |U|^2), summed with the latitude weights and over the sector,
+        then integrated in r by the Gauss-Legendre rule."""
         x = self.to_complex(vec)
-        g = self.grid_fields(x)
-        # angular integral on the de-aliased radii, then Chebyshev interpolation in r
+        nq = nquad or 2 * self.Nr + 16
+        xq, wq = np.polynomial.legendre.leggauss(nq)
+        rq = basis.x_to_r(xq, self.r_in, self.r_out)
+        E0 = basis.cheb_matrix(xq, self.Nr, 0, self.r_in, self.r_out)
+        E1 = basis.cheb_matrix(xq, self.Nr, 1, self.r_in, self.r_out)
+        e, f = x[0], x[1]
+        r = rq[None, :]
+        lam = self.lam[:, None]
+        ur = lam * (f @ E0.T) / r ** 2
+        Su = (f @ E1.T) / r
+        Tu = (e @ E0.T) / r
+        s = self.sph
+        g_ur = s.fourier_to_grid(s.synth_scalar(self.split_m(ur)))
+        ut, up = s.synth_vector(self.split_m(Su), self.split_m(Tu))
+        g_ut, g_up = s.fourier_to_grid(ut), s.fourier_to_grid(up)
         w = self.sph.w[None, :, None]
         dphi = 2.0 * np.pi / self.sph.nphi  # sector mean times 2 pi
-        e2 = g["ur"] ** 2 + g["ut"] ** 2 + g["up"] ** 2
-        ang = (e2 * w).sum(axis=(0, 1)) * dphi  # [N_d]
-        Td = basis.cheb_matrix(self.xd, self.Nd, 0, self.r_in, self.r_out)
-        coef = np.linalg.solve(Td, ang * self.rd ** 2)
-        nq = nquad or 2 * self.Nd
-        xq, wq = np.polynomial.legendre.leggauss(nq)
-        vals = basis.cheb_matrix(xq, self.Nd, 0, self.r_in, self.r_out) @ coef
-        integral = 0.5 * (self.r_out - self.r_in) * (wq * vals).sum()
+        ang = ((g_ur ** 2 + g_ut ** 2 + g_up ** 2) * w).sum(axis=(0, 1)) * dphi  # [nq]
+        integral = 0.5 * (self.r_out - self.r_in) * (wq * rq ** 2 * ang).sum()
         V = 4.0 * np.pi * (self.r_out ** 3 - self.r_in ** 3) / 3.0
         return 0.5 * integral / V
 
