@@ -194,6 +194,18 @@ const char* rsc_kernel_name(int kernel_id);
 /* Number of kernel launches issued by this context since rsc_create.        */
 rsc_status rsc_launch_count(const rsc_ctx* ctx, long* count);
 
+/* Diagnostics of the bifurcation diagrams (Secs. 4-5), synchronous:
+ *   KE     = (1/V) int |U|^2 / 2 dV over the shell, V = 4 pi (r_out^3 - r_in^3)/3,
+ *            from the potentials by Parseval's identity (Sec. 2.1, Eq. Ylm_norm)
+ *            and a Gauss-Legendre rule of 2 Nr + 16 radii;
+ *   Nu_in, Nu_out = d_r of the spherical mean temperature at r_in, r_out divided
+ *            by the conductive gradient -r_out r_in / r^2 there (1 for the
+ *            conductive state of Sec. 2.1).
+ * U is a device state; any of KE, Nu_in, Nu_out may be NULL (host pointers).
+ * Returns RSC_EINVAL when ctx or U is NULL.                                 */
+rsc_status rsc_diagnostics(rsc_ctx* ctx, const double* U, double* KE, double* Nu_in,
+                           double* Nu_out);
+
 /* Euclidean norm of a device vector of n doubles (synchronous).            */
 rsc_status rsc_norm2(rsc_ctx* ctx, const double* v, size_t n, double* out);
 

@@ -75,6 +75,7 @@ struct rsc_ctx {
   // Krylov
   double* V = nullptr;
   int V_cols = 0;
+  long ldV = 0;   // column stride of V
   double* partial = nullptr;
   double* dots = nullptr;
   double* h_pinned = nullptr;
@@ -100,6 +101,10 @@ struct rsc_ctx {
   const double** d_slots = nullptr;   // [u, out] of the replayed action
   double* d_cslot = nullptr;          // c = u_J of the replayed action
   double* jvp_y = nullptr;            // solve output of the replayed action
+  // diagnostics: Gauss-Legendre radial rule and Chebyshev tables (built on first use)
+  int ke_nq = 0;
+  double *d_keT = nullptr, *d_kedT = nullptr, *d_ker = nullptr, *d_kew = nullptr;
+  double* d_diag = nullptr;   // [KE, Nu_in, Nu_out]
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double prof_ms[RSC_NUM_KERNELS] = {0};
@@ -751,13 +756,23 @@ rsc_status dots(rsc_ctx* ctx, const double* V, long ld, int nv, const double* w,
   return RSC_OK;
 }
 
+// Krylov basis: kmax + 1 columns of ldV doubles, ldV = n rounded up to a multiple of 1024,
+// zero-filled once so that the padding of every column stays zero.
 rsc_status ensure_krylov(rsc_ctx* ctx, int kmax) {
   if (ctx->V_cols >= kmax + 1) return RSC_OK;
   CK(cudaStreamSynchronize(ctx->s));
   cudaFree(ctx->V);
   ctx->V = nullptr;
+  ctx->V_cols = 0;
   const long n = ctx->d.n();
-  CK(cudaMalloc(&ctx->V, (size_t)(kmax + 1) * n * sizeof(double)));
+  ctx->ldV = (n + 1023) / 1024 * 1024;
+  const size_t bytes = (size_t)(kmax + 1) * ctx->ldV * sizeof(double);
+  if (cudaMalloc(&ctx->V, bytes) != cudaSuccess) {
+    ctx->V = nullptr;
+    ctx->err = "cudaMalloc of the Krylov basis failed";
+    return RSC_ENOMEM;
+  }
+  CK(cudaMemsetAsync(ctx->V, 0, bytes, ctx->s));
   ctx->V_cols = kmax + 1;
   return RSC_OK;
 }
@@ -782,15 +797,26 @@ rsc_status norm2(rsc_ctx* ctx, const double* v, long n, double* out) {
   return RSC_OK;
 }
 
-// GMRES (Saad-Schultz) with classical Gram-Schmidt and one re-orthogonalisation
-// (CGS2), zero initial guess, no restart.  Solves (B_U - I) x = b; x returned
-// in `x`.  Each iteration reads k + 3 doubles back for the Hessenberg column.
+// GMRES (Saad-Schultz), zero initial guess, no restart, solving (B_U - I) x = b
+// (Sec. 3.3) with modified Gram-Schmidt in its one-reduction form: iteration k
+//   1. w = A v_k (one Jacobian action);
+//   2. one pass over the basis gives s = V^T w and t = V^T v_k; t is the new row
+//      of the strictly lower part L of V^T V;
+//   3. on the host, (I + L) h = s by forward substitution: h are exactly the MGS
+//      coefficients h_j = v_j . (w - sum_{i<j} h_i v_i), since the MGS projector
+//      prod_j (I - v_j v_j^T) equals I - V (I + L)^{-1} V^T;
+//   4. one pass w <- w - V h that also sums |w|^2, then w <- w / |w| on the device.
+// |w| reaches the host with the next iteration's products, so the Hessenberg
+// column k (and the convergence test) completes one iteration late; a solve that
+// converges at column k has run one Jacobian action more than it uses.
+// Two passes over the basis per iteration (classical Gram-Schmidt with
+// re-orthogonalisation takes four) and one host synchronisation.
 rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* b, double* x,
                  double dt, int kmax, double tol, bool fp32, int* iters, double* relres) {
   const long n = ctx->d.n();
   CKS(ensure_krylov(ctx, kmax));
   int nb;
-  launch_1d_grid(n, &nb);
+  launch_1d_grid(n / 2, &nb);
   double beta;
   CKS(norm2(ctx, b, n, &beta));
   if (!std::isfinite(beta)) {
@@ -802,84 +828,170 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
   *relres = 0.0;
   if (beta == 0.0) return RSC_OK;
   double* V = ctx->V;
+  const long ld = ctx->ldV;
   {
     KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 1.0 * n);
     k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / beta, b, 0.0, V, n);
     CK(cudaGetLastError());
   }
+  // device buffer: [0] |w|^2 of the previous iteration, [1, k+2) s, [k+2, 2k+3) t
+  double* dbuf = ctx->dots;
+  double* d_h = ctx->dots + (2 * kMaxKrylov + 4);
+  double* h_in = ctx->h_pinned;
+  double* h_out = ctx->h_pinned + (2 * kMaxKrylov + 4);
+  const int nchunk = (int)(ld / 1024);
   std::vector<double> H((size_t)(kmax + 1) * kmax, 0.0), cs(kmax), sn(kmax), gvec(kmax + 1, 0.0);
+  std::vector<double> Lrow((size_t)kmax * (kmax + 1) / 2 + 1, 0.0);   // packed rows of L
+  auto Lr = [&](int i) { return Lrow.data() + (size_t)i * (i - 1) / 2; };   // row i, i entries
   gvec[0] = beta;
-  int k = 0;
   double res = beta;
-  for (k = 0; k < kmax; ++k) {
-    double* w = V + (long)(k + 1) * n;
-    CKS(jvp_any(ctx, U, C, J, V + (long)k * n, w, dt, fp32));
-    // CGS2
-    CKS(dots(ctx, V, n, k + 1, w, n, ctx->dots));
-    {
-      KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (k + 3), 2.0 * n * (k + 1));
-      k_multi_axpy2<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots, -1.0, w, n);
-      CK(cudaGetLastError());
+  int ncols = 0;
+  for (int k = 0;; ++k) {
+    const bool next = k < kmax;
+    double* vk = V + (long)k * ld;
+    double* w = V + (long)(k + 1) * ld;
+    if (next) {
+      CKS(jvp_any(ctx, U, C, J, vk, w, dt, fp32));
+      {
+        KSpan sp(ctx, RSC_K_DOTS, 8.0 * n * (k + 3), 4.0 * n * (k + 1));
+        k_dots_pair<<<dim3(nchunk, (k + 1 + 15) / 16), 256, 0, ctx->s>>>(V, ld, k + 1, w, vk,
+                                                                          ctx->partial);
+        CK(cudaGetLastError());
+      }
+      {
+        KSpan sp(ctx, RSC_K_DOTS, 16.0 * (k + 1) * nchunk, 2.0 * (k + 1) * nchunk);
+        k_reduce_rows<<<2 * (k + 1), 256, 0, ctx->s>>>(ctx->partial, nchunk, dbuf + 1);
+        CK(cudaGetLastError());
+      }
     }
-    CKS(dots(ctx, V, n, k + 1, w, n, ctx->dots + (k + 1)));
-    {
-      KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (k + 3), 2.0 * n * (k + 1));
-      k_multi_axpy2<<<nb, 256, 0, ctx->s>>>(V, n, k + 1, ctx->dots + (k + 1), -1.0, w, n);
-      CK(cudaGetLastError());
-    }
-    CKS(dots(ctx, w, n, 1, w, n, ctx->dots + 2 * (k + 1)));
-    CK(cudaMemcpyAsync(ctx->h_pinned, ctx->dots, (2 * (k + 1) + 1) * sizeof(double),
-                       cudaMemcpyDeviceToHost, ctx->s));
+    const int nread = next ? 2 * k + 3 : 1;
+    CK(cudaMemcpyAsync(h_in, dbuf, nread * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaStreamSynchronize(ctx->s));
-    const double* hh = ctx->h_pinned;
-    for (int i = 0; i <= k; ++i) H[(size_t)i * kmax + k] = hh[i] + hh[k + 1 + i];
-    const double hn = std::sqrt(std::max(0.0, hh[2 * (k + 1)]));
-    if (!std::isfinite(hn)) {
+    if (k >= 1) {
+      // complete column k - 1 with |w_{k-1}| and its Givens rotation
+      const int c = k - 1;
+      const double hn = std::sqrt(std::max(0.0, h_in[0]));
+      if (!std::isfinite(hn)) {
+        ctx->err = "non-finite Krylov vector";
+        return RSC_ENAN;
+      }
+      const double a = H[(size_t)c * kmax + c];
+      const double rr = std::hypot(a, hn);
+      cs[c] = (rr == 0.0) ? 1.0 : a / rr;
+      sn[c] = (rr == 0.0) ? 0.0 : hn / rr;
+      H[(size_t)c * kmax + c] = rr;
+      gvec[c + 1] = -sn[c] * gvec[c];
+      gvec[c] = cs[c] * gvec[c];
+      res = std::fabs(gvec[c + 1]);
+      ncols = k;
+      if (res <= tol * beta || hn == 0.0) break;
+    }
+    if (!next) break;
+    // new row of L, then (I + L) h = s
+    const double* sv = h_in + 1;
+    const double* tv = h_in + k + 2;
+    double* Lk = Lr(k);
+    for (int j = 0; j < k; ++j) Lk[j] = tv[j];
+    for (int i = 0; i <= k; ++i) {
+      double a = sv[i];
+      const double* Li = Lr(i);
+      for (int j = 0; j < i; ++j) a -= Li[j] * h_out[j];
+      h_out[i] = a;
+    }
+    if (!std::isfinite(h_out[k])) {
       ctx->err = "non-finite Krylov vector";
       return RSC_ENAN;
     }
-    H[(size_t)(k + 1) * kmax + k] = hn;
-    // Givens rotations
+    // Hessenberg column k with the earlier rotations applied (rows 0..k)
+    for (int i = 0; i <= k; ++i) H[(size_t)i * kmax + k] = h_out[i];
     for (int i = 0; i < k; ++i) {
       const double a = H[(size_t)i * kmax + k], bb = H[(size_t)(i + 1) * kmax + k];
       H[(size_t)i * kmax + k] = cs[i] * a + sn[i] * bb;
       H[(size_t)(i + 1) * kmax + k] = -sn[i] * a + cs[i] * bb;
     }
-    const double a = H[(size_t)k * kmax + k], bb = H[(size_t)(k + 1) * kmax + k];
-    const double rr = std::hypot(a, bb);
-    cs[k] = (rr == 0.0) ? 1.0 : a / rr;
-    sn[k] = (rr == 0.0) ? 0.0 : bb / rr;
-    H[(size_t)k * kmax + k] = rr;
-    H[(size_t)(k + 1) * kmax + k] = 0.0;
-    gvec[k + 1] = -sn[k] * gvec[k];
-    gvec[k] = cs[k] * gvec[k];
-    res = std::fabs(gvec[k + 1]);
-    if (res <= tol * beta || hn == 0.0) {
-      ++k;
-      break;
+    CK(cudaMemcpyAsync(d_h, h_out, (k + 1) * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+    {
+      KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (k + 3), 2.0 * n * (k + 2));
+      k_axpy_norm<<<nb, 256, 0, ctx->s>>>(V, ld, k + 1, d_h, w, n, ctx->partial);
+      CK(cudaGetLastError());
+    }
+    {
+      KSpan sp(ctx, RSC_K_BLAS, 8.0 * nb, 1.0 * nb);
+      k_reduce_rows<<<1, 256, 0, ctx->s>>>(ctx->partial, nb, dbuf);
+      CK(cudaGetLastError());
     }
     {
       KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 1.0 * n);
-      k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / hn, w, 0.0, w, n);
+      k_scale_inv_sqrt<<<nb, 256, 0, ctx->s>>>(w, n, dbuf);
       CK(cudaGetLastError());
     }
   }
-  const int kk = std::min(k, kmax);
+  const int kk = ncols;
   std::vector<double> y(kk, 0.0);
   for (int i = kk - 1; i >= 0; --i) {
     double s = gvec[i];
     for (int q = i + 1; q < kk; ++q) s -= H[(size_t)i * kmax + q] * y[q];
     y[i] = s / H[(size_t)i * kmax + i];
   }
-  CK(cudaMemcpyAsync(ctx->dots, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+  for (int i = 0; i < kk; ++i) h_out[i] = y[i];
+  CK(cudaMemcpyAsync(d_h, h_out, kk * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
   {
     KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (kk + 2), 2.0 * n * kk);
-    k_multi_axpy2<<<nb, 256, 0, ctx->s>>>(V, n, kk, ctx->dots, 1.0, x, n);
+    k_multi_axpy2<<<nb, 256, 0, ctx->s>>>(V, ld, kk, d_h, 1.0, x, n);
     CK(cudaGetLastError());
   }
   CK(cudaStreamSynchronize(ctx->s));
   *iters = kk;
   *relres = res / beta;
+  return RSC_OK;
+}
+
+// Kinetic energy and Nusselt numbers of U (diagnostics of Secs. 4-5).
+rsc_status diagnostics(rsc_ctx* ctx, const double* U, double out[3]) {
+  const Dims& d = ctx->d;
+  if (!ctx->d_diag) {
+    const int nq = 2 * d.Nr + 16;
+    std::vector<double> x, w;
+    gauss_legendre(nq, x, w);
+    const double h = 0.5 * (d.r_out - d.r_in), dxdr = 1.0 / h;
+    std::vector<double> T((size_t)nq * d.Nr), dT((size_t)nq * d.Nr), r(nq), wq(nq);
+    for (int q = 0; q < nq; ++q) {
+      const double th = std::acos(x[q]), st = std::sin(th);
+      r[q] = h * x[q] + 0.5 * (d.r_out + d.r_in);
+      wq[q] = h * w[q];
+      for (int k = 0; k < d.Nr; ++k) {
+        T[(size_t)q * d.Nr + k] = std::cos(k * th);
+        dT[(size_t)q * d.Nr + k] = k * std::sin(k * th) / st * dxdr;   // T_k' = k U_{k-1}
+      }
+    }
+    rsc_status st;
+    if ((st = upload(ctx, &ctx->d_keT, T.data(), T.size())) != RSC_OK) return st;
+    if ((st = upload(ctx, &ctx->d_kedT, dT.data(), dT.size())) != RSC_OK) return st;
+    if ((st = upload(ctx, &ctx->d_ker, r.data(), r.size())) != RSC_OK) return st;
+    if ((st = upload(ctx, &ctx->d_kew, wq.data(), wq.size())) != RSC_OK) return st;
+    CK(cudaMalloc((void**)&ctx->d_diag, 3 * sizeof(double)));
+    ctx->ke_nq = nq;
+  }
+  const double V = 4.0 * M_PI * (std::pow(d.r_out, 3) - std::pow(d.r_in, 3)) / 3.0;
+  const double g_in = -d.r_out * d.r_in / (d.r_in * d.r_in);
+  const double g_out = -d.r_out * d.r_in / (d.r_out * d.r_out);
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 16.0 * d.P * d.Nr * 2, 12.0 * d.P * d.Nr * ctx->ke_nq);
+    k_ke_pairs<<<d.P, 128, 2 * d.Nr * sizeof(double2), ctx->s>>>(
+        U, d.P, d.Nr, ctx->ke_nq, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_pair_l,
+        ctx->d_pair_m, ctx->partial);
+    CK(cudaGetLastError());
+  }
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 8.0 * d.P, 1.0 * d.P);
+    k_diag_finish<<<1, 256, 0, ctx->s>>>(ctx->partial, d.P, U, d.Nr, 0.5 / V,
+                                         2.0 / (d.r_out - d.r_in), g_in, g_out, ctx->d_diag);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_diag, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                     ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  for (int i = 0; i < 3; ++i) out[i] = ctx->h_pinned[i];
   return RSC_OK;
 }
 
@@ -996,8 +1108,8 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = alloc((void**)&ctx->xtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->vtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->rtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
-  ctx->nblk_dot = (int)std::max<long>((n + 2047) / 2048, 304);
-  if ((st = alloc((void**)&ctx->partial, (size_t)ctx->nblk_dot * (kMaxKrylov + 2) * sizeof(double))) != RSC_OK)
+  ctx->nblk_dot = (int)std::max<long>((n + 1023) / 1024, 152L * 8);   // pass-A chunks, pass-B blocks
+  if ((st = alloc((void**)&ctx->partial, (size_t)ctx->nblk_dot * (2 * kMaxKrylov + 4) * sizeof(double))) != RSC_OK)
     return fail(st);
   if ((st = alloc((void**)&ctx->dots, (size_t)(3 * kMaxKrylov + 8) * sizeof(double))) != RSC_OK)
     return fail(st);
@@ -1020,7 +1132,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
                   ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->partial,
-                  ctx->dots};
+                  ctx->dots, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
   for (void* b : bufs) cudaFree(b);
   for (int q = 0; q < 8; ++q) {
     cudaFree(ctx->leg64.buf[q]);
@@ -1169,6 +1281,17 @@ rsc_status rsc_launch_count(const rsc_ctx* ctx, long* count) {
 rsc_status rsc_norm2(rsc_ctx* ctx, const double* v, size_t n, double* out) {
   if (!ctx || !v || !out) return RSC_EINVAL;
   return norm2(ctx, v, (long)n, out);
+}
+
+rsc_status rsc_diagnostics(rsc_ctx* ctx, const double* U, double* KE, double* Nu_in,
+                           double* Nu_out) {
+  if (!ctx || !U) return RSC_EINVAL;
+  double v[3];
+  CKS(diagnostics(ctx, U, v));
+  if (KE) *KE = v[0];
+  if (Nu_in) *Nu_in = v[1];
+  if (Nu_out) *Nu_out = v[2];
+  return RSC_OK;
 }
 
 rsc_status rsc_newton_rw(rsc_ctx* ctx, double* U, double* C, long J, const rsc_newton_opts* o,

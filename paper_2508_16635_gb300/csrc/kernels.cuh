@@ -943,29 +943,6 @@ __global__ void k_temp_solve(DevGeom g, const double* __restrict__ Tinv,
 
 // ---------------------------------------------------------------------------
 // GMRES / Newton BLAS-1 (FP64).
-// partial[j * nblk + b] = sum over block b's chunk of V_j . w
-__global__ void k_dots(const double* __restrict__ V, long ld, int nv, const double* __restrict__ w,
-                       long n, double* __restrict__ partial) {
-  __shared__ double red[32];
-  const int j = blockIdx.y;
-  const double* v = V + (long)j * ld;
-  double s = 0.0;
-  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-       idx += (long)gridDim.x * blockDim.x)
-    s = fma(v[idx], w[idx], s);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) partial[(long)j * gridDim.x + blockIdx.x] = s;
-  }
-  (void)nv;
-}
-
 // Tiled V^T w: block b owns elements [b * 2048, (b+1) * 2048) (8 per thread),
 // keeps its slice of w in registers and streams every V_j over it; per-warp
 // sums go to shared memory, one cross-warp pass writes partial[j * nblk + b].
@@ -1074,6 +1051,119 @@ __global__ void __launch_bounds__(256) k_dots_split(const double* __restrict__ V
   }
 }
 
+// First pass of the one-reduction modified Gram-Schmidt step (the low-synchronisation
+// MGS of Swirydowicz, Langou, Ananthan, Yang, Thomas, Numer. Linear Algebra Appl. 2021):
+// one read of the basis gives both V^T w and V^T q (q = the newest basis vector, whose
+// products with the older vectors form the new row of the strictly lower Gram matrix).
+// Block (c, g) stages elements [c * 1024, (c+1) * 1024) of w and q in shared memory;
+// warp u then streams basis vectors j = 16 g + u and 16 g + 8 + u over that chunk
+// (16 double2 loads per lane issued together) and writes
+//   partial[j * nchunk + c] = V_j . w,   partial[(nv + j) * nchunk + c] = V_j . q.
+// grid = (ld / 1024, ceil(nv / 16)), block = 256.  The basis columns (and w, q) are
+// padded to ld, a multiple of 1024, with zeros beyond the vector length, so no
+// element needs a bounds check.  On GB300 this pass is bound by the FP64 FMA rate
+// (two FMAs per basis element), not by HBM.
+__global__ void __launch_bounds__(256) k_dots_pair(const double* __restrict__ V, long ld, int nv,
+                                                   const double* __restrict__ w,
+                                                   const double* __restrict__ q,
+                                                   double* __restrict__ partial) {
+  constexpr int E2 = 512, PER = E2 / 32;
+  __shared__ double2 ws[E2], qs[E2];
+  const long b2 = (long)blockIdx.x * E2;
+  const double2* w2 = reinterpret_cast<const double2*>(w) + b2;
+  const double2* q2 = reinterpret_cast<const double2*>(q) + b2;
+  for (int i = threadIdx.x; i < E2; i += blockDim.x) {
+    ws[i] = w2[i];
+    qs[i] = q2[i];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunk = gridDim.x;
+#pragma unroll 1
+  for (int r = 0; r < 2; ++r) {
+    const int j = blockIdx.y * 16 + warp + 8 * r;
+    if (j >= nv) break;
+    const double2* v2 = reinterpret_cast<const double2*>(V + (long)j * ld) + b2 + lane;
+    double2 vv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) vv[u] = __ldcs(v2 + u * 32);
+    double a = 0.0, b = 0.0;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const double2 x = ws[u * 32 + lane], y = qs[u * 32 + lane];
+      a = fma(vv[u].x, x.x, fma(vv[u].y, x.y, a));
+      b = fma(vv[u].x, y.x, fma(vv[u].y, y.y, b));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      partial[(long)j * nchunk + blockIdx.x] = a;
+      partial[(long)(nv + j) * nchunk + blockIdx.x] = b;
+    }
+  }
+}
+
+// Second pass of the one-reduction MGS step: w <- w - sum_j h[j] V_j with double2 loads
+// (eight basis vectors per iteration), and partial[b] = block b's share of |w_new|^2.
+// grid = nb (grid-stride over double2 elements), block = 256.  Same alignment rule.
+__global__ void __launch_bounds__(256) k_axpy_norm(const double* __restrict__ V, long ld, int nv,
+                                                   const double* __restrict__ h,
+                                                   double* __restrict__ w, long n,
+                                                   double* __restrict__ partial) {
+  __shared__ double red[8];
+  const long n2 = n >> 1;
+  double2* w2 = reinterpret_cast<double2*>(w);
+  double ss = 0.0;
+  for (long i2 = (long)blockIdx.x * blockDim.x + threadIdx.x; i2 < n2;
+       i2 += (long)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0, tx = 0.0, ty = 0.0;
+    int j = 0;
+    for (; j + 8 <= nv; j += 8) {
+      double2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = reinterpret_cast<const double2*>(V + (long)(j + u) * ld)[i2];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const double c0 = h[j + u], c1 = h[j + u + 1];
+        sx = fma(c0, v[u].x, sx); sy = fma(c0, v[u].y, sy);
+        tx = fma(c1, v[u + 1].x, tx); ty = fma(c1, v[u + 1].y, ty);
+      }
+    }
+    for (; j < nv; ++j) {
+      const double2 v = reinterpret_cast<const double2*>(V + (long)j * ld)[i2];
+      sx = fma(h[j], v.x, sx);
+      sy = fma(h[j], v.y, sy);
+    }
+    double2 o = w2[i2];
+    o.x -= sx + tx;
+    o.y -= sy + ty;
+    w2[i2] = o;
+    ss = fma(o.x, o.x, fma(o.y, o.y, ss));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int r = 0; r < (int)(blockDim.x >> 5); ++r) a += red[r];
+    partial[blockIdx.x] = a;
+  }
+}
+
+// w <- w / sqrt(nrm2[0]) (left unchanged when nrm2[0] is zero: a breakdown the host sees).
+__global__ void k_scale_inv_sqrt(double* __restrict__ w, long n, const double* __restrict__ nrm2) {
+  const double s2 = nrm2[0];
+  if (!(s2 > 0.0)) return;
+  const double inv = 1.0 / sqrt(s2);
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x)
+    w[idx] *= inv;
+}
+
 // w += sign * sum_j coef[j] V_j with double2 loads, eight vectors per iteration.
 // Requires n even and 16-byte aligned V, w (ld even).
 __global__ void k_multi_axpy2(const double* __restrict__ V, long ld, int nv,
@@ -1126,25 +1216,6 @@ __global__ void k_reduce_rows(const double* __restrict__ partial, int nblk, doub
   }
 }
 
-// w += sign * sum_j coef[j] V_j  (four independent accumulators for memory parallelism)
-__global__ void k_multi_axpy(const double* __restrict__ V, long ld, int nv,
-                             const double* __restrict__ coef, double sign, double* __restrict__ w,
-                             long n) {
-  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-       idx += (long)gridDim.x * blockDim.x) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int j = 0;
-    for (; j + 4 <= nv; j += 4) {
-      s0 = fma(coef[j], V[(long)j * ld + idx], s0);
-      s1 = fma(coef[j + 1], V[(long)(j + 1) * ld + idx], s1);
-      s2 = fma(coef[j + 2], V[(long)(j + 2) * ld + idx], s2);
-      s3 = fma(coef[j + 3], V[(long)(j + 3) * ld + idx], s3);
-    }
-    for (; j < nv; ++j) s0 = fma(coef[j], V[(long)j * ld + idx], s0);
-    w[idx] = fma(sign, (s0 + s1) + (s2 + s3), w[idx]);
-  }
-}
-
 // y = a * x + b * y
 __global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y,
                         long n) {
@@ -1193,6 +1264,88 @@ __global__ void k_copy_zero_slot(const double* __restrict__ u, long J, double* _
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long)gridDim.x * blockDim.x)
     x[idx] = (idx == J) ? 0.0 : u[idx];
+}
+
+
+// ---------------------------------------------------------------------------
+// Diagnostics (kinetic energy and Nusselt numbers).
+// Kinetic energy of one pair by Parseval's identity for the potentials of
+// Sec. 2.1: int |U|^2 dOmega = w_m [l(l+1)|e|^2/r^2 + (l(l+1))^2 |f|^2/r^4
+// + l(l+1)|d_r f|^2/r^2], w_m = 4 pi (m = 0) or 16 pi (m > 0, the real field
+// a Y + conj(a Y)), integrated against r^2 dr with the Gauss-Legendre rule
+// (rq, wq; wq includes dr/dx).  Tq[q][k] = T_k(x_q), dTq[q][k] = d T_k/dr.
+// grid = P, block = 128, dynamic smem = 2 Nr double2.
+__global__ void k_ke_pairs(const double* __restrict__ U, int P, int Nr, int nq,
+                           const double* __restrict__ Tq, const double* __restrict__ dTq,
+                           const double* __restrict__ rq, const double* __restrict__ wq,
+                           const int* __restrict__ pair_l, const int* __restrict__ pair_m,
+                           double* __restrict__ partial) {
+  extern __shared__ double2 kes[];
+  __shared__ double red[32];
+  const int p = blockIdx.x;
+  const double2* U2 = reinterpret_cast<const double2*>(U);
+  for (int k = threadIdx.x; k < Nr; k += blockDim.x) {
+    kes[k] = U2[(long)p * Nr + k];                 // e
+    kes[Nr + k] = U2[((long)P + p) * Nr + k];      // f
+  }
+  __syncthreads();
+  const double lam = pair_l[p] * (pair_l[p] + 1.0);
+  double s = 0.0;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    double er = 0, ei = 0, fr = 0, fi = 0, gr = 0, gi = 0;
+    for (int k = 0; k < Nr; ++k) {
+      const double t = Tq[(long)q * Nr + k], dt = dTq[(long)q * Nr + k];
+      const double2 e = kes[k], f = kes[Nr + k];
+      er = fma(t, e.x, er); ei = fma(t, e.y, ei);
+      fr = fma(t, f.x, fr); fi = fma(t, f.y, fi);
+      gr = fma(dt, f.x, gr); gi = fma(dt, f.y, gi);
+    }
+    const double r = rq[q], ir2 = 1.0 / (r * r);
+    const double dens = lam * (er * er + ei * ei) * ir2 +
+                        lam * lam * (fr * fr + fi * fi) * ir2 * ir2 +
+                        lam * (gr * gr + gi * gi) * ir2;
+    s = fma(wq[q] * r * r, dens, s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
+    const double pi = 3.141592653589793238;
+    partial[p] = (pair_m[p] == 0 ? 4.0 * pi : 16.0 * pi) * a;
+  }
+}
+
+// out[0] = KE = (1/2) sum_p partial[p] / V; out[1], out[2] = Nu at r_in, r_out:
+// d_r of the mean temperature T_00 at each wall (T'_k(+-1) = (+-1)^(k+1) k^2)
+// over the conductive gradient g_in, g_out.  One block of 256 threads.
+__global__ void k_diag_finish(const double* __restrict__ partial, int P,
+                              const double* __restrict__ U, int Nr, double inv_2V,
+                              double dxdr, double g_in, double g_out, double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) s += partial[p];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
+    out[0] = a * inv_2V;
+    // T_00: field 2, pair 0 (m = 0, l = 0), real parts
+    const double* T00 = U + 2L * P * Nr * 2;
+    double din = 0.0, dout = 0.0;
+    for (int k = 0; k < Nr; ++k) {
+      const double k2 = (double)k * k;
+      dout = fma(k2, T00[2 * k], dout);
+      din = fma((k & 1) ? k2 : -k2, T00[2 * k], din);
+    }
+    out[1] = din * dxdr / g_in;
+    out[2] = dout * dxdr / g_out;
+  }
 }
 
 }  // namespace rsc

@@ -59,6 +59,8 @@ void build_tables(const rsc_params& p, const Dims& d, HostTables& t);
 // Returns 0 on success, or 1 + chain index of a singular block.
 int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double dt,
                  HostFactor& f);
+// Gauss-Legendre nodes (descending from +1) and weights on [-1, 1].
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 void conductive_T00(const rsc_params& p, const Dims& d, const HostTables& t,
                     std::vector<double>& coef);
 

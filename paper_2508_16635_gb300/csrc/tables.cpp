@@ -83,7 +83,7 @@ static void cheb_table(int npts, int nk, int order, double r_in, double r_out,
   }
 }
 
-static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.resize(n);
   w.resize(n);
   for (int i = 0; i < n; ++i) {

@@ -22,7 +22,8 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_conductive_state", "rsc_step", "rsc_step_host", "rsc_explicit_terms",
            "rsc_apply_jacobian", "rsc_newton_rw", "rsc_newton_rw_host", "rsc_norm2",
            "rsc_last_error", "rsc_status_string", "rsc_abi_version", "rsc_profile_enable",
-           "rsc_profile_query", "rsc_kernel_name", "rsc_launch_count", "rsc_norm2_noalloc")
+           "rsc_profile_query", "rsc_kernel_name", "rsc_launch_count", "rsc_norm2_noalloc",
+           "rsc_diagnostics")
 NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
            "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
@@ -97,6 +98,7 @@ def load_library(path=LIB_PATH):
         "rsc_kernel_name": ([I], ctypes.c_char_p),
         "rsc_launch_count": ([P, ctypes.POINTER(ctypes.c_long)], I),
         "rsc_norm2_noalloc": ([P, ctypes.c_size_t, P, P], I),
+        "rsc_diagnostics": ([P, P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -251,6 +253,13 @@ class RotatingShell:
         c = ctypes.c_long()
         self._check(self.lib.rsc_launch_count(self._ctx, ctypes.byref(c)))
         return c.value
+
+    def diagnostics(self, U):
+        """(KE, Nu_in, Nu_out) of the device state U (rsc_diagnostics)."""
+        ke, ni, no = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.rsc_diagnostics(self._ctx, _ptr(U), ctypes.byref(ke), ctypes.byref(ni),
+                                             ctypes.byref(no)))
+        return ke.value, ni.value, no.value
 
     def norm2(self, v):
         out = ctypes.c_double()

@@ -253,3 +253,23 @@ def test_explicit_and_implicit_coriolis_reach_the_same_wave_on_the_gpu(torch):
     Ue, Ce, ge = res["explicit"]
     assert _rel(Ue, Ui) < 1e-8 and abs(Ce - Ci) < 1e-8 * abs(Ci)
     assert ge > gi
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES)
+def test_diagnostics_parity(torch, name, L, Ms, Nr, Ek, Ra):
+    """rsc_diagnostics (Parseval on the GPU) against the oracle's grid quadrature."""
+    from paper_2508_16635_gb300 import RotatingShell
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra)
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=33, amp=3e-2)
+    ke, nu_in, nu_out = gpu.diagnostics(torch.tensor(x, device="cuda"))
+    ke_o = s.kinetic_energy(x)
+    nu_in_o, nu_out_o = s.nusselt(x)
+    assert abs(ke - ke_o) < 1e-11 * ke_o
+    assert abs(nu_in - nu_in_o) < 1e-11 * abs(nu_in_o)
+    assert abs(nu_out - nu_out_o) < 1e-11 * abs(nu_out_o)
+    cond = s.conductive_state()
+    ke0, n0, n1 = gpu.diagnostics(torch.tensor(cond, device="cuda"))
+    c_in, c_out = s.nusselt(cond)       # 1 up to the N_r truncation of the 1/r profile
+    assert ke0 == 0.0 and abs(n0 - c_in) < 1e-11 and abs(n1 - c_out) < 1e-11
+    gpu.close()
