@@ -430,6 +430,46 @@ class Shell:
             x = self.solve(self.apply_rows(rhs, homogeneous=False), dt)
         return self.to_real(x)
 
+    def diffusion(self, x):
+        """The diffusive part of K applied to x at the collocation radii, [3, P, N_r]."""
+        out = np.zeros_like(x)
+        r = self._rows()
+        for p in range(self.P):
+            l = int(self.pair_l[p])
+            for fi, fl in enumerate(FIELDS):
+                out[fi, p] = self.diffusion_rows(fl, l, self.E, r) @ x[fi, p]
+        return out
+
+    def step2(self, vec, dt=1e-4, nsteps=1):
+        """Second-order time step in the laboratory frame (the scheme of the time-stepping
+        runs of Sec. 5, which combines a Runge-Kutta predictor-corrector with the implicit
+        treatment of the linear operator).  Reading: Crank-Nicolson for the implicit
+        operator K (diffusion, plus Coriolis when implicit) and Heun's predictor-corrector
+        for the explicit terms N (products, buoyancy, plus Coriolis when explicit):
+            (M/dt + K/2) x*      = (M/dt - K/2) x^n + N(x^n)
+            (M/dt + K/2) x^{n+1} = (M/dt - K/2) x^n + (N(x^n) + N(x*)) / 2
+        with the boundary rows of Eq. BCs.  M/dt + K/2 = (M (2/dt) + K)/2 is solved with
+        the factorisation at dt/2 and a doubled right-hand side."""
+        x = self.to_complex(vec)
+
+        def explicit(z):
+            n = self.explicit_terms(z)
+            if self.coriolis == "explicit":
+                n = n - self.coriolis_terms(z)
+            return n
+
+        for _ in range(nsteps):
+            Kx = self.diffusion(x)
+            if self.coriolis == "implicit":
+                Kx = Kx + self.coriolis_terms(x)
+            base = self.mass(x) / dt - 0.5 * Kx
+            Nx = explicit(x)
+            xs = self.solve(self.apply_rows(2.0 * (base + Nx), homogeneous=False), 0.5 * dt)
+            Ns = explicit(xs)
+            x = self.solve(self.apply_rows(2.0 * (base + 0.5 * (Nx + Ns)), homogeneous=False),
+                           0.5 * dt)
+        return self.to_real(x)
+
     def jvp(self, Uvec, C, J, uvec, dt, gU=None):
         """(B_U - I) applied to (u, c) with c stored in slot J (Secs. 3.3-3.4).
 
