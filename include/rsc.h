@@ -129,6 +129,18 @@ rsc_status rsc_conductive_state(rsc_ctx* ctx, double* U);
  * (Eqs. impcor_e_final, impcor_f_final); it is factorised once per dt.     */
 rsc_status rsc_step(rsc_ctx* ctx, double* U, double C, double dt, int nsteps);
 
+/* nsteps second-order steps in place in the laboratory frame (no drift term),
+ * the time-stepping scheme of Sec. 5 (a Runge-Kutta predictor-corrector with
+ * the linear operator treated implicitly; Table 1 measures its drift error).
+ * Reading: Crank-Nicolson for the implicit operator K (diffusion, plus
+ * Coriolis unless explicit_coriolis) and Heun's predictor-corrector for the
+ * explicit terms N:
+ *   (M/dt + K/2) x*      = (M/dt - K/2) x^n + N(x^n)
+ *   (M/dt + K/2) x^{n+1} = (M/dt - K/2) x^n + (N(x^n) + N(x*))/2.
+ * U must satisfy the boundary conditions (every state the library writes
+ * does).  The implicit operator is factorised at dt/2.                      */
+rsc_status rsc_step2(rsc_ctx* ctx, double* U, double dt, int nsteps);
+
 /* Same as rsc_step on a HOST buffer: copies to the device, steps, copies
  * back (synchronous).  For end-to-end timing.                              */
 rsc_status rsc_step_host(rsc_ctx* ctx, double* U_host, double C, double dt, int nsteps);

@@ -64,6 +64,7 @@ struct rsc_ctx {
   LegDev<float> leg32;
   // workspace (sized for FP64; the FP32 path uses the front part)
   void *SR = nullptr, *FC = nullptr, *FCU = nullptr, *FA = nullptr, *AR = nullptr;
+  void* AR0 = nullptr;   // analysed products of x^n during a second-order step
   double2* rhs = nullptr;
   double2* mid = nullptr;   // chain sweep staging, [2 nm][3][Nr]
   double* xtmp = nullptr;
@@ -460,7 +461,7 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
 
 template <typename R>
 rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const double* U,
-                     const double* u_orig, double2* out) {
+                     const double* u_orig, double2* out, const double* xe = nullptr) {
   using V = typename C2<R>::T;
   const Dims& d = ctx->d;
   const int PPB = std::max(1, 256 / round32(d.Nr));
@@ -471,7 +472,8 @@ rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const d
            d.P * (double)d.Nr * (16.0 * d.Nd + 32.0 * d.Nr));
   k_rhs<R><<<(d.P + PPB - 1) / PPB, dim3(round32(d.Nr), PPB), smem, ctx->s>>>(
       ctx->geom(), rp, reinterpret_cast<const V*>(ctx->AR), reinterpret_cast<const double2*>(x),
-      reinterpret_cast<const double2*>(U), u_orig, out);
+      reinterpret_cast<const double2*>(U), u_orig,
+      reinterpret_cast<const double2*>(xe ? xe : x), out);
   CK(cudaGetLastError());
   return RSC_OK;
 }
@@ -619,6 +621,66 @@ rsc_status do_step(rsc_ctx* ctx, double* U, double C, double dt) {
   return RSC_OK;
 }
 
+rsc_status launch_1d_grid(long n, int* blocks) {
+  *blocks = (int)std::min<long>((n + 255) / 256, 152L * 8);
+  return RSC_OK;
+}
+
+// One second-order step in the laboratory frame, in place (Crank-Nicolson for the
+// implicit operator, Heun's predictor-corrector for the explicit terms; the time-stepping
+// scheme of Sec. 5).  Each Crank-Nicolson solve
+//     (M/dt + K/2) x' = (M/dt - K/2) x + N
+// is carried out as the half step (M (2/dt) + K) y = (2/dt) M x + N, x' = 2 y - x, whose
+// boundary rows are (bc + B x)/2; so both solves use the factorisation at dt/2 and the
+// right-hand-side kernel of the Euler step, and K x is never formed.  Predictor: N = N(x);
+// corrector: N = (N(x) + N(x*))/2 with the products averaged after analysis and the
+// linear explicit terms (buoyancy, explicit Coriolis) taken at (x + x*)/2.
+template <typename R>
+rsc_status do_step2(rsc_ctx* ctx, double* U, double dt) {
+  using V = typename C2<R>::T;
+  const long n = ctx->d.n();
+  const long nar = (long)ctx->d.P * ctx->d.Nd * 4;
+  int nb;
+  launch_1d_grid(n, &nb);
+  DevFactor* f = nullptr;
+  CKS(get_factor(ctx, 0.5 * dt, &f));
+  const RhsParams rp = make_rp(ctx, 0.5 * dt, 0.0, 3);
+  // predictor: x* = 2 y* - x
+  CKS(stage_synth<R>(ctx, U, ctx->FC));
+  CKS(stage_products_analysis<R>(ctx, false));
+  CK(cudaMemcpyAsync(ctx->AR0, ctx->AR, nar * sizeof(V), cudaMemcpyDeviceToDevice, ctx->s));
+  CKS(stage_rhs<R>(ctx, rp, U, nullptr, nullptr, ctx->rhs));
+  CKS(stage_solve(ctx, f, ctx->vtmp));
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
+    k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, U, 2.0, ctx->vtmp, n);
+    CK(cudaGetLastError());
+  }
+  // corrector
+  CKS(stage_synth<R>(ctx, ctx->vtmp, ctx->FC));
+  CKS(stage_products_analysis<R>(ctx, false));
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 3.0 * nar * sizeof(V), 2.0 * nar);
+    k_average<R><<<nb, 256, 0, ctx->s>>>(reinterpret_cast<V*>(ctx->AR),
+                                        reinterpret_cast<const V*>(ctx->AR0), nar);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(ctx->xtmp, U, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
+    k_axpby<<<nb, 256, 0, ctx->s>>>(0.5, ctx->vtmp, 0.5, ctx->xtmp, n);
+    CK(cudaGetLastError());
+  }
+  CKS(stage_rhs<R>(ctx, rp, U, nullptr, nullptr, ctx->rhs, ctx->xtmp));
+  CKS(stage_solve(ctx, f, ctx->vtmp));
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
+    k_axpby<<<nb, 256, 0, ctx->s>>>(2.0, ctx->vtmp, -1.0, U, n);
+    CK(cudaGetLastError());
+  }
+  return RSC_OK;
+}
+
 rsc_status step_any(rsc_ctx* ctx, double* U, double C, double dt, bool fp32) {
   return fp32 ? do_step<float>(ctx, U, C, dt) : do_step<double>(ctx, U, C, dt);
 }
@@ -626,11 +688,6 @@ rsc_status step_any(rsc_ctx* ctx, double* U, double C, double dt, bool fp32) {
 // Base-state grid coefficients for Jacobian actions.
 rsc_status cache_base(rsc_ctx* ctx, const double* U, bool fp32) {
   return fp32 ? stage_synth<float>(ctx, U, ctx->FCU) : stage_synth<double>(ctx, U, ctx->FCU);
-}
-
-rsc_status launch_1d_grid(long n, int* blocks) {
-  *blocks = (int)std::min<long>((n + 255) / 256, 152L * 8);
-  return RSC_OK;
 }
 
 // out = (B_U - I) u with the drift unknown in slot J (Sec. 3.4); base cached.
@@ -1100,6 +1157,7 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = alloc(&ctx->FCU, 9 * (size_t)d.Nd * K1 * d.nlat * c16)) != RSC_OK) return fail(st);
   if ((st = alloc(&ctx->FA, 4 * (size_t)d.Nd * K1 * d.nlat * c16)) != RSC_OK) return fail(st);
   if ((st = alloc(&ctx->AR, (size_t)d.P * d.Nd * 4 * c16)) != RSC_OK) return fail(st);
+  if ((st = alloc(&ctx->AR0, (size_t)d.P * d.Nd * 4 * c16)) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->rhs, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->mid, (size_t)2 * d.nm * 3 * d.Nr * c16)) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->d_slots, 2 * sizeof(double*))) != RSC_OK) return fail(st);
@@ -1132,7 +1190,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
                   ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->partial,
-                  ctx->dots, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
+                  ctx->dots, ctx->AR0, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
   for (void* b : bufs) cudaFree(b);
   for (int q = 0; q < 8; ++q) {
     cudaFree(ctx->leg64.buf[q]);
@@ -1198,6 +1256,14 @@ rsc_status rsc_step(rsc_ctx* ctx, double* U, double C, double dt, int nsteps) {
   if (!ctx || !U || nsteps < 0 || !(dt > 0)) return RSC_EINVAL;
   const bool fp32 = ctx->p.precision == RSC_MIXED;
   for (int s = 0; s < nsteps; ++s) CKS(step_any(ctx, U, C, dt, fp32));
+  return RSC_OK;
+}
+
+rsc_status rsc_step2(rsc_ctx* ctx, double* U, double dt, int nsteps) {
+  if (!ctx || !U || nsteps < 0 || !(dt > 0)) return RSC_EINVAL;
+  const bool fp32 = ctx->p.precision == RSC_MIXED;
+  for (int s = 0; s < nsteps; ++s)
+    CKS(fp32 ? do_step2<float>(ctx, U, dt) : do_step2<double>(ctx, U, dt));
   return RSC_OK;
 }
 

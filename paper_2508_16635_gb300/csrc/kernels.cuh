@@ -462,14 +462,16 @@ __global__ void k_analysis(DevGeom g, DevLegendre<R> T, const typename C2<R>::T*
 struct RhsParams {
   double inv_dt, C, Ek, Ra, r_out;
   long J;        // drift slot (Sec. 3.4), < 0 for none; c is read from u_orig[J]
-  int mode;
+  int mode;      // 0 step, 1 Jacobian action, 2 explicit terms only, 3 half step of the
+                 // second-order scheme (boundary rows (bc + B x)/2, linear explicit terms at xe)
   int explicit_coriolis;  // subtract the Coriolis rows of x (Eqs. expcor_e/f) in modes 0, 1
 };
 
 template <typename R>
 __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restrict__ AR,
                       const double2* __restrict__ x, const double2* __restrict__ U,
-                      const double* __restrict__ u_orig, double2* __restrict__ rhs) {
+                      const double* __restrict__ u_orig, const double2* __restrict__ xe,
+                      double2* __restrict__ rhs) {
   const int has_c = rp.J >= 0;
   using V = typename C2<R>::T;
   extern __shared__ double2 sh2[];
@@ -488,6 +490,9 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   double2* nb = reinterpret_cast<double2*>(ar + 4 * Nd);    // [4][Nr]: f_{l-1}, f_{l+1}, e_{l-1}, e_{l+1}
   const int p = blockIdx.x * blockDim.y + threadIdx.y;
   const bool coriolis_rhs = rp.explicit_coriolis && rp.mode != 2;
+  // mode 3: buoyancy and explicit Coriolis of the state xe (held in `us`)
+  const bool sep = rp.mode == 3 && xe != x;
+  const double2* xc = sep ? xe : x;     // source of the Coriolis neighbours
   if (p < P) {
     for (int idx = threadIdx.x; idx < 4 * Nd; idx += blockDim.x) ar[idx] = AR[(long)p * Nd * 4 + idx];
     for (int idx = threadIdx.x; idx < 3 * Nr; idx += blockDim.x) {
@@ -500,6 +505,7 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
         us[idx] = uv;
         if (low) uf[idx] = make_float2((float)uv.x, (float)uv.y);
       }
+      if (sep) us[idx] = xe[((long)f * P + p) * Nr + k];
     }
     if (coriolis_rhs) {
       const int lp = g.pair_l[p], mp = g.pair_m[p];
@@ -509,7 +515,7 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
         const int side = (w & 1) ? 1 : -1;
         const int l2 = lp + side;
         double2 v = make_double2(0, 0);
-        if (lp > 0 && l2 >= mp && l2 <= g.L) v = x[((long)fld * P + p + side) * Nr + k];
+        if (lp > 0 && l2 >= mp && l2 <= g.L) v = xc[((long)fld * P + p + side) * Nr + k];
         nb[idx] = v;
       }
     }
@@ -575,6 +581,13 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   };
   double2 Me, Mf, MT;
   mass(xs, xf, Me, Mf, MT);
+  // boundary values of x for the half step of the second-order scheme
+  const double2 bxe = e0v, bxf = f0v, bxT = MT;
+  double2 MTe = MT;   // temperature of the state whose buoyancy enters (xe in mode 3)
+  if (sep) {
+    double2 t0_, t1_;
+    mass(us, uf, t0_, t1_, MTe);   // also leaves e0v, f0v, f2v of xe for the Coriolis rows
+  }
   // explicit Coriolis rows (Eqs. impcor_e_final / impcor_f_final applied to x)
   double2 Ce = {0, 0}, Cf = {0, 0};
   if (coriolis_rhs && l > 0) {
@@ -605,7 +618,7 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
   // explicit terms (curl projections and buoyancy)
   double2 Ne = make_double2(lam * ir * Tc.x, lam * ir * Tc.y);
   const double cb = lam * rp.Ra * ir / rp.r_out;
-  double2 Nf = make_double2(lam * ir2 * (Qc.x - dS.x) + cb * MT.x, lam * ir2 * (Qc.y - dS.y) + cb * MT.y);
+  double2 Nf = make_double2(lam * ir2 * (Qc.x - dS.x) + cb * MTe.x, lam * ir2 * (Qc.y - dS.y) + cb * MTe.y);
   double2 NT = make_double2(-Nc.x, -Nc.y);
   double2 out[3];
   if (rp.mode == 2) {
@@ -631,12 +644,51 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
     // boundary rows (Sec. 3.1) and identity rows of e_00, f_00
     if (j == 0 || j == Nr - 1) { out[0] = make_double2(0, 0); out[2] = make_double2(0, 0); }
     if (j == 0 || j == 1 || j == Nr - 2 || j == Nr - 1) out[1] = make_double2(0, 0);
-    if (rp.mode == 0 && l == 0 && j == Nr - 1) out[2] = make_double2(1.0, 0.0);  // T(r_in) = 1
+    if ((rp.mode == 0 || rp.mode == 3) && l == 0 && j == Nr - 1)
+      out[2] = make_double2(1.0, 0.0);  // T(r_in) = 1
     if (l == 0) { out[0] = make_double2(0, 0); out[1] = make_double2(0, 0); }
+    if (rp.mode == 3) {
+      // the half step solves for y = (x^{n+1} + x)/2: boundary rows (bc + B x)/2 so that
+      // x^{n+1} = 2 y - x meets the boundary conditions exactly
+      auto half = [](double2 a, double2 b) { return make_double2(0.5 * (a.x + b.x), 0.5 * (a.y + b.y)); };
+      if (j == 0 || j == Nr - 1) {
+        out[0] = half(out[0], bxe);
+        out[2] = half(out[2], bxT);
+        out[1] = half(out[1], bxf);
+      }
+      if (j == 1 || j == Nr - 2) {
+        const int jj = (j == 1) ? 0 : Nr - 1;     // d_r f at the wall next to row j
+        double2 d1 = {0, 0};
+        for (int k = 0; k < Nr; ++k) {
+          const double c1 = g.EcT1[k * Nr + jj];
+          d1.x += c1 * xs[Nr + k].x;
+          d1.y += c1 * xs[Nr + k].y;
+        }
+        out[1] = half(out[1], d1);
+      }
+      if (l == 0) {   // identity rows of e_00, f_00: y = x / 2 keeps them at zero
+        out[0] = make_double2(0.5 * xs[j].x, 0.5 * xs[j].y);
+        out[1] = make_double2(0.5 * xs[Nr + j].x, 0.5 * xs[Nr + j].y);
+      }
+    }
     if (m == 0) { out[0].y = 0; out[1].y = 0; out[2].y = 0; }
   }
 #pragma unroll
   for (int f = 0; f < 3; ++f) rhs[((long)f * P + p) * Nr + j] = out[f];
+}
+
+// a <- (a + b) / 2 over n complex values in precision R (the Heun average of the analysed
+// products of the second-order scheme).
+template <typename R>
+__global__ void k_average(typename C2<R>::T* __restrict__ a, const typename C2<R>::T* __restrict__ b,
+                          long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    typename C2<R>::T v = a[i];
+    const typename C2<R>::T w = b[i];
+    v.x = (R)0.5 * (v.x + w.x);
+    v.y = (R)0.5 * (v.y + w.y);
+    a[i] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------

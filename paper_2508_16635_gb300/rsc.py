@@ -23,7 +23,7 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_apply_jacobian", "rsc_newton_rw", "rsc_newton_rw_host", "rsc_norm2",
            "rsc_last_error", "rsc_status_string", "rsc_abi_version", "rsc_profile_enable",
            "rsc_profile_query", "rsc_kernel_name", "rsc_launch_count", "rsc_norm2_noalloc",
-           "rsc_diagnostics")
+           "rsc_diagnostics", "rsc_step2")
 NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
            "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
@@ -98,6 +98,7 @@ def load_library(path=LIB_PATH):
         "rsc_kernel_name": ([I], ctypes.c_char_p),
         "rsc_launch_count": ([P, ctypes.POINTER(ctypes.c_long)], I),
         "rsc_norm2_noalloc": ([P, ctypes.c_size_t, P, P], I),
+        "rsc_step2": ([P, P, D, I], I),
         "rsc_diagnostics": ([P, P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)], I),
     }
     for name, (args, res) in sig.items():
@@ -181,6 +182,11 @@ class RotatingShell:
 
     def step(self, U, C=0.0, dt=1e-4, nsteps=1):
         self._check(self.lib.rsc_step(self._ctx, self._vec(U), C, dt, nsteps))
+        return U
+
+    def step2(self, U, dt=1e-4, nsteps=1):
+        """Second-order steps in the laboratory frame (rsc_step2), in place."""
+        self._check(self.lib.rsc_step2(self._ctx, self._vec(U), dt, nsteps))
         return U
 
     def step_host(self, U_host, C=0.0, dt=1e-4, nsteps=1):

@@ -273,3 +273,41 @@ def test_diagnostics_parity(torch, name, L, Ms, Nr, Ek, Ra):
     c_in, c_out = s.nusselt(cond)       # 1 up to the N_r truncation of the 1/r profile
     assert ke0 == 0.0 and abs(n0 - c_in) < 1e-11 and abs(n1 - c_out) < 1e-11
     gpu.close()
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES)
+@pytest.mark.parametrize("coriolis", ["implicit", "explicit"])
+def test_step2_parity(torch, name, L, Ms, Nr, Ek, Ra, coriolis):
+    """Second-order step (Crank-Nicolson + Heun): the GPU's half-step form against the
+    oracle's direct Crank-Nicolson form, FP64, from a state that meets the BCs."""
+    from paper_2508_16635_gb300 import RotatingShell
+    make = lambda: Shell(L, Ms, Nr, Ek, Ra, coriolis=coriolis)
+    dt = 2e-4
+    x = make().step(make().conductive_state() + si.perturbation(L, Ms, Nr, seed=24, amp=1e-2),
+                    0.0, dt)
+    want, spread = _oracle_spread(make, lambda s: s.step2(x, dt, nsteps=2))
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, coriolis=coriolis)
+    U = torch.tensor(x, device="cuda")
+    gpu.step2(U, dt, nsteps=2)
+    errs = _rel_fields(make(), U.cpu().numpy(), want)
+    # the GPU forms x' = 2 y - x from the half-step solution y, which doubles the solve's
+    # rounding error relative to the oracle's direct Crank-Nicolson solve
+    tol = [2.0 * t for t in _tolerances(spread)]
+    assert all(e < t for e, t in zip(errs, tol)), (errs, tol, spread)
+    gpu.close()
+
+
+def test_step2_mixed_precision_error(torch):
+    """The mixed path's second-order step (FP32 transforms) stays within 1e-5 of the oracle."""
+    from paper_2508_16635_gb300 import RotatingShell
+    L, Ms, Nr, Ek, Ra = 31, 4, 24, 1e-3, 120.0
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    dt = 2e-4
+    x = s.step(s.conductive_state() + si.perturbation(L, Ms, Nr, seed=25, amp=1e-2), 0.0, dt)
+    want = s.step2(x, dt, nsteps=3)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
+    U = torch.tensor(x, device="cuda")
+    gpu.step2(U, dt, nsteps=3)
+    errs = _rel_fields(s, U.cpu().numpy(), want)
+    assert max(errs) < 1e-5, errs
+    gpu.close()
