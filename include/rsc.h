@@ -168,6 +168,56 @@ rsc_status rsc_apply_jacobian(rsc_ctx* ctx, const double* U, double C, long J,
 rsc_status rsc_newton_rw(rsc_ctx* ctx, double* U, double* C, long J,
                          const rsc_newton_opts* opts, rsc_newton_report* report);
 
+/* Natural-parameter continuation in Ra (Sec. 4.3).  Points are Newton solves
+ * (Sec. 3.4) at successive Rayleigh numbers; the paper adds no equation to
+ * Newton's method and only chooses the next Ra and the initial estimate:
+ *   Ra^(i+1) = Ra^(i) + alpha (Ra^(i) - Ra^(i-1))              (Eq. new_Ra)
+ *   alpha = (n_opt + 1) / (N^(i) + 1), N^(i) the Newton iterations of the
+ *   last point                                                   (Eq. alpha_cont)
+ *   U^(i+1) = a U^(i) + b U^(i-1) + c U^(i-2) (and C likewise) with (a, b, c)
+ *   the Lagrange weights of the new Ra at the last three Ra    (Eq. lagrange)
+ * and near turning points (Eqs. tp_detection_Ra, quad_extra_Ra): while
+ * |Delta U_J / U_J| > gamma |Delta Ra / Ra|, with J the element of largest
+ * |U - U_cond| of the last point, U_J is extrapolated instead and
+ * Ra^(i+1) = a Ra^(i) + b Ra^(i-1) + c Ra^(i-2).  Two points give linear
+ * weights.  A Newton failure retries the step with alpha halved.           */
+typedef struct {
+  double Ra0, Ra1;     /* the first two points are solved at these Ra              */
+  double Ra_end;       /* stop once a point passes Ra_end in the direction Ra0->Ra1 */
+  int n_opt;           /* target Newton iterations (the paper uses 4 to 6)         */
+  double gamma;        /* turning-point switch factor (the paper uses 10 to 100)   */
+  int max_points;      /* capacity of the points array                             */
+  int retries;         /* halvings of alpha after a Newton failure                 */
+  rsc_newton_opts newton;
+} rsc_continuation_opts;
+
+typedef struct {
+  double Ra, C;                 /* parameter and drift of the converged wave           */
+  double KE, Nu_in, Nu_out;     /* rsc_diagnostics of the wave                         */
+  double residual;              /* final Newton residual                               */
+  int newton_iterations, gmres_total;
+  int mode;                     /* predictor: 0 Ra independent, 1 U_J independent      */
+} rsc_continuation_point;
+
+/* Prediction step of the continuation (host only, no GPU): Ra[0..npts) and
+ * s[0..npts) are the last Rayleigh numbers and U_J values, most recent first
+ * (npts = 2 or 3; s at the most recent point's J).  Writes the mode (0: Ra,
+ * 1: U_J independent), the new Ra and the weights w[3] of the last states.
+ * Returns RSC_EINVAL for npts < 2 or null pointers.                        */
+rsc_status rsc_continuation_predict(const double* Ra, const double* s, int npts, int n_its,
+                                    int n_opt, double gamma, double alpha_scale, int* mode,
+                                    double* Ra_new, double* w);
+
+/* Follow a rotating-wave branch.  U (device) holds the initial estimate at
+ * Ra0 and returns the last converged wave; *C its drift; J the frozen phase
+ * slot (Sec. 3.4).  points[0..*npoints) receive the branch.  The context's Ra
+ * is left at the last point.  Returns RSC_OK when the branch reached Ra_end
+ * or max_points, RSC_ENOCONV when a step failed after all retries (the points
+ * so far are kept).                                                         */
+rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
+                           const rsc_continuation_opts* opts, rsc_continuation_point* points,
+                           int* npoints);
+
 /* Newton-GMRES on a HOST state (copies in and out inside the call).        */
 rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
                               const rsc_newton_opts* opts, rsc_newton_report* report);

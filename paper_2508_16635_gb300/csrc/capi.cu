@@ -106,6 +106,11 @@ struct rsc_ctx {
   int ke_nq = 0;
   double *d_keT = nullptr, *d_kedT = nullptr, *d_ker = nullptr, *d_kew = nullptr;
   double* d_diag = nullptr;   // [KE, Nu_in, Nu_out]
+  // Ra continuation: the last three converged states, the conductive state, argmax scratch
+  double* cont_hist = nullptr;
+  double* cont_cond = nullptr;
+  double* amax_v = nullptr;
+  long* amax_i = nullptr;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double prof_ms[RSC_NUM_KERNELS] = {0};
@@ -1190,7 +1195,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
                   ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->partial,
-                  ctx->dots, ctx->AR0, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
+                  ctx->dots, ctx->AR0, ctx->cont_hist, ctx->cont_cond, ctx->amax_v, ctx->amax_i, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
   for (void* b : bufs) cudaFree(b);
   for (int q = 0; q < 8; ++q) {
     cudaFree(ctx->leg64.buf[q]);
@@ -1442,6 +1447,163 @@ rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
   cudaStreamSynchronize(ctx->s);
   cudaFree(Ud);
   return st;
+}
+
+
+rsc_status rsc_continuation_predict(const double* Ra, const double* s, int npts, int n_its,
+                                    int n_opt, double gamma, double alpha_scale, int* mode,
+                                    double* Ra_new, double* w) {
+  if (!Ra || !s || !mode || !Ra_new || !w || npts < 2) return RSC_EINVAL;
+  const int k = npts < 3 ? npts : 3;
+  const double alpha = alpha_scale * (n_opt + 1.0) / (n_its + 1.0);
+  const double dRa = (Ra[0] - Ra[1]) / Ra[0];
+  const double ds = s[0] != 0.0 ? (s[0] - s[1]) / s[0] : 0.0;
+  *mode = std::fabs(ds) > gamma * std::fabs(dRa) ? 1 : 0;
+  const double* nodes = *mode == 0 ? Ra : s;
+  const double x = nodes[0] + alpha * (nodes[0] - nodes[1]);
+  for (int p = 0; p < 3; ++p) {
+    double v = 0.0;
+    if (p < k) {
+      v = 1.0;
+      for (int q = 0; q < k; ++q)
+        if (q != p) v *= (x - nodes[q]) / (nodes[p] - nodes[q]);
+    }
+    w[p] = v;
+  }
+  if (*mode == 0) {
+    *Ra_new = x;
+  } else {
+    double r = 0.0;
+    for (int p = 0; p < k; ++p) r += w[p] * Ra[p];
+    *Ra_new = r;
+  }
+  return RSC_OK;
+}
+
+rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
+                           const rsc_continuation_opts* o, rsc_continuation_point* pts,
+                           int* npoints) {
+  if (!ctx || !U || !C || !o || !pts || !npoints || o->max_points < 2 || o->retries < 0 ||
+      !(o->Ra0 > 0) || !(o->Ra1 > 0) || o->Ra0 == o->Ra1)
+    return RSC_EINVAL;
+  *npoints = 0;
+  const long n = ctx->d.n();
+  int nb;
+  launch_1d_grid(n, &nb);
+  if (!ctx->cont_hist) {
+    CK(cudaMalloc((void**)&ctx->cont_hist, 3 * (size_t)n * sizeof(double)));
+    CK(cudaMalloc((void**)&ctx->cont_cond, (size_t)n * sizeof(double)));
+    CK(cudaMalloc((void**)&ctx->amax_v, 1024 * sizeof(double)));
+    CK(cudaMalloc((void**)&ctx->amax_i, 1025 * sizeof(long)));
+  }
+  CKS(rsc_conductive_state(ctx, ctx->cont_cond));
+  double* H[3] = {ctx->cont_hist, ctx->cont_hist + n, ctx->cont_hist + 2 * n};
+  int slot[3] = {-1, -1, -1};   // history slots, most recent first
+  double hRa[3] = {0, 0, 0}, hC[3] = {0, 0, 0};
+  int last_its = 0;
+  const double Ra_orig = ctx->p.Ra;
+  // one Newton solve at Ra from the estimate in U
+  auto set_ra = [&](double Ra) -> rsc_status {
+    rsc_params q = ctx->p;     // Ra enters only the explicit terms: no refactorisation
+    q.Ra = Ra;
+    return rsc_set_params(ctx, &q);
+  };
+  auto solve = [&](double Ra, double* Cv, rsc_continuation_point* pt) -> bool {
+    if (set_ra(Ra) != RSC_OK) return false;
+    rsc_newton_report rep{};
+    const rsc_status st = rsc_newton_rw(ctx, U, Cv, J, &o->newton, &rep);
+    if (st != RSC_OK) return false;
+    pt->Ra = Ra;
+    pt->C = *Cv;
+    pt->residual = rep.residual;
+    pt->newton_iterations = rep.iterations;
+    pt->gmres_total = rep.gmres_total;
+    double dg[3];
+    if (diagnostics(ctx, U, dg) != RSC_OK) return false;
+    pt->KE = dg[0];
+    pt->Nu_in = dg[1];
+    pt->Nu_out = dg[2];
+    return true;
+  };
+  auto push = [&](const rsc_continuation_point& pt) -> rsc_status {
+    const int fresh = slot[2] >= 0 ? slot[2] : (slot[1] >= 0 ? 2 : (slot[0] >= 0 ? 1 : 0));
+    CK(cudaMemcpyAsync(H[fresh], U, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+    slot[2] = slot[1]; slot[1] = slot[0]; slot[0] = fresh;
+    hRa[2] = hRa[1]; hRa[1] = hRa[0]; hRa[0] = pt.Ra;
+    hC[2] = hC[1]; hC[1] = hC[0]; hC[0] = pt.C;
+    last_its = pt.newton_iterations;
+    pts[(*npoints)++] = pt;
+    return RSC_OK;
+  };
+  rsc_status result = RSC_OK;
+  double Cv = *C;
+  rsc_continuation_point pt{};
+  if (!solve(o->Ra0, &Cv, &pt)) {
+    set_ra(Ra_orig);
+    ctx->err = "Newton did not converge at the first continuation point";
+    return RSC_ENOCONV;
+  }
+  pt.mode = 0;
+  CKS(push(pt));
+  if (!solve(o->Ra1, &Cv, &pt)) {
+    result = RSC_ENOCONV;
+  } else {
+    pt.mode = 0;
+    CKS(push(pt));
+  }
+  const double dir = o->Ra1 > o->Ra0 ? 1.0 : -1.0;
+  while (result == RSC_OK && *npoints < o->max_points &&
+         dir * (pts[*npoints - 1].Ra - o->Ra_end) < 0) {
+    const int k = *npoints < 3 ? *npoints : 3;
+    // J of the last point: the largest |U - U_cond|
+    {
+      KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 1.0 * n);
+      k_argmax_absdiff<<<nb, 256, 0, ctx->s>>>(H[slot[0]], ctx->cont_cond, n, ctx->amax_v,
+                                               ctx->amax_i);
+      CK(cudaGetLastError());
+    }
+    {
+      KSpan sp(ctx, RSC_K_BLAS, 16.0 * nb, 1.0 * nb);
+      k_argmax_finish<<<1, 256, 0, ctx->s>>>(ctx->amax_v, ctx->amax_i, nb, ctx->amax_i + 1024);
+      CK(cudaGetLastError());
+    }
+    long jm = 0;
+    CK(cudaMemcpyAsync(&jm, ctx->amax_i + 1024, sizeof(long), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    double sv[3] = {0, 0, 0}, uc = 0.0;
+    CK(cudaMemcpy(&uc, ctx->cont_cond + jm, sizeof(double), cudaMemcpyDeviceToHost));
+    for (int q = 0; q < k; ++q) {
+      CK(cudaMemcpy(&sv[q], H[slot[q]] + jm, sizeof(double), cudaMemcpyDeviceToHost));
+      sv[q] -= uc;
+    }
+    bool ok = false;
+    for (int attempt = 0; attempt <= o->retries && !ok; ++attempt) {
+      int mode = 0;
+      double Ra_new = 0.0, w[3];
+      CKS(rsc_continuation_predict(hRa, sv, k, last_its, o->n_opt, o->gamma,
+                                   std::ldexp(1.0, -attempt), &mode, &Ra_new, w));
+      {
+        KSpan sp(ctx, RSC_K_BLAS, 8.0 * n * (k + 1), 2.0 * n * k);
+        k_lincomb3<<<nb, 256, 0, ctx->s>>>(U, w[0], H[slot[0]], w[1], H[slot[1]], w[2],
+                                           k > 2 ? H[slot[2]] : nullptr, n);
+        CK(cudaGetLastError());
+      }
+      Cv = w[0] * hC[0] + w[1] * hC[1] + (k > 2 ? w[2] * hC[2] : 0.0);
+      if (Ra_new > 0 && solve(Ra_new, &Cv, &pt)) {
+        pt.mode = mode;
+        CKS(push(pt));
+        ok = true;
+      }
+    }
+    if (!ok) result = RSC_ENOCONV;
+  }
+  // leave the last converged wave in U and the context at its Ra
+  CK(cudaMemcpyAsync(U, H[slot[0]], n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  CKS(set_ra(hRa[0]));
+  *C = hC[0];
+  if (result != RSC_OK) ctx->err = "a continuation step did not converge after all retries";
+  return result;
 }
 
 }  // extern "C"

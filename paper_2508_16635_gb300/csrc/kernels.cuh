@@ -16,6 +16,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <climits>
 
 namespace rsc {
 
@@ -1398,6 +1399,77 @@ __global__ void k_diag_finish(const double* __restrict__ partial, int P,
     out[1] = din * dxdr / g_in;
     out[2] = dout * dxdr / g_out;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Continuation helpers.
+// out = a x0 + b x1 + c x2 (the Lagrange extrapolation of Sec. 4.3); x1 / x2 may be null
+// when their weight is unused.
+__global__ void k_lincomb3(double* __restrict__ out, double a, const double* __restrict__ x0,
+                           double b, const double* __restrict__ x1, double c,
+                           const double* __restrict__ x2, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    double v = a * x0[i];
+    if (x1) v = fma(b, x1[i], v);
+    if (x2) v = fma(c, x2[i], v);
+    out[i] = v;
+  }
+}
+
+// Index of the largest |x - y| (lowest index on ties): per-block (value, index) pairs,
+// then one block reduces them.  grid = nb <= 1024, block = 256.
+__device__ __forceinline__ void argmax_merge(double& v, long& i, double v2, long i2) {
+  if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+}
+
+__global__ void k_argmax_absdiff(const double* __restrict__ x, const double* __restrict__ y, long n,
+                                 double* __restrict__ pv, long* __restrict__ pi) {
+  __shared__ double sv[256];
+  __shared__ long si[256];
+  double v = -1.0;
+  long idx = n;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    argmax_merge(v, idx, fabs(x[i] - y[i]), i);
+  sv[threadIdx.x] = v;
+  si[threadIdx.x] = idx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      double a = sv[threadIdx.x];
+      long ia = si[threadIdx.x];
+      argmax_merge(a, ia, sv[threadIdx.x + o], si[threadIdx.x + o]);
+      sv[threadIdx.x] = a;
+      si[threadIdx.x] = ia;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pv[blockIdx.x] = sv[0];
+    pi[blockIdx.x] = si[0];
+  }
+}
+
+__global__ void k_argmax_finish(const double* __restrict__ pv, const long* __restrict__ pi, int nb,
+                                long* __restrict__ out) {
+  __shared__ double sv[256];
+  __shared__ long si[256];
+  double v = -1.0;
+  long idx = LONG_MAX;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) argmax_merge(v, idx, pv[b], pi[b]);
+  sv[threadIdx.x] = v;
+  si[threadIdx.x] = idx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      double a = sv[threadIdx.x];
+      long ia = si[threadIdx.x];
+      argmax_merge(a, ia, sv[threadIdx.x + o], si[threadIdx.x + o]);
+      sv[threadIdx.x] = a;
+      si[threadIdx.x] = ia;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = si[0];
 }
 
 }  // namespace rsc

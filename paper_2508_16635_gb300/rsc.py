@@ -23,7 +23,7 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_apply_jacobian", "rsc_newton_rw", "rsc_newton_rw_host", "rsc_norm2",
            "rsc_last_error", "rsc_status_string", "rsc_abi_version", "rsc_profile_enable",
            "rsc_profile_query", "rsc_kernel_name", "rsc_launch_count", "rsc_norm2_noalloc",
-           "rsc_diagnostics", "rsc_step2")
+           "rsc_diagnostics", "rsc_step2", "rsc_continuation_predict", "rsc_continue_ra")
 NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
            "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
@@ -39,6 +39,22 @@ class Params(ctypes.Structure):
 class NewtonOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_newton", ctypes.c_int), ("kmax", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("dt_newton", ctypes.c_double)]
+
+
+class ContinuationOpts(ctypes.Structure):
+    _fields_ = [("Ra0", ctypes.c_double), ("Ra1", ctypes.c_double), ("Ra_end", ctypes.c_double),
+                ("n_opt", ctypes.c_int), ("gamma", ctypes.c_double), ("max_points", ctypes.c_int),
+                ("retries", ctypes.c_int), ("newton", NewtonOpts)]
+
+
+class ContinuationPoint(ctypes.Structure):
+    _fields_ = [("Ra", ctypes.c_double), ("C", ctypes.c_double), ("KE", ctypes.c_double),
+                ("Nu_in", ctypes.c_double), ("Nu_out", ctypes.c_double),
+                ("residual", ctypes.c_double), ("newton_iterations", ctypes.c_int),
+                ("gmres_total", ctypes.c_int), ("mode", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class NewtonReport(ctypes.Structure):
@@ -99,6 +115,9 @@ def load_library(path=LIB_PATH):
         "rsc_launch_count": ([P, ctypes.POINTER(ctypes.c_long)], I),
         "rsc_norm2_noalloc": ([P, ctypes.c_size_t, P, P], I),
         "rsc_step2": ([P, P, D, I], I),
+        "rsc_continuation_predict": ([P, P, I, I, I, D, D, ctypes.POINTER(I), ctypes.POINTER(D), P], I),
+        "rsc_continue_ra": ([P, P, ctypes.POINTER(D), ctypes.c_long, ctypes.POINTER(ContinuationOpts),
+                             P, ctypes.POINTER(I)], I),
         "rsc_diagnostics": ([P, P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)], I),
     }
     for name, (args, res) in sig.items():
@@ -222,6 +241,23 @@ class RotatingShell:
             self._check(st)
         return Cv.value, rep.as_dict(), st
 
+    def continue_ra(self, U, C, J, Ra0, Ra1, Ra_end, n_opt=4, gamma=20.0, max_points=8,
+                    retries=3, tol=1e-10, max_newton=12, kmax=200, gmres_tol=1e-10,
+                    dt_newton=200.0):
+        """Ra continuation (rsc_continue_ra) from the estimate U at Ra0; U returns the last
+        wave.  Returns (list of point dicts, last C, status)."""
+        opts = ContinuationOpts(Ra0, Ra1, Ra_end, n_opt, gamma, max_points, retries,
+                                NewtonOpts(tol, max_newton, kmax, gmres_tol, dt_newton))
+        pts = (ContinuationPoint * max_points)()
+        npts = ctypes.c_int(0)
+        Cv = ctypes.c_double(C)
+        st = self.lib.rsc_continue_ra(self._ctx, self._vec(U), ctypes.byref(Cv),
+                                      -1 if J is None else int(J), ctypes.byref(opts),
+                                      ctypes.cast(pts, ctypes.c_void_p), ctypes.byref(npts))
+        if st not in (0, 4):
+            self._check(st)
+        return [pts[i].as_dict() for i in range(npts.value)], Cv.value, st
+
     def newton_rw_host(self, U_host, C, J, tol=1e-10, max_newton=10, kmax=100,
                        gmres_tol=1e-10, dt_newton=200.0):
         opts = NewtonOpts(tol, max_newton, kmax, gmres_tol, dt_newton)
@@ -271,3 +307,17 @@ class RotatingShell:
         out = ctypes.c_double()
         self._check(self.lib.rsc_norm2(self._ctx, _ptr(v), v.numel(), ctypes.byref(out)))
         return out.value
+
+
+def continuation_predict(Ra, s, n_its, n_opt, gamma, alpha_scale=1.0, lib=None):
+    """rsc_continuation_predict (host only): (mode, Ra_new, [a, b, c])."""
+    lib = lib or load_library()
+    k = len(Ra)
+    ra = (ctypes.c_double * k)(*Ra)
+    sv = (ctypes.c_double * k)(*s)
+    mode, rn, w = ctypes.c_int(0), ctypes.c_double(0.0), (ctypes.c_double * 3)()
+    st = lib.rsc_continuation_predict(ra, sv, k, n_its, n_opt, gamma, alpha_scale,
+                                      ctypes.byref(mode), ctypes.byref(rn), w)
+    if st != 0:
+        raise RscError(st, "rsc_continuation_predict rejected its arguments")
+    return mode.value, rn.value, list(w)

@@ -311,3 +311,30 @@ def test_step2_mixed_precision_error(torch):
     errs = _rel_fields(s, U.cpu().numpy(), want)
     assert max(errs) < 1e-5, errs
     gpu.close()
+
+
+def test_ra_continuation_parity(torch):
+    """rsc_continue_ra against the oracle's continuation (Sec. 4.3) on the RW4 branch from
+    the same oracle-made estimate: the same Ra sequence and Newton counts, and waves that
+    agree to the converged-wave tolerance."""
+    from oracle import continuation as ct
+    from paper_2508_16635_gb300 import RotatingShell
+    L, Ms, Nr, Ek, M = 31, 4, 24, 1e-3, 4
+    s = Shell(L, Ms, Nr, Ek, 120.0)
+    U0, C0, J = _rw_initial_guess(s, M)
+    kw = dict(n_opt=4, gamma=20.0, max_points=4, kmax=150)
+    pts_o = ct.continue_ra(s, U0, C0, J, 120.0, 121.0, 200.0, **kw)
+    gpu = RotatingShell(L, Ms, Nr, Ek, 120.0)
+    U = torch.tensor(U0, device="cuda")
+    pts_g, Cg, st = gpu.continue_ra(U, C0, J, 120.0, 121.0, 200.0, **kw)
+    assert st == 0 and len(pts_g) == len(pts_o) == 4
+    for a, b in zip(pts_o, pts_g):
+        assert a["its"] == b["newton_iterations"]
+        assert abs(a["Ra"] - b["Ra"]) <= 1e-12 * a["Ra"]
+        assert b["residual"] < 1e-10
+        assert abs(a["C"] - b["C"]) <= 1e-9 * abs(a["C"])
+        ke = s.kinetic_energy(a["U"])
+        assert abs(ke - b["KE"]) <= 1e-8 * ke
+    assert _rel(U.cpu().numpy(), pts_o[-1]["U"]) < 1e-9
+    assert Cg == pts_g[-1]["C"]
+    gpu.close()
