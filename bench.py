@@ -50,6 +50,7 @@ def parse():
                     help="Jacobian actions per Newton iteration (the RW12 solve takes 208-216)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-rw", action="store_true", help="skip the time-to-rotating-wave run")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances run")
     ap.add_argument("--dt-study", default=None,
                     help="only run the Table 1 time-step study for the given rows (e.g. 0,1,2)")
     ap.add_argument("--coriolis-study", action="store_true",
@@ -350,6 +351,68 @@ def coriolis_study(torch, RotatingShell):
     return out
 
 
+def batch_measure(torch, Batch, count=16, reps=5):
+    """Batched uneven instances: 32 continuation points at Ek = 3e-5 with azimuthal
+    symmetries M_s = 4, 6, 8, 10, 12 (instance i has M_s = [4, 6, 8, 10, 12][i % 5], so 24, 16,
+    12, 10 and 8 active m), L = 95, N_r = 48, Ra_i = linspace(1.05, 2.0, 32)_i x Ra_c with the
+    onset estimate Ra_c = 2.7 Ek^(-1/3) (the paper prints no onset values; RW12 exists at
+    Ek = 1e-5, Ra = 126 = 2.7 Ek^(-1/3), and the throughput does not depend on Ra).
+    16 Jacobian actions (Newton pseudo-step dt = 200) per instance per launch, all instances
+    in one CUDA graph (rsc_batch_apply_jacobian), against the same actions issued instance
+    by instance."""
+    import numpy as np
+    Ek = 3e-5
+    Rac = 2.7 * Ek ** (-1.0 / 3.0)
+    ms_list = [4, 6, 8, 10, 12]
+    inst = [dict(L=95, Ms=ms_list[i % 5], Nr=48, Ek=Ek, Ra=float(f * Rac), precision="mixed")
+            for i, f in enumerate(np.linspace(1.05, 2.0, 32))]
+    t0 = time.perf_counter()
+    b = Batch(inst)
+    t_create = time.perf_counter() - t0
+    U, u, out, C, J = [], [], [], [], []
+    for i, sh in enumerate(b.shells):
+        d = inst[i]
+        U.append(sh.conductive_state() + torch.tensor(
+            si.perturbation(d["L"], d["Ms"], d["Nr"], seed=6000 + i), device="cuda"))
+        u.append(torch.tensor(np.concatenate([si.random_vector(d["L"], d["Ms"], d["Nr"],
+                                                               seed=7000 + 100 * i + q)
+                                              for q in range(count)]), device="cuda"))
+        out.append(torch.empty_like(u[-1]))
+        C.append(0.0)
+        J.append(None)
+    t0 = time.perf_counter()
+    b.apply_jacobian(U, C, J, u, 200.0, out=out)     # factorisations and graph capture
+    b.synchronize()
+    t_first = time.perf_counter() - t0
+    b.apply_jacobian(U, C, J, u, 200.0, out=out)
+    b.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        b.apply_jacobian(U, C, J, u, 200.0, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / reps * 1e-3
+    # the same actions instance by instance (each context's own per-action graph, on its own
+    # stream; the device is synchronised after each instance so that they do not overlap)
+    for i, sh in enumerate(b.shells):
+        sh.apply_jacobian(U[i], 0.0, None, u[i], 200.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, sh in enumerate(b.shells):
+        sh.apply_jacobian(U[i], 0.0, None, u[i], 200.0)
+        torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    n_act = len(inst) * count
+    b.close()
+    return {"config": "32 instances, Ek=3e-5, L=95, Nr=48, Ms=[4,6,8,10,12][i%5], "
+                      "Ra=linspace(1.05,2,32) x 2.7 Ek^(-1/3), 16 actions each, mixed precision",
+            "actions_per_launch": n_act, "graph_ms_per_launch": t_graph * 1e3,
+            "jvps_per_s_batched": n_act / t_graph, "jvps_per_s_sequential": n_act / t_seq,
+            "batching_speedup": t_seq / t_graph, "create_s": t_create,
+            "first_launch_s_including_factorisation_and_capture": t_first}
+
+
 def _wave_from_seed(torch, RotatingShell, c, precision="mixed", max_steps=60000):
     """Time-step an m = M seed (the route of Sec. 2.2) until the m = M temperature amplitude
     settles; return the state, the drift estimate from its phase rate and the phase slot J
@@ -618,7 +681,7 @@ def run_gpu(args):
             "data": "synthetic (seeded perturbation of the conductive state)",
             "config": {"workload": w["name"], "precision": args.precision,
                        "step": f"1 Newton iteration: FP64 residual, GMRES with {K} Jacobian "
-                               f"actions (CGS2), update, FP64 residual",
+                               f"actions (one-reduction MGS), update, FP64 residual",
                        "krylov_per_iteration": K, "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MB write, outside the timed interval)"},
             "timesteps_per_s": steps_per_s,
@@ -636,6 +699,9 @@ def run_gpu(args):
         }
         if not args.no_rw:
             line["newton_rw"] = newton_rw_measure(torch, RotatingShell, w)
+        if not args.no_batch:
+            from paper_2508_16635_gb300 import Batch
+            line["batch"] = batch_measure(torch, Batch)
         if not args.no_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(K)
         print(json.dumps(line), flush=True)

@@ -222,6 +222,42 @@ rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
 rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
                               const rsc_newton_opts* opts, rsc_newton_report* report);
 
+/* Batches of instances: the continuation points in Ra of a branch and waves
+ * of different azimuthal symmetries M_s (hence different active-m counts),
+ * each a full context on a stream of its own that the batch creates and
+ * owns.  The parameters of instance i are params[i] (any L, Ms, Nr, Ra, Ek).
+ * rsc_batch_apply_jacobian issues the Jacobian actions of every instance as
+ * one CUDA graph (captured on the first call with a given set of pointers,
+ * drifts, slots, count and dt, replayed afterwards) whose branches run the
+ * instances concurrently; rsc_batch_newton_rw runs every instance's
+ * Newton-GMRES at once (one host thread per instance, each on its stream).
+ * The streams of the instances are ordered after `stream` only inside
+ * rsc_batch_apply_jacobian; synchronise the contexts (rsc_batch_context)
+ * before reading their results otherwise.                                   */
+typedef struct rsc_batch rsc_batch;
+
+rsc_status rsc_batch_create(const rsc_params* params, int n, void* stream, rsc_batch** out);
+rsc_status rsc_batch_destroy(rsc_batch* batch);
+rsc_status rsc_batch_size(const rsc_batch* batch, int* n);
+/* The context of instance i (owned by the batch; do not destroy it).        */
+rsc_status rsc_batch_context(rsc_batch* batch, int i, rsc_ctx** ctx);
+const char* rsc_batch_last_error(const rsc_batch* batch);
+
+/* For every instance i: out[i][q] = (B_{U[i]} - I) u[i][q], q < count, with
+ * drift C[i] and slot J[i] (< 0: none), as rsc_apply_jacobian; u[i], out[i]
+ * hold count vectors of that instance's length back to back.  All pointer
+ * arrays are host arrays of n device pointers.  Asynchronous on `stream`.   */
+rsc_status rsc_batch_apply_jacobian(rsc_batch* batch, const double* const* U, const double* C,
+                                    const long* J, const double* const* u, double* const* out,
+                                    int count, double dt);
+
+/* rsc_newton_rw for every instance concurrently; reports (may be NULL) and
+ * status are arrays of n.  Returns the first hard error, else RSC_ENOCONV if
+ * any instance did not converge, else RSC_OK.                               */
+rsc_status rsc_batch_newton_rw(rsc_batch* batch, double* const* U, double* C, const long* J,
+                               const rsc_newton_opts* opts, rsc_newton_report* reports,
+                               rsc_status* status);
+
 /* Tracing.  Kernel identifiers of rsc_profile_query / rsc_kernel_name.     */
 enum {
   RSC_K_RADIAL = 0,    /* Chebyshev evaluation on the de-aliased radii        */

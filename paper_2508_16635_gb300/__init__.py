@@ -4,4 +4,4 @@ its Jacobian action and the Newton-GMRES rotating-wave solver.
 The compute path is the CUDA library librsc.so (C ABI in include/rsc.h);
 `rsc` is its ctypes binding.  There is no CPU fallback.
 """
-from .rsc import RotatingShell, RscError, load_library, EXPORTS  # noqa: F401
+from .rsc import Batch, RotatingShell, RscError, load_library, EXPORTS  # noqa: F401

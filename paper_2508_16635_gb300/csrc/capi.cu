@@ -13,7 +13,9 @@
 #include <new>
 #include <string>
 #include <cstdint>
+#include <thread>
 #include <type_traits>
+#include <vector>
 
 #include "kernels.cuh"
 #include "legendre_tc.cuh"
@@ -1312,7 +1314,7 @@ rsc_status rsc_apply_jacobian(rsc_ctx* ctx, const double* U, double C, long J, c
 
 static const char* kKernelNames[RSC_NUM_KERNELS] = {
     "radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
-    "chain_solve", "temp_solve", "gmres_dots", "gmres_axpy", "blas1"};
+    "chain_solve", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep"};
 
 const char* rsc_kernel_name(int id) {
   return (id >= 0 && id < RSC_NUM_KERNELS) ? kKernelNames[id] : "unknown";
@@ -1604,6 +1606,206 @@ rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
   *C = hC[0];
   if (result != RSC_OK) ctx->err = "a continuation step did not converge after all retries";
   return result;
+}
+
+
+// ===========================================================================
+// Batches of instances (continuation points in Ra, waves of different azimuthal
+// symmetries): one context per instance on its own stream; batched Jacobian actions
+// are captured into one CUDA graph whose branches run the instances concurrently.
+}  // extern "C"
+
+struct rsc_batch {
+  std::vector<rsc_ctx*> ctx;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t s = nullptr;          // the caller's stream (graph launches)
+  cudaGraphExec_t exec = nullptr;
+  long nodes = 0;
+  // key of the captured graph
+  std::vector<const double*> kU, ku;
+  std::vector<double*> kout;
+  std::vector<double> kC;
+  std::vector<long> kJ;
+  int kcount = -1;
+  double kdt = 0;
+  std::string err;
+};
+
+namespace {
+void batch_free(rsc_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (rsc_ctx* c : b->ctx)
+    if (c) rsc_destroy(c);
+  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+}  // namespace
+
+extern "C" {
+
+rsc_status rsc_batch_create(const rsc_params* params, int n, void* stream, rsc_batch** out) {
+  if (!params || !out || n < 1 || n > 4096) return RSC_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) CKS(check_params(&params[i]));
+  rsc_batch* b = new (std::nothrow) rsc_batch();
+  if (!b) return RSC_ENOMEM;
+  b->s = reinterpret_cast<cudaStream_t>(stream);
+  b->ctx.assign(n, nullptr);
+  b->streams.assign(n, nullptr);
+  b->join.assign(n, nullptr);
+  rsc_status st = RSC_OK;
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) st = RSC_ECUDA;
+  for (int i = 0; i < n && st == RSC_OK; ++i) {
+    if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess) {
+      st = RSC_ECUDA;
+      break;
+    }
+    st = rsc_create(&params[i], b->streams[i], &b->ctx[i]);
+    if (st != RSC_OK) b->err = "instance " + std::to_string(i) + ": " + rsc_last_error(b->ctx[i]);
+  }
+  if (st != RSC_OK) {
+    batch_free(b);
+    return st;
+  }
+  *out = b;
+  return RSC_OK;
+}
+
+rsc_status rsc_batch_destroy(rsc_batch* b) {
+  if (!b) return RSC_EINVAL;
+  if (b->s) cudaStreamSynchronize(b->s);
+  for (cudaStream_t st : b->streams) cudaStreamSynchronize(st);
+  batch_free(b);
+  return RSC_OK;
+}
+
+rsc_status rsc_batch_size(const rsc_batch* b, int* n) {
+  if (!b || !n) return RSC_EINVAL;
+  *n = (int)b->ctx.size();
+  return RSC_OK;
+}
+
+rsc_status rsc_batch_context(rsc_batch* b, int i, rsc_ctx** ctx) {
+  if (!b || !ctx || i < 0 || i >= (int)b->ctx.size()) return RSC_EINVAL;
+  *ctx = b->ctx[i];
+  return RSC_OK;
+}
+
+const char* rsc_batch_last_error(const rsc_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+rsc_status rsc_batch_apply_jacobian(rsc_batch* b, const double* const* U, const double* C,
+                                    const long* J, const double* const* u, double* const* out,
+                                    int count, double dt) {
+  if (!b || !U || !C || !J || !u || !out || count < 1 || !(dt > 0)) return RSC_EINVAL;
+  const int n = (int)b->ctx.size();
+  for (int i = 0; i < n; ++i)
+    if (!U[i] || !u[i] || !out[i] || J[i] >= b->ctx[i]->d.n()) return RSC_EINVAL;
+  bool same = b->exec && b->kcount == count && b->kdt == dt;
+  for (int i = 0; i < n && same; ++i)
+    same = b->kU[i] == U[i] && b->ku[i] == u[i] && b->kout[i] == out[i] && b->kC[i] == C[i] &&
+           b->kJ[i] == J[i];
+  auto fail = [&](rsc_status st, const std::string& what) {
+    b->err = what;
+    return st;
+  };
+  if (!same) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    // factorisations first: nothing may allocate or copy synchronously during capture
+    for (int i = 0; i < n; ++i) {
+      DevFactor* f = nullptr;
+      if (get_factor(b->ctx[i], dt, &f) != RSC_OK || cudaStreamSynchronize(b->streams[i]) != cudaSuccess)
+        return fail(RSC_ECUDA, "instance " + std::to_string(i) + ": " + b->ctx[i]->err);
+    }
+    cudaStream_t origin = b->s;
+    cudaStream_t own = nullptr;
+    if (!origin) {   // the legacy stream cannot be captured: use a private one
+      if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(RSC_ECUDA, "stream creation failed");
+      origin = own;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return fail(RSC_ECUDA, "cudaStreamBeginCapture failed");
+    rsc_status st = RSC_OK;
+    long nodes = 0;
+    if (cudaEventRecord(b->fork, origin) != cudaSuccess) st = RSC_ECUDA;
+    for (int i = 0; i < n && st == RSC_OK; ++i) {
+      rsc_ctx* c = b->ctx[i];
+      if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) { st = RSC_ECUDA; break; }
+      const bool prof = c->prof_on;
+      c->prof_on = false;
+      const long before = c->launches;
+      const bool fp32 = c->p.precision == RSC_MIXED;
+      DevFactor* f = nullptr;
+      st = get_factor(c, dt, &f);
+      if (st == RSC_OK) st = cache_base(c, U[i], fp32);
+      const long nn = c->d.n();
+      for (int q = 0; q < count && st == RSC_OK; ++q) {
+        const long Jq = J[i] < 0 ? -1 : J[i];
+        st = fp32 ? do_jvp_eager<float>(c, U[i], C[i], Jq, u[i] + q * nn, out[i] + q * nn, f, dt)
+                  : do_jvp_eager<double>(c, U[i], C[i], Jq, u[i] + q * nn, out[i] + q * nn, f, dt);
+      }
+      nodes += c->launches - before;
+      c->prof_on = prof;
+      if (st == RSC_OK && (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess ||
+                           cudaStreamWaitEvent(origin, b->join[i], 0) != cudaSuccess))
+        st = RSC_ECUDA;
+      if (st != RSC_OK) b->err = "instance " + std::to_string(i) + ": " + c->err;
+    }
+    const cudaError_t ce = cudaStreamEndCapture(origin, &graph);
+    if (st == RSC_OK && ce != cudaSuccess) st = fail(RSC_ECUDA, cudaGetErrorString(ce));
+    if (st == RSC_OK && cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess)
+      st = fail(RSC_ECUDA, "cudaGraphInstantiate failed");
+    if (graph) cudaGraphDestroy(graph);
+    if (own) cudaStreamDestroy(own);
+    if (st != RSC_OK) {
+      b->exec = nullptr;
+      return st;
+    }
+    b->nodes = nodes;
+    b->kU.assign(U, U + n);
+    b->ku.assign(u, u + n);
+    b->kout.assign(out, out + n);
+    b->kC.assign(C, C + n);
+    b->kJ.assign(J, J + n);
+    b->kcount = count;
+    b->kdt = dt;
+  }
+  cudaStream_t origin = b->s;
+  if (cudaGraphLaunch(b->exec, origin) != cudaSuccess)
+    return fail(RSC_ECUDA, "cudaGraphLaunch failed");
+  for (rsc_ctx* c : b->ctx) c->launches += b->nodes / n;
+  return RSC_OK;
+}
+
+rsc_status rsc_batch_newton_rw(rsc_batch* b, double* const* U, double* C, const long* J,
+                               const rsc_newton_opts* opts, rsc_newton_report* reports,
+                               rsc_status* status) {
+  if (!b || !U || !C || !J || !opts || !status) return RSC_EINVAL;
+  const int n = (int)b->ctx.size();
+  if (b->s) cudaStreamSynchronize(b->s);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i] {
+      status[i] = rsc_newton_rw(b->ctx[i], U[i], &C[i], J[i], opts, reports ? &reports[i] : nullptr);
+    });
+  for (auto& t : th) t.join();
+  rsc_status worst = RSC_OK;
+  for (int i = 0; i < n; ++i)
+    if (status[i] != RSC_OK && status[i] != RSC_ENOCONV) worst = status[i];
+  if (worst != RSC_OK) return worst;
+  for (int i = 0; i < n; ++i)
+    if (status[i] == RSC_ENOCONV) return RSC_ENOCONV;
+  return RSC_OK;
 }
 
 }  // extern "C"

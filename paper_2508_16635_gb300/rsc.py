@@ -23,7 +23,9 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_apply_jacobian", "rsc_newton_rw", "rsc_newton_rw_host", "rsc_norm2",
            "rsc_last_error", "rsc_status_string", "rsc_abi_version", "rsc_profile_enable",
            "rsc_profile_query", "rsc_kernel_name", "rsc_launch_count", "rsc_norm2_noalloc",
-           "rsc_diagnostics", "rsc_step2", "rsc_continuation_predict", "rsc_continue_ra")
+           "rsc_diagnostics", "rsc_step2", "rsc_continuation_predict", "rsc_continue_ra",
+           "rsc_batch_create", "rsc_batch_destroy", "rsc_batch_size", "rsc_batch_context",
+           "rsc_batch_last_error", "rsc_batch_apply_jacobian", "rsc_batch_newton_rw")
 NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
            "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
@@ -115,6 +117,13 @@ def load_library(path=LIB_PATH):
         "rsc_launch_count": ([P, ctypes.POINTER(ctypes.c_long)], I),
         "rsc_norm2_noalloc": ([P, ctypes.c_size_t, P, P], I),
         "rsc_step2": ([P, P, D, I], I),
+        "rsc_batch_create": ([ctypes.POINTER(Params), I, P, ctypes.POINTER(P)], I),
+        "rsc_batch_destroy": ([P], I),
+        "rsc_batch_size": ([P, ctypes.POINTER(I)], I),
+        "rsc_batch_context": ([P, I, ctypes.POINTER(P)], I),
+        "rsc_batch_last_error": ([P], ctypes.c_char_p),
+        "rsc_batch_apply_jacobian": ([P, P, P, P, P, P, I, D], I),
+        "rsc_batch_newton_rw": ([P, P, P, P, ctypes.POINTER(NewtonOpts), P, P], I),
         "rsc_continuation_predict": ([P, P, I, I, I, D, D, ctypes.POINTER(I), ctypes.POINTER(D), P], I),
         "rsc_continue_ra": ([P, P, ctypes.POINTER(D), ctypes.c_long, ctypes.POINTER(ContinuationOpts),
                              P, ctypes.POINTER(I)], I),
@@ -177,10 +186,24 @@ class RotatingShell:
     def new_state(self):
         return self.torch.zeros(self.n, dtype=self.torch.float64, device=self.device)
 
+    @classmethod
+    def _borrow(cls, lib, ctx, params, device):
+        """A view of a context owned elsewhere (an instance of a Batch)."""
+        import torch
+        self = cls.__new__(cls)
+        self.torch, self.device, self.lib, self.params = torch, device, lib, params
+        self.L, self.Ms, self.Nr = params.L, params.Ms, params.Nr
+        self._ctx = ctx
+        self._owned = False
+        n, P = ctypes.c_size_t(), ctypes.c_int()
+        self._check(lib.rsc_state_size(ctx, ctypes.byref(n), ctypes.byref(P)))
+        self.n, self.P = n.value, P.value
+        return self
+
     def close(self):
-        if self._ctx:
+        if self._ctx and getattr(self, "_owned", True):
             self.lib.rsc_destroy(self._ctx)
-            self._ctx = ctypes.c_void_p()
+        self._ctx = ctypes.c_void_p()
 
     def __del__(self):
         try:
@@ -321,3 +344,95 @@ def continuation_predict(Ra, s, n_its, n_opt, gamma, alpha_scale=1.0, lib=None):
     if st != 0:
         raise RscError(st, "rsc_continuation_predict rejected its arguments")
     return mode.value, rn.value, list(w)
+
+
+class Batch:
+    """Instances solved together (rsc_batch_*): continuation points in Ra and waves of
+    different azimuthal symmetries.  `instances` is a list of dicts with the keyword
+    arguments of RotatingShell (L, Ms, Nr, Ek, Ra and optionally Pr, eta, precision,
+    coriolis)."""
+
+    def __init__(self, instances, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Batch needs a CUDA device")
+        self.torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        self.lib = load_library()
+        n = len(instances)
+        arr = (Params * n)()
+        for i, d in enumerate(instances):
+            cor = d.get("coriolis", "implicit")
+            arr[i] = Params(d["Ra"], d["Ek"], d.get("Pr", 1.0), d.get("eta", 0.35), d["L"], d["Ms"],
+                            d["Nr"], RSC_MIXED if d.get("precision", "fp64") == "mixed" else RSC_FP64,
+                            1 if cor == "explicit" else 0)
+        self._b = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            st = self.lib.rsc_batch_create(arr, n, ctypes.c_void_p(stream), ctypes.byref(self._b))
+        if st != 0:
+            raise RscError(st, "rsc_batch_create failed")
+        self.shells = []
+        for i in range(n):
+            c = ctypes.c_void_p()
+            self._check(self.lib.rsc_batch_context(self._b, i, ctypes.byref(c)))
+            self.shells.append(RotatingShell._borrow(self.lib, c, arr[i], self.device))
+
+    def _check(self, st):
+        if st != 0:
+            raise RscError(st, self.lib.rsc_batch_last_error(self._b).decode())
+
+    def __len__(self):
+        return len(self.shells)
+
+    def synchronize(self):
+        self.torch.cuda.synchronize(self.device)
+
+    def apply_jacobian(self, U, C, J, u, dt, out=None):
+        """Jacobian actions of every instance in one graph launch: u[i] holds `count`
+        directions of instance i back to back; returns the list of outputs."""
+        n = len(self.shells)
+        count = u[0].numel() // self.shells[0].n
+        if out is None:
+            out = [self.torch.empty_like(x) for x in u]
+        P = ctypes.c_void_p
+        pU = (P * n)(*[self.shells[i]._vec(U[i]) for i in range(n)])
+        pu = (P * n)(*[self.shells[i]._vec(u[i], count) for i in range(n)])
+        po = (P * n)(*[self.shells[i]._vec(out[i], count) for i in range(n)])
+        cC = (ctypes.c_double * n)(*C)
+        cJ = (ctypes.c_long * n)(*[-1 if j is None else int(j) for j in J])
+        c = lambda a: ctypes.cast(a, P)
+        self._check(self.lib.rsc_batch_apply_jacobian(self._b, c(pU), c(cC), c(cJ), c(pu), c(po),
+                                                      count, dt))
+        return out
+
+    def newton_rw(self, U, C, J, tol=1e-10, max_newton=10, kmax=100, gmres_tol=1e-10,
+                  dt_newton=200.0):
+        """Newton-GMRES on every instance at once; returns (drifts, reports, statuses)."""
+        n = len(self.shells)
+        P = ctypes.c_void_p
+        pU = (P * n)(*[self.shells[i]._vec(U[i]) for i in range(n)])
+        cC = (ctypes.c_double * n)(*C)
+        cJ = (ctypes.c_long * n)(*[-1 if j is None else int(j) for j in J])
+        reps = (NewtonReport * n)()
+        sts = (ctypes.c_int * n)()
+        opts = NewtonOpts(tol, max_newton, kmax, gmres_tol, dt_newton)
+        c = lambda a: ctypes.cast(a, P)
+        st = self.lib.rsc_batch_newton_rw(self._b, c(pU), c(cC), c(cJ), ctypes.byref(opts),
+                                          c(reps), c(sts))
+        if st not in (0, 4):
+            self._check(st)
+        return list(cC), [reps[i].as_dict() for i in range(n)], list(sts)
+
+    def close(self):
+        if self._b:
+            for sh in self.shells:
+                sh._ctx = ctypes.c_void_p()
+            self.lib.rsc_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

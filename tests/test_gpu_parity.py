@@ -338,3 +338,61 @@ def test_ra_continuation_parity(torch):
     assert _rel(U.cpu().numpy(), pts_o[-1]["U"]) < 1e-9
     assert Cg == pts_g[-1]["C"]
     gpu.close()
+
+
+def test_batch_jacobian_parity(torch):
+    """rsc_batch_apply_jacobian: instances of different symmetries and Ra in one graph launch,
+    each against the oracle's Jacobian action; a second call with new directions in the same
+    buffers replays the graph."""
+    from paper_2508_16635_gb300 import Batch
+    inst = [dict(L=15, Ms=4, Nr=12, Ek=1e-3, Ra=100.0), dict(L=15, Ms=6, Nr=12, Ek=1e-3, Ra=130.0),
+            dict(L=13, Ms=3, Nr=11, Ek=3e-3, Ra=90.0)]
+    b = Batch(inst)
+    shells = [Shell(d["L"], d["Ms"], d["Nr"], d["Ek"], d["Ra"]) for d in inst]
+    count, dt, C = 2, 200.0, [0.3, -0.7, 1.1]
+    J = [shells[0].real_index("T", 4, 4, 1, 1), None, shells[2].real_index("T", 3, 3, 2, 1)]
+    U = [s.conductive_state() + si.perturbation(s.L, s.Ms, s.Nr, seed=50 + i, amp=3e-2)
+         for i, s in enumerate(shells)]
+    Ug = [torch.tensor(x, device="cuda") for x in U]
+    ug = [torch.zeros(count * s.n, dtype=torch.float64, device="cuda") for s in shells]
+    out = [torch.zeros_like(x) for x in ug]
+    for rep in range(2):
+        dirs = []
+        for i, s in enumerate(shells):
+            d = np.concatenate([si.random_vector(s.L, s.Ms, s.Nr, seed=100 * rep + 10 * i + q)
+                                for q in range(count)])
+            if J[i] is not None:
+                d[J[i]] = 0.4
+                d[s.n + J[i]] = -0.2
+            dirs.append(d)
+            ug[i].copy_(torch.tensor(d, device="cuda"))
+        b.apply_jacobian(Ug, C, J, ug, dt, out=out)
+        b.synchronize()
+        for i, s in enumerate(shells):
+            got = out[i].cpu().numpy()
+            for q in range(count):
+                want = s.jvp(U[i], C[i], J[i], dirs[i][q * s.n:(q + 1) * s.n], dt)
+                assert _rel(got[q * s.n:(q + 1) * s.n], want) < 1e-9
+    b.close()
+
+
+def test_batch_newton_matches_single_instance_solves(torch):
+    """rsc_batch_newton_rw (instances concurrently) gives bit-identical waves to the
+    single-context solves (whose parity with the oracle is tested above)."""
+    from paper_2508_16635_gb300 import Batch, RotatingShell
+    L, Ms, Nr, Ek, M = 31, 4, 24, 1e-3, 4
+    s = Shell(L, Ms, Nr, Ek, 120.0)
+    U0, C0, J = _rw_initial_guess(s, M)
+    inst = [dict(L=L, Ms=Ms, Nr=Nr, Ek=Ek, Ra=Ra) for Ra in (120.0, 121.0)]
+    b = Batch(inst)
+    Ub = [torch.tensor(U0, device="cuda") for _ in inst]
+    Cb, reps, sts = b.newton_rw(Ub, [C0, C0], [J, J], tol=1e-10, max_newton=10, kmax=150)
+    assert sts == [0, 0]
+    for i, d in enumerate(inst):
+        g = RotatingShell(L, Ms, Nr, Ek, d["Ra"])
+        Us = torch.tensor(U0, device="cuda")
+        Cs, rep, st = g.newton_rw(Us, C0, J, tol=1e-10, max_newton=10, kmax=150)
+        assert st == 0 and Cs == Cb[i] and torch.equal(Us, Ub[i])
+        assert rep["iterations"] == reps[i]["iterations"]
+        g.close()
+    b.close()
