@@ -381,6 +381,9 @@ def batch_measure(torch, Batch, count=16, reps=5):
         C.append(0.0)
         J.append(None)
     t0 = time.perf_counter()
+    tuning = b.autotune()
+    t_tune = time.perf_counter() - t0
+    t0 = time.perf_counter()
     b.apply_jacobian(U, C, J, u, 200.0, out=out)     # factorisations and graph capture
     b.synchronize()
     t_first = time.perf_counter() - t0
@@ -409,7 +412,8 @@ def batch_measure(torch, Batch, count=16, reps=5):
                       "Ra=linspace(1.05,2,32) x 2.7 Ek^(-1/3), 16 actions each, mixed precision",
             "actions_per_launch": n_act, "graph_ms_per_launch": t_graph * 1e3,
             "jvps_per_s_batched": n_act / t_graph, "jvps_per_s_sequential": n_act / t_seq,
-            "batching_speedup": t_seq / t_graph, "create_s": t_create,
+            "batching_speedup": t_seq / t_graph, "create_s": t_create, "autotune_s": t_tune,
+            "tuning_by_Ms": {inst[i]["Ms"]: tuning[i] for i in range(5)},
             "first_launch_s_including_factorisation_and_capture": t_first}
 
 
@@ -473,7 +477,7 @@ def dt_study(torch, RotatingShell, rows=(0, 1, 2)):
         dict(name="RW12 Ek=1e-5 Ra=140 (Table 1 row 3), L=89, Nr=76", L=89, Ms=12, Nr=76,
              Ek=1e-5, Ra=140.0, seed_dt=2e-5, paper=dict(C=51.2817, explicit_diverges=1.6e-6,
                                                          two_percent=2.8e-5),
-             dts=dict(implicit=[2e-6, 6e-6, 1.2e-5, 2.4e-5, 5e-5, 1e-4, 2e-4],
+             dts=dict(implicit=[2e-6, 6e-6, 1.2e-5, 2.4e-5, 5e-5, 1e-4, 2e-4, 4e-4, 8e-4],
                       explicit=[1e-6, 1.5e-6, 2e-6, 2.5e-6, 3e-6])),
     ]
     out = []
@@ -567,6 +571,7 @@ def run_gpu(args):
     peaks = measured_peaks(torch)
     sh = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
                        precision=args.precision)
+    tuning = sh.autotune()      # launch shapes picked by timing, before any measurement
     U0 = sh.conductive_state() + torch.tensor(
         si.perturbation(w["L"], w["Ms"], w["Nr"], seed=3000 + rank), device="cuda")
     # phase slot: Im of the T coefficient (l = m = 12, k*) with k* = argmax |Re|
@@ -689,6 +694,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 8 * sh.n,
                     "d2h_bytes_per_step": 8 * sh.n, "ms_per_step": e2e_t * 1e3},
             "gpu_launches": int(launches),
+            "tuning": tuning,
             "kernel_ms_per_step": {k: round(v["ms"], 4) for k, v in prof_all.items()},
             "kernel_ms_per_jacobian_action": prof_jvp,
             "kernel_ms_per_fp64_step": prof_step64,

@@ -251,12 +251,39 @@ rsc_status rsc_batch_apply_jacobian(rsc_batch* batch, const double* const* U, co
                                     const long* J, const double* const* u, double* const* out,
                                     int count, double dt);
 
+/* rsc_autotune on the first instance of each distinct shape (L, Ms, Nr,
+ * precision, Ek, Pr, Coriolis treatment), rsc_set_tuning on the others.       */
+rsc_status rsc_batch_autotune(rsc_batch* batch);
+
 /* rsc_newton_rw for every instance concurrently; reports (may be NULL) and
  * status are arrays of n.  Returns the first hard error, else RSC_ENOCONV if
  * any instance did not converge, else RSC_OK.                               */
 rsc_status rsc_batch_newton_rw(rsc_batch* batch, double* const* U, double* C, const long* J,
                                const rsc_newton_opts* opts, rsc_newton_report* reports,
                                rsc_status* status);
+
+/* Launch shapes of the transform, right-hand-side and chain kernels (no
+ * counterpart in the paper: GPU tiling).  [2] = [FP64 path, mixed path].     */
+typedef struct {
+  int products_warps[2];   /* warps per block of the DFT + grid products kernel       */
+  int analysis_radii[2];   /* radii per block of the Legendre analysis                */
+  int synth_radii;         /* radii per block of the CUDA-core (FP64) synthesis       */
+  int rhs_pairs[2];        /* (l, m) pairs per block of the right-hand-side kernel    */
+  int chain_cluster;       /* CTAs per thread-block cluster of the chain sweeps       */
+  double ms[5];            /* after rsc_autotune: best times (ms) of products +
+                              analysis (mixed), FP64 synthesis, RHS (mixed), chain
+                              solve; zero otherwise                                   */
+} rsc_tuning;
+
+/* Autotuner: times every feasible candidate of each shape on this context's
+ * workspace (the conductive state as input; 3 launches after a warm-up) and
+ * keeps the fastest; factorises dt = 200 if needed.  Synchronous, a few
+ * hundred launches.  `out` (may be NULL) receives the choice.               */
+rsc_status rsc_autotune(rsc_ctx* ctx, rsc_tuning* out);
+rsc_status rsc_get_tuning(const rsc_ctx* ctx, rsc_tuning* out);
+/* Apply shapes (for example tuned on another context of the same size);
+ * RSC_EINVAL if one is infeasible here.                                     */
+rsc_status rsc_set_tuning(rsc_ctx* ctx, const rsc_tuning* t);
 
 /* Tracing.  Kernel identifiers of rsc_profile_query / rsc_kernel_name.     */
 enum {

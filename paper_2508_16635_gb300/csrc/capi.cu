@@ -85,6 +85,9 @@ struct rsc_ctx {
   int nblk_dot = 0;
   int cluster = 8;  // CTAs per chain in the cluster chain solve
   int rt_synth[2] = {1, 1}, rt_anal[2] = {1, 1};  // radii per block, [fp64, fp32]
+  int wpb[2] = {0, 0};     // warps per block of the products kernel (0: largest that fits)
+  int ppb[2] = {0, 0};     // pairs per block of the right-hand-side kernel (0: 256 / Nr)
+  double tune_ms[5] = {0, 0, 0, 0, 0};
   // tensor-core Legendre synthesis (FP32 path): A tiles, offsets, padded K, status word
   float* tc_tiles = nullptr;
   long* tc_off = nullptr;
@@ -421,6 +424,23 @@ rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
   return RSC_OK;
 }
 
+// Shared memory of the DFT + products kernel for `wpb` warps per block.
+template <typename R>
+size_t products_smem(const Dims& d, bool lin, int wpb) {
+  using V = typename C2<R>::T;
+  const int K1 = d.K + 1, NF = lin ? 18 : 9;
+  return (size_t)wpb * NF * K1 * sizeof(V) + 4 * (size_t)K1 * d.nphi * sizeof(R) +
+         (size_t)wpb * 4 * d.nphi * sizeof(R);
+}
+
+// Shared memory of the right-hand-side kernel for `ppb` pairs per block.
+template <typename R>
+size_t rhs_smem(const Dims& d, int ppb) {
+  using V = typename C2<R>::T;
+  return (size_t)ppb * (10 * (size_t)d.Nr * sizeof(double2) + 6 * (size_t)d.Nr * sizeof(float2) +
+                        4 * (size_t)d.Nd * sizeof(V));
+}
+
 template <typename R>
 rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
   using V = typename C2<R>::T;
@@ -429,11 +449,8 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
   const LegDev<R>& L = leg<R>(ctx);
   const int K1 = d.K + 1;
   const int NF = lin ? 18 : 9;
-  int WPB = 8;
-  auto smem_for = [&](int wpb) {
-    return (size_t)wpb * NF * K1 * sizeof(V) + 4 * (size_t)K1 * d.nphi * sizeof(R) +
-           (size_t)wpb * 4 * d.nphi * sizeof(R);
-  };
+  int WPB = ctx->wpb[sizeof(R) == 4 ? 1 : 0] > 0 ? ctx->wpb[sizeof(R) == 4 ? 1 : 0] : 8;
+  auto smem_for = [&](int wpb) { return products_smem<R>(d, lin, wpb); };
   while (WPB > 1 && smem_for(WPB) > 190 * 1024) WPB /= 2;
   const size_t smem = smem_for(WPB);
   dim3 grid(d.Nd, (d.nlat + WPB - 1) / WPB);
@@ -471,9 +488,9 @@ rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const d
                      const double* u_orig, double2* out, const double* xe = nullptr) {
   using V = typename C2<R>::T;
   const Dims& d = ctx->d;
-  const int PPB = std::max(1, 256 / round32(d.Nr));
-  const size_t smem = (size_t)PPB * (10 * (size_t)d.Nr * sizeof(double2) +
-                                     6 * (size_t)d.Nr * sizeof(float2) + 4 * (size_t)d.Nd * sizeof(V));
+  const int tuned = ctx->ppb[sizeof(R) == 4 ? 1 : 0];
+  const int PPB = tuned > 0 ? tuned : std::max(1, 256 / round32(d.Nr));
+  const size_t smem = rhs_smem<R>(d, PPB);
   KSpan sp(ctx, RSC_K_RHS,
            4.0 * d.P * d.Nd * sizeof(V) + (rp.J >= 0 ? 144.0 : 96.0) * d.P * d.Nr,
            d.P * (double)d.Nr * (16.0 * d.Nd + 32.0 * d.Nr));
@@ -1010,6 +1027,194 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
   return RSC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: the launch shapes of the transform, right-hand-side and chain kernels are
+// picked by timing each candidate (CUDA events, 3 launches after a warm-up) on this
+// context's own workspace, with the conductive state as input.
+int radii_limit(const void* fn, int threads_x) {
+  cudaFuncAttributes at{};
+  if (cudaFuncGetAttributes(&at, fn) != cudaSuccess) return 1;
+  int rt = 4;
+  while (rt > 1 && ((long)rt * threads_x * std::max(at.numRegs, 1) > 65536 || rt * threads_x > 1024))
+    --rt;
+  return rt;
+}
+
+bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
+  const Dims& d = ctx->d;
+  auto pow2 = [](int v, int hi) { return v >= 1 && v <= hi && (v & (v - 1)) == 0; };
+  for (int p = 0; p < 2; ++p) {
+    if (!pow2(t.products_warps[p], 8)) return false;
+    const size_t sm = p ? products_smem<float>(d, true, t.products_warps[p])
+                        : products_smem<double>(d, true, t.products_warps[p]);
+    if (sm > 190 * 1024) return false;
+    const int ra = radii_limit(p ? (const void*)k_analysis<float> : (const void*)k_analysis<double>,
+                               round32(d.L + 1));
+    if (t.analysis_radii[p] < 1 || t.analysis_radii[p] > ra) return false;
+    if (!pow2(t.rhs_pairs[p], 8) || round32(d.Nr) * t.rhs_pairs[p] > 1024) return false;
+    if ((p ? rhs_smem<float>(d, t.rhs_pairs[p]) : rhs_smem<double>(d, t.rhs_pairs[p])) > 200 * 1024)
+      return false;
+  }
+  if (t.synth_radii < 1 || t.synth_radii > radii_limit((const void*)k_synth<double>, round32(d.nlat2)))
+    return false;
+  bool ok = false;
+  switch (chain_maxq(d.Nr)) {
+    case 2: ok = cluster_ok<2>(d, t.chain_cluster); break;
+    case 4: ok = cluster_ok<4>(d, t.chain_cluster); break;
+    case 8: ok = cluster_ok<8>(d, t.chain_cluster); break;
+    case 12: ok = cluster_ok<12>(d, t.chain_cluster); break;
+    default: ok = cluster_ok<16>(d, t.chain_cluster); break;
+  }
+  return ok && t.chain_cluster <= d.Nr;
+}
+
+void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
+  const Dims& d = ctx->d;
+  for (int p = 0; p < 2; ++p) {
+    int w = ctx->wpb[p] > 0 ? ctx->wpb[p] : 8;
+    while (w > 1 && (p ? products_smem<float>(d, true, w) : products_smem<double>(d, true, w)) >
+                        190 * 1024)
+      w /= 2;
+    t->products_warps[p] = w;
+    t->analysis_radii[p] = ctx->rt_anal[p];
+    t->rhs_pairs[p] = ctx->ppb[p] > 0 ? ctx->ppb[p] : std::max(1, 256 / round32(d.Nr));
+  }
+  t->synth_radii = ctx->rt_synth[0];
+  t->chain_cluster = ctx->cluster;
+  for (int q = 0; q < 5; ++q) t->ms[q] = ctx->tune_ms[q];
+}
+
+void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
+  for (int p = 0; p < 2; ++p) {
+    ctx->wpb[p] = t.products_warps[p];
+    ctx->rt_anal[p] = t.analysis_radii[p];
+    ctx->ppb[p] = t.rhs_pairs[p];
+  }
+  ctx->rt_synth[0] = t.synth_radii;
+  ctx->cluster = t.chain_cluster;
+  if (ctx->jvp_exec) {   // the captured Jacobian action embeds the old launch shapes
+    cudaGraphExecDestroy(ctx->jvp_exec);
+    ctx->jvp_exec = nullptr;
+  }
+}
+
+template <typename R>
+rsc_status tune_precision(rsc_ctx* ctx, rsc_tuning& t, cudaEvent_t e0, cudaEvent_t e1) {
+  const int p = sizeof(R) == 4 ? 1 : 0;
+  const Dims& d = ctx->d;
+  rsc_status st = RSC_OK;
+  auto timeit = [&](auto&& launch) -> double {
+    st = launch();
+    if (st != RSC_OK) return 1e30;
+    cudaEventRecord(e0, ctx->s);
+    for (int r = 0; r < 3 && st == RSC_OK; ++r) st = launch();
+    cudaEventRecord(e1, ctx->s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return st == RSC_OK ? ms / 3.0 : 1e30;
+  };
+  CKS(stage_synth<R>(ctx, ctx->rtmp, ctx->FC));
+  CKS(stage_synth<R>(ctx, ctx->rtmp, ctx->FCU));
+  auto pa = [&] { return stage_products_analysis<R>(ctx, true); };
+  // products: warps per block
+  double best = 1e30;
+  int bw = t.products_warps[p];
+  for (int w : {1, 2, 4, 8}) {
+    if (products_smem<R>(d, true, w) > 190 * 1024) continue;
+    ctx->wpb[p] = w;
+    const double ms = timeit(pa);
+    CKS(st);
+    if (ms < best) { best = ms; bw = w; }
+  }
+  ctx->wpb[p] = t.products_warps[p] = bw;
+  // analysis: radii per block
+  best = 1e30;
+  int br = t.analysis_radii[p];
+  const int rmax = radii_limit((const void*)k_analysis<R>, round32(d.L + 1));
+  for (int r = 1; r <= rmax; r *= 2) {
+    ctx->rt_anal[p] = r;
+    const double ms = timeit(pa);
+    CKS(st);
+    if (ms < best) { best = ms; br = r; }
+  }
+  ctx->rt_anal[p] = t.analysis_radii[p] = br;
+  if (p == 1) ctx->tune_ms[0] = best;   // products + analysis of the mixed path
+  // synthesis (CUDA-core FP64 path): radii per block
+  if (p == 0) {
+    best = 1e30;
+    int bs = t.synth_radii;
+    const int smax = radii_limit((const void*)k_synth<double>, round32(d.nlat2));
+    for (int r = 1; r <= smax; r *= 2) {
+      ctx->rt_synth[0] = r;
+      const double ms = timeit([&] { return stage_synth<double>(ctx, ctx->rtmp, ctx->FC); });
+      CKS(st);
+      if (ms < best) { best = ms; bs = r; }
+    }
+    ctx->rt_synth[0] = t.synth_radii = bs;
+    ctx->tune_ms[1] = best;
+  }
+  // right-hand side: pairs per block (Jacobian-action mode)
+  RhsParams rp = make_rp(ctx, 200.0, 0.0, 1);
+  best = 1e30;
+  int bp = t.rhs_pairs[p];
+  for (int q : {1, 2, 4, 8}) {
+    if (round32(d.Nr) * q > 1024 || rhs_smem<R>(d, q) > 200 * 1024) continue;
+    ctx->ppb[p] = q;
+    const double ms = timeit([&] { return stage_rhs<R>(ctx, rp, ctx->rtmp, ctx->rtmp, nullptr, ctx->rhs); });
+    CKS(st);
+    if (ms < best) { best = ms; bp = q; }
+  }
+  ctx->ppb[p] = t.rhs_pairs[p] = bp;
+  if (p == 1) ctx->tune_ms[2] = best;
+  return RSC_OK;
+}
+
+rsc_status autotune(rsc_ctx* ctx, rsc_tuning* out) {
+  rsc_tuning t{};
+  get_tuning(ctx, &t);
+  CKS(rsc_conductive_state(ctx, ctx->rtmp));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool prof = ctx->prof_on;
+  ctx->prof_on = false;
+  rsc_status st = tune_precision<double>(ctx, t, e0, e1);
+  if (st == RSC_OK) st = tune_precision<float>(ctx, t, e0, e1);
+  // chain sweeps: CTAs per cluster, on the Newton factorisation (dt = 200)
+  if (st == RSC_OK) {
+    DevFactor* f = nullptr;
+    st = get_factor(ctx, 200.0, &f);
+    double best = 1e30;
+    int bc = t.chain_cluster;
+    for (int cs : {16, 8, 4, 2}) {
+      if (st != RSC_OK) break;
+      rsc_tuning probe = t;
+      probe.chain_cluster = cs;
+      if (!tuning_ok(ctx, probe)) continue;
+      ctx->cluster = cs;
+      st = stage_solve(ctx, f, ctx->xtmp);
+      cudaEventRecord(e0, ctx->s);
+      for (int r = 0; r < 3 && st == RSC_OK; ++r) st = stage_solve(ctx, f, ctx->xtmp);
+      cudaEventRecord(e1, ctx->s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (st == RSC_OK && ms / 3.0 < best) { best = ms / 3.0; bc = cs; }
+    }
+    t.chain_cluster = bc;
+    ctx->tune_ms[3] = best;
+  }
+  ctx->prof_on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != RSC_OK) return st;
+  set_tuning(ctx, t);
+  get_tuning(ctx, &t);
+  if (out) *out = t;
+  return RSC_OK;
+}
+
 // Kinetic energy and Nusselt numbers of U (diagnostics of Secs. 4-5).
 rsc_status diagnostics(rsc_ctx* ctx, const double* U, double out[3]) {
   const Dims& d = ctx->d;
@@ -1452,6 +1657,28 @@ rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
 }
 
 
+rsc_status rsc_autotune(rsc_ctx* ctx, rsc_tuning* out) {
+  if (!ctx) return RSC_EINVAL;
+  return autotune(ctx, out);
+}
+
+rsc_status rsc_get_tuning(const rsc_ctx* ctx, rsc_tuning* out) {
+  if (!ctx || !out) return RSC_EINVAL;
+  get_tuning(ctx, out);
+  return RSC_OK;
+}
+
+rsc_status rsc_set_tuning(rsc_ctx* ctx, const rsc_tuning* t) {
+  if (!ctx || !t) return RSC_EINVAL;
+  if (!tuning_ok(ctx, *t)) {
+    ctx->err = "launch shapes not feasible for this context";
+    return RSC_EINVAL;
+  }
+  CK(cudaStreamSynchronize(ctx->s));
+  set_tuning(ctx, *t);
+  return RSC_OK;
+}
+
 rsc_status rsc_continuation_predict(const double* Ra, const double* s, int npts, int n_its,
                                     int n_opt, double gamma, double alpha_scale, int* mode,
                                     double* Ra_new, double* w) {
@@ -1783,6 +2010,33 @@ rsc_status rsc_batch_apply_jacobian(rsc_batch* b, const double* const* U, const 
   if (cudaGraphLaunch(b->exec, origin) != cudaSuccess)
     return fail(RSC_ECUDA, "cudaGraphLaunch failed");
   for (rsc_ctx* c : b->ctx) c->launches += b->nodes / n;
+  return RSC_OK;
+}
+
+rsc_status rsc_batch_autotune(rsc_batch* b) {
+  if (!b) return RSC_EINVAL;
+  const int n = (int)b->ctx.size();
+  for (int i = 0; i < n; ++i) {
+    const rsc_params& p = b->ctx[i]->p;
+    int src = -1;   // an earlier instance with the same shape
+    for (int j = 0; j < i && src < 0; ++j) {
+      const rsc_params& q = b->ctx[j]->p;
+      if (q.L == p.L && q.Ms == p.Ms && q.Nr == p.Nr && q.precision == p.precision &&
+          q.Ek == p.Ek && q.Pr == p.Pr && q.explicit_coriolis == p.explicit_coriolis)
+        src = j;
+    }
+    rsc_tuning t{};
+    rsc_status st = src < 0 ? rsc_autotune(b->ctx[i], &t) : rsc_get_tuning(b->ctx[src], &t);
+    if (st == RSC_OK && src >= 0) st = rsc_set_tuning(b->ctx[i], &t);
+    if (st != RSC_OK) {
+      b->err = "instance " + std::to_string(i) + ": " + b->ctx[i]->err;
+      return st;
+    }
+  }
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
   return RSC_OK;
 }
 

@@ -25,7 +25,8 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_profile_query", "rsc_kernel_name", "rsc_launch_count", "rsc_norm2_noalloc",
            "rsc_diagnostics", "rsc_step2", "rsc_continuation_predict", "rsc_continue_ra",
            "rsc_batch_create", "rsc_batch_destroy", "rsc_batch_size", "rsc_batch_context",
-           "rsc_batch_last_error", "rsc_batch_apply_jacobian", "rsc_batch_newton_rw")
+           "rsc_batch_last_error", "rsc_batch_apply_jacobian", "rsc_batch_newton_rw",
+           "rsc_autotune", "rsc_get_tuning", "rsc_set_tuning", "rsc_batch_autotune")
 NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
            "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
@@ -41,6 +42,18 @@ class Params(ctypes.Structure):
 class NewtonOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_newton", ctypes.c_int), ("kmax", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("dt_newton", ctypes.c_double)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("products_warps", ctypes.c_int * 2), ("analysis_radii", ctypes.c_int * 2),
+                ("synth_radii", ctypes.c_int), ("rhs_pairs", ctypes.c_int * 2),
+                ("chain_cluster", ctypes.c_int), ("ms", ctypes.c_double * 5)]
+
+    def as_dict(self):
+        return {"products_warps": list(self.products_warps),
+                "analysis_radii": list(self.analysis_radii), "synth_radii": self.synth_radii,
+                "rhs_pairs": list(self.rhs_pairs), "chain_cluster": self.chain_cluster,
+                "ms": list(self.ms)}
 
 
 class ContinuationOpts(ctypes.Structure):
@@ -117,6 +130,10 @@ def load_library(path=LIB_PATH):
         "rsc_launch_count": ([P, ctypes.POINTER(ctypes.c_long)], I),
         "rsc_norm2_noalloc": ([P, ctypes.c_size_t, P, P], I),
         "rsc_step2": ([P, P, D, I], I),
+        "rsc_autotune": ([P, ctypes.POINTER(Tuning)], I),
+        "rsc_get_tuning": ([P, ctypes.POINTER(Tuning)], I),
+        "rsc_set_tuning": ([P, ctypes.POINTER(Tuning)], I),
+        "rsc_batch_autotune": ([P], I),
         "rsc_batch_create": ([ctypes.POINTER(Params), I, P, ctypes.POINTER(P)], I),
         "rsc_batch_destroy": ([P], I),
         "rsc_batch_size": ([P, ctypes.POINTER(I)], I),
@@ -264,6 +281,26 @@ class RotatingShell:
             self._check(st)
         return Cv.value, rep.as_dict(), st
 
+    def autotune(self):
+        """Pick the launch shapes by timing (rsc_autotune); returns them as a dict."""
+        t = Tuning()
+        self._check(self.lib.rsc_autotune(self._ctx, ctypes.byref(t)))
+        return t.as_dict()
+
+    def tuning(self):
+        t = Tuning()
+        self._check(self.lib.rsc_get_tuning(self._ctx, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, d):
+        t = Tuning()
+        t.products_warps[:] = d["products_warps"]
+        t.analysis_radii[:] = d["analysis_radii"]
+        t.synth_radii = d["synth_radii"]
+        t.rhs_pairs[:] = d["rhs_pairs"]
+        t.chain_cluster = d["chain_cluster"]
+        self._check(self.lib.rsc_set_tuning(self._ctx, ctypes.byref(t)))
+
     def continue_ra(self, U, C, J, Ra0, Ra1, Ra_end, n_opt=4, gamma=20.0, max_points=8,
                     retries=3, tol=1e-10, max_newton=12, kmax=200, gmres_tol=1e-10,
                     dt_newton=200.0):
@@ -405,6 +442,11 @@ class Batch:
         self._check(self.lib.rsc_batch_apply_jacobian(self._b, c(pU), c(cC), c(cJ), c(pu), c(po),
                                                       count, dt))
         return out
+
+    def autotune(self):
+        """rsc_batch_autotune: tune each distinct shape once; returns the instances' shapes."""
+        self._check(self.lib.rsc_batch_autotune(self._b))
+        return [sh.tuning() for sh in self.shells]
 
     def newton_rw(self, U, C, J, tol=1e-10, max_newton=10, kmax=100, gmres_tol=1e-10,
                   dt_newton=200.0):

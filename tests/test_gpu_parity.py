@@ -396,3 +396,27 @@ def test_batch_newton_matches_single_instance_solves(torch):
         assert rep["iterations"] == reps[i]["iterations"]
         g.close()
     b.close()
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES)
+def test_autotune_keeps_results_bitwise(torch, name, L, Ms, Nr, Ek, Ra):
+    """The autotuner only changes launch shapes (which rows, radii or pairs a block takes),
+    never the order of any sum: steps and Jacobian actions are bit-identical after it."""
+    from paper_2508_16635_gb300 import RotatingShell
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=61, amp=3e-2)
+    u = si.random_vector(L, Ms, Nr, seed=62)
+    for prec in ("fp64", "mixed"):
+        gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision=prec)
+        U = torch.tensor(x, device="cuda")
+        a0 = gpu.apply_jacobian(U, 0.3, None, torch.tensor(u, device="cuda"), 200.0).clone()
+        s0 = gpu.step(U.clone(), 0.0, 1e-3).clone()
+        t = gpu.autotune()
+        assert t["chain_cluster"] in (2, 4, 8, 16) and min(t["rhs_pairs"]) >= 1
+        a1 = gpu.apply_jacobian(U, 0.3, None, torch.tensor(u, device="cuda"), 200.0)
+        s1 = gpu.step(U.clone(), 0.0, 1e-3)
+        assert torch.equal(a0, a1) and torch.equal(s0, s1)
+        bad = dict(t, rhs_pairs=[3, 3])
+        with pytest.raises(Exception):
+            gpu.set_tuning(bad)
+        gpu.close()
