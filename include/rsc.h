@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RSC_ABI_VERSION 2
+#define RSC_ABI_VERSION 3
 
 typedef struct rsc_ctx rsc_ctx;
 
@@ -57,7 +57,8 @@ typedef enum {
   RSC_ENOCONV = 4,     /* Newton or GMRES reached its iteration cap           */
   RSC_ENAN = 5,        /* a non-finite residual or Krylov norm                */
   RSC_ESINGULAR = 6,   /* zero pivot while factorising the implicit operator  */
-  RSC_ETIMEOUT = 7     /* a bounded device wait gave up                       */
+  RSC_ETIMEOUT = 7,    /* a bounded device wait gave up                       */
+  RSC_ERESOLUTION = 8  /* a continuation stopped on an under-resolved state   */
 } rsc_status;
 
 typedef enum {
@@ -217,6 +218,57 @@ rsc_status rsc_continuation_predict(const double* Ra, const double* s, int npts,
 rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
                            const rsc_continuation_opts* opts, rsc_continuation_point* points,
                            int* npoints);
+
+/* Continuation in the Ekman number (Sec. 4.4): the same procedure as
+ * rsc_continue_ra with log10 Ek as the parameter (Eq. new_EK; the paper uses
+ * n_opt = 3 and gamma 400 to 500).  Every new Ek refactorises the implicit
+ * operator.  With ra_coef > 0, Ra = ra_coef Ek^(-1/3) at every point, which
+ * keeps the distance to onset (the paper's Ra = 6.5 Ek^(-1/3)); ra_coef = 0
+ * keeps the context's Ra.  Grid refinement: when tail_threshold > 0 and a
+ * converged point's spectral tail (rsc_spectral_tail) exceeds it, the call
+ * returns RSC_ERESOLUTION with that point in U; the caller then creates a
+ * finer context (rsc_refine_params), moves U there (rsc_regrid) and resumes
+ * from the last Ek (the paper recomputes the last step on the finer grid).  */
+typedef struct {
+  double Ek0, Ek1;     /* the first two points are solved at these Ek              */
+  double Ek_end;       /* stop once a point passes Ek_end in the direction Ek0->Ek1 */
+  double ra_coef;      /* > 0: Ra = ra_coef Ek^(-1/3); 0: Ra unchanged              */
+  int n_opt;
+  double gamma;
+  int max_points;
+  int retries;
+  double tail_threshold;   /* > 0: stop on an under-resolved point (paper: 1e-6)   */
+  rsc_newton_opts newton;
+} rsc_ek_continuation_opts;
+
+typedef struct {
+  double Ek, Ra, C, KE, Nu_in, Nu_out, residual;
+  double cheb_tail, sh_tail;    /* rsc_spectral_tail of the wave                     */
+  int newton_iterations, gmres_total, mode;
+} rsc_ek_point;
+
+rsc_status rsc_continue_ek(rsc_ctx* ctx, double* U, double* C, long J,
+                           const rsc_ek_continuation_opts* opts, rsc_ek_point* points,
+                           int* npoints);
+
+/* Under-resolution measure of Sec. 4.4: with A the largest |coefficient| of
+ * U - U_cond (all fields, complex magnitude), cheb = the largest at the last
+ * Chebyshev degree k = Nr - 1 divided by A, sh = the largest at the last
+ * spherical-harmonic degree l = L divided by A (synchronous).               */
+rsc_status rsc_spectral_tail(rsc_ctx* ctx, const double* U, double* cheb, double* sh);
+
+/* Spectral interpolation between two contexts of the same Ms and eta: every
+ * coefficient of U_dst is the one of U_src with the same (field, m, l, k), or
+ * zero where the source truncation has none (Fourier interpolation by zero
+ * fill, exact for the represented function; coarser targets truncate).
+ * Asynchronous on dst's stream; U_src must be ready there.                  */
+rsc_status rsc_regrid(const rsc_ctx* src, const double* U_src, rsc_ctx* dst, double* U_dst);
+
+/* Refinement rule of Sec. 4.4: Nr grows by `growth` (the paper: 1.2) when
+ * cheb_tail > threshold, L when sh_tail > threshold (caps 128 and 255);
+ * *refined = 1 (radial) | 2 (angular), 0 when nothing changed.  Host only.   */
+rsc_status rsc_refine_params(const rsc_params* p, double cheb_tail, double sh_tail,
+                             double threshold, double growth, rsc_params* out, int* refined);
 
 /* Newton-GMRES on a HOST state (copies in and out inside the call).        */
 rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,

@@ -117,3 +117,40 @@ def continue_ra(shell, U0, C0, J, Ra0, Ra1, Ra_end, n_opt=4, gamma=20.0, max_poi
 
     return follow(solve, U0, C0, Ra0, Ra1, Ra_end, shell.conductive_state(), n_opt, gamma,
                   max_points, retries)
+
+
+def continue_ek(shell, U0, C0, J, Ek0, Ek1, Ek_end, ra_coef=0.0, n_opt=3, gamma=400.0,
+                max_points=8, tol=1e-10, max_newton=12, kmax=200, gmres_tol=1e-10,
+                dt_newton=200.0, retries=3):
+    """Continuation in the Ekman number (Sec. 4.4, Eq. new_EK): the loop of `follow` with
+    log10 Ek as the parameter; every new Ek refactorises, and with ra_coef > 0 the
+    Rayleigh number follows Ra = ra_coef Ek^(-1/3).  Returns points whose "Ra" entry holds
+    log10 Ek (as in `follow`)."""
+
+    def solve(U, C, x):
+        shell.Ek = 10.0 ** x
+        if ra_coef > 0:
+            shell.Ra = ra_coef * shell.Ek ** (-1.0 / 3.0)
+        shell._fact = {}          # Ek enters the implicit operator: refactorise
+        Us, Cs, hist = krylov.newton(shell, U, C, J, dt=dt_newton, tol=tol, max_newton=max_newton,
+                                     kmax=kmax, gmres_tol=gmres_tol)
+        return Us, Cs, len(hist) - 1, hist[-1]["residual"] < tol
+
+    return follow(solve, U0, C0, np.log10(Ek0), np.log10(Ek1), np.log10(Ek_end),
+                  shell.conductive_state(), n_opt, gamma, max_points, retries)
+
+
+def regrid(vec, L0, Ms, Nr0, L1, Nr1):
+    """Zero-fill (or truncate) the coefficients of a state between truncations of the same
+    M_s (Sec. 4.4: the new modes of a refined grid start at zero)."""
+    def pairs(L):
+        return [(m, l) for m in range(0, L + 1, Ms) for l in range(m, L + 1)]
+    p0 = {pl: i for i, pl in enumerate(pairs(L0))}
+    x0 = np.asarray(vec, dtype=float).reshape(3, len(p0), Nr0, 2)
+    P1 = pairs(L1)
+    x1 = np.zeros((3, len(P1), Nr1, 2))
+    k = min(Nr0, Nr1)
+    for i, pl in enumerate(P1):
+        if pl in p0:
+            x1[:, i, :k] = x0[:, p0[pl], :k]
+    return x1.reshape(-1)

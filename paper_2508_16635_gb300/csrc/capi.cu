@@ -1281,6 +1281,7 @@ const char* rsc_status_string(int s) {
     case RSC_ENAN: return "RSC_ENAN";
     case RSC_ESINGULAR: return "RSC_ESINGULAR";
     case RSC_ETIMEOUT: return "RSC_ETIMEOUT";
+    case RSC_ERESOLUTION: return "RSC_ERESOLUTION";
     default: return "unknown status";
   }
 }
@@ -1709,13 +1710,27 @@ rsc_status rsc_continuation_predict(const double* Ra, const double* s, int npts,
   return RSC_OK;
 }
 
-rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
-                           const rsc_continuation_opts* o, rsc_continuation_point* pts,
-                           int* npoints) {
-  if (!ctx || !U || !C || !o || !pts || !npoints || o->max_points < 2 || o->retries < 0 ||
-      !(o->Ra0 > 0) || !(o->Ra1 > 0) || o->Ra0 == o->Ra1)
-    return RSC_EINVAL;
-  *npoints = 0;
+}  // extern "C"
+
+namespace {
+
+// One branch of a natural-parameter continuation (Sec. 4.3; Sec. 4.4 with x = log10 Ek):
+// Newton solves at x0, x1, then predicted points until x passes x_end, max_points is
+// reached, a step fails after all retries (RSC_ENOCONV) or, when tail_threshold > 0, a
+// converged point's spectral tail exceeds it (RSC_ERESOLUTION).  set_x applies x to the
+// context.  U returns the last converged state and *C its drift.
+struct BranchPoint {
+  double x, C, KE, Nu_in, Nu_out, residual, cheb_tail, sh_tail;
+  int its, gmres, mode;
+};
+
+rsc_status spectral_tail(rsc_ctx* ctx, const double* U, double* cheb, double* sh);
+
+template <typename SetX>
+rsc_status follow_branch(rsc_ctx* ctx, double* U, double* C, long J, double x0, double x1,
+                         double x_end, int n_opt, double gamma, int max_points, int retries,
+                         double tail_threshold, const rsc_newton_opts* nopts, SetX set_x,
+                         std::vector<BranchPoint>& pts) {
   const long n = ctx->d.n();
   int nb;
   launch_1d_grid(n, &nb);
@@ -1728,62 +1743,58 @@ rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
   CKS(rsc_conductive_state(ctx, ctx->cont_cond));
   double* H[3] = {ctx->cont_hist, ctx->cont_hist + n, ctx->cont_hist + 2 * n};
   int slot[3] = {-1, -1, -1};   // history slots, most recent first
-  double hRa[3] = {0, 0, 0}, hC[3] = {0, 0, 0};
+  double hx[3] = {0, 0, 0}, hC[3] = {0, 0, 0};
   int last_its = 0;
-  const double Ra_orig = ctx->p.Ra;
-  // one Newton solve at Ra from the estimate in U
-  auto set_ra = [&](double Ra) -> rsc_status {
-    rsc_params q = ctx->p;     // Ra enters only the explicit terms: no refactorisation
-    q.Ra = Ra;
-    return rsc_set_params(ctx, &q);
-  };
-  auto solve = [&](double Ra, double* Cv, rsc_continuation_point* pt) -> bool {
-    if (set_ra(Ra) != RSC_OK) return false;
+  bool under = false;
+  auto solve = [&](double x, double* Cv, BranchPoint* pt) -> bool {
+    if (set_x(x) != RSC_OK) return false;
     rsc_newton_report rep{};
-    const rsc_status st = rsc_newton_rw(ctx, U, Cv, J, &o->newton, &rep);
-    if (st != RSC_OK) return false;
-    pt->Ra = Ra;
+    if (rsc_newton_rw(ctx, U, Cv, J, nopts, &rep) != RSC_OK) return false;
+    pt->x = x;
     pt->C = *Cv;
     pt->residual = rep.residual;
-    pt->newton_iterations = rep.iterations;
-    pt->gmres_total = rep.gmres_total;
+    pt->its = rep.iterations;
+    pt->gmres = rep.gmres_total;
     double dg[3];
     if (diagnostics(ctx, U, dg) != RSC_OK) return false;
     pt->KE = dg[0];
     pt->Nu_in = dg[1];
     pt->Nu_out = dg[2];
+    if (spectral_tail(ctx, U, &pt->cheb_tail, &pt->sh_tail) != RSC_OK) return false;
     return true;
   };
-  auto push = [&](const rsc_continuation_point& pt) -> rsc_status {
+  auto push = [&](const BranchPoint& pt) -> rsc_status {
     const int fresh = slot[2] >= 0 ? slot[2] : (slot[1] >= 0 ? 2 : (slot[0] >= 0 ? 1 : 0));
     CK(cudaMemcpyAsync(H[fresh], U, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
     slot[2] = slot[1]; slot[1] = slot[0]; slot[0] = fresh;
-    hRa[2] = hRa[1]; hRa[1] = hRa[0]; hRa[0] = pt.Ra;
+    hx[2] = hx[1]; hx[1] = hx[0]; hx[0] = pt.x;
     hC[2] = hC[1]; hC[1] = hC[0]; hC[0] = pt.C;
-    last_its = pt.newton_iterations;
-    pts[(*npoints)++] = pt;
+    last_its = pt.its;
+    pts.push_back(pt);
+    if (tail_threshold > 0 && std::max(pt.cheb_tail, pt.sh_tail) > tail_threshold) under = true;
     return RSC_OK;
   };
   rsc_status result = RSC_OK;
   double Cv = *C;
-  rsc_continuation_point pt{};
-  if (!solve(o->Ra0, &Cv, &pt)) {
-    set_ra(Ra_orig);
+  BranchPoint pt{};
+  if (!solve(x0, &Cv, &pt)) {
     ctx->err = "Newton did not converge at the first continuation point";
     return RSC_ENOCONV;
   }
   pt.mode = 0;
   CKS(push(pt));
-  if (!solve(o->Ra1, &Cv, &pt)) {
-    result = RSC_ENOCONV;
-  } else {
-    pt.mode = 0;
-    CKS(push(pt));
+  if (!under) {
+    if (!solve(x1, &Cv, &pt)) {
+      result = RSC_ENOCONV;
+    } else {
+      pt.mode = 0;
+      CKS(push(pt));
+    }
   }
-  const double dir = o->Ra1 > o->Ra0 ? 1.0 : -1.0;
-  while (result == RSC_OK && *npoints < o->max_points &&
-         dir * (pts[*npoints - 1].Ra - o->Ra_end) < 0) {
-    const int k = *npoints < 3 ? *npoints : 3;
+  const double dir = x1 > x0 ? 1.0 : -1.0;
+  while (result == RSC_OK && !under && (int)pts.size() < max_points &&
+         dir * (pts.back().x - x_end) < 0) {
+    const int k = pts.size() < 3 ? (int)pts.size() : 3;
     // J of the last point: the largest |U - U_cond|
     {
       KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 1.0 * n);
@@ -1806,11 +1817,11 @@ rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
       sv[q] -= uc;
     }
     bool ok = false;
-    for (int attempt = 0; attempt <= o->retries && !ok; ++attempt) {
+    for (int attempt = 0; attempt <= retries && !ok; ++attempt) {
       int mode = 0;
-      double Ra_new = 0.0, w[3];
-      CKS(rsc_continuation_predict(hRa, sv, k, last_its, o->n_opt, o->gamma,
-                                   std::ldexp(1.0, -attempt), &mode, &Ra_new, w));
+      double x_new = 0.0, w[3];
+      CKS(rsc_continuation_predict(hx, sv, k, last_its, n_opt, gamma, std::ldexp(1.0, -attempt),
+                                   &mode, &x_new, w));
       {
         KSpan sp(ctx, RSC_K_BLAS, 8.0 * n * (k + 1), 2.0 * n * k);
         k_lincomb3<<<nb, 256, 0, ctx->s>>>(U, w[0], H[slot[0]], w[1], H[slot[1]], w[2],
@@ -1818,7 +1829,7 @@ rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
         CK(cudaGetLastError());
       }
       Cv = w[0] * hC[0] + w[1] * hC[1] + (k > 2 ? w[2] * hC[2] : 0.0);
-      if (Ra_new > 0 && solve(Ra_new, &Cv, &pt)) {
+      if (solve(x_new, &Cv, &pt)) {
         pt.mode = mode;
         CKS(push(pt));
         ok = true;
@@ -1826,15 +1837,143 @@ rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
     }
     if (!ok) result = RSC_ENOCONV;
   }
-  // leave the last converged wave in U and the context at its Ra
+  // leave the last converged state in U and the context at its parameter
   CK(cudaMemcpyAsync(U, H[slot[0]], n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
-  CKS(set_ra(hRa[0]));
+  CKS(set_x(hx[0]));
   *C = hC[0];
-  if (result != RSC_OK) ctx->err = "a continuation step did not converge after all retries";
+  if (result == RSC_ENOCONV) ctx->err = "a continuation step did not converge after all retries";
+  if (result == RSC_OK && under) {
+    ctx->err = "the last point is under-resolved (spectral tail above the threshold)";
+    result = RSC_ERESOLUTION;
+  }
   return result;
 }
 
+rsc_status spectral_tail(rsc_ctx* ctx, const double* U, double* cheb, double* sh) {
+  const Dims& d = ctx->d;
+  const long n = d.n();
+  if (!ctx->cont_cond) CK(cudaMalloc((void**)&ctx->cont_cond, (size_t)n * sizeof(double)));
+  if (!ctx->amax_v) CK(cudaMalloc((void**)&ctx->amax_v, 1024 * sizeof(double)));
+  if (!ctx->amax_i) CK(cudaMalloc((void**)&ctx->amax_i, 1025 * sizeof(long)));
+  CKS(rsc_conductive_state(ctx, ctx->cont_cond));
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(ctx->amax_v);
+  CK(cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), ctx->s));
+  int nb;
+  launch_1d_grid(n / 2, &nb);
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 4.0 * n);
+    k_spectral_tail<<<nb, 256, 0, ctx->s>>>(reinterpret_cast<const double2*>(U),
+                                            reinterpret_cast<const double2*>(ctx->cont_cond),
+                                            d.P, d.Nr, d.L, ctx->d_pair_l, acc);
+    CK(cudaGetLastError());
+  }
+  unsigned long long h[3];
+  CK(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  double v[3];
+  std::memcpy(v, h, sizeof(v));
+  *cheb = v[0] > 0 ? v[1] / v[0] : 0.0;
+  *sh = v[0] > 0 ? v[2] / v[0] : 0.0;
+  return RSC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsc_status rsc_continue_ra(rsc_ctx* ctx, double* U, double* C, long J,
+                           const rsc_continuation_opts* o, rsc_continuation_point* pts,
+                           int* npoints) {
+  if (!ctx || !U || !C || !o || !pts || !npoints || o->max_points < 2 || o->retries < 0 ||
+      !(o->Ra0 > 0) || !(o->Ra1 > 0) || o->Ra0 == o->Ra1)
+    return RSC_EINVAL;
+  *npoints = 0;
+  auto set_ra = [&](double Ra) -> rsc_status {
+    rsc_params q = ctx->p;     // Ra enters only the explicit terms: no refactorisation
+    q.Ra = Ra;
+    return rsc_set_params(ctx, &q);
+  };
+  std::vector<BranchPoint> bp;
+  const rsc_status st = follow_branch(ctx, U, C, J, o->Ra0, o->Ra1, o->Ra_end, o->n_opt, o->gamma,
+                                      o->max_points, o->retries, 0.0, &o->newton, set_ra, bp);
+  for (const BranchPoint& b : bp) {
+    rsc_continuation_point& q = pts[(*npoints)++];
+    q.Ra = b.x; q.C = b.C; q.KE = b.KE; q.Nu_in = b.Nu_in; q.Nu_out = b.Nu_out;
+    q.residual = b.residual; q.newton_iterations = b.its; q.gmres_total = b.gmres; q.mode = b.mode;
+  }
+  return st;
+}
+
+rsc_status rsc_continue_ek(rsc_ctx* ctx, double* U, double* C, long J,
+                           const rsc_ek_continuation_opts* o, rsc_ek_point* pts, int* npoints) {
+  if (!ctx || !U || !C || !o || !pts || !npoints || o->max_points < 2 || o->retries < 0 ||
+      !(o->Ek0 > 0) || !(o->Ek1 > 0) || !(o->Ek_end > 0) || o->Ek0 == o->Ek1 || o->ra_coef < 0)
+    return RSC_EINVAL;
+  *npoints = 0;
+  // x = log10 Ek (Eq. new_EK); Ek enters the implicit operator, so every new value refactorises
+  auto set_ek = [&](double x) -> rsc_status {
+    rsc_params q = ctx->p;
+    q.Ek = std::pow(10.0, x);
+    if (o->ra_coef > 0) q.Ra = o->ra_coef * std::pow(q.Ek, -1.0 / 3.0);
+    if (q.Ek == ctx->p.Ek && q.Ra == ctx->p.Ra) return RSC_OK;
+    return rsc_set_params(ctx, &q);
+  };
+  std::vector<BranchPoint> bp;
+  const rsc_status st = follow_branch(ctx, U, C, J, std::log10(o->Ek0), std::log10(o->Ek1),
+                                      std::log10(o->Ek_end), o->n_opt, o->gamma, o->max_points,
+                                      o->retries, o->tail_threshold, &o->newton, set_ek, bp);
+  for (const BranchPoint& b : bp) {
+    rsc_ek_point& q = pts[(*npoints)++];
+    q.Ek = std::pow(10.0, b.x);
+    q.Ra = o->ra_coef > 0 ? o->ra_coef * std::pow(q.Ek, -1.0 / 3.0) : ctx->p.Ra;
+    q.C = b.C; q.KE = b.KE; q.Nu_in = b.Nu_in; q.Nu_out = b.Nu_out; q.residual = b.residual;
+    q.cheb_tail = b.cheb_tail; q.sh_tail = b.sh_tail;
+    q.newton_iterations = b.its; q.gmres_total = b.gmres; q.mode = b.mode;
+  }
+  return st;
+}
+
+rsc_status rsc_spectral_tail(rsc_ctx* ctx, const double* U, double* cheb, double* sh) {
+  if (!ctx || !U || !cheb || !sh) return RSC_EINVAL;
+  return spectral_tail(ctx, U, cheb, sh);
+}
+
+rsc_status rsc_regrid(const rsc_ctx* src, const double* U_src, rsc_ctx* dst, double* U_dst) {
+  if (!src || !dst || !U_src || !U_dst) return RSC_EINVAL;
+  if (src->d.Ms != dst->d.Ms || src->p.eta != dst->p.eta) {
+    dst->err = "regrid needs the same azimuthal symmetry and radius ratio";
+    return RSC_EINVAL;
+  }
+  rsc_ctx* ctx = dst;
+  const long n = dst->d.n();
+  int nb;
+  launch_1d_grid(n / 2, &nb);
+  {
+    KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 0.0);
+    k_regrid<<<nb, 256, 0, dst->s>>>(reinterpret_cast<const double2*>(U_src), src->d.L, src->d.Nr,
+                                     src->d.P, reinterpret_cast<double2*>(U_dst), dst->d.Nr,
+                                     dst->d.P, dst->d_pair_l, dst->d_pair_m, dst->d.Ms);
+    CK(cudaGetLastError());
+  }
+  return RSC_OK;
+}
+
+rsc_status rsc_refine_params(const rsc_params* p, double cheb_tail, double sh_tail,
+                             double threshold, double growth, rsc_params* out, int* refined) {
+  if (!p || !out || !refined || !(growth > 1.0) || !(threshold > 0)) return RSC_EINVAL;
+  *out = *p;
+  *refined = 0;
+  if (cheb_tail > threshold) {
+    out->Nr = std::min(128, (int)std::ceil(p->Nr * growth));
+    if (out->Nr > p->Nr) *refined |= 1;
+  }
+  if (sh_tail > threshold) {
+    out->L = std::min(255, (int)std::ceil(p->L * growth));
+    if (out->L > p->L) *refined |= 2;
+  }
+  return RSC_OK;
+}
 
 // ===========================================================================
 // Batches of instances (continuation points in Ra, waves of different azimuthal

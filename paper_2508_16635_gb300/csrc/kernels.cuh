@@ -1472,4 +1472,60 @@ __global__ void k_argmax_finish(const double* __restrict__ pv, const long* __res
   if (threadIdx.x == 0) out[0] = si[0];
 }
 
+// Spectral tail of a state (the under-resolution test of Sec. 4.4): out[0] = the largest
+// |coefficient| of U - Uc, out[1] = the largest at the last Chebyshev degree k = Nr - 1,
+// out[2] = the largest at the last spherical-harmonic degree l = L, as the bit patterns
+// of non-negative doubles (whose unsigned order is their numeric order).
+__global__ void k_spectral_tail(const double2* __restrict__ U, const double2* __restrict__ Uc,
+                                int P, int Nr, int L, const int* __restrict__ pair_l,
+                                unsigned long long* __restrict__ out) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  const long n = 3L * P * Nr;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x) {
+    const double2 z = U[idx], c = Uc[idx];
+    const double a = hypot(z.x - c.x, z.y - c.y);
+    const int k = (int)(idx % Nr);
+    const int p = (int)((idx / Nr) % P);
+    a0 = fmax(a0, a);
+    if (k == Nr - 1) a1 = fmax(a1, a);
+    if (pair_l[p] == L) a2 = fmax(a2, a);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 = fmax(a0, __shfl_xor_sync(0xffffffffu, a0, o));
+    a1 = fmax(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+    a2 = fmax(a2, __shfl_xor_sync(0xffffffffu, a2, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out + 0, (unsigned long long)__double_as_longlong(a0));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(a1));
+    atomicMax(out + 2, (unsigned long long)__double_as_longlong(a2));
+  }
+}
+
+// Spectral interpolation between truncations of the same M_s (Sec. 4.4, refinement by
+// zero-filling the new modes): dst coefficient (field, m, l, k) = src coefficient when
+// l <= Ls, m <= Ls and k < Nrs, else zero.  One thread per complex dst coefficient.
+// The src pair of (m = a M_s, l) is a (Ls + 1) - M_s a (a - 1) / 2 + (l - m).
+__global__ void k_regrid(const double2* __restrict__ src, int Ls, int Nrs, int Ps,
+                         double2* __restrict__ dst, int Nrd, int Pd,
+                         const int* __restrict__ dpair_l, const int* __restrict__ dpair_m, int Ms) {
+  const long n = 3L * Pd * Nrd;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % Nrd);
+    const int p = (int)((idx / Nrd) % Pd);
+    const int f = (int)(idx / ((long)Nrd * Pd));
+    const int l = dpair_l[p], m = dpair_m[p];
+    double2 v = make_double2(0.0, 0.0);
+    if (l <= Ls && k < Nrs) {
+      const int a = m / Ms;
+      const long ps = (long)a * (Ls + 1) - (long)Ms * a * (a - 1) / 2 + (l - m);
+      v = src[((long)f * Ps + ps) * Nrs + k];
+    }
+    dst[idx] = v;
+  }
+}
+
 }  // namespace rsc

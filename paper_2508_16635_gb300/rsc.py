@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "librsc.so")
 
 RSC_FP64, RSC_MIXED = 0, 1
 STATUS = {0: "RSC_OK", 1: "RSC_EINVAL", 2: "RSC_ENOMEM", 3: "RSC_ECUDA", 4: "RSC_ENOCONV",
-          5: "RSC_ENAN", 6: "RSC_ESINGULAR", 7: "RSC_ETIMEOUT"}
+          5: "RSC_ENAN", 6: "RSC_ESINGULAR", 7: "RSC_ETIMEOUT", 8: "RSC_ERESOLUTION"}
 MAX_HISTORY = 64
 
 # Every symbol of include/rsc.h.
@@ -26,7 +26,8 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_diagnostics", "rsc_step2", "rsc_continuation_predict", "rsc_continue_ra",
            "rsc_batch_create", "rsc_batch_destroy", "rsc_batch_size", "rsc_batch_context",
            "rsc_batch_last_error", "rsc_batch_apply_jacobian", "rsc_batch_newton_rw",
-           "rsc_autotune", "rsc_get_tuning", "rsc_set_tuning", "rsc_batch_autotune")
+           "rsc_autotune", "rsc_get_tuning", "rsc_set_tuning", "rsc_batch_autotune",
+           "rsc_continue_ek", "rsc_spectral_tail", "rsc_regrid", "rsc_refine_params")
 NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
            "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
@@ -66,6 +67,24 @@ class ContinuationPoint(ctypes.Structure):
     _fields_ = [("Ra", ctypes.c_double), ("C", ctypes.c_double), ("KE", ctypes.c_double),
                 ("Nu_in", ctypes.c_double), ("Nu_out", ctypes.c_double),
                 ("residual", ctypes.c_double), ("newton_iterations", ctypes.c_int),
+                ("gmres_total", ctypes.c_int), ("mode", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class EkContinuationOpts(ctypes.Structure):
+    _fields_ = [("Ek0", ctypes.c_double), ("Ek1", ctypes.c_double), ("Ek_end", ctypes.c_double),
+                ("ra_coef", ctypes.c_double), ("n_opt", ctypes.c_int), ("gamma", ctypes.c_double),
+                ("max_points", ctypes.c_int), ("retries", ctypes.c_int),
+                ("tail_threshold", ctypes.c_double), ("newton", NewtonOpts)]
+
+
+class EkPoint(ctypes.Structure):
+    _fields_ = [("Ek", ctypes.c_double), ("Ra", ctypes.c_double), ("C", ctypes.c_double),
+                ("KE", ctypes.c_double), ("Nu_in", ctypes.c_double), ("Nu_out", ctypes.c_double),
+                ("residual", ctypes.c_double), ("cheb_tail", ctypes.c_double),
+                ("sh_tail", ctypes.c_double), ("newton_iterations", ctypes.c_int),
                 ("gmres_total", ctypes.c_int), ("mode", ctypes.c_int)]
 
     def as_dict(self):
@@ -130,6 +149,12 @@ def load_library(path=LIB_PATH):
         "rsc_launch_count": ([P, ctypes.POINTER(ctypes.c_long)], I),
         "rsc_norm2_noalloc": ([P, ctypes.c_size_t, P, P], I),
         "rsc_step2": ([P, P, D, I], I),
+        "rsc_continue_ek": ([P, P, ctypes.POINTER(D), ctypes.c_long,
+                             ctypes.POINTER(EkContinuationOpts), P, ctypes.POINTER(I)], I),
+        "rsc_spectral_tail": ([P, P, ctypes.POINTER(D), ctypes.POINTER(D)], I),
+        "rsc_regrid": ([P, P, P, P], I),
+        "rsc_refine_params": ([ctypes.POINTER(Params), D, D, D, D, ctypes.POINTER(Params),
+                               ctypes.POINTER(I)], I),
         "rsc_autotune": ([P, ctypes.POINTER(Tuning)], I),
         "rsc_get_tuning": ([P, ctypes.POINTER(Tuning)], I),
         "rsc_set_tuning": ([P, ctypes.POINTER(Tuning)], I),
@@ -280,6 +305,43 @@ class RotatingShell:
         if st not in (0, 4):
             self._check(st)
         return Cv.value, rep.as_dict(), st
+
+    def continue_ek(self, U, C, J, Ek0, Ek1, Ek_end, ra_coef=0.0, n_opt=3, gamma=400.0,
+                    max_points=8, retries=3, tail_threshold=0.0, tol=1e-10, max_newton=12,
+                    kmax=200, gmres_tol=1e-10, dt_newton=200.0):
+        """Ek continuation at this resolution (rsc_continue_ek); returns (points, C, status),
+        status 8 (RSC_ERESOLUTION) when the last point is under-resolved."""
+        opts = EkContinuationOpts(Ek0, Ek1, Ek_end, ra_coef, n_opt, gamma, max_points, retries,
+                                  tail_threshold,
+                                  NewtonOpts(tol, max_newton, kmax, gmres_tol, dt_newton))
+        pts = (EkPoint * max_points)()
+        npts = ctypes.c_int(0)
+        Cv = ctypes.c_double(C)
+        st = self.lib.rsc_continue_ek(self._ctx, self._vec(U), ctypes.byref(Cv),
+                                      -1 if J is None else int(J), ctypes.byref(opts),
+                                      ctypes.cast(pts, ctypes.c_void_p), ctypes.byref(npts))
+        if st not in (0, 4, 8):
+            self._check(st)
+        return [pts[i].as_dict() for i in range(npts.value)], Cv.value, st
+
+    def spectral_tail(self, U):
+        """(Chebyshev, spherical-harmonic) tail ratios of U - U_cond (rsc_spectral_tail)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.rsc_spectral_tail(self._ctx, self._vec(U), ctypes.byref(a),
+                                               ctypes.byref(b)))
+        return a.value, b.value
+
+    def regrid_from(self, other, U_other):
+        """This context's state holding `other`'s state U_other (rsc_regrid)."""
+        out = self.new_state()
+        self._check(self.lib.rsc_regrid(other._ctx, other._vec(U_other), self._ctx, _ptr(out)))
+        return out
+
+    def phase_slot(self, M, k):
+        """Index of Im T at (l = m = M, Chebyshev degree k) in this layout."""
+        a = M // self.Ms
+        p = a * (self.L + 1) - self.Ms * a * (a - 1) // 2
+        return ((2 * self.P + p) * self.Nr + k) * 2 + 1
 
     def autotune(self):
         """Pick the launch shapes by timing (rsc_autotune); returns them as a dict."""
@@ -478,3 +540,45 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def refine_params(params, cheb_tail, sh_tail, threshold, growth=1.2, lib=None):
+    """rsc_refine_params: (new Params, refined bits: 1 radial, 2 angular)."""
+    lib = lib or load_library()
+    out = Params()
+    refined = ctypes.c_int(0)
+    st = lib.rsc_refine_params(ctypes.byref(params), cheb_tail, sh_tail, threshold, growth,
+                               ctypes.byref(out), ctypes.byref(refined))
+    if st != 0:
+        raise RscError(st, "rsc_refine_params rejected its arguments")
+    return out, refined.value
+
+
+def follow_ek(shell, U, C, M, k_phase, Ek0, Ek1, Ek_end, tail_threshold=1e-6, growth=1.2,
+              max_refinements=4, **kw):
+    """Ek continuation with grid refinement (Sec. 4.4): rsc_continue_ek on the current
+    resolution; on an under-resolved point, a context refined by rsc_refine_params receives
+    the state by rsc_regrid and the continuation resumes from that point's Ek with the same
+    step ratio.  The phase slot is Im T at (l = m = M, Chebyshev degree k_phase).  Returns
+    (points with the resolution of each, the final shell, its state, C)."""
+    points = []
+    for r in range(max_refinements + 1):
+        pts, C, st = shell.continue_ek(U, C, shell.phase_slot(M, k_phase), Ek0, Ek1, Ek_end,
+                                       tail_threshold=tail_threshold, **kw)
+        points += [dict(p, L=shell.L, Nr=shell.Nr) for p in pts]
+        if st != 8 or r == max_refinements or not pts:
+            return points, shell, U, C
+        last = pts[-1]
+        newp, bits = refine_params(shell.params, last["cheb_tail"], last["sh_tail"],
+                                   tail_threshold, growth, shell.lib)
+        if bits == 0:
+            return points, shell, U, C
+        prec = "mixed" if newp.precision == RSC_MIXED else "fp64"
+        fine = RotatingShell(newp.L, newp.Ms, newp.Nr, newp.Ek, newp.Ra, newp.Pr, newp.eta,
+                             precision=prec, device=shell.device,
+                             coriolis="explicit" if newp.explicit_coriolis else "implicit")
+        U = fine.regrid_from(shell, U)
+        ratio = (pts[-1]["Ek"] / pts[-2]["Ek"]) if len(pts) > 1 else Ek1 / Ek0
+        Ek0, Ek1 = last["Ek"], last["Ek"] * ratio
+        shell = fine
+    return points, shell, U, C

@@ -420,3 +420,76 @@ def test_autotune_keeps_results_bitwise(torch, name, L, Ms, Nr, Ek, Ra):
         with pytest.raises(Exception):
             gpu.set_tuning(bad)
         gpu.close()
+
+
+def test_regrid_and_spectral_tail_parity(torch):
+    """rsc_regrid against the oracle's zero fill (bitwise), both ways; rsc_spectral_tail
+    against the ratios computed from the coefficients in numpy."""
+    from oracle import continuation as ct
+    from paper_2508_16635_gb300 import RotatingShell
+    L0, Ms, Nr0, L1, Nr1 = 15, 4, 12, 19, 15
+    a = RotatingShell(L0, Ms, Nr0, 1e-3, 100.0)
+    b = RotatingShell(L1, Ms, Nr1, 1e-3, 100.0)
+    s0 = Shell(L0, Ms, Nr0, 1e-3, 100.0)
+    x = s0.conductive_state() + si.perturbation(L0, Ms, Nr0, seed=71)
+    Ub = b.regrid_from(a, torch.tensor(x, device="cuda"))
+    y = ct.regrid(x, L0, Ms, Nr0, L1, Nr1)
+    assert np.array_equal(Ub.cpu().numpy(), y)
+    Ua = a.regrid_from(b, Ub)
+    assert np.array_equal(Ua.cpu().numpy(), x)
+    cheb, sh = a.spectral_tail(torch.tensor(x, device="cuda"))
+    z = s0.to_complex(x - s0.conductive_state())
+    A = np.abs(z).max()
+    assert abs(cheb - np.abs(z[:, :, -1]).max() / A) < 1e-14
+    assert abs(sh - np.abs(z[:, s0.pair_l == L0, :]).max() / A) < 1e-14
+    a.close()
+    b.close()
+
+
+def test_ek_continuation_parity(torch):
+    """rsc_continue_ek against the oracle's continuation in log10 Ek (Sec. 4.4) on the RW4
+    branch with Ra = 12 Ek^(-1/3) (Ra = 120 at Ek = 1e-3)."""
+    from oracle import continuation as ct
+    from paper_2508_16635_gb300 import RotatingShell
+    L, Ms, Nr, Ek, M = 31, 4, 24, 1e-3, 4
+    s = Shell(L, Ms, Nr, Ek, 120.0)
+    U0, C0, J = _rw_initial_guess(s, M)
+    kw = dict(n_opt=3, gamma=400.0, max_points=3, kmax=150)
+    pts_o = ct.continue_ek(s, U0, C0, J, 1e-3, 0.97e-3, 0.5e-3, ra_coef=12.0, **kw)
+    gpu = RotatingShell(L, Ms, Nr, Ek, 120.0)
+    U = torch.tensor(U0, device="cuda")
+    pts_g, Cg, st = gpu.continue_ek(U, C0, J, 1e-3, 0.97e-3, 0.5e-3, ra_coef=12.0, **kw)
+    assert st == 0 and len(pts_g) == len(pts_o) == 3
+    for a, b in zip(pts_o, pts_g):
+        assert a["its"] == b["newton_iterations"]
+        assert abs(10 ** a["Ra"] - b["Ek"]) <= 1e-12 * b["Ek"]
+        assert abs(b["Ra"] - 12.0 * b["Ek"] ** (-1.0 / 3.0)) < 1e-10
+        assert b["residual"] < 1e-10
+        assert abs(a["C"] - b["C"]) <= 1e-9 * abs(a["C"])
+    assert _rel(U.cpu().numpy(), pts_o[-1]["U"]) < 1e-9
+    gpu.close()
+
+
+def test_ek_continuation_refines_the_grid(torch):
+    """A tail threshold below the wave's own tail forces one refinement: the continuation
+    resumes on the finer grid from the regridded wave, which converges to nearly the same
+    drift (the coarse grid already resolves it to about 1e-4)."""
+    from paper_2508_16635_gb300.rsc import RotatingShell, follow_ek
+    L, Ms, Nr, Ek, M = 31, 4, 24, 1e-3, 4
+    s = Shell(L, Ms, Nr, Ek, 120.0)
+    U0, C0, J = _rw_initial_guess(s, M)
+    k_phase = (J // 2) % Nr
+    gpu = RotatingShell(L, Ms, Nr, Ek, 120.0)
+    U = torch.tensor(U0, device="cuda")
+    cheb, sh = gpu.spectral_tail(U)
+    thr = 0.5 * max(cheb, sh)
+    pts, fine, Uf, Cf = follow_ek(gpu, U, C0, M, k_phase, 1e-3, 0.98e-3, 0.9e-3, tail_threshold=thr,
+                                  max_refinements=1, ra_coef=12.0, max_points=3, kmax=150)
+    assert (fine.L, fine.Nr) != (L, Nr)
+    coarse = [p for p in pts if (p["L"], p["Nr"]) == (L, Nr)]
+    refined = [p for p in pts if (p["L"], p["Nr"]) == (fine.L, fine.Nr)]
+    assert coarse and refined and refined[0]["residual"] < 1e-10
+    assert abs(refined[0]["Ek"] - coarse[-1]["Ek"]) < 1e-15
+    assert abs(refined[0]["C"] - coarse[-1]["C"]) < 1e-3 * abs(coarse[-1]["C"])
+    fine.close()
+    gpu.close()
