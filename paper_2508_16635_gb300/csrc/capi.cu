@@ -508,6 +508,14 @@ int chain_maxq(int Nr) {
   return q <= 2 ? 2 : q <= 4 ? 4 : q <= 8 ? 8 : q <= 12 ? 12 : 16;
 }
 
+// Dynamic shared memory of the chain sweeps: vectors, plus this CTA's rows of every swept
+// block (a sweep has at most (L + 1) / 2 + 1 steps).
+size_t chain_smem(const Dims& d, int CS, bool outward) {
+  const int RPC = (d.Nr + CS - 1) / CS;
+  const int steps = (d.L + 2) / 2 + 1;
+  return ((outward ? 4 : 2) * (size_t)d.Nr + (size_t)steps * RPC) * sizeof(double2);
+}
+
 template <int Q>
 cudaError_t launch_chain_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
   const Dims& d = ctx->d;
@@ -516,7 +524,7 @@ cudaError_t launch_chain_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool o
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * 2 * d.nm * CS);
   cfg.blockDim = dim3(32 * ((RPC + 3) / 4));
-  cfg.dynamicSmemBytes = (outward ? 4 : 2) * (size_t)d.Nr * sizeof(double2);
+  cfg.dynamicSmemBytes = chain_smem(d, CS, outward);
   cfg.stream = ctx->s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -578,11 +586,18 @@ bool cluster_ok(const Dims& d, int CS) {
   for (int w = 0; w < 2; ++w) {
     cudaFuncSetAttribute(fns[w], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaGetLastError();
+    const size_t smem = chain_smem(d, CS, w == 1);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fns[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
     const int RPC = (d.Nr + CS - 1) / CS;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * 2 * d.nm * CS);
     cfg.blockDim = dim3(32 * ((RPC + 3) / 4));
-    cfg.dynamicSmemBytes = (w ? 4 : 2) * (size_t)d.Nr * sizeof(double2);
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CS;

@@ -847,16 +847,18 @@ __global__ void k_chain_half(DevGeom g, const long* __restrict__ chain_off,
                              double2* __restrict__ mid, int CS) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ double2 sv[];  // [2][Nr]
+  extern __shared__ double2 sv[];  // [2][Nr] ping-pong, then hist[steps][RPC]
   const ChainInfo ci = chain_info(g, chain_off, CS);
   const int Nr = ci.Nr;
   const int rank = (int)cluster.block_rank();
   const int RPC = (Nr + CS - 1) / CS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lr = warp * 4 + (lane >> 3);   // row within this CTA
+  double2* hist = sv + 2 * Nr;              // this CTA's rows of every swept block
   ChainLane<MAXQ> ln;
-  ln.r = rank * RPC + warp * 4 + (lane >> 3);
+  ln.r = rank * RPC + lr;
   ln.s = lane & 7;
-  ln.active = (warp * 4 + (lane >> 3)) < RPC && ln.r < Nr;
+  ln.active = lr < RPC && ln.r < Nr;
   // top: start at block 0, sweep 1 .. km-1; bottom: start at nb-1, sweep nb-2 .. km+1
   const bool has = ci.dir == 0 ? (ci.km >= 1) : (ci.km <= ci.nb - 2);
   const int first = ci.dir == 0 ? 0 : ci.nb - 1;
@@ -883,11 +885,17 @@ __global__ void k_chain_half(DevGeom g, const long* __restrict__ chain_off,
     const double2 acc = ln.dot(mc, sv + ((t - 1) & 1) * Nr, Nr, ci.m == 0);
     const double2 v = make_double2(gc.x - acc.x, gc.y - acc.y);
     if (ln.active) {
-      if (ln.s == 0) out[ci.row(i) + ln.r] = v;
+      // the global store waits until after the sweep: the barrier's release fence would
+      // otherwise wait for it at every block
+      if (ln.s == 0) hist[(t - 1) * RPC + lr] = v;
       for (int dst = ln.s; dst < CS; dst += 8)
         cluster.map_shared_rank(sv + (t & 1) * Nr, dst)[ln.r] = v;
     }
     cluster.sync();
+  }
+  for (int idx = threadIdx.x; idx < count * RPC; idx += blockDim.x) {
+    const int t = idx / RPC + 1, r = rank * RPC + idx % RPC;
+    if (r < Nr) out[ci.row(first + t * step) + r] = hist[idx];
   }
   if (rank == 0) {
     const double2* last = sv + ((count > 0 ? count : 0) & 1) * Nr;
@@ -906,16 +914,18 @@ __global__ void k_chain_out(DevGeom g, const long* __restrict__ chain_off,
                             double2* __restrict__ out, const double2* __restrict__ mid, int CS) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ double2 sv[];  // [2][Nr] ping-pong, [2][Nr] middle inputs
+  extern __shared__ double2 sv[];  // [2][Nr] ping-pong, [2][Nr] middle inputs, hist[steps][RPC]
   const ChainInfo ci = chain_info(g, chain_off, CS);
   const int Nr = ci.Nr;
   const int rank = (int)cluster.block_rank();
   const int RPC = (Nr + CS - 1) / CS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lr = warp * 4 + (lane >> 3);
+  double2* hist = sv + 4 * Nr;
   ChainLane<MAXQ> ln;
-  ln.r = rank * RPC + warp * 4 + (lane >> 3);
+  ln.r = rank * RPC + lr;
   ln.s = lane & 7;
-  ln.active = (warp * 4 + (lane >> 3)) < RPC && ln.r < Nr;
+  ln.active = lr < RPC && ln.r < Nr;
   const int km = ci.km, nb = ci.nb;
   double2* yup = sv + 2 * Nr;   // y_{k-1}
   double2* zdn = sv + 3 * Nr;   // z_{k+1}
@@ -966,11 +976,15 @@ __global__ void k_chain_out(DevGeom g, const long* __restrict__ chain_off,
     const double2 a3 = ln.dot(mc, sv + ((t - 1) & 1) * Nr, Nr, ci.m == 0);
     const double2 v = make_double2(yc.x - a3.x, yc.y - a3.y);
     if (ln.active) {
-      if (ln.s == 0) out[ci.row(i) + ln.r] = v;
+      if (ln.s == 0) hist[(t - 1) * RPC + lr] = v;   // stored after the sweep
       for (int dst = ln.s; dst < CS; dst += 8)
         cluster.map_shared_rank(sv + (t & 1) * Nr, dst)[ln.r] = v;
     }
     cluster.sync();
+  }
+  for (int idx = threadIdx.x; idx < count * RPC; idx += blockDim.x) {
+    const int t = idx / RPC + 1, r = rank * RPC + idx % RPC;
+    if (r < Nr) out[ci.row(km + t * step) + r] = hist[idx];
   }
 }
 
