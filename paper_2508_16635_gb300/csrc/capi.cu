@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "chain_async.cuh"
 #include "legendre_tc.cuh"
 #include "rsc_internal.h"
 
@@ -84,6 +85,7 @@ struct rsc_ctx {
   double* h_pinned = nullptr;
   int nblk_dot = 0;
   int cluster = 8;  // CTAs per chain in the cluster chain solve
+  int chain_async = 0;   // 1: sweeps with column-split warps and st.async / mbarrier exchange
   int rt_synth[2] = {1, 1}, rt_anal[2] = {1, 1};  // radii per block, [fp64, fp32]
   int wpb[2] = {0, 0};     // warps per block of the products kernel (0: largest that fits)
   int ppb[2] = {0, 0};     // pairs per block of the right-hand-side kernel (0: 256 / Nr)
@@ -516,8 +518,45 @@ size_t chain_smem(const Dims& d, int CS, bool outward) {
   return ((outward ? 4 : 2) * (size_t)d.Nr + (size_t)steps * RPC) * sizeof(double2);
 }
 
+// Dynamic shared memory of the asynchronous-exchange sweeps (chain_async.cuh).
+int chain_steps_cap(const Dims& d) { return (d.L + 2) / 2 + 1; }
+size_t chain_smem_async(const Dims& d, int CS, bool outward) {
+  const int RPC = (d.Nr + CS - 1) / CS;
+  return ((outward ? 4 : 2) * (size_t)d.Nr + (size_t)RPC * (1 + chain_steps_cap(d))) *
+             sizeof(double2) + 16;
+}
+
+template <int Q>
+cudaError_t launch_chain_async_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
+  const Dims& d = ctx->d;
+  const int CS = ctx->cluster;
+  const int RPC = (d.Nr + CS - 1) / CS;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * 2 * d.nm * CS);
+  cfg.blockDim = dim3(64 * ((RPC + 3) / 4));
+  cfg.dynamicSmemBytes = chain_smem_async(d, CS, outward);
+  cfg.stream = ctx->s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int cap = chain_steps_cap(d);
+  if (outward)
+    return cudaLaunchKernelEx(&cfg, k_chain_out_async<Q / 2>, ctx->geom(), (const long*)f->chain_off,
+                              (const double2*)f->H, (const double2*)f->W,
+                              reinterpret_cast<double2*>(out), (const double2*)ctx->mid, CS, cap,
+                              ctx->d_status);
+  return cudaLaunchKernelEx(&cfg, k_chain_half_async<Q / 2>, ctx->geom(), (const long*)f->chain_off,
+                            (const double2*)f->H, reinterpret_cast<double2*>(out), ctx->mid, CS,
+                            cap, ctx->d_status);
+}
+
 template <int Q>
 cudaError_t launch_chain_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
+  if (ctx->chain_async) return launch_chain_async_q<Q>(ctx, f, out, outward);
   const Dims& d = ctx->d;
   const int CS = ctx->cluster;
   const int RPC = (d.Nr + CS - 1) / CS;
@@ -579,6 +618,44 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
   return RSC_OK;
 }
 
+// Whether the device can co-schedule clusters of CS CTAs for the asynchronous sweeps.
+template <int Q>
+bool cluster_ok_async(const Dims& d, int CS) {
+  const void* fns[2] = {(const void*)k_chain_half_async<Q / 2>, (const void*)k_chain_out_async<Q / 2>};
+  for (int w = 0; w < 2; ++w) {
+    cudaFuncSetAttribute(fns[w], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaGetLastError();
+    const size_t smem = chain_smem_async(d, CS, w == 1);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fns[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    const int RPC = (d.Nr + CS - 1) / CS;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * 2 * d.nm * CS);
+    cfg.blockDim = dim3(64 * ((RPC + 3) / 4));
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cfg.blockDim.x > 1024 ||
+        cudaOccupancyMaxActiveClusters(&n, fns[w], &cfg) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  return true;
+}
+
+bool chain_config_ok(const Dims& d, int CS, int async_mode);
+
 // Largest cluster (16, else 8, 4, 2) that the device can co-schedule for the chain sweeps.
 template <int Q>
 bool cluster_ok(const Dims& d, int CS) {
@@ -633,6 +710,17 @@ rsc_status choose_cluster(rsc_ctx* ctx) {
   }
   ctx->err = "no thread-block cluster configuration available for the chain solve";
   return RSC_ECUDA;
+}
+
+bool chain_config_ok(const Dims& d, int CS, int async_mode) {
+  if (CS > d.Nr) return false;
+  switch (chain_maxq(d.Nr)) {
+    case 2: return async_mode ? cluster_ok_async<2>(d, CS) : cluster_ok<2>(d, CS);
+    case 4: return async_mode ? cluster_ok_async<4>(d, CS) : cluster_ok<4>(d, CS);
+    case 8: return async_mode ? cluster_ok_async<8>(d, CS) : cluster_ok<8>(d, CS);
+    case 12: return async_mode ? cluster_ok_async<12>(d, CS) : cluster_ok<12>(d, CS);
+    default: return async_mode ? cluster_ok_async<16>(d, CS) : cluster_ok<16>(d, CS);
+  }
 }
 
 RhsParams make_rp(rsc_ctx* ctx, double dt, double C, int mode) {
@@ -1072,15 +1160,8 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
   }
   if (t.synth_radii < 1 || t.synth_radii > radii_limit((const void*)k_synth<double>, round32(d.nlat2)))
     return false;
-  bool ok = false;
-  switch (chain_maxq(d.Nr)) {
-    case 2: ok = cluster_ok<2>(d, t.chain_cluster); break;
-    case 4: ok = cluster_ok<4>(d, t.chain_cluster); break;
-    case 8: ok = cluster_ok<8>(d, t.chain_cluster); break;
-    case 12: ok = cluster_ok<12>(d, t.chain_cluster); break;
-    default: ok = cluster_ok<16>(d, t.chain_cluster); break;
-  }
-  return ok && t.chain_cluster <= d.Nr;
+  if (t.chain_async != 0 && t.chain_async != 1) return false;
+  return chain_config_ok(d, t.chain_cluster, t.chain_async);
 }
 
 void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
@@ -1096,6 +1177,7 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
   }
   t->synth_radii = ctx->rt_synth[0];
   t->chain_cluster = ctx->cluster;
+  t->chain_async = ctx->chain_async;
   for (int q = 0; q < 5; ++q) t->ms[q] = ctx->tune_ms[q];
 }
 
@@ -1107,6 +1189,7 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
   }
   ctx->rt_synth[0] = t.synth_radii;
   ctx->cluster = t.chain_cluster;
+  ctx->chain_async = t.chain_async;
   if (ctx->jvp_exec) {   // the captured Jacobian action embeds the old launch shapes
     cudaGraphExecDestroy(ctx->jvp_exec);
     ctx->jvp_exec = nullptr;
@@ -1201,23 +1284,26 @@ rsc_status autotune(rsc_ctx* ctx, rsc_tuning* out) {
     DevFactor* f = nullptr;
     st = get_factor(ctx, 200.0, &f);
     double best = 1e30;
-    int bc = t.chain_cluster;
-    for (int cs : {16, 8, 4, 2}) {
-      if (st != RSC_OK) break;
-      rsc_tuning probe = t;
-      probe.chain_cluster = cs;
-      if (!tuning_ok(ctx, probe)) continue;
-      ctx->cluster = cs;
-      st = stage_solve(ctx, f, ctx->xtmp);
-      cudaEventRecord(e0, ctx->s);
-      for (int r = 0; r < 3 && st == RSC_OK; ++r) st = stage_solve(ctx, f, ctx->xtmp);
-      cudaEventRecord(e1, ctx->s);
-      if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (st == RSC_OK && ms / 3.0 < best) { best = ms / 3.0; bc = cs; }
+    int bc = t.chain_cluster, ba = t.chain_async;
+    for (int am : {0, 1}) {
+      for (int cs : {16, 8, 4, 2}) {
+        if (st != RSC_OK) break;
+        if (!chain_config_ok(ctx->d, cs, am)) continue;
+        ctx->cluster = cs;
+        ctx->chain_async = am;
+        st = stage_solve(ctx, f, ctx->xtmp);
+        cudaEventRecord(e0, ctx->s);
+        for (int r = 0; r < 3 && st == RSC_OK; ++r) st = stage_solve(ctx, f, ctx->xtmp);
+        cudaEventRecord(e1, ctx->s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st == RSC_OK && ms / 3.0 < best) { best = ms / 3.0; bc = cs; ba = am; }
+      }
     }
+    if (st == RSC_OK) st = check_status(ctx);   // a timed-out wait of a sweep candidate
     t.chain_cluster = bc;
+    t.chain_async = ba;
     ctx->tune_ms[3] = best;
   }
   ctx->prof_on = prof;

@@ -48,13 +48,14 @@ class NewtonOpts(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("products_warps", ctypes.c_int * 2), ("analysis_radii", ctypes.c_int * 2),
                 ("synth_radii", ctypes.c_int), ("rhs_pairs", ctypes.c_int * 2),
-                ("chain_cluster", ctypes.c_int), ("ms", ctypes.c_double * 5)]
+                ("chain_cluster", ctypes.c_int), ("chain_async", ctypes.c_int),
+                ("ms", ctypes.c_double * 5)]
 
     def as_dict(self):
         return {"products_warps": list(self.products_warps),
                 "analysis_radii": list(self.analysis_radii), "synth_radii": self.synth_radii,
                 "rhs_pairs": list(self.rhs_pairs), "chain_cluster": self.chain_cluster,
-                "ms": list(self.ms)}
+                "chain_async": self.chain_async, "ms": list(self.ms)}
 
 
 class ContinuationOpts(ctypes.Structure):
@@ -361,6 +362,7 @@ class RotatingShell:
         t.synth_radii = d["synth_radii"]
         t.rhs_pairs[:] = d["rhs_pairs"]
         t.chain_cluster = d["chain_cluster"]
+        t.chain_async = d.get("chain_async", 0)
         self._check(self.lib.rsc_set_tuning(self._ctx, ctypes.byref(t)))
 
     def continue_ra(self, U, C, J, Ra0, Ra1, Ra_end, n_opt=4, gamma=20.0, max_points=8,

@@ -399,9 +399,44 @@ def test_batch_newton_matches_single_instance_solves(torch):
 
 
 @pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES)
+@pytest.mark.parametrize("cluster", [16, 8, 4, 2])
+def test_async_chain_sweeps_parity(torch, name, L, Ms, Nr, Ek, Ra, cluster):
+    """The sweeps with column-split warps and st.async / mbarrier exchange (chain_async = 1)
+    against the oracle, for every cluster size the device accepts."""
+    from paper_2508_16635_gb300 import RotatingShell
+    make = lambda: Shell(L, Ms, Nr, Ek, Ra)
+    x = make().conductive_state() + si.perturbation(L, Ms, Nr, seed=22, amp=1e-2)
+    want, spread = _oracle_spread(make, lambda s: s.step(x, -2.7, 2e-3, nsteps=2))
+    u = si.random_vector(L, Ms, Nr, seed=24)
+    J = make().real_index("T", Ms, Ms, 1, 1)
+    u[J] = 0.7
+    wantj, spreadj = _oracle_spread(make, lambda so: so.jvp(x, -1.1, J, u, 200.0))
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra)
+    t = gpu.tuning()
+    t.update(chain_cluster=cluster, chain_async=1)
+    try:
+        gpu.set_tuning(t)
+    except Exception:
+        gpu.close()
+        pytest.skip(f"cluster of {cluster} not schedulable for N_r = {Nr}")
+    U = torch.tensor(x, device="cuda")
+    gpu.step(U, -2.7, 2e-3, nsteps=2)
+    errs = _rel_fields(make(), U.cpu().numpy(), want)
+    tol = _tolerances(spread)
+    assert all(e < tt for e, tt in zip(errs, tol)), (errs, tol, spread)
+    got = gpu.apply_jacobian(torch.tensor(x, device="cuda"), -1.1, J,
+                             torch.tensor(u, device="cuda"), 200.0).cpu().numpy()
+    errs = _rel_fields(make(), got, wantj)
+    tol = [max(1e-10, tt) for tt in _tolerances(spreadj)]
+    assert all(e < tt for e, tt in zip(errs, tol)), (errs, tol, spreadj)
+    gpu.close()
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES)
 def test_autotune_keeps_results_bitwise(torch, name, L, Ms, Nr, Ek, Ra):
     """The autotuner only changes launch shapes (which rows, radii or pairs a block takes),
-    never the order of any sum: steps and Jacobian actions are bit-identical after it."""
+    never the order of any sum: with the sweep variant held fixed, steps and Jacobian
+    actions are bit-identical after it."""
     from paper_2508_16635_gb300 import RotatingShell
     s = Shell(L, Ms, Nr, Ek, Ra)
     x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=61, amp=3e-2)
@@ -413,6 +448,7 @@ def test_autotune_keeps_results_bitwise(torch, name, L, Ms, Nr, Ek, Ra):
         s0 = gpu.step(U.clone(), 0.0, 1e-3).clone()
         t = gpu.autotune()
         assert t["chain_cluster"] in (2, 4, 8, 16) and min(t["rhs_pairs"]) >= 1
+        gpu.set_tuning(dict(t, chain_async=0))   # the sweep variant sums rows in another order
         a1 = gpu.apply_jacobian(U, 0.3, None, torch.tensor(u, device="cuda"), 200.0)
         s1 = gpu.step(U.clone(), 0.0, 1e-3)
         assert torch.equal(a0, a1) and torch.equal(s0, s1)
