@@ -323,8 +323,9 @@ typedef struct {
   int rhs_pairs[2];        /* (l, m) pairs per block of the right-hand-side kernel    */
   int chain_cluster;       /* CTAs per thread-block cluster of the chain sweeps       */
   int chain_async;         /* 0: one warp per 4 rows, a cluster barrier per block;
-                              1: two warps per 4 rows (column halves), rows sent with
-                              st.async to mbarriers (changes the order of the row sums) */
+                              1 / 2: two / four warps per 4 rows (column parts), rows
+                              sent with st.async to mbarriers (changes the order of the
+                              row sums)                                                */
   double ms[5];            /* after rsc_autotune: best times (ms) of products +
                               analysis (mixed), FP64 synthesis, RHS (mixed), chain
                               solve; zero otherwise                                   */

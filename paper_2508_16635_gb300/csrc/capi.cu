@@ -520,21 +520,21 @@ size_t chain_smem(const Dims& d, int CS, bool outward) {
 
 // Dynamic shared memory of the asynchronous-exchange sweeps (chain_async.cuh).
 int chain_steps_cap(const Dims& d) { return (d.L + 2) / 2 + 1; }
-size_t chain_smem_async(const Dims& d, int CS, bool outward) {
+size_t chain_smem_async(const Dims& d, int CS, bool outward, int NS) {
   const int RPC = (d.Nr + CS - 1) / CS;
-  return ((outward ? 4 : 2) * (size_t)d.Nr + (size_t)RPC * (1 + chain_steps_cap(d))) *
+  return ((outward ? 4 : 2) * (size_t)d.Nr + (size_t)RPC * (NS - 1 + chain_steps_cap(d))) *
              sizeof(double2) + 16;
 }
 
-template <int Q>
+template <int Q, int NS>
 cudaError_t launch_chain_async_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
   const Dims& d = ctx->d;
   const int CS = ctx->cluster;
   const int RPC = (d.Nr + CS - 1) / CS;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * 2 * d.nm * CS);
-  cfg.blockDim = dim3(64 * ((RPC + 3) / 4));
-  cfg.dynamicSmemBytes = chain_smem_async(d, CS, outward);
+  cfg.blockDim = dim3(32 * NS * ((RPC + 3) / 4));
+  cfg.dynamicSmemBytes = chain_smem_async(d, CS, outward, NS);
   cfg.stream = ctx->s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -545,18 +545,22 @@ cudaError_t launch_chain_async_q(rsc_ctx* ctx, const DevFactor* f, double* out, 
   cfg.numAttrs = 1;
   const int cap = chain_steps_cap(d);
   if (outward)
-    return cudaLaunchKernelEx(&cfg, k_chain_out_async<Q / 2>, ctx->geom(), (const long*)f->chain_off,
-                              (const double2*)f->H, (const double2*)f->W,
-                              reinterpret_cast<double2*>(out), (const double2*)ctx->mid, CS, cap,
-                              ctx->d_status);
-  return cudaLaunchKernelEx(&cfg, k_chain_half_async<Q / 2>, ctx->geom(), (const long*)f->chain_off,
-                            (const double2*)f->H, reinterpret_cast<double2*>(out), ctx->mid, CS,
-                            cap, ctx->d_status);
+    return cudaLaunchKernelEx(&cfg, k_chain_out_async<Q / NS, NS>, ctx->geom(),
+                              (const long*)f->chain_off, (const double2*)f->H,
+                              (const double2*)f->W, reinterpret_cast<double2*>(out),
+                              (const double2*)ctx->mid, CS, cap, ctx->d_status);
+  return cudaLaunchKernelEx(&cfg, k_chain_half_async<Q / NS, NS>, ctx->geom(),
+                            (const long*)f->chain_off, (const double2*)f->H,
+                            reinterpret_cast<double2*>(out), ctx->mid, CS, cap, ctx->d_status);
 }
 
 template <int Q>
 cudaError_t launch_chain_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
-  if (ctx->chain_async) return launch_chain_async_q<Q>(ctx, f, out, outward);
+  if (ctx->chain_async == 1) return launch_chain_async_q<Q, 2>(ctx, f, out, outward);
+  if (ctx->chain_async == 2) {
+    if constexpr (Q % 4 == 0) return launch_chain_async_q<Q, 4>(ctx, f, out, outward);
+    return cudaErrorInvalidValue;
+  }
   const Dims& d = ctx->d;
   const int CS = ctx->cluster;
   const int RPC = (d.Nr + CS - 1) / CS;
@@ -619,13 +623,14 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
 }
 
 // Whether the device can co-schedule clusters of CS CTAs for the asynchronous sweeps.
-template <int Q>
+template <int Q, int NS>
 bool cluster_ok_async(const Dims& d, int CS) {
-  const void* fns[2] = {(const void*)k_chain_half_async<Q / 2>, (const void*)k_chain_out_async<Q / 2>};
+  const void* fns[2] = {(const void*)k_chain_half_async<Q / NS, NS>,
+                        (const void*)k_chain_out_async<Q / NS, NS>};
   for (int w = 0; w < 2; ++w) {
     cudaFuncSetAttribute(fns[w], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaGetLastError();
-    const size_t smem = chain_smem_async(d, CS, w == 1);
+    const size_t smem = chain_smem_async(d, CS, w == 1, NS);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(fns[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess) {
@@ -635,7 +640,7 @@ bool cluster_ok_async(const Dims& d, int CS) {
     const int RPC = (d.Nr + CS - 1) / CS;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * 2 * d.nm * CS);
-    cfg.blockDim = dim3(64 * ((RPC + 3) / 4));
+    cfg.blockDim = dim3(32 * NS * ((RPC + 3) / 4));
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -712,14 +717,22 @@ rsc_status choose_cluster(rsc_ctx* ctx) {
   return RSC_ECUDA;
 }
 
+template <int Q>
+bool chain_config_ok_q(const Dims& d, int CS, int async_mode) {
+  if (async_mode == 0) return cluster_ok<Q>(d, CS);
+  if (async_mode == 1) return cluster_ok_async<Q, 2>(d, CS);
+  if constexpr (Q % 4 == 0) return async_mode == 2 && cluster_ok_async<Q, 4>(d, CS);
+  return false;
+}
+
 bool chain_config_ok(const Dims& d, int CS, int async_mode) {
-  if (CS > d.Nr) return false;
+  if (CS > d.Nr || async_mode < 0 || async_mode > 2) return false;
   switch (chain_maxq(d.Nr)) {
-    case 2: return async_mode ? cluster_ok_async<2>(d, CS) : cluster_ok<2>(d, CS);
-    case 4: return async_mode ? cluster_ok_async<4>(d, CS) : cluster_ok<4>(d, CS);
-    case 8: return async_mode ? cluster_ok_async<8>(d, CS) : cluster_ok<8>(d, CS);
-    case 12: return async_mode ? cluster_ok_async<12>(d, CS) : cluster_ok<12>(d, CS);
-    default: return async_mode ? cluster_ok_async<16>(d, CS) : cluster_ok<16>(d, CS);
+    case 2: return chain_config_ok_q<2>(d, CS, async_mode);
+    case 4: return chain_config_ok_q<4>(d, CS, async_mode);
+    case 8: return chain_config_ok_q<8>(d, CS, async_mode);
+    case 12: return chain_config_ok_q<12>(d, CS, async_mode);
+    default: return chain_config_ok_q<16>(d, CS, async_mode);
   }
 }
 
@@ -1160,7 +1173,6 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
   }
   if (t.synth_radii < 1 || t.synth_radii > radii_limit((const void*)k_synth<double>, round32(d.nlat2)))
     return false;
-  if (t.chain_async != 0 && t.chain_async != 1) return false;
   return chain_config_ok(d, t.chain_cluster, t.chain_async);
 }
 
@@ -1285,7 +1297,7 @@ rsc_status autotune(rsc_ctx* ctx, rsc_tuning* out) {
     st = get_factor(ctx, 200.0, &f);
     double best = 1e30;
     int bc = t.chain_cluster, ba = t.chain_async;
-    for (int am : {0, 1}) {
+    for (int am : {0, 1, 2}) {
       for (int cs : {16, 8, 4, 2}) {
         if (st != RSC_OK) break;
         if (!chain_config_ok(ctx->d, cs, am)) continue;

@@ -1,8 +1,8 @@
 // Chain sweeps of the implicit-Coriolis solve (Sec. 3.2) with asynchronous cluster
 // exchange: the same twisted block-Thomas sweeps as k_chain_half / k_chain_out, laid out for
 // GB300's FP64 units (one per SM sub-partition, 64 cycles per warp instruction):
-//   * each row group of 4 rows (8 lanes per row) is split over two warps by columns, so one
-//     block step issues half as many FP64 instructions per warp;
+//   * each row group of 4 rows (8 lanes per row) is split over NS = 2 or 4 warps by
+//     columns, so one block step issues 1/NS as many FP64 multiply-adds per warp;
 //   * a block's new rows travel to every CTA of the cluster as st.async stores that
 //     complete on the receiver's mbarrier (expect_tx of Nr x 16 bytes per step), instead of
 //     a cluster-wide barrier per block.
@@ -98,14 +98,14 @@ struct CaLane {
   bool active;
 };
 
-template <int QH>
+template <int QH, int NS>
 __device__ __forceinline__ CaLane ca_lane(int Nr, int CS, int rank) {
   CaLane c;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   c.rank = rank;
   c.RPC = (Nr + CS - 1) / CS;
-  c.h = warp & 1;                        // column half
-  c.lr = (warp >> 1) * 4 + (lane >> 3);  // row within the CTA
+  c.h = warp % NS;                        // column part
+  c.lr = (warp / NS) * 4 + (lane >> 3);   // row within the CTA
   c.r = rank * c.RPC + c.lr;
   c.s = lane & 7;
   c.q0 = c.h * QH;
@@ -113,10 +113,10 @@ __device__ __forceinline__ CaLane ca_lane(int Nr, int CS, int rank) {
   return c;
 }
 
-// Shared memory: v[2][Nr] (double2), part[RPC] (double2), hist[steps][RPC] (double2),
-// then two mbarriers (8-byte aligned: every region is a multiple of 16 bytes).
-// grid = 2 * 2 * nm * CS (clusters of CS), block = 64 * ceil(RPC / 4).
-template <int QH>
+// Shared memory: v[2][Nr] (double2), part[NS-1][RPC], hist[steps][RPC], then two
+// mbarriers (8-byte aligned: every region is a multiple of 16 bytes).
+// grid = 2 * 2 * nm * CS (clusters of CS), block = 32 NS ceil(RPC / 4).
+template <int QH, int NS>
 __global__ void k_chain_half_async(DevGeom g, const long* __restrict__ chain_off,
                                    const double2* __restrict__ H, double2* __restrict__ out,
                                    double2* __restrict__ mid, int CS, int steps_cap,
@@ -126,10 +126,10 @@ __global__ void k_chain_half_async(DevGeom g, const long* __restrict__ chain_off
   extern __shared__ double2 ca_sh[];
   const ChainInfo ci = chain_info(g, chain_off, CS);
   const int Nr = ci.Nr;
-  const CaLane c = ca_lane<QH>(Nr, CS, (int)cluster.block_rank());
+  const CaLane c = ca_lane<QH, NS>(Nr, CS, (int)cluster.block_rank());
   double2* v = ca_sh;                       // [2][Nr]
-  double2* part = v + 2 * Nr;               // [RPC]
-  double2* hist = part + c.RPC;             // [steps_cap][RPC]
+  double2* part = v + 2 * Nr;               // [NS - 1][RPC]
+  double2* hist = part + (NS - 1) * c.RPC;  // [steps_cap][RPC]
   uint64_t* bar = reinterpret_cast<uint64_t*>(hist + (long)steps_cap * c.RPC);
   const uint32_t bar0 = ca_smem(&bar[0]);
   const bool has = ci.dir == 0 ? (ci.km >= 1) : (ci.km <= ci.nb - 2);
@@ -163,11 +163,16 @@ __global__ void k_chain_half_async(DevGeom g, const long* __restrict__ chain_off
       if (c.active) gn = out[ci.row(i + step) + c.r];
     }
     const double2 acc = ca_dot<QH>(mc, v + (b ^ 1) * Nr, c.s, c.q0, Nr, ci.m == 0);
-    if (c.h == 1 && c.s == 0 && c.active) part[c.lr] = acc;
+    if (c.h > 0 && c.s == 0 && c.active) part[(c.h - 1) * c.RPC + c.lr] = acc;
     __syncthreads();
     if (c.h == 0 && c.active) {
-      const double2 p = part[c.lr];
-      const double2 y = make_double2(gc.x - (acc.x + p.x), gc.y - (acc.y + p.y));
+      double2 p = acc;
+#pragma unroll
+      for (int q = 1; q < NS; ++q) {
+        p.x += part[(q - 1) * c.RPC + c.lr].x;
+        p.y += part[(q - 1) * c.RPC + c.lr].y;
+      }
+      const double2 y = make_double2(gc.x - p.x, gc.y - p.y);
       if (c.s == 0) hist[(t - 1) * c.RPC + c.lr] = y;
       const uint32_t la = ca_smem(v + b * Nr + c.r);
       for (int dst = c.s; dst < CS; dst += 8)
@@ -192,8 +197,8 @@ __global__ void k_chain_half_async(DevGeom g, const long* __restrict__ chain_off
   cluster.sync();   // no CTA leaves while a peer may still write into its shared memory
 }
 
-// Shared memory: v[2][Nr], yup[Nr], zdn[Nr], part[RPC], hist[steps][RPC], two mbarriers.
-template <int QH>
+// Shared memory: v[2][Nr], yup[Nr], zdn[Nr], part[NS-1][RPC], hist[steps][RPC], two mbarriers.
+template <int QH, int NS>
 __global__ void k_chain_out_async(DevGeom g, const long* __restrict__ chain_off,
                                   const double2* __restrict__ H, const double2* __restrict__ W,
                                   double2* __restrict__ out, const double2* __restrict__ mid,
@@ -203,12 +208,12 @@ __global__ void k_chain_out_async(DevGeom g, const long* __restrict__ chain_off,
   extern __shared__ double2 ca_sh[];
   const ChainInfo ci = chain_info(g, chain_off, CS);
   const int Nr = ci.Nr;
-  const CaLane c = ca_lane<QH>(Nr, CS, (int)cluster.block_rank());
+  const CaLane c = ca_lane<QH, NS>(Nr, CS, (int)cluster.block_rank());
   double2* v = ca_sh;
   double2* yup = v + 2 * Nr;    // y_{k-1}
   double2* zdn = yup + Nr;      // z_{k+1}
-  double2* part = zdn + Nr;
-  double2* hist = part + c.RPC;
+  double2* part = zdn + Nr;                 // [NS - 1][RPC]
+  double2* hist = part + (NS - 1) * c.RPC;
   uint64_t* bar = reinterpret_cast<uint64_t*>(hist + (long)steps_cap * c.RPC);
   const uint32_t bar0 = ca_smem(&bar[0]);
   const int km = ci.km, nb = ci.nb;
@@ -243,14 +248,19 @@ __global__ void k_chain_out_async(DevGeom g, const long* __restrict__ chain_off,
     ca_load<QH>(W + (ci.boff + km + step) * ci.blk, c.r, c.s, c.q0, Nr, c.active, mn);
     if (c.active) yn = out[ci.row(km + step) + c.r];
   }
-  if (c.h == 1 && c.s == 0 && c.active) part[c.lr] = acc;
+  if (c.h > 0 && c.s == 0 && c.active) part[(c.h - 1) * c.RPC + c.lr] = acc;
   cluster.sync();   // barriers initialised everywhere, part written
   bool ok = true;
   if (threadIdx.x == 0) ca_expect(bar0, (uint32_t)Nr * 16u);
   if (c.h == 0 && c.active) {
     const double2 gk = mc0[2 * Nr + c.r];
-    const double2 p = part[c.lr];
-    const double2 xk = make_double2(gk.x - (acc.x + p.x), gk.y - (acc.y + p.y));
+    double2 p = acc;
+#pragma unroll
+    for (int q = 1; q < NS; ++q) {
+      p.x += part[(q - 1) * c.RPC + c.lr].x;
+      p.y += part[(q - 1) * c.RPC + c.lr].y;
+    }
+    const double2 xk = make_double2(gk.x - p.x, gk.y - p.y);
     if (c.s == 0 && ci.dir == 0) out[ci.row(km) + c.r] = xk;
     const uint32_t la = ca_smem(v + c.r);
     for (int dst = c.s; dst < CS; dst += 8)
@@ -270,11 +280,16 @@ __global__ void k_chain_out_async(DevGeom g, const long* __restrict__ chain_off,
       if (c.active) yn = out[ci.row(i + step) + c.r];
     }
     const double2 a3 = ca_dot<QH>(mc, v + (b ^ 1) * Nr, c.s, c.q0, Nr, ci.m == 0);
-    if (c.h == 1 && c.s == 0 && c.active) part[c.lr] = a3;
+    if (c.h > 0 && c.s == 0 && c.active) part[(c.h - 1) * c.RPC + c.lr] = a3;
     __syncthreads();
     if (c.h == 0 && c.active) {
-      const double2 p = part[c.lr];
-      const double2 x = make_double2(yc.x - (a3.x + p.x), yc.y - (a3.y + p.y));
+      double2 p = a3;
+#pragma unroll
+      for (int q = 1; q < NS; ++q) {
+        p.x += part[(q - 1) * c.RPC + c.lr].x;
+        p.y += part[(q - 1) * c.RPC + c.lr].y;
+      }
+      const double2 x = make_double2(yc.x - p.x, yc.y - p.y);
       if (c.s == 0) hist[(t - 1) * c.RPC + c.lr] = x;
       const uint32_t la = ca_smem(v + b * Nr + c.r);
       for (int dst = c.s; dst < CS; dst += 8)

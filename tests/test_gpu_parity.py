@@ -400,8 +400,9 @@ def test_batch_newton_matches_single_instance_solves(torch):
 
 @pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES)
 @pytest.mark.parametrize("cluster", [16, 8, 4, 2])
-def test_async_chain_sweeps_parity(torch, name, L, Ms, Nr, Ek, Ra, cluster):
-    """The sweeps with column-split warps and st.async / mbarrier exchange (chain_async = 1)
+@pytest.mark.parametrize("mode", [1, 2])
+def test_async_chain_sweeps_parity(torch, name, L, Ms, Nr, Ek, Ra, cluster, mode):
+    """The sweeps with column-split warps (2 or 4 parts) and st.async / mbarrier exchange
     against the oracle, for every cluster size the device accepts."""
     from paper_2508_16635_gb300 import RotatingShell
     make = lambda: Shell(L, Ms, Nr, Ek, Ra)
@@ -413,7 +414,7 @@ def test_async_chain_sweeps_parity(torch, name, L, Ms, Nr, Ek, Ra, cluster):
     wantj, spreadj = _oracle_spread(make, lambda so: so.jvp(x, -1.1, J, u, 200.0))
     gpu = RotatingShell(L, Ms, Nr, Ek, Ra)
     t = gpu.tuning()
-    t.update(chain_cluster=cluster, chain_async=1)
+    t.update(chain_cluster=cluster, chain_async=mode)
     try:
         gpu.set_tuning(t)
     except Exception:
