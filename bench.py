@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-rw", action="store_true", help="skip the time-to-rotating-wave run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances run")
+    ap.add_argument("--tuning", default=None,
+                    help="launch shapes as JSON (the line's `tuning`) instead of autotuning, so "
+                         "that a profiled run uses the shapes of a measured one")
     ap.add_argument("--dt-study", default=None,
                     help="only run the Table 1 time-step study for the given rows (e.g. 0,1,2)")
     ap.add_argument("--coriolis-study", action="store_true",
@@ -571,7 +574,11 @@ def run_gpu(args):
     peaks = measured_peaks(torch)
     sh = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
                        precision=args.precision)
-    tuning = sh.autotune()      # launch shapes picked by timing, before any measurement
+    if args.tuning:             # fixed shapes (a profiler distorts the autotuner's timings)
+        sh.set_tuning(json.loads(args.tuning))
+        tuning = sh.tuning()
+    else:
+        tuning = sh.autotune()  # launch shapes picked by timing, before any measurement
     U0 = sh.conductive_state() + torch.tensor(
         si.perturbation(w["L"], w["Ms"], w["Nr"], seed=3000 + rank), device="cuda")
     # phase slot: Im of the T coefficient (l = m = 12, k*) with k* = argmax |Re|

@@ -86,6 +86,9 @@ struct rsc_ctx {
   int nblk_dot = 0;
   int cluster = 8;  // CTAs per chain in the cluster chain solve
   int chain_async = 0;   // 1: sweeps with column-split warps and st.async / mbarrier exchange
+  // second stream: the temperature solve runs beside the e/f chain solve
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int rt_synth[2] = {1, 1}, rt_anal[2] = {1, 1};  // radii per block, [fp64, fp32]
   int wpb[2] = {0, 0};     // warps per block of the products kernel (0: largest that fits)
   int ppb[2] = {0, 0};     // pairs per block of the right-hand-side kernel (0: 256 / Nr)
@@ -596,6 +599,23 @@ cudaError_t launch_chain(rsc_ctx* ctx, const DevFactor* f, double* out, bool out
 
 rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
   const Dims& d = ctx->d;
+  // the temperature solve depends only on the right-hand side: it runs on a second stream
+  // beside the e/f chain solve (sequentially while tracing, so that every launch is timed)
+  const bool fork = !ctx->prof_on;
+  if (fork) {
+    if (!ctx->s2) {
+      CK(cudaStreamCreateWithFlags(&ctx->s2, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(ctx->ev_fork, ctx->s));
+    CK(cudaStreamWaitEvent(ctx->s2, ctx->ev_fork, 0));
+    KSpan sp(ctx, RSC_K_TEMP, 0.0, 0.0);
+    k_temp_solve<<<d.P, round32(d.Nr), (size_t)d.Nr * sizeof(double2), ctx->s2>>>(
+        ctx->geom(), f->Tinv, ctx->rhs, reinterpret_cast<double2*>(out));
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(ctx->ev_join, ctx->s2));
+  }
   {
     KSpan sp(ctx, RSC_K_CHAIN, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
@@ -613,6 +633,10 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
     KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
     CK(launch_chain(ctx, f, out, true));
+  }
+  if (fork) {
+    CK(cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0));
+    return RSC_OK;
   }
   KSpan sp(ctx, RSC_K_TEMP, (double)(d.L + 1) * d.Nr * d.Nr * 8.0 + 2.0 * d.P * d.Nr * 16.0,
            4.0 * d.P * d.Nr * d.Nr);
@@ -1511,6 +1535,9 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
   else cudaDeviceSynchronize();
   if (ctx->jvp_exec) cudaGraphExecDestroy(ctx->jvp_exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->s2) cudaStreamSynchronize(ctx->s2), cudaStreamDestroy(ctx->s2);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   void* bufs[] = {(void*)ctx->d_slots, ctx->d_cslot, ctx->jvp_y, ctx->tc_tiles, ctx->tc_off, ctx->tc_kpad, ctx->d_status, ctx->d_EcT1, ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,

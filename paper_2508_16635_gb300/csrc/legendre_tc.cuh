@@ -133,10 +133,13 @@ __global__ void __launch_bounds__(128) k_synth_tc(DevGeom g, TcTables tt, const 
   const uint32_t sbo = (uint32_t)(Kp / 4) * 128u;
   const int nks = Kp / 8;
   uint32_t ph = 0;
-  for (int w = 0; w < 3 && ok; ++w) {
+  // phases (s, w): parity class outer, table type inner, so that the B operand of
+  // w = 2 (P/sin) is the one already staged for w = 1 (dP/dtheta): the same columns
+  for (int s = 0; s < 2 && ok; ++s) {
+    for (int w = 0; w < 3 && ok; ++w) {
     const int NC = (w == 0) ? 3 : 5;          // components of this table type
     const int NW = (w == 0) ? kTcNP : kTcNV;  // N of the GEMM (padded)
-    for (int s = 0; s < 2 && ok; ++s) {
+    {
       // (1) tables: bulk copy of the hi and lo tiles
       if (tid == 0) {
         const float* src = tt.tiles + tt.off[((a * 2 + s) * 3 + w) * tt.nmt + mt];
@@ -155,26 +158,43 @@ __global__ void __launch_bounds__(128) k_synth_tc(DevGeom g, TcTables tt, const 
             "l"(src + 128 * Kp), "r"(bytes), "r"(bar_copy)
             : "memory");
       }
-      // (2) B: columns n = (radius, component, re/im), K-major core-matrix layout
+      // (2) B: columns n = (radius, component, re/im), K-major core-matrix layout; eight
+      // independent gathers per thread are in flight before the first store
       const int vi[5] = {1, 2, 4, 5, 7};
-      for (int idx = tid; idx < NW * Kp; idx += 128) {
-        const int k = idx / NW;
-        const int n = idx - k * NW;
-        const int q = s + 2 * k;
-        const int rr = n / (2 * NC);
-        const int rem = n - rr * 2 * NC;
-        const int c = rem >> 1, ri = rem & 1;
-        const int i = i0 + rr;
-        float v = 0.f;
-        if (q < nl && rr < kTcRadii && i < Nd) {
-          const int comp = (w == 0) ? (c == 0 ? 0 : (c == 1 ? 3 : 6)) : vi[c];
-          const float2 z = SR[((long)(p0 + q) * Nd + i) * 8 + comp];
-          v = ri ? z.y : z.x;
+      const int total = (w == 2) ? 0 : NW * Kp;   // w = 2 reuses the operand of w = 1
+      for (int base = tid; base < total; base += 128 * 8) {
+        float vals[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + 128 * u;
+          const int k = idx / NW;
+          const int n = idx - k * NW;
+          const int q = s + 2 * k;
+          const int rr = n / (2 * NC);
+          const int rem = n - rr * 2 * NC;
+          const int c = rem >> 1, ri = rem & 1;
+          const int i = i0 + rr;
+          float v = 0.f;
+          if (idx < total && q < nl && rr < kTcRadii && i < Nd) {
+            const int comp = (w == 0) ? (c == 0 ? 0 : (c == 1 ? 3 : 6)) : vi[c];
+            const float* z = reinterpret_cast<const float*>(SR + ((long)(p0 + q) * Nd + i) * 8 + comp);
+            v = __ldg(z + ri);
+          }
+          vals[u] = v;
         }
-        const float h = tf32_hi(v);
-        const int off = (n >> 3) * (Kp / 4) * 32 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
-        sBh[off] = h;
-        sBl[off] = v - h;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + 128 * u;
+          if (idx < total) {
+            const int k = idx / NW;
+            const int n = idx - k * NW;
+            const float v = vals[u];
+            const float h = tf32_hi(v);
+            const int off = (n >> 3) * (Kp / 4) * 32 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
+            sBh[off] = h;
+            sBl[off] = v - h;
+          }
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -203,6 +223,7 @@ __global__ void __launch_bounds__(128) k_synth_tc(DevGeom g, TcTables tt, const 
       ok = ok && mma_ok;
       ph ^= 1u;
       __syncthreads();
+    }
     }
   }
   if (!ok && tid == 0) atomicExch(tt.status, 7);
