@@ -318,7 +318,9 @@ rsc_status rsc_batch_newton_rw(rsc_batch* batch, double* const* U, double* C, co
  * counterpart in the paper: GPU tiling).  [2] = [FP64 path, mixed path].     */
 typedef struct {
   int products_warps[2];   /* warps per block of the DFT + grid products kernel       */
+  int products_lats[2];    /* latitudes per warp of that kernel                       */
   int analysis_radii[2];   /* radii per block of the Legendre analysis                */
+  int analysis_chunk[2];   /* latitudes per staged chunk of the analysis tables       */
   int synth_radii;         /* radii per block of the CUDA-core (FP64) synthesis       */
   int rhs_pairs[2];        /* (l, m) pairs per block of the right-hand-side kernel    */
   int chain_cluster;       /* CTAs per thread-block cluster of the chain sweeps       */

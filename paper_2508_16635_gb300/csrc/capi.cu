@@ -92,6 +92,8 @@ struct rsc_ctx {
   int rt_synth[2] = {1, 1}, rt_anal[2] = {1, 1};  // radii per block, [fp64, fp32]
   int wpb[2] = {0, 0};     // warps per block of the products kernel (0: largest that fits)
   int ppb[2] = {0, 0};     // pairs per block of the right-hand-side kernel (0: 256 / Nr)
+  int atc[2] = {16, 16};   // latitudes per staged chunk of the analysis tables
+  int lpw[2] = {1, 1};     // latitudes per warp of the products kernel
   double tune_ms[5] = {0, 0, 0, 0, 0};
   // tensor-core Legendre synthesis (FP32 path): A tiles, offsets, padded K, status word
   float* tc_tiles = nullptr;
@@ -438,6 +440,13 @@ size_t products_smem(const Dims& d, bool lin, int wpb) {
          (size_t)wpb * 4 * d.nphi * sizeof(R);
 }
 
+// Shared memory of the Legendre analysis for RT radii per block and TC staged latitudes.
+template <typename R>
+size_t analysis_smem(const Dims& d, int RT, int TC) {
+  using V = typename C2<R>::T;
+  return (size_t)RT * 8 * d.nlat2 * sizeof(V) + (size_t)TC * 3 * (d.L + 1) * sizeof(R);
+}
+
 // Shared memory of the right-hand-side kernel for `ppb` pairs per block.
 template <typename R>
 size_t rhs_smem(const Dims& d, int ppb) {
@@ -458,7 +467,8 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
   auto smem_for = [&](int wpb) { return products_smem<R>(d, lin, wpb); };
   while (WPB > 1 && smem_for(WPB) > 190 * 1024) WPB /= 2;
   const size_t smem = smem_for(WPB);
-  dim3 grid(d.Nd, (d.nlat + WPB - 1) / WPB);
+  const int LPW = ctx->lpw[sizeof(R) == 4 ? 1 : 0];
+  dim3 grid(d.Nd, (d.nlat + WPB * LPW - 1) / (WPB * LPW));
   const double npts = (double)d.Nd * d.nlat * d.nphi;
   {
   KSpan sp(ctx, RSC_K_PRODUCTS, (double)(NF + 4) * d.Nd * K1 * d.nlat * sizeof(V),
@@ -466,11 +476,11 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
   if (lin)
     k_products<R, true><<<grid, 32 * WPB, smem, ctx->s>>>(
         g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC),
-        reinterpret_cast<const V*>(ctx->FCU), reinterpret_cast<V*>(ctx->FA));
+        reinterpret_cast<const V*>(ctx->FCU), reinterpret_cast<V*>(ctx->FA), LPW);
   else
     k_products<R, false><<<grid, 32 * WPB, smem, ctx->s>>>(
         g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC), nullptr,
-        reinterpret_cast<V*>(ctx->FA));
+        reinterpret_cast<V*>(ctx->FA), LPW);
   CK(cudaGetLastError());
   }
   {
@@ -479,10 +489,10 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
                3.0 * d.P * d.nlat2 * sizeof(R),
            24.0 * d.P * d.nlat2 * d.Nd);
   const int RTa = ctx->rt_anal[sizeof(R) == 4 ? 1 : 0];
+  const int TC = ctx->atc[sizeof(R) == 4 ? 1 : 0];
   k_analysis<R><<<dim3(d.nm, (d.Nd + RTa - 1) / RTa), dim3(round32(d.L + 1), RTa),
-                  (size_t)RTa * 8 * d.nlat2 * sizeof(V) + 16 * 3 * (size_t)(d.L + 1) * sizeof(R),
-                  ctx->s>>>(
-      g, L.view(), reinterpret_cast<const V*>(ctx->FA), reinterpret_cast<V*>(ctx->AR));
+                  analysis_smem<R>(d, RTa, TC), ctx->s>>>(
+      g, L.view(), reinterpret_cast<const V*>(ctx->FA), reinterpret_cast<V*>(ctx->AR), TC);
   CK(cudaGetLastError());
   }
   return RSC_OK;
@@ -1191,6 +1201,11 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
     const int ra = radii_limit(p ? (const void*)k_analysis<float> : (const void*)k_analysis<double>,
                                round32(d.L + 1));
     if (t.analysis_radii[p] < 1 || t.analysis_radii[p] > ra) return false;
+    if (t.analysis_chunk[p] < 1) return false;
+    if (!pow2(t.products_lats[p], 16)) return false;
+    if ((p ? analysis_smem<float>(d, t.analysis_radii[p], t.analysis_chunk[p])
+           : analysis_smem<double>(d, t.analysis_radii[p], t.analysis_chunk[p])) > 200 * 1024)
+      return false;
     if (!pow2(t.rhs_pairs[p], 8) || round32(d.Nr) * t.rhs_pairs[p] > 1024) return false;
     if ((p ? rhs_smem<float>(d, t.rhs_pairs[p]) : rhs_smem<double>(d, t.rhs_pairs[p])) > 200 * 1024)
       return false;
@@ -1210,6 +1225,8 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
     t->products_warps[p] = w;
     t->analysis_radii[p] = ctx->rt_anal[p];
     t->rhs_pairs[p] = ctx->ppb[p] > 0 ? ctx->ppb[p] : std::max(1, 256 / round32(d.Nr));
+    t->analysis_chunk[p] = ctx->atc[p];
+    t->products_lats[p] = ctx->lpw[p];
   }
   t->synth_radii = ctx->rt_synth[0];
   t->chain_cluster = ctx->cluster;
@@ -1222,6 +1239,8 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
     ctx->wpb[p] = t.products_warps[p];
     ctx->rt_anal[p] = t.analysis_radii[p];
     ctx->ppb[p] = t.rhs_pairs[p];
+    ctx->atc[p] = t.analysis_chunk[p];
+    ctx->lpw[p] = t.products_lats[p];
   }
   ctx->rt_synth[0] = t.synth_radii;
   ctx->cluster = t.chain_cluster;
@@ -1251,28 +1270,37 @@ rsc_status tune_precision(rsc_ctx* ctx, rsc_tuning& t, cudaEvent_t e0, cudaEvent
   CKS(stage_synth<R>(ctx, ctx->rtmp, ctx->FC));
   CKS(stage_synth<R>(ctx, ctx->rtmp, ctx->FCU));
   auto pa = [&] { return stage_products_analysis<R>(ctx, true); };
-  // products: warps per block
+  // products: warps per block x latitudes per warp
   double best = 1e30;
-  int bw = t.products_warps[p];
+  int bw = t.products_warps[p], bl = t.products_lats[p];
   for (int w : {1, 2, 4, 8}) {
     if (products_smem<R>(d, true, w) > 190 * 1024) continue;
-    ctx->wpb[p] = w;
-    const double ms = timeit(pa);
-    CKS(st);
-    if (ms < best) { best = ms; bw = w; }
+    for (int lp : {1, 2, 4, 8}) {
+      ctx->wpb[p] = w;
+      ctx->lpw[p] = lp;
+      const double ms = timeit(pa);
+      CKS(st);
+      if (ms < best) { best = ms; bw = w; bl = lp; }
+    }
   }
   ctx->wpb[p] = t.products_warps[p] = bw;
-  // analysis: radii per block
+  ctx->lpw[p] = t.products_lats[p] = bl;
+  // analysis: radii per block x latitudes per staged table chunk
   best = 1e30;
-  int br = t.analysis_radii[p];
+  int br = t.analysis_radii[p], bc = t.analysis_chunk[p];
   const int rmax = radii_limit((const void*)k_analysis<R>, round32(d.L + 1));
   for (int r = 1; r <= rmax; r *= 2) {
-    ctx->rt_anal[p] = r;
-    const double ms = timeit(pa);
-    CKS(st);
-    if (ms < best) { best = ms; br = r; }
+    for (int tc : {16, 32, 48, d.nlat2}) {
+      if (tc > d.nlat2 || analysis_smem<R>(d, r, tc) > 200 * 1024) continue;
+      ctx->rt_anal[p] = r;
+      ctx->atc[p] = tc;
+      const double ms = timeit(pa);
+      CKS(st);
+      if (ms < best) { best = ms; br = r; bc = tc; }
+    }
   }
   ctx->rt_anal[p] = t.analysis_radii[p] = br;
+  ctx->atc[p] = t.analysis_chunk[p] = bc;
   if (p == 1) ctx->tune_ms[0] = best;   // products + analysis of the mixed path
   // synthesis (CUDA-core FP64 path): radii per block
   if (p == 0) {

@@ -262,8 +262,8 @@ __global__ void k_synth(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __
 }
 
 // ---------------------------------------------------------------------------
-// a3-a5: inverse DFT, products, forward DFT.  grid = (Nd, ceil(nlat / WPB)),
-// block = 32 x WPB: warp w handles latitude th0 + w.  Inverse DFT: lane j
+// a3-a5: inverse DFT, products, forward DFT.  grid = (Nd, ceil(nlat / (WPB LPW))),
+// block = 32 x WPB: warp w handles latitudes th0 + w + WPB r, r < LPW.  Inverse DFT: lane j
 // sums the (K+1) coefficients of each field at its longitudes (coefficients
 // are warp broadcasts, twiddles [a][j] are bank-conflict free).  Forward DFT:
 // lane a sums its wavenumber over the nphi longitudes (twiddles stored [j][a]).
@@ -274,7 +274,7 @@ template <typename R, bool LIN>
 __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
                            const typename C2<R>::T* __restrict__ FC,
                            const typename C2<R>::T* __restrict__ FCU,
-                           typename C2<R>::T* __restrict__ FA) {
+                           typename C2<R>::T* __restrict__ FA, int LPW) {
   using V = typename C2<R>::T;
   constexpr int NF = LIN ? 18 : 9;
   extern __shared__ unsigned char sh_raw[];
@@ -287,7 +287,6 @@ __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
   R* twsT = twcT + K1 * nphi;
   R* prod = twsT + K1 * nphi;                             // [WPB][4][nphi]
   const int i = blockIdx.x;
-  const int th0 = blockIdx.y * WPB;
   const R inv = (R)1 / (R)nphi;
   for (int idx = threadIdx.x; idx < K1 * nphi; idx += blockDim.x) {
     const int a = idx / nphi, j = idx - a * nphi;
@@ -298,84 +297,86 @@ __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
     twcT[j * K1 + a] = c * inv;
     twsT[j * K1 + a] = sn * inv;
   }
-  for (int idx = threadIdx.x; idx < WPB * NF * K1; idx += blockDim.x) {
-    const int w = idx % WPB;              // latitude fastest: coalesced reads of FC
-    const int rest = idx / WPB;
-    const int a = rest % K1;
-    const int f = rest / K1;
-    const int th = th0 + w;
-    V v = mk<R>(0, 0);
-    if (th < nlat) {
-      const V* src = (f < 9) ? FC : FCU;
-      const int ff = (f < 9) ? f : f - 9;
-      v = src[(((long)ff * Nd + i) * K1 + a) * nlat + th];
-    }
-    if (a == 0) v.y = 0;                  // the m = 0 coefficient enters with its real part
-    coef[(w * NF + f) * K1 + a] = v;
-  }
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int th = th0 + w;
-  const V* cw = coef + w * NF * K1;
+  V* cw = coef + w * NF * K1;
   R* pw = prod + w * 4 * nphi;
-  for (int j = lane; j < nphi; j += 32) {
-    R val[NF];
+  // warp w takes latitudes th0 + w, th0 + w + WPB, ... (LPW of them): the twiddles staged
+  // above serve all of them
+  const int th0 = blockIdx.y * WPB * LPW;
+  for (int rep = 0; rep < LPW; ++rep) {
+    const int th = th0 + w + WPB * rep;
+    if (th >= nlat) break;
+    __syncwarp();
+    for (int idx = lane; idx < NF * K1; idx += 32) {
+      const int a = idx % K1;
+      const int f = idx / K1;
+      const V* src = (f < 9) ? FC : FCU;
+      const int ff = (f < 9) ? f : f - 9;
+      V v = src[(((long)ff * Nd + i) * K1 + a) * nlat + th];
+      if (a == 0) v.y = 0;                // the m = 0 coefficient enters with its real part
+      cw[f * K1 + a] = v;
+    }
+    __syncwarp();
+    for (int j = lane; j < nphi; j += 32) {
+      R val[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) val[f] = 0;
-    for (int a = 0; a < K1; ++a) {
-      const R c = twc[a * nphi + j], sn = tws[a * nphi + j];
+      for (int f = 0; f < NF; ++f) val[f] = 0;
+      for (int a = 0; a < K1; ++a) {
+        const R c = twc[a * nphi + j], sn = tws[a * nphi + j];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const V cf = cw[f * K1 + a];
-        val[f] += cf.x * c - cf.y * sn;
+        for (int f = 0; f < NF; ++f) {
+          const V cf = cw[f * K1 + a];
+          val[f] += cf.x * c - cf.y * sn;
+        }
       }
-    }
-    R Fr, Ft, Fp, N;
-    if (!LIN) {
-      // val: 0 ur 1 ut 2 up 3 wr 4 wt 5 wp 6 Tr 7 Tt 8 Tp
-      Fr = Ek * (val[1] * val[5] - val[2] * val[4]);
-      Ft = Ek * (val[2] * val[3] - val[0] * val[5]);
-      Fp = Ek * (val[0] * val[4] - val[1] * val[3]);
-      N = val[0] * val[6] + val[1] * val[7] + val[2] * val[8];
-    } else {
-      const R* u = val;      // perturbation
-      const R* U = val + 9;  // base state
-      Fr = Ek * ((U[1] * u[5] - U[2] * u[4]) + (u[1] * U[5] - u[2] * U[4]));
-      Ft = Ek * ((U[2] * u[3] - U[0] * u[5]) + (u[2] * U[3] - u[0] * U[5]));
-      Fp = Ek * ((U[0] * u[4] - U[1] * u[3]) + (u[0] * U[4] - u[1] * U[3]));
-      N = U[0] * u[6] + U[1] * u[7] + U[2] * u[8] + u[0] * U[6] + u[1] * U[7] + u[2] * U[8];
-    }
-    pw[0 * nphi + j] = Fr;
-    pw[1 * nphi + j] = Ft;
-    pw[2 * nphi + j] = Fp;
-    pw[3 * nphi + j] = N;
-  }
-  __syncwarp();
-  if (th >= nlat) return;
-  for (int a = lane; a < K1; a += 32) {
-    R sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0};
-    for (int j = 0; j < nphi; ++j) {
-      const R c = twcT[j * K1 + a], sn = twsT[j * K1 + a];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const R v = pw[q * nphi + j];
-        sr[q] += v * c;
-        si[q] -= v * sn;
+      R Fr, Ft, Fp, N;
+      if (!LIN) {
+        // val: 0 ur 1 ut 2 up 3 wr 4 wt 5 wp 6 Tr 7 Tt 8 Tp
+        Fr = Ek * (val[1] * val[5] - val[2] * val[4]);
+        Ft = Ek * (val[2] * val[3] - val[0] * val[5]);
+        Fp = Ek * (val[0] * val[4] - val[1] * val[3]);
+        N = val[0] * val[6] + val[1] * val[7] + val[2] * val[8];
+      } else {
+        const R* u = val;      // perturbation
+        const R* U = val + 9;  // base state
+        Fr = Ek * ((U[1] * u[5] - U[2] * u[4]) + (u[1] * U[5] - u[2] * U[4]));
+        Ft = Ek * ((U[2] * u[3] - U[0] * u[5]) + (u[2] * U[3] - u[0] * U[5]));
+        Fp = Ek * ((U[0] * u[4] - U[1] * u[3]) + (u[0] * U[4] - u[1] * U[3]));
+        N = U[0] * u[6] + U[1] * u[7] + U[2] * u[8] + u[0] * U[6] + u[1] * U[7] + u[2] * U[8];
       }
+      pw[0 * nphi + j] = Fr;
+      pw[1 * nphi + j] = Ft;
+      pw[2 * nphi + j] = Fp;
+      pw[3 * nphi + j] = N;
     }
+    __syncwarp();
+    for (int a = lane; a < K1; a += 32) {
+      R sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0};
+      for (int j = 0; j < nphi; ++j) {
+        const R c = twcT[j * K1 + a], sn = twsT[j * K1 + a];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      FA[(((long)q * Nd + i) * K1 + a) * nlat + th] = mk<R>(sr[q], si[q]);
+        for (int q = 0; q < 4; ++q) {
+          const R v = pw[q * nphi + j];
+          sr[q] += v * c;
+          si[q] -= v * sn;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        FA[(((long)q * Nd + i) * K1 + a) * nlat + th] = mk<R>(sr[q], si[q]);
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // a6: Legendre analysis.  grid = (nm, ceil(Nd / blockDim.y)), block =
-// (>= L + 1, multiple of 32) x RT radii.
+// (>= L + 1, multiple of 32) x RT radii; the Legendre tables are staged TC latitudes at a
+// time (dynamic shared memory RT 8 nlat/2 sizeof(V) + TC 3 (L + 1) sizeof(R)).
 // AR[((p * Nd) + i) * 4 + c], c = Q (F_r), S_F, T_F, (U.grad T).
 template <typename R>
 __global__ void k_analysis(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __restrict__ FA,
-                           typename C2<R>::T* __restrict__ AR) {
+                           typename C2<R>::T* __restrict__ AR, int TC) {
   using V = typename C2<R>::T;
   extern __shared__ unsigned char sh_raw[];
   const int n2 = g.nlat2, nlat = g.nlat, K1 = g.K + 1, Nd = g.Nd;
@@ -411,8 +412,7 @@ __global__ void k_analysis(DevGeom g, DevLegendre<R> T, const typename C2<R>::T*
   const long off = g.leg_off[a];
   R Qr = 0, Qi = 0, Nr_ = 0, Ni = 0, Sr = 0, Si = 0, Tr = 0, Ti = 0;
   const R mm = (R)m;
-  constexpr int TC = 16;
-  R* tab = reinterpret_cast<R*>(ant + RT * 4 * n2);   // [TC][3][nl]
+  R* tab = reinterpret_cast<R*>(ant + RT * 4 * n2);   // [TC][3][nl]: TC latitudes per stage
   const int nthr = blockDim.x * RT;
   for (int tc = 0; tc < n2; tc += TC) {
     const int nt = min(TC, n2 - tc);

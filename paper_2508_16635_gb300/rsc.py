@@ -46,14 +46,18 @@ class NewtonOpts(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("products_warps", ctypes.c_int * 2), ("analysis_radii", ctypes.c_int * 2),
+    _fields_ = [("products_warps", ctypes.c_int * 2), ("products_lats", ctypes.c_int * 2),
+                ("analysis_radii", ctypes.c_int * 2),
+                ("analysis_chunk", ctypes.c_int * 2),
                 ("synth_radii", ctypes.c_int), ("rhs_pairs", ctypes.c_int * 2),
                 ("chain_cluster", ctypes.c_int), ("chain_async", ctypes.c_int),
                 ("ms", ctypes.c_double * 5)]
 
     def as_dict(self):
         return {"products_warps": list(self.products_warps),
-                "analysis_radii": list(self.analysis_radii), "synth_radii": self.synth_radii,
+                "products_lats": list(self.products_lats),
+                "analysis_radii": list(self.analysis_radii),
+                "analysis_chunk": list(self.analysis_chunk), "synth_radii": self.synth_radii,
                 "rhs_pairs": list(self.rhs_pairs), "chain_cluster": self.chain_cluster,
                 "chain_async": self.chain_async, "ms": list(self.ms)}
 
@@ -358,7 +362,9 @@ class RotatingShell:
     def set_tuning(self, d):
         t = Tuning()
         t.products_warps[:] = d["products_warps"]
+        t.products_lats[:] = d.get("products_lats", [1, 1])
         t.analysis_radii[:] = d["analysis_radii"]
+        t.analysis_chunk[:] = d.get("analysis_chunk", [16, 16])
         t.synth_radii = d["synth_radii"]
         t.rhs_pairs[:] = d["rhs_pairs"]
         t.chain_cluster = d["chain_cluster"]
