@@ -56,6 +56,9 @@ def parse():
                          "that a profiled run uses the shapes of a measured one")
     ap.add_argument("--dt-study", default=None,
                     help="only run the Table 1 time-step study for the given rows (e.g. 0,1,2)")
+    ap.add_argument("--configs-study", action="store_true",
+                    help="only run the other configurations (C1, C2, C5 throughput, C2 wave, "
+                         "mixed batched Newton)")
     ap.add_argument("--coriolis-study", action="store_true",
                     help="only run the implicit vs explicit Coriolis comparison (Sec. 5)")
     return ap.parse_args()
@@ -554,6 +557,110 @@ def dt_study(torch, RotatingShell, rows=(0, 1, 2)):
     return out
 
 
+def _throughput(torch, RotatingShell, c, precision, krylov, nsteps):
+    """Time steps/s (IMEX Euler, lab frame) and Jacobian actions/s (one Newton iteration with
+    `krylov` actions) of one configuration, after autotuning; CUDA events, 2 warm-ups."""
+    sh = RotatingShell(c["L"], c["Ms"], c["Nr"], c["Ek"], c["Ra"], precision=precision)
+    sh.autotune()
+    U0 = sh.conductive_state() + torch.tensor(
+        si.perturbation(c["L"], c["Ms"], c["Nr"], seed=5000), device="cuda")
+    U = U0.clone()
+    sh.step(U, 0.0, c["dt"], nsteps=2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    sh.step(U, 0.0, c["dt"], nsteps=nsteps)
+    e1.record()
+    torch.cuda.synchronize()
+    tps = nsteps / (e0.elapsed_time(e1) * 1e-3)
+    J = sh.phase_slot(c["Ms"], 1)
+    for rep in range(3):
+        U = U0.clone()
+        torch.cuda.synchronize()
+        e0.record()
+        _, r, _ = sh.newton_rw(U, 0.5, J, tol=0.0, max_newton=1, kmax=krylov, gmres_tol=0.0)
+        e1.record()
+        torch.cuda.synchronize()
+    jvps = r["gmres_total"] / (e0.elapsed_time(e1) * 1e-3)
+    sh.close()
+    return {"timesteps_per_s": tps, "jvps_per_s": jvps, "krylov": krylov, "n": sh.n}
+
+
+def configs_study(torch, RotatingShell, Batch):
+    """The other configurations: throughput at C1 (L = 31), C2 (L = 63) and C5 (L = 255,
+    N_r = 96), FP64 and mixed; the C2 rotating wave (RW8, Ek = 1e-4, Ra = 130) solved by
+    Newton on both paths with the mixed path's errors in drift, kinetic energy and Nusselt
+    numbers against the FP64 solution; and the mixed batched Newton (rsc_batch_newton_rw) on
+    four RW4 continuation points against FP64 single solves."""
+    out = {"throughput": []}
+    for name in ("C1", "C2", "C5"):
+        c = si.config(name)
+        c.update(Ms={"C1": 4, "C2": 8, "C5": 8}[name])
+        row = {"config": name, "L": c["L"], "Ms": c["Ms"], "Nr": c["Nr"]}
+        for prec in ("fp64", "mixed"):
+            row[prec] = _throughput(torch, RotatingShell, c, prec,
+                                    krylov=100, nsteps=200 if name != "C5" else 50)
+        out["throughput"].append(row)
+        print(json.dumps({"configs_row": row}), flush=True)
+    # C2 rotating wave: FP64 vs mixed Newton from the same time-stepped guess
+    c = dict(si.config("C2"), Ms=8, seed_dt=2e-4)
+    guess, C0, J, seed_steps = _wave_from_seed(torch, RotatingShell, c)
+    rw = {"config": "C2 RW8 Ek=1e-4 Ra=130 L=63 Nr=48", "seed_steps": seed_steps}
+    states = {}
+    for prec in ("fp64", "mixed"):
+        sh = RotatingShell(c["L"], c["Ms"], c["Nr"], c["Ek"], c["Ra"], precision=prec)
+        sh.autotune()
+        sh.step(sh.new_state(), 0.0, 200.0, nsteps=1)
+        U = guess.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Cx, rep, st = sh.newton_rw(U, C0, J, tol=1e-10, max_newton=20, kmax=400,
+                                   gmres_tol=1e-10, dt_newton=200.0)
+        torch.cuda.synchronize()
+        ke, nui, nuo = sh.diagnostics(U)
+        rw[prec] = {"seconds": time.perf_counter() - t0, "status": st, "C": Cx, "KE": ke,
+                    "Nu_in": nui, "Nu_out": nuo, "residual": rep["residual"],
+                    "newton_iterations": rep["iterations"], "jacobian_actions": rep["gmres_total"]}
+        states[prec] = U
+        sh.close()
+    f, m = rw["fp64"], rw["mixed"]
+    rw["mixed_vs_fp64"] = {
+        "drift_rel": abs(m["C"] - f["C"]) / abs(f["C"]), "KE_rel": abs(m["KE"] - f["KE"]) / f["KE"],
+        "Nu_in_rel": abs(m["Nu_in"] - f["Nu_in"]) / f["Nu_in"],
+        "Nu_out_rel": abs(m["Nu_out"] - f["Nu_out"]) / f["Nu_out"],
+        "state_rel": float((torch.linalg.norm(states["mixed"] - states["fp64"]) /
+                            torch.linalg.norm(states["fp64"])).item()),
+        "speedup": f["seconds"] / m["seconds"]}
+    rw["paper_C_exact"] = 3.9998
+    out["rw_C2"] = rw
+    print(json.dumps({"rw_C2": rw}), flush=True)
+    # mixed batched Newton on four RW4 continuation points
+    c = dict(si.config("C1"), Ms=4, seed_dt=2e-3)
+    guess, C0, J, _ = _wave_from_seed(torch, RotatingShell, c)
+    Ras = [120.0, 121.0, 122.0, 123.0]
+    b = Batch([dict(L=c["L"], Ms=4, Nr=c["Nr"], Ek=c["Ek"], Ra=Ra, precision="mixed") for Ra in Ras])
+    b.autotune()
+    Ub = [guess.clone() for _ in Ras]
+    t0 = time.perf_counter()
+    Cb, reps, sts = b.newton_rw(Ub, [C0] * 4, [J] * 4, tol=1e-10, max_newton=12, kmax=300)
+    b.synchronize()
+    t_batch = time.perf_counter() - t0
+    b.close()
+    bat = {"config": "4 RW4 points, Ek=1e-3, L=31, Nr=24, Ra=120..123, mixed, concurrent",
+           "seconds": t_batch, "status": sts, "residuals": [r["residual"] for r in reps]}
+    drift_rel = []
+    for i, Ra in enumerate(Ras):
+        sh = RotatingShell(c["L"], 4, c["Nr"], c["Ek"], Ra, precision="fp64")
+        U = guess.clone()
+        Cf, rep, st = sh.newton_rw(U, C0, J, tol=1e-10, max_newton=12, kmax=300)
+        drift_rel.append(abs(Cb[i] - Cf) / abs(Cf))
+        sh.close()
+    bat["drift_rel_vs_fp64"] = drift_rel
+    out["batch_mixed_newton"] = bat
+    print(json.dumps({"batch_mixed_newton": bat}), flush=True)
+    return out
+
+
 def run_gpu(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -578,6 +685,12 @@ def run_gpu(args):
         if rank == 0:
             rows = tuple(int(r) for r in args.dt_study.split(","))
             print(json.dumps({"dt_study": dt_study(torch, RotatingShell, rows)}), flush=True)
+        return 0
+    if args.configs_study:
+        if rank == 0:
+            from paper_2508_16635_gb300 import Batch
+            print(json.dumps({"configs_study": configs_study(torch, RotatingShell, Batch)}),
+                  flush=True)
         return 0
     if args.coriolis_study:
         if rank == 0:

@@ -142,7 +142,25 @@ def test_jacobian_batch_of_directions(torch):
     gpu.close()
 
 
-@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES + [("C3-ish", 127, 12, 24, 1e-5, 140.0)])
+LARGE = [("C3-ish", 127, 12, 24, 1e-5, 140.0), ("L255", 255, 16, 8, 3e-6, 200.0),
+         ("L255-Ms8", 255, 8, 12, 3e-6, 200.0)]
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", LARGE)
+def test_explicit_terms_parity_large_truncations(torch, name, L, Ms, Nr, Ek, Ra):
+    """The FP64 transform pipeline at the largest truncations (the C5 degree L = 255)."""
+    from paper_2508_16635_gb300 import RotatingShell
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra)
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=29, amp=3e-2)
+    got = gpu.explicit_terms(torch.tensor(x, device="cuda")).cpu().numpy()
+    want = s.to_real(s.explicit_terms(s.to_complex(x)))
+    errs = _rel_fields(s, got, want)
+    assert max(errs) < 1e-12, errs
+    gpu.close()
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES + LARGE)
 def test_mixed_explicit_terms_accuracy(torch, name, L, Ms, Nr, Ek, Ra):
     """Mixed path: FP32 radial evaluation, tensor-core (3xTF32) Legendre synthesis, FP32 DFT,
     products and analysis; the explicit terms agree with the FP64 oracle to FP32 accuracy."""
