@@ -330,6 +330,14 @@ rsc_status build_tc_tables(rsc_ctx* ctx) {
   return RSC_OK;
 }
 
+// Whether `threads` threads of `fn` fit the register file and the block size limit.
+bool threads_fit(const void* fn, int threads) {
+  cudaFuncAttributes at{};
+  if (cudaFuncGetAttributes(&at, fn) != cudaSuccess) return false;
+  return threads <= 1024 && (long)threads * std::max(at.numRegs, 1) <= 65536 &&
+         threads <= at.maxThreadsPerBlock;
+}
+
 rsc_status set_smem_limits(rsc_ctx* ctx) {
   const int big = 200 * 1024;
   CK(cudaFuncSetAttribute(k_products<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -351,6 +359,13 @@ rsc_status set_smem_limits(rsc_ctx* ctx) {
   ctx->rt_synth[1] = rt_for((const void*)k_synth<float>, round32(ctx->d.nlat2));
   ctx->rt_anal[0] = rt_for((const void*)k_analysis<double>, round32(ctx->d.L + 1));
   ctx->rt_anal[1] = rt_for((const void*)k_analysis<float>, round32(ctx->d.L + 1));
+  // pairs per block of the right-hand side: 256 / Nr, halved until the registers fit
+  for (int p = 0; p < 2; ++p) {
+    int q = std::max(1, 256 / round32(ctx->d.Nr));
+    const void* fn = p ? (const void*)k_rhs<float> : (const void*)k_rhs<double>;
+    while (q > 1 && !threads_fit(fn, round32(ctx->d.Nr) * q)) q /= 2;
+    ctx->ppb[p] = q;
+  }
   CK(cudaFuncSetAttribute(k_synth<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_synth<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_analysis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -1206,7 +1221,10 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
     if ((p ? analysis_smem<float>(d, t.analysis_radii[p], t.analysis_chunk[p])
            : analysis_smem<double>(d, t.analysis_radii[p], t.analysis_chunk[p])) > 200 * 1024)
       return false;
-    if (!pow2(t.rhs_pairs[p], 8) || round32(d.Nr) * t.rhs_pairs[p] > 1024) return false;
+    if (!pow2(t.rhs_pairs[p], 8) ||
+        !threads_fit(p ? (const void*)k_rhs<float> : (const void*)k_rhs<double>,
+                     round32(d.Nr) * t.rhs_pairs[p]))
+      return false;
     if ((p ? rhs_smem<float>(d, t.rhs_pairs[p]) : rhs_smem<double>(d, t.rhs_pairs[p])) > 200 * 1024)
       return false;
   }
@@ -1321,7 +1339,8 @@ rsc_status tune_precision(rsc_ctx* ctx, rsc_tuning& t, cudaEvent_t e0, cudaEvent
   best = 1e30;
   int bp = t.rhs_pairs[p];
   for (int q : {1, 2, 4, 8}) {
-    if (round32(d.Nr) * q > 1024 || rhs_smem<R>(d, q) > 200 * 1024) continue;
+    if (!threads_fit((const void*)k_rhs<R>, round32(d.Nr) * q) || rhs_smem<R>(d, q) > 200 * 1024)
+      continue;
     ctx->ppb[p] = q;
     const double ms = timeit([&] { return stage_rhs<R>(ctx, rp, ctx->rtmp, ctx->rtmp, nullptr, ctx->rhs); });
     CKS(st);

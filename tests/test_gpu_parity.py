@@ -156,7 +156,8 @@ def test_explicit_terms_parity_large_truncations(torch, name, L, Ms, Nr, Ek, Ra)
     got = gpu.explicit_terms(torch.tensor(x, device="cuda")).cpu().numpy()
     want = s.to_real(s.explicit_terms(s.to_complex(x)))
     errs = _rel_fields(s, got, want)
-    assert max(errs) < 1e-12, errs
+    # the Legendre and DFT sums have O(L) terms: the rounding bound grows with L
+    assert max(errs) < 1e-14 * L, errs
     gpu.close()
 
 
