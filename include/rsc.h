@@ -324,6 +324,8 @@ typedef struct {
   int synth_radii;         /* radii per block of the CUDA-core (FP64) synthesis       */
   int rhs_pairs[2];        /* (l, m) pairs per block of the right-hand-side kernel    */
   int chain_cluster;       /* CTAs per thread-block cluster of the chain sweeps       */
+  int analysis_tc;         /* 1: tensor-core (tcgen05, 3xTF32) Legendre analysis on the
+                              mixed path; 0: CUDA-core FP32 analysis                   */
   int chain_async;         /* 0: one warp per 4 rows, a cluster barrier per block;
                               1 / 2: two / four warps per 4 rows (column parts), rows
                               sent with st.async to mbarriers (changes the order of the

@@ -20,6 +20,7 @@
 #include "kernels.cuh"
 #include "chain_async.cuh"
 #include "legendre_tc.cuh"
+#include "legendre_tc_analysis.cuh"
 #include "rsc_internal.h"
 
 using namespace rsc;
@@ -94,6 +95,10 @@ struct rsc_ctx {
   int ppb[2] = {0, 0};     // pairs per block of the right-hand-side kernel (0: 256 / Nr)
   int atc[2] = {16, 16};   // latitudes per staged chunk of the analysis tables
   int lpw[2] = {1, 1};     // latitudes per warp of the products kernel
+  int anal_tc = 0;         // 1: tensor-core Legendre analysis on the mixed path
+  float* ta_tiles = nullptr;   // its A tiles (hi | lo per (m, parity, table, chunk))
+  long* ta_off = nullptr;
+  int ta_nchunk = 0;
   double tune_ms[5] = {0, 0, 0, 0, 0};
   // tensor-core Legendre synthesis (FP32 path): A tiles, offsets, padded K, status word
   float* tc_tiles = nullptr;
@@ -330,6 +335,50 @@ rsc_status build_tc_tables(rsc_ctx* ctx) {
   return RSC_OK;
 }
 
+// A tiles of the tensor-core analysis: per (m, parity s, table w in {P, P/sin, dP/dtheta},
+// latitude chunk c) a 128 x kTaKc tile, rows = degrees l = m + s + 2 row, columns = north
+// latitudes c kTaKc + k, weights folded (the analysis tables), TF32 hi and lo parts in the
+// K-major core-matrix layout of the synthesis tiles.
+rsc_status build_ta_tables(rsc_ctx* ctx) {
+  const Dims& d = ctx->d;
+  const HostTables& t = ctx->t;
+  const int nchunk = (d.nlat2 + kTaKc - 1) / kTaKc;
+  std::vector<long> off((size_t)d.nm * 2 * 3 * nchunk);
+  const long tile = 2L * 128 * kTaKc;
+  for (size_t q = 0; q < off.size(); ++q) off[q] = (long)q * tile;
+  std::vector<float> tiles(off.size() * (size_t)tile, 0.0f);
+  const std::vector<double>* tab[3] = {&t.Pw, &t.Psw, &t.dPw};
+  for (int a = 0; a < d.nm; ++a) {
+    const int nl = d.L - t.m_of[a] + 1;
+    for (int sp = 0; sp < 2; ++sp)
+      for (int w = 0; w < 3; ++w)
+        for (int c = 0; c < nchunk; ++c) {
+          float* hi = &tiles[(size_t)off[((size_t)(a * 2 + sp) * 3 + w) * nchunk + c]];
+          float* lo = hi + 128 * kTaKc;
+          for (int row = 0; row < 128; ++row)
+            for (int k = 0; k < kTaKc; ++k) {
+              const int th = c * kTaKc + k;
+              const int q = sp + 2 * row;
+              float v = 0.0f;
+              if (th < d.nlat2 && q < nl) v = (float)(*tab[w])[t.leg_off[a] + (size_t)th * nl + q];
+              uint32_t bits;
+              std::memcpy(&bits, &v, 4);
+              bits &= 0xFFFFE000u;
+              float h;
+              std::memcpy(&h, &bits, 4);
+              const size_t o = (size_t)(row >> 3) * (kTaKc / 4) * 32 + (size_t)(k >> 2) * 32 +
+                               (row & 7) * 4 + (k & 3);
+              hi[o] = h;
+              lo[o] = v - h;
+            }
+        }
+  }
+  CKS(upload(ctx, &ctx->ta_tiles, tiles.data(), tiles.size()));
+  CKS(upload(ctx, &ctx->ta_off, off.data(), off.size()));
+  ctx->ta_nchunk = nchunk;
+  return RSC_OK;
+}
+
 // Whether `threads` threads of `fn` fit the register file and the block size limit.
 bool threads_fit(const void* fn, int threads) {
   cudaFuncAttributes at{};
@@ -373,6 +422,7 @@ rsc_status set_smem_limits(rsc_ctx* ctx) {
   CK(cudaFuncSetAttribute(k_rhs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_rhs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+  CK(cudaFuncSetAttribute(k_analysis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ta_smem()));
   CK(cudaFuncSetAttribute(k_dots_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * (kMaxKrylov + 2) * 8));
   return RSC_OK;
 }
@@ -505,9 +555,15 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
            24.0 * d.P * d.nlat2 * d.Nd);
   const int RTa = ctx->rt_anal[sizeof(R) == 4 ? 1 : 0];
   const int TC = ctx->atc[sizeof(R) == 4 ? 1 : 0];
-  k_analysis<R><<<dim3(d.nm, (d.Nd + RTa - 1) / RTa), dim3(round32(d.L + 1), RTa),
-                  analysis_smem<R>(d, RTa, TC), ctx->s>>>(
-      g, L.view(), reinterpret_cast<const V*>(ctx->FA), reinterpret_cast<V*>(ctx->AR), TC);
+  if (sizeof(R) == 4 && ctx->anal_tc) {
+    TaTables ta{ctx->ta_tiles, ctx->ta_off, ctx->ta_nchunk, ctx->d_status};
+    k_analysis_tc<<<dim3(d.nm, (d.Nd + kTaRadii - 1) / kTaRadii), 128, ta_smem(), ctx->s>>>(
+        g, ta, reinterpret_cast<const float2*>(ctx->FA), reinterpret_cast<float2*>(ctx->AR));
+  } else {
+    k_analysis<R><<<dim3(d.nm, (d.Nd + RTa - 1) / RTa), dim3(round32(d.L + 1), RTa),
+                    analysis_smem<R>(d, RTa, TC), ctx->s>>>(
+        g, L.view(), reinterpret_cast<const V*>(ctx->FA), reinterpret_cast<V*>(ctx->AR), TC);
+  }
   CK(cudaGetLastError());
   }
   return RSC_OK;
@@ -1230,6 +1286,7 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
   }
   if (t.synth_radii < 1 || t.synth_radii > radii_limit((const void*)k_synth<double>, round32(d.nlat2)))
     return false;
+  if (t.analysis_tc != 0 && t.analysis_tc != 1) return false;
   return chain_config_ok(d, t.chain_cluster, t.chain_async);
 }
 
@@ -1249,6 +1306,7 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
   t->synth_radii = ctx->rt_synth[0];
   t->chain_cluster = ctx->cluster;
   t->chain_async = ctx->chain_async;
+  t->analysis_tc = ctx->anal_tc;
   for (int q = 0; q < 5; ++q) t->ms[q] = ctx->tune_ms[q];
 }
 
@@ -1263,6 +1321,7 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
   ctx->rt_synth[0] = t.synth_radii;
   ctx->cluster = t.chain_cluster;
   ctx->chain_async = t.chain_async;
+  ctx->anal_tc = t.analysis_tc;
   if (ctx->jvp_exec) {   // the captured Jacobian action embeds the old launch shapes
     cudaGraphExecDestroy(ctx->jvp_exec);
     ctx->jvp_exec = nullptr;
@@ -1319,6 +1378,14 @@ rsc_status tune_precision(rsc_ctx* ctx, rsc_tuning& t, cudaEvent_t e0, cudaEvent
   }
   ctx->rt_anal[p] = t.analysis_radii[p] = br;
   ctx->atc[p] = t.analysis_chunk[p] = bc;
+  if (p == 1) {   // tensor-core analysis against the best CUDA-core shape
+    ctx->anal_tc = 1;
+    const double ms = timeit(pa);
+    CKS(st);
+    CKS(check_status(ctx));
+    ctx->anal_tc = t.analysis_tc = (ms < best) ? 1 : 0;
+    if (ms < best) best = ms;
+  }
   if (p == 1) ctx->tune_ms[0] = best;   // products + analysis of the mixed path
   // synthesis (CUDA-core FP64 path): radii per block
   if (p == 0) {
@@ -1533,6 +1600,7 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = upload_legendre(ctx, ctx->leg32)) != RSC_OK) return fail(st);
   if ((st = set_smem_limits(ctx)) != RSC_OK) return fail(st);
   if ((st = build_tc_tables(ctx)) != RSC_OK) return fail(st);
+  if ((st = build_ta_tables(ctx)) != RSC_OK) return fail(st);
   if (cudaMalloc((void**)&ctx->d_status, sizeof(int)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
     ctx->err = "cudaMalloc of the status word failed";
@@ -1590,7 +1658,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
                   ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->partial,
-                  ctx->dots, ctx->AR0, ctx->cont_hist, ctx->cont_cond, ctx->amax_v, ctx->amax_i, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
+                  ctx->dots, ctx->AR0, ctx->ta_tiles, ctx->ta_off, ctx->cont_hist, ctx->cont_cond, ctx->amax_v, ctx->amax_i, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
   for (void* b : bufs) cudaFree(b);
   for (int q = 0; q < 8; ++q) {
     cudaFree(ctx->leg64.buf[q]);

@@ -50,7 +50,8 @@ class Tuning(ctypes.Structure):
                 ("analysis_radii", ctypes.c_int * 2),
                 ("analysis_chunk", ctypes.c_int * 2),
                 ("synth_radii", ctypes.c_int), ("rhs_pairs", ctypes.c_int * 2),
-                ("chain_cluster", ctypes.c_int), ("chain_async", ctypes.c_int),
+                ("chain_cluster", ctypes.c_int), ("analysis_tc", ctypes.c_int),
+                ("chain_async", ctypes.c_int),
                 ("ms", ctypes.c_double * 5)]
 
     def as_dict(self):
@@ -59,7 +60,8 @@ class Tuning(ctypes.Structure):
                 "analysis_radii": list(self.analysis_radii),
                 "analysis_chunk": list(self.analysis_chunk), "synth_radii": self.synth_radii,
                 "rhs_pairs": list(self.rhs_pairs), "chain_cluster": self.chain_cluster,
-                "chain_async": self.chain_async, "ms": list(self.ms)}
+                "analysis_tc": self.analysis_tc, "chain_async": self.chain_async,
+                "ms": list(self.ms)}
 
 
 class ContinuationOpts(ctypes.Structure):
@@ -369,6 +371,7 @@ class RotatingShell:
         t.rhs_pairs[:] = d["rhs_pairs"]
         t.chain_cluster = d["chain_cluster"]
         t.chain_async = d.get("chain_async", 0)
+        t.analysis_tc = d.get("analysis_tc", 0)
         self._check(self.lib.rsc_set_tuning(self._ctx, ctypes.byref(t)))
 
     def continue_ra(self, U, C, J, Ra0, Ra1, Ra_end, n_opt=4, gamma=20.0, max_points=8,

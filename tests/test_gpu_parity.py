@@ -187,6 +187,22 @@ def test_mixed_explicit_terms_accuracy(torch, name, L, Ms, Nr, Ek, Ra):
     gpu.close()
 
 
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES + LARGE)
+def test_tensor_core_analysis_accuracy(torch, name, L, Ms, Nr, Ek, Ra):
+    """Mixed path with the tensor-core Legendre analysis (tcgen05, 3xTF32; analysis_tc = 1):
+    the explicit terms agree with the FP64 oracle to FP32 accuracy, like the CUDA-core one."""
+    from paper_2508_16635_gb300 import RotatingShell
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
+    gpu.set_tuning(dict(gpu.tuning(), analysis_tc=1))
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=28, amp=3e-2)
+    got = gpu.explicit_terms(torch.tensor(x, device="cuda")).cpu().numpy()
+    want = s.to_real(s.explicit_terms(s.to_complex(x)))
+    errs = _rel_fields(s, got, want)
+    assert max(errs) < 2e-5, errs
+    gpu.close()
+
+
 def test_mixed_precision_step_error(torch):
     from paper_2508_16635_gb300 import RotatingShell
     L, Ms, Nr, Ek, Ra = 31, 4, 24, 1e-3, 120.0
@@ -479,7 +495,8 @@ def test_autotune_keeps_results_bitwise(torch, name, L, Ms, Nr, Ek, Ra):
         s0 = gpu.step(U.clone(), 0.0, 1e-3).clone()
         t = gpu.autotune()
         assert t["chain_cluster"] in (2, 4, 8, 16) and min(t["rhs_pairs"]) >= 1
-        gpu.set_tuning(dict(t, chain_async=0))   # the sweep variant sums rows in another order
+        # the sweep variant and the tensor-core analysis sum in another order
+        gpu.set_tuning(dict(t, chain_async=0, analysis_tc=0))
         a1 = gpu.apply_jacobian(U, 0.3, None, torch.tensor(u, device="cuda"), 200.0)
         s1 = gpu.step(U.clone(), 0.0, 1e-3)
         assert torch.equal(a0, a1) and torch.equal(s0, s1)
