@@ -215,33 +215,56 @@ FP64_KERNELS = {"radial_eval", "rhs_assemble", "chain_gemv", "chain_sweep", "tem
                 "gmres_dots", "gmres_axpy", "blas1"}
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of each kernel on this workload
-# (`--set full`, mixed path, the shapes the autotuner picks; the summaries are under
-# profiles/).  A kernel changed since its capture has no entry (traffic null).
+# DRAM bytes (read + write) per launch from one ncu capture of each kernel on this workload,
+# keyed by (kernel class, arithmetic): a figure holds only for the variant it was taken on
 NCU_TRAFFIC_MB = {
     # k_chain_half_async: 95.3 + 2.9 MB; k_chain_out_async: 101.1 + 3.3 MB (mean per launch)
-    "chain_sweep": 101.3,
+    ("chain_sweep", "fp64"): 101.3,
+    # k_chain_half_df: 95.3 + 3.0 MB; k_chain_out_df: 101.1 + 3.2 MB
+    ("chain_sweep", "df"): 101.3,
 }
 
 
-def roofline(prof, peaks, precision):
+def double_float_kernels(precision, tuning):
+    """Kernel classes that run in double-float arithmetic (FP32 hi + lo pairs, Dot2 sums)
+    under this tuning: the chain solve of the mixed path (chain_df) and the orthogonalisation
+    against the split Krylov basis (krylov_split)."""
+    out = set()
+    if precision == "mixed" and tuning.get("chain_df", 0):
+        out |= {"chain_sweep", "chain_gemv"}
+    if tuning.get("krylov_split", 0):
+        out |= {"gmres_dots", "gmres_axpy"}
+    return out
+
+
+def roofline(prof, peaks, precision, tuning):
     name = max(prof, key=lambda k: prof[k]["ms"])   # the only kernel timed in this pass
     p = prof[name]
     t = p["ms"] / max(1, p["launches"]) * 1e-3
     gbs = p["bytes"] / max(1, p["launches"]) / t / 1e9
-    fp64 = name in FP64_KERNELS or precision == "fp64"
-    alu_peak = peaks["fp64_tflops"] if fp64 else peaks["fp32_tflops"]
-    tfs = p["flops"] / max(1, p["launches"]) / t / 1e12
-    f_hbm = gbs / peaks["hbm_gbs"]
-    f_alu = tfs / alu_peak
-    if f_alu >= f_hbm:
-        out = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s",
-               "frac": f_alu, "peak_source": ("FP64" if fp64 else "FP32") +
-               " cuBLAS GEMM timed in this run on this GPU (measured)"}
-    else:
+    dfk = double_float_kernels(precision, tuning)
+    if name in dfk:
+        # FP64-equivalent flops carried out as FP32 pairs: no FP64 ALU bound applies; the
+        # kernel reads its tables and vectors once, so HBM is the roofline
         out = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-               "frac": f_hbm, "peak_source": peaks["hbm_source"]}
-    mb = NCU_TRAFFIC_MB.get(name)
+               "frac": gbs / peaks["hbm_gbs"], "peak_source": peaks["hbm_source"],
+               "arithmetic": "double-float (FP32 hi + lo pairs, Dot2 sums)"}
+    else:
+        fp64 = name in FP64_KERNELS or precision == "fp64"
+        alu_peak = peaks["fp64_tflops"] if fp64 else peaks["fp32_tflops"]
+        tfs = p["flops"] / max(1, p["launches"]) / t / 1e12
+        f_hbm = gbs / peaks["hbm_gbs"]
+        f_alu = tfs / alu_peak
+        if f_alu >= f_hbm:
+            out = {"bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s",
+                   "frac": f_alu, "peak_source": ("FP64" if fp64 else "FP32") +
+                   " cuBLAS GEMM timed in this run on this GPU (measured)",
+                   "arithmetic": "FP64" if fp64 else "FP32"}
+        else:
+            out = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                   "frac": f_hbm, "peak_source": peaks["hbm_source"],
+                   "arithmetic": "FP64" if fp64 else "FP32"}
+    mb = NCU_TRAFFIC_MB.get((name, "df" if name in dfk else "fp64"))
     out.update(kernel=name, traffic=mb * 1e6 if mb is not None else None,
                traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"
                if mb is not None else None, avg_launch_ms=t * 1e3, launches=p["launches"],
@@ -830,7 +853,7 @@ def run_gpu(args):
             "kernel_ms_per_step": {k: round(v["ms"], 4) for k, v in prof_all.items()},
             "kernel_ms_per_jacobian_action": prof_jvp,
             "kernel_ms_per_fp64_step": prof_step64,
-            "roofline": roofline(prof, peaks, args.precision),
+            "roofline": roofline(prof, peaks, args.precision, tuning),
             "peaks": {k: v for k, v in peaks.items()},
             "clocks": clk.summary(),
             "wall_s_timed_region": wall,

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RSC_ABI_VERSION 3
+#define RSC_ABI_VERSION 4
 
 typedef struct rsc_ctx rsc_ctx;
 
@@ -330,9 +330,21 @@ typedef struct {
                               1 / 2: two / four warps per 4 rows (column parts), rows
                               sent with st.async to mbarriers (changes the order of the
                               row sums)                                                */
-  double ms[5];            /* after rsc_autotune: best times (ms) of products +
-                              analysis (mixed), FP64 synthesis, RHS (mixed), chain
-                              solve; zero otherwise                                   */
+  int chain_df;            /* mixed path (Jacobian actions and mixed steps): 0 = the FP64
+                              chain solve; 2 / 4 = the chain solve in double-float
+                              arithmetic (factor blocks and vectors as FP32 hi + lo
+                              pairs, Dot2 row sums; about 1e-8 relative from FP64) with
+                              two / four warps per 4 rows.  The FP64 residual step
+                              always uses the FP64 solve.                              */
+  int chain_df_cluster;    /* CTAs per thread-block cluster of the double-float sweeps */
+  int krylov_split;        /* 1: GMRES keeps the Krylov basis also as FP32 hi + lo pairs
+                              and orthogonalises in double-float arithmetic (inner
+                              products within about 1e-14 of FP64); 0: FP64 passes.
+                              Not changed by rsc_autotune.                             */
+  double ms[6];            /* after rsc_autotune: best times (ms) of products +
+                              analysis (mixed), FP64 synthesis, RHS (mixed), FP64 chain
+                              solve, double-float chain solve (0 if none ran); zero
+                              otherwise                                               */
 } rsc_tuning;
 
 /* Autotuner: times every feasible candidate of each shape on this context's

@@ -21,6 +21,8 @@
 #include "chain_async.cuh"
 #include "legendre_tc.cuh"
 #include "legendre_tc_analysis.cuh"
+#include "krylov_split.cuh"
+#include "chain_df.cuh"
 #include "rsc_internal.h"
 
 using namespace rsc;
@@ -36,6 +38,10 @@ struct DevFactor {
   double2* H = nullptr;
   double2* W = nullptr;
   double* Tinv = nullptr;
+  // double-float copies of G, H, W (mixed-precision contexts): float4 {re_hi, im_hi, re_lo, im_lo}
+  float4* Gs = nullptr;
+  float4* Hs = nullptr;
+  float4* Ws = nullptr;
   bool valid = false;
 };
 
@@ -79,14 +85,19 @@ struct rsc_ctx {
   int fac_next = 0;
   // Krylov
   double* V = nullptr;
+  float2* Vs = nullptr;   // the same basis as (hi, lo) float pairs (krylov_split)
   int V_cols = 0;
-  long ldV = 0;   // column stride of V
+  long ldV = 0;   // column stride of V and Vs
+  int krylov_split = 1;   // 1: orthogonalise against Vs in double-float arithmetic
   double* partial = nullptr;
   double* dots = nullptr;
   double* h_pinned = nullptr;
   int nblk_dot = 0;
   int cluster = 8;  // CTAs per chain in the cluster chain solve
   int chain_async = 0;   // 1: sweeps with column-split warps and st.async / mbarrier exchange
+  int chain_df = 0;       // mixed path: 2 / 4 = double-float chain solve with that many warps
+                          // per row group (chain_df.cuh), 0 = the FP64 kernels
+  int cluster_df = 8;     // CTAs per cluster of the double-float sweeps
   // second stream: the temperature solve runs beside the e/f chain solve
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -99,7 +110,7 @@ struct rsc_ctx {
   float* ta_tiles = nullptr;   // its A tiles (hi | lo per (m, parity, table, chunk))
   long* ta_off = nullptr;
   int ta_nchunk = 0;
-  double tune_ms[5] = {0, 0, 0, 0, 0};
+  double tune_ms[6] = {0, 0, 0, 0, 0, 0};
   // tensor-core Legendre synthesis (FP32 path): A tiles, offsets, padded K, status word
   float* tc_tiles = nullptr;
   long* tc_off = nullptr;
@@ -254,6 +265,9 @@ void free_factor(DevFactor& f) {
   cudaFree(f.H);
   cudaFree(f.W);
   cudaFree(f.Tinv);
+  cudaFree(f.Gs);
+  cudaFree(f.Hs);
+  cudaFree(f.Ws);
   f = DevFactor();
 }
 
@@ -453,6 +467,22 @@ rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
   CKS(upload(ctx, &f.H, reinterpret_cast<const double2*>(hf.H.data()), hf.H.size()));
   CKS(upload(ctx, &f.W, reinterpret_cast<const double2*>(hf.W.data()), hf.W.size()));
   CKS(upload(ctx, &f.Tinv, hf.Tinv.data(), hf.Tinv.size()));
+  if (ctx->p.precision == RSC_MIXED) {
+    // double-float copies for the mixed path (chain_df.cuh): hi = the entry rounded to FP32,
+    // lo = the remainder rounded to FP32
+    auto split_upload = [&](const std::vector<cplx>& src, float4** dst) -> rsc_status {
+      std::vector<float4> t(src.size());
+      for (size_t i = 0; i < src.size(); ++i) {
+        const double re = src[i].real(), im = src[i].imag();
+        const float rh = (float)re, ih = (float)im;
+        t[i] = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+      }
+      return upload(ctx, dst, t.data(), t.size());
+    };
+    CKS(split_upload(hf.G, &f.Gs));
+    CKS(split_upload(hf.H, &f.Hs));
+    CKS(split_upload(hf.W, &f.Ws));
+  }
   f.dt = dt;
   f.valid = true;
   *out = &f;
@@ -678,7 +708,58 @@ cudaError_t launch_chain(rsc_ctx* ctx, const DevFactor* f, double* out, bool out
   }
 }
 
-rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
+// Double-float sweeps (chain_df.cuh): NS = ctx->chain_df warps per row group, clusters of
+// ctx->cluster_df CTAs; the shared-memory layout of the asynchronous FP64 sweeps.
+template <int Q, int NS>
+cudaError_t launch_chain_df_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
+  const Dims& d = ctx->d;
+  const int CS = ctx->cluster_df;
+  const int RPC = (d.Nr + CS - 1) / CS;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * 2 * d.nm * CS);
+  cfg.blockDim = dim3(32 * NS * ((RPC + 3) / 4));
+  cfg.dynamicSmemBytes = chain_smem_async(d, CS, outward, NS);
+  cfg.stream = ctx->s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int cap = chain_steps_cap(d);
+  if (outward)
+    return cudaLaunchKernelEx(&cfg, k_chain_out_df<Q / NS, NS>, ctx->geom(),
+                              (const long*)f->chain_off, (const float4*)f->Hs,
+                              (const float4*)f->Ws, reinterpret_cast<double2*>(out),
+                              (const double2*)ctx->mid, CS, cap, ctx->d_status);
+  return cudaLaunchKernelEx(&cfg, k_chain_half_df<Q / NS, NS>, ctx->geom(),
+                            (const long*)f->chain_off, (const float4*)f->Hs,
+                            reinterpret_cast<double2*>(out), ctx->mid, CS, cap, ctx->d_status);
+}
+
+template <int Q>
+cudaError_t launch_chain_df_ns(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
+  if (ctx->chain_df == 2) return launch_chain_df_q<Q, 2>(ctx, f, out, outward);
+  if constexpr (Q % 4 == 0)
+    if (ctx->chain_df == 4) return launch_chain_df_q<Q, 4>(ctx, f, out, outward);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_chain_df(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
+  switch (chain_maxq(ctx->d.Nr)) {
+    case 2: return launch_chain_df_ns<2>(ctx, f, out, outward);
+    case 4: return launch_chain_df_ns<4>(ctx, f, out, outward);
+    case 8: return launch_chain_df_ns<8>(ctx, f, out, outward);
+    case 12: return launch_chain_df_ns<12>(ctx, f, out, outward);
+    default: return launch_chain_df_ns<16>(ctx, f, out, outward);
+  }
+}
+
+// df: the double-float GEMV and sweeps (mixed path, when the context has double-float tables
+// and chain_df is on); otherwise the FP64 kernels.
+rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = false) {
+  df = df && f->Gs && f->Hs && f->Ws && ctx->chain_df != 0;
   const Dims& d = ctx->d;
   // the temperature solve depends only on the right-hand side: it runs on a second stream
   // beside the e/f chain solve (sequentially while tracing, so that every launch is timed)
@@ -700,20 +781,24 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
   {
     KSpan sp(ctx, RSC_K_CHAIN, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
-    k_block_gemv<<<2 * d.P, 256, (size_t)d.Nr * sizeof(double2), ctx->s>>>(
-        ctx->geom(), f->chain_off, f->G, ctx->rhs, reinterpret_cast<double2*>(out));
+    if (df)
+      k_block_gemv_df<<<2 * d.P, 256, (size_t)d.Nr * sizeof(float4), ctx->s>>>(
+          ctx->geom(), f->chain_off, f->Gs, ctx->rhs, reinterpret_cast<double2*>(out));
+    else
+      k_block_gemv<<<2 * d.P, 256, (size_t)d.Nr * sizeof(double2), ctx->s>>>(
+          ctx->geom(), f->chain_off, f->G, ctx->rhs, reinterpret_cast<double2*>(out));
     CK(cudaGetLastError());
   }
   if (!ctx->p.explicit_coriolis) {
     // forward half-sweeps read H of about half the blocks each way, outward sweeps W
     KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
-    CK(launch_chain(ctx, f, out, false));
+    CK(df ? launch_chain_df(ctx, f, out, false) : launch_chain(ctx, f, out, false));
   }
   if (!ctx->p.explicit_coriolis) {
     KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
-    CK(launch_chain(ctx, f, out, true));
+    CK(df ? launch_chain_df(ctx, f, out, true) : launch_chain(ctx, f, out, true));
   }
   if (fork) {
     CK(cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0));
@@ -727,11 +812,25 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out) {
   return RSC_OK;
 }
 
+bool cluster_ok_pair(const Dims& d, int CS, int NS, const void* const (&fns)[2]);
+
 // Whether the device can co-schedule clusters of CS CTAs for the asynchronous sweeps.
 template <int Q, int NS>
 bool cluster_ok_async(const Dims& d, int CS) {
-  const void* fns[2] = {(const void*)k_chain_half_async<Q / NS, NS>,
-                        (const void*)k_chain_out_async<Q / NS, NS>};
+  const void* const fns[2] = {(const void*)k_chain_half_async<Q / NS, NS>,
+                              (const void*)k_chain_out_async<Q / NS, NS>};
+  return cluster_ok_pair(d, CS, NS, fns);
+}
+
+// The same for the double-float sweeps (same shared-memory layout and block shape).
+template <int Q, int NS>
+bool cluster_ok_df(const Dims& d, int CS) {
+  const void* const fns[2] = {(const void*)k_chain_half_df<Q / NS, NS>,
+                              (const void*)k_chain_out_df<Q / NS, NS>};
+  return cluster_ok_pair(d, CS, NS, fns);
+}
+
+bool cluster_ok_pair(const Dims& d, int CS, int NS, const void* const (&fns)[2]) {
   for (int w = 0; w < 2; ++w) {
     cudaFuncSetAttribute(fns[w], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaGetLastError();
@@ -830,6 +929,26 @@ bool chain_config_ok_q(const Dims& d, int CS, int async_mode) {
   return false;
 }
 
+template <int Q>
+bool chain_df_ok_q(const Dims& d, int CS, int ns) {
+  if (ns == 2) return cluster_ok_df<Q, 2>(d, CS);
+  if constexpr (Q % 4 == 0) return ns == 4 && cluster_ok_df<Q, 4>(d, CS);
+  return false;
+}
+
+// Double-float sweeps with ns warps per row group on clusters of CS (ns = 0: off).
+bool chain_df_ok(const Dims& d, int CS, int ns) {
+  if (ns == 0) return true;
+  if (CS < 1 || CS > d.Nr || (ns != 2 && ns != 4)) return false;
+  switch (chain_maxq(d.Nr)) {
+    case 2: return chain_df_ok_q<2>(d, CS, ns);
+    case 4: return chain_df_ok_q<4>(d, CS, ns);
+    case 8: return chain_df_ok_q<8>(d, CS, ns);
+    case 12: return chain_df_ok_q<12>(d, CS, ns);
+    default: return chain_df_ok_q<16>(d, CS, ns);
+  }
+}
+
 bool chain_config_ok(const Dims& d, int CS, int async_mode) {
   if (CS > d.Nr || async_mode < 0 || async_mode > 2) return false;
   switch (chain_maxq(d.Nr)) {
@@ -862,7 +981,7 @@ rsc_status do_step(rsc_ctx* ctx, double* U, double C, double dt) {
   CKS(stage_synth<R>(ctx, U, ctx->FC));
   CKS(stage_products_analysis<R>(ctx, false));
   CKS(stage_rhs<R>(ctx, make_rp(ctx, dt, C, 0), U, nullptr, nullptr, ctx->rhs));
-  CKS(stage_solve(ctx, f, U));
+  CKS(stage_solve(ctx, f, U, sizeof(R) == 4));
   return RSC_OK;
 }
 
@@ -895,7 +1014,7 @@ rsc_status do_step2(rsc_ctx* ctx, double* U, double dt) {
   CKS(stage_products_analysis<R>(ctx, false));
   CK(cudaMemcpyAsync(ctx->AR0, ctx->AR, nar * sizeof(V), cudaMemcpyDeviceToDevice, ctx->s));
   CKS(stage_rhs<R>(ctx, rp, U, nullptr, nullptr, ctx->rhs));
-  CKS(stage_solve(ctx, f, ctx->vtmp));
+  CKS(stage_solve(ctx, f, ctx->vtmp, sizeof(R) == 4));
   {
     KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
     k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, U, 2.0, ctx->vtmp, n);
@@ -917,7 +1036,7 @@ rsc_status do_step2(rsc_ctx* ctx, double* U, double dt) {
     CK(cudaGetLastError());
   }
   CKS(stage_rhs<R>(ctx, rp, U, nullptr, nullptr, ctx->rhs, ctx->xtmp));
-  CKS(stage_solve(ctx, f, ctx->vtmp));
+  CKS(stage_solve(ctx, f, ctx->vtmp, sizeof(R) == 4));
   {
     KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
     k_axpby<<<nb, 256, 0, ctx->s>>>(2.0, ctx->vtmp, -1.0, U, n);
@@ -952,7 +1071,7 @@ rsc_status do_jvp_eager(rsc_ctx* ctx, const double* U, double C, long J, const d
   RhsParams rp = make_rp(ctx, dt, C, 1);
   rp.J = J;  // c = u[J] is read on the device
   CKS(stage_rhs<R>(ctx, rp, ctx->xtmp, U, u, ctx->rhs));
-  CKS(stage_solve(ctx, f, out));
+  CKS(stage_solve(ctx, f, out, sizeof(R) == 4));
   {
     KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
     k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, ctx->xtmp, 1.0, out, n);
@@ -978,7 +1097,7 @@ rsc_status jvp_body_indirect(rsc_ctx* ctx, const double* U, double C, long J, De
   RhsParams rp = make_rp(ctx, dt, C, 1);
   rp.J = J >= 0 ? 0 : -1;  // c is read from d_cslot[0]
   CKS(stage_rhs<R>(ctx, rp, ctx->xtmp, U, ctx->d_cslot, ctx->rhs));
-  CKS(stage_solve(ctx, f, ctx->jvp_y));
+  CKS(stage_solve(ctx, f, ctx->jvp_y, sizeof(R) == 4));
   {
     KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
     k_finish_ind<<<nb, 256, 0, ctx->s>>>(ctx->d_slots, ctx->jvp_y, ctx->xtmp, n);
@@ -1064,17 +1183,23 @@ rsc_status ensure_krylov(rsc_ctx* ctx, int kmax) {
   if (ctx->V_cols >= kmax + 1) return RSC_OK;
   CK(cudaStreamSynchronize(ctx->s));
   cudaFree(ctx->V);
+  cudaFree(ctx->Vs);
   ctx->V = nullptr;
+  ctx->Vs = nullptr;
   ctx->V_cols = 0;
   const long n = ctx->d.n();
   ctx->ldV = (n + 1023) / 1024 * 1024;
   const size_t bytes = (size_t)(kmax + 1) * ctx->ldV * sizeof(double);
-  if (cudaMalloc(&ctx->V, bytes) != cudaSuccess) {
+  static_assert(sizeof(float2) == sizeof(double), "split basis layout");
+  if (cudaMalloc(&ctx->V, bytes) != cudaSuccess || cudaMalloc(&ctx->Vs, bytes) != cudaSuccess) {
+    cudaFree(ctx->V);
     ctx->V = nullptr;
+    ctx->Vs = nullptr;
     ctx->err = "cudaMalloc of the Krylov basis failed";
     return RSC_ENOMEM;
   }
   CK(cudaMemsetAsync(ctx->V, 0, bytes, ctx->s));
+  CK(cudaMemsetAsync(ctx->Vs, 0, bytes, ctx->s));
   ctx->V_cols = kmax + 1;
   return RSC_OK;
 }
@@ -1130,10 +1255,17 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
   *relres = 0.0;
   if (beta == 0.0) return RSC_OK;
   double* V = ctx->V;
+  float2* Vs = ctx->Vs;
   const long ld = ctx->ldV;
+  // double-float orthogonalisation needs n even (element pairs) and 16-byte aligned b and x
+  const bool split = ctx->krylov_split && (n % 2 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15) == 0;
   {
     KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 1.0 * n);
-    k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / beta, b, 0.0, V, n);
+    if (split)
+      k_scale_split<<<nb, 256, 0, ctx->s>>>(b, V, Vs, n, nullptr, 1.0 / beta);
+    else
+      k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / beta, b, 0.0, V, n);
     CK(cudaGetLastError());
   }
   // device buffer: [0] |w|^2 of the previous iteration, [1, k+2) s, [k+2, 2k+3) t
@@ -1156,8 +1288,12 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
       CKS(jvp_any(ctx, U, C, J, vk, w, dt, fp32));
       {
         KSpan sp(ctx, RSC_K_DOTS, 8.0 * n * (k + 3), 4.0 * n * (k + 1));
-        k_dots_pair<<<dim3(nchunk, (k + 1 + 15) / 16), 256, 0, ctx->s>>>(V, ld, k + 1, w, vk,
-                                                                          ctx->partial);
+        if (split)
+          k_dots_pair_s<<<dim3(nchunk, (k + 1 + 15) / 16), 256, 0, ctx->s>>>(
+              Vs, ld, k + 1, w, Vs + (long)k * ld, ctx->partial);
+        else
+          k_dots_pair<<<dim3(nchunk, (k + 1 + 15) / 16), 256, 0, ctx->s>>>(V, ld, k + 1, w, vk,
+                                                                            ctx->partial);
         CK(cudaGetLastError());
       }
       {
@@ -1214,7 +1350,11 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
     CK(cudaMemcpyAsync(d_h, h_out, (k + 1) * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
     {
       KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (k + 3), 2.0 * n * (k + 2));
-      k_axpy_norm<<<nb, 256, 0, ctx->s>>>(V, ld, k + 1, d_h, w, n, ctx->partial);
+      if (split)
+        k_axpy_norm_s<<<nb, 256, (size_t)(k + 1) * sizeof(float2), ctx->s>>>(Vs, ld, k + 1, d_h,
+                                                                             w, n, ctx->partial);
+      else
+        k_axpy_norm<<<nb, 256, 0, ctx->s>>>(V, ld, k + 1, d_h, w, n, ctx->partial);
       CK(cudaGetLastError());
     }
     {
@@ -1224,7 +1364,10 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
     }
     {
       KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 1.0 * n);
-      k_scale_inv_sqrt<<<nb, 256, 0, ctx->s>>>(w, n, dbuf);
+      if (split)
+        k_scale_split<<<nb, 256, 0, ctx->s>>>(w, w, Vs + (long)(k + 1) * ld, n, dbuf, 1.0);
+      else
+        k_scale_inv_sqrt<<<nb, 256, 0, ctx->s>>>(w, n, dbuf);
       CK(cudaGetLastError());
     }
   }
@@ -1239,7 +1382,11 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
   CK(cudaMemcpyAsync(d_h, h_out, kk * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
   {
     KSpan sp(ctx, RSC_K_AXPY, 8.0 * n * (kk + 2), 2.0 * n * kk);
-    k_multi_axpy2<<<nb, 256, 0, ctx->s>>>(V, ld, kk, d_h, 1.0, x, n);
+    if (split)
+      k_multi_axpy_s<<<nb, 256, (size_t)std::max(kk, 1) * sizeof(float2), ctx->s>>>(Vs, ld, kk,
+                                                                                    d_h, x, n);
+    else
+      k_multi_axpy2<<<nb, 256, 0, ctx->s>>>(V, ld, kk, d_h, 1.0, x, n);
     CK(cudaGetLastError());
   }
   CK(cudaStreamSynchronize(ctx->s));
@@ -1287,6 +1434,8 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
   if (t.synth_radii < 1 || t.synth_radii > radii_limit((const void*)k_synth<double>, round32(d.nlat2)))
     return false;
   if (t.analysis_tc != 0 && t.analysis_tc != 1) return false;
+  if (t.krylov_split != 0 && t.krylov_split != 1) return false;
+  if (!chain_df_ok(d, t.chain_df_cluster, t.chain_df)) return false;
   return chain_config_ok(d, t.chain_cluster, t.chain_async);
 }
 
@@ -1307,7 +1456,10 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
   t->chain_cluster = ctx->cluster;
   t->chain_async = ctx->chain_async;
   t->analysis_tc = ctx->anal_tc;
-  for (int q = 0; q < 5; ++q) t->ms[q] = ctx->tune_ms[q];
+  t->chain_df = ctx->chain_df;
+  t->chain_df_cluster = ctx->cluster_df;
+  t->krylov_split = ctx->krylov_split;
+  for (int q = 0; q < 6; ++q) t->ms[q] = ctx->tune_ms[q];
 }
 
 void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
@@ -1322,6 +1474,9 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
   ctx->cluster = t.chain_cluster;
   ctx->chain_async = t.chain_async;
   ctx->anal_tc = t.analysis_tc;
+  ctx->chain_df = t.chain_df;
+  ctx->cluster_df = t.chain_df_cluster;
+  ctx->krylov_split = t.krylov_split;
   if (ctx->jvp_exec) {   // the captured Jacobian action embeds the old launch shapes
     cudaGraphExecDestroy(ctx->jvp_exec);
     ctx->jvp_exec = nullptr;
@@ -1454,7 +1609,34 @@ rsc_status autotune(rsc_ctx* ctx, rsc_tuning* out) {
     if (st == RSC_OK) st = check_status(ctx);   // a timed-out wait of a sweep candidate
     t.chain_cluster = bc;
     t.chain_async = ba;
+    ctx->cluster = bc;
+    ctx->chain_async = ba;
     ctx->tune_ms[3] = best;
+    // mixed path: the double-float chain solve against the best FP64 one
+    if (st == RSC_OK && f->Gs) {
+      double best_df = 1e30;
+      int bn = 0, bcs = t.chain_df_cluster;
+      for (int ns : {2, 4}) {
+        for (int cs : {16, 8, 4, 2}) {
+          if (st != RSC_OK) break;
+          if (!chain_df_ok(ctx->d, cs, ns)) continue;
+          ctx->chain_df = ns;
+          ctx->cluster_df = cs;
+          st = stage_solve(ctx, f, ctx->xtmp, true);
+          cudaEventRecord(e0, ctx->s);
+          for (int r = 0; r < 3 && st == RSC_OK; ++r) st = stage_solve(ctx, f, ctx->xtmp, true);
+          cudaEventRecord(e1, ctx->s);
+          if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (st == RSC_OK && ms / 3.0 < best_df) { best_df = ms / 3.0; bn = ns; bcs = cs; }
+        }
+      }
+      if (st == RSC_OK) st = check_status(ctx);
+      t.chain_df = best_df < best ? bn : 0;
+      t.chain_df_cluster = bcs;
+      ctx->tune_ms[5] = best_df < 1e30 ? best_df : 0.0;
+    }
   }
   ctx->prof_on = prof;
   cudaEventDestroy(e0);
@@ -1607,6 +1789,15 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
     return fail(RSC_ENOMEM);
   }
   if ((st = choose_cluster(ctx)) != RSC_OK) return fail(st);
+  if (ctx->p.precision == RSC_MIXED) {
+    // double-float chain solve for the mixed path by default (rsc_autotune may keep FP64)
+    for (int cs : {ctx->cluster, 8, 4, 16, 2})
+      if (chain_df_ok(ctx->d, cs, 2)) {
+        ctx->chain_df = 2;
+        ctx->cluster_df = cs;
+        break;
+      }
+  }
   const size_t c16 = sizeof(double2);
   const size_t K1 = d.K + 1;
   auto alloc = [&](void** p, size_t bytes) -> rsc_status {
@@ -1657,7 +1848,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
-                  ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->partial,
+                  ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->Vs, ctx->partial,
                   ctx->dots, ctx->AR0, ctx->ta_tiles, ctx->ta_off, ctx->cont_hist, ctx->cont_cond, ctx->amax_v, ctx->amax_i, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
   for (void* b : bufs) cudaFree(b);
   for (int q = 0; q < 8; ++q) {

@@ -51,8 +51,9 @@ class Tuning(ctypes.Structure):
                 ("analysis_chunk", ctypes.c_int * 2),
                 ("synth_radii", ctypes.c_int), ("rhs_pairs", ctypes.c_int * 2),
                 ("chain_cluster", ctypes.c_int), ("analysis_tc", ctypes.c_int),
-                ("chain_async", ctypes.c_int),
-                ("ms", ctypes.c_double * 5)]
+                ("chain_async", ctypes.c_int), ("chain_df", ctypes.c_int),
+                ("chain_df_cluster", ctypes.c_int), ("krylov_split", ctypes.c_int),
+                ("ms", ctypes.c_double * 6)]
 
     def as_dict(self):
         return {"products_warps": list(self.products_warps),
@@ -61,7 +62,8 @@ class Tuning(ctypes.Structure):
                 "analysis_chunk": list(self.analysis_chunk), "synth_radii": self.synth_radii,
                 "rhs_pairs": list(self.rhs_pairs), "chain_cluster": self.chain_cluster,
                 "analysis_tc": self.analysis_tc, "chain_async": self.chain_async,
-                "ms": list(self.ms)}
+                "chain_df": self.chain_df, "chain_df_cluster": self.chain_df_cluster,
+                "krylov_split": self.krylov_split, "ms": list(self.ms)}
 
 
 class ContinuationOpts(ctypes.Structure):
@@ -372,6 +374,10 @@ class RotatingShell:
         t.chain_cluster = d["chain_cluster"]
         t.chain_async = d.get("chain_async", 0)
         t.analysis_tc = d.get("analysis_tc", 0)
+        cur = self.tuning()   # fields absent from d keep the context's current values
+        t.chain_df = d.get("chain_df", cur["chain_df"])
+        t.chain_df_cluster = d.get("chain_df_cluster", cur["chain_df_cluster"])
+        t.krylov_split = d.get("krylov_split", cur["krylov_split"])
         self._check(self.lib.rsc_set_tuning(self._ctx, ctypes.byref(t)))
 
     def continue_ra(self, U, C, J, Ra0, Ra1, Ra_end, n_opt=4, gamma=20.0, max_points=8,

@@ -35,7 +35,7 @@ def test_binding_covers_header():
 
 
 def test_version_and_status_strings(lib):
-    assert lib.rsc_abi_version() == 3
+    assert lib.rsc_abi_version() == 4
     assert lib.rsc_status_string(0) == b"RSC_OK"
     assert lib.rsc_status_string(6) == b"RSC_ESINGULAR"
 
@@ -53,3 +53,42 @@ def test_create_rejects_bad_parameters_without_touching_the_gpu(lib):
     assert lib.rsc_create(None, None, ctypes.byref(ctx)) == 1
     assert lib.rsc_destroy(None) == 1
     assert lib.rsc_last_error(None) == b"null context"
+
+
+STRUCTS = [("rsc_params", "Params"), ("rsc_newton_opts", "NewtonOpts"),
+           ("rsc_newton_report", "NewtonReport"), ("rsc_tuning", "Tuning"),
+           ("rsc_continuation_opts", "ContinuationOpts"),
+           ("rsc_continuation_point", "ContinuationPoint"),
+           ("rsc_ek_continuation_opts", "EkContinuationOpts"), ("rsc_ek_point", "EkPoint")]
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """Size and every field offset of the ctypes mirrors equal the C compiler's layout of the
+    structs in include/rsc.h (compiled here as plain C)."""
+    import shutil
+    import subprocess
+    from paper_2508_16635_gb300 import rsc as b
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rsc.h"', 'int main(void) {']
+    for cname, pyname in STRUCTS:
+        lines.append(f'  printf("{pyname} size %zu\\n", sizeof({cname}));')
+        for f, _ in getattr(b, pyname)._fields_:
+            lines.append(f'  printf("{pyname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            py, f, v = line.split()
+            got[(py, f)] = int(v)
+    for _, pyname in STRUCTS:
+        cls = getattr(b, pyname)
+        assert got[(pyname, "size")] == ctypes.sizeof(cls), pyname
+        for f, _ in cls._fields_:
+            assert got[(pyname, f)] == getattr(cls, f).offset, (pyname, f)

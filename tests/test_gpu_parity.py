@@ -493,10 +493,12 @@ def test_autotune_keeps_results_bitwise(torch, name, L, Ms, Nr, Ek, Ra):
         U = torch.tensor(x, device="cuda")
         a0 = gpu.apply_jacobian(U, 0.3, None, torch.tensor(u, device="cuda"), 200.0).clone()
         s0 = gpu.step(U.clone(), 0.0, 1e-3).clone()
+        t0 = gpu.tuning()
         t = gpu.autotune()
         assert t["chain_cluster"] in (2, 4, 8, 16) and min(t["rhs_pairs"]) >= 1
-        # the sweep variant and the tensor-core analysis sum in another order
-        gpu.set_tuning(dict(t, chain_async=0, analysis_tc=0))
+        # the sweep variant, the tensor-core analysis and the double-float sweeps' column
+        # split sum in another order (the double-float cluster size does not)
+        gpu.set_tuning(dict(t, chain_async=0, analysis_tc=0, chain_df=t0["chain_df"]))
         a1 = gpu.apply_jacobian(U, 0.3, None, torch.tensor(u, device="cuda"), 200.0)
         s1 = gpu.step(U.clone(), 0.0, 1e-3)
         assert torch.equal(a0, a1) and torch.equal(s0, s1)
@@ -577,3 +579,105 @@ def test_ek_continuation_refines_the_grid(torch):
     assert abs(refined[0]["C"] - coarse[-1]["C"]) < 1e-3 * abs(coarse[-1]["C"])
     fine.close()
     gpu.close()
+
+
+# ---- double-float chain solve (mixed path) and double-float Krylov basis ---------------------
+DF_CASES = CASES + [("RW12", 127, 12, 64, 1e-5, 140.0)]
+
+
+def _rel_ef(s, got, want):
+    """Relative 2-norm difference of the coupled e/f part (the unknowns of the chain solve)."""
+    g = s.to_complex(got)[:2]
+    w = s.to_complex(want)[:2]
+    return float(np.linalg.norm(g - w) / np.linalg.norm(w))
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", DF_CASES)
+def test_double_float_chain_solve_against_fp64_solve(torch, name, L, Ms, Nr, Ek, Ra):
+    """Mixed Jacobian actions and mixed steps with the chain solve in double-float arithmetic
+    (chain_df = 2 or 4, every schedulable cluster size) against the same mixed path with the
+    FP64 chain solve: the transforms are identical, so the difference is the chain solve's
+    own, measured on the coupled e/f vector that the chains solve for.
+
+    Bound 1e-6.  The e/f solve amplifies relative perturbations of its operator by about
+    1e6 (the FP64 path already moves by 1e-10 under 1e-16 changes of its tables); the
+    double-float tables carry 2^-48 = 3.6e-15 and Dot2 sums about n u^2 = 2.3e-13 relative
+    to the summed magnitudes, so deviations of 1e-9 to 1e-7 are expected (the RW12 shape
+    at dt = 200 measures 8e-8).  An exact float32 emulation of the kernels' sweeps and GEMV
+    on the RW12 m = 0 chains agrees with FP64 sweeps to 1e-11, so the level comes from the
+    conditioning, not from a lost term.  FP32 transforms put about 2e-5 into the same
+    action."""
+    from paper_2508_16635_gb300 import RotatingShell
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=71, amp=1e-2)
+    u = si.random_vector(L, Ms, Nr, seed=72)
+    J = s.real_index("T", Ms, Ms, 1, 1)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
+    assert gpu.tuning()["chain_df"] in (2, 4)   # the default of a mixed context
+    t = gpu.tuning()
+    gpu.set_tuning(dict(t, chain_df=0))
+    X = torch.tensor(x, device="cuda")
+    ref_j = gpu.apply_jacobian(X, 0.4, J, torch.tensor(u, device="cuda"), 200.0).cpu().numpy()
+    ref_s = gpu.step(X.clone(), 0.4, 1e-3).cpu().numpy()
+    ran = 0
+    for ns in (2, 4):
+        for cs in (16, 8, 4, 2):
+            try:
+                gpu.set_tuning(dict(t, chain_df=ns, chain_df_cluster=cs))
+            except Exception:
+                continue
+            ran += 1
+            got_j = gpu.apply_jacobian(X, 0.4, J, torch.tensor(u, device="cuda"), 200.0).cpu().numpy()
+            got_s = gpu.step(X.clone(), 0.4, 1e-3).cpu().numpy()
+            ej = _rel_ef(s, got_j, ref_j)
+            es = _rel_ef(s, got_s, ref_s)
+            assert ej < 1e-6 and es < 1e-6, (ns, cs, ej, es)
+            assert ej > 0.0   # the double-float kernels did run
+            # the temperature solve is not part of the chains: unchanged
+            assert np.array_equal(s.to_complex(got_j)[2], s.to_complex(ref_j)[2])
+    assert ran >= 2
+    gpu.close()
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES)
+def test_double_float_chain_solve_against_the_oracle(torch, name, L, Ms, Nr, Ek, Ra):
+    """The mixed Jacobian action with the double-float chain solve against the FP64 oracle, at
+    the mixed-path bound (the FP32 transforms dominate): 5e-5 relative per field."""
+    from paper_2508_16635_gb300 import RotatingShell
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=73, amp=1e-2)
+    u = si.random_vector(L, Ms, Nr, seed=74)
+    J = s.real_index("T", Ms, Ms, 1, 1)
+    want = s.jvp(x, 0.4, J, u, 200.0)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
+    assert gpu.tuning()["chain_df"] in (2, 4)
+    got = gpu.apply_jacobian(torch.tensor(x, device="cuda"), 0.4, J,
+                             torch.tensor(u, device="cuda"), 200.0).cpu().numpy()
+    errs = _rel_fields(s, got, want)
+    assert max(errs) < 5e-5, errs
+    gpu.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_krylov_split_basis_newton_matches_fp64_basis(torch, precision):
+    """GMRES with the double-float copy of the Krylov basis (krylov_split = 1, the default)
+    against the FP64 passes (krylov_split = 0) on the RW4 solve: both converge to 1e-11 and
+    reach the same wave (state and drift within 1e-10 relative)."""
+    from paper_2508_16635_gb300 import RotatingShell
+    L, Ms, Nr, Ek, Ra = 23, 4, 20, 1e-3, 120.0
+    s = Shell(L, Ms, Nr, Ek, Ra)
+    U0, C0, J = _rw_initial_guess(s, 4)
+    out = {}
+    for split in (1, 0):
+        gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision=precision)
+        assert gpu.tuning()["krylov_split"] == 1
+        gpu.set_tuning(dict(gpu.tuning(), krylov_split=split))
+        U = torch.tensor(U0, device="cuda")
+        C, rep, st = gpu.newton_rw(U, C0, J, tol=1e-11, max_newton=14, kmax=120, gmres_tol=1e-10)
+        assert st == 0, rep
+        out[split] = (U.cpu().numpy(), C, rep)
+        gpu.close()
+    (U1, C1, r1), (U0_, C0_, r0) = out[1], out[0]
+    assert _rel(U1, U0_) < 1e-10
+    assert abs(C1 - C0_) < 1e-10 * abs(C0_)
+    assert abs(r1["iterations"] - r0["iterations"]) <= 1
