@@ -756,6 +756,19 @@ cudaError_t launch_chain_df(rsc_ctx* ctx, const DevFactor* f, double* out, bool 
   }
 }
 
+void launch_gemv_df(rsc_ctx* ctx, const DevFactor* f, double* out) {
+  const Dims& d = ctx->d;
+  const size_t sm = (size_t)d.Nr * sizeof(float4);
+  double2* o = reinterpret_cast<double2*>(out);
+  switch (chain_maxq(d.Nr)) {
+    case 2: k_block_gemv_df<2><<<2 * d.P, 256, sm, ctx->s>>>(ctx->geom(), f->chain_off, f->Gs, ctx->rhs, o); break;
+    case 4: k_block_gemv_df<4><<<2 * d.P, 256, sm, ctx->s>>>(ctx->geom(), f->chain_off, f->Gs, ctx->rhs, o); break;
+    case 8: k_block_gemv_df<8><<<2 * d.P, 256, sm, ctx->s>>>(ctx->geom(), f->chain_off, f->Gs, ctx->rhs, o); break;
+    case 12: k_block_gemv_df<12><<<2 * d.P, 256, sm, ctx->s>>>(ctx->geom(), f->chain_off, f->Gs, ctx->rhs, o); break;
+    default: k_block_gemv_df<16><<<2 * d.P, 256, sm, ctx->s>>>(ctx->geom(), f->chain_off, f->Gs, ctx->rhs, o); break;
+  }
+}
+
 // df: the double-float GEMV and sweeps (mixed path, when the context has double-float tables
 // and chain_df is on); otherwise the FP64 kernels.
 rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = false) {
@@ -782,8 +795,7 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = 
     KSpan sp(ctx, RSC_K_CHAIN, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
     if (df)
-      k_block_gemv_df<<<2 * d.P, 256, (size_t)d.Nr * sizeof(float4), ctx->s>>>(
-          ctx->geom(), f->chain_off, f->Gs, ctx->rhs, reinterpret_cast<double2*>(out));
+      launch_gemv_df(ctx, f, out);
     else
       k_block_gemv<<<2 * d.P, 256, (size_t)d.Nr * sizeof(double2), ctx->s>>>(
           ctx->geom(), f->chain_off, f->G, ctx->rhs, reinterpret_cast<double2*>(out));

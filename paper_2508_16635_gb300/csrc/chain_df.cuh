@@ -56,42 +56,6 @@ __device__ __forceinline__ void cd_reduce8(dfl& re, dfl& im) {
   }
 }
 
-// g = G b per diagonal block; the layout and grid of k_block_gemv (grid = 2 P,
-// block = 256, 8 lanes per row).  Dynamic shared memory: Nr float4.
-__global__ void __launch_bounds__(256) k_block_gemv_df(DevGeom g, const long* __restrict__ chain_off,
-                                                       const float4* __restrict__ G,
-                                                       const double2* __restrict__ rhs,
-                                                       double2* __restrict__ out) {
-  extern __shared__ float4 svf[];
-  const int Nr = g.Nr, P = g.P;
-  const int p = blockIdx.x >> 1, fld = blockIdx.x & 1;
-  const int m = g.pair_m[p], a = m / g.Ms, i = g.pair_l[p] - m;
-  const int cls = (fld == 0) ? (i & 1) : 1 - (i & 1);
-  const float4* Gi = G + (chain_off[2 * a + cls] + i) * (long)Nr * Nr;
-  const long row0 = ((long)fld * P + p) * Nr;
-  for (int k = threadIdx.x; k < Nr; k += blockDim.x) svf[k] = cd_split(rhs[row0 + k]);
-  __syncthreads();
-  const int s8 = threadIdx.x & 7;
-  const int rows_per_pass = blockDim.x >> 3;
-  const bool real_op = (m == 0);
-  for (int r = threadIdx.x >> 3; r < Nr + ((rows_per_pass - Nr % rows_per_pass) % rows_per_pass);
-       r += rows_per_pass) {
-    dfl re0 = dfl_zero(), im0 = dfl_zero(), re1 = dfl_zero(), im1 = dfl_zero();
-    if (r < Nr) {
-      const float4* Gr = Gi + (long)r * Nr;
-      int k = s8;
-      for (; k + 8 < Nr; k += 16) {
-        cd_cmac(re0, im0, Gr[k], svf[k], real_op);
-        cd_cmac(re1, im1, Gr[k + 8], svf[k + 8], real_op);
-      }
-      if (k < Nr) cd_cmac(re0, im0, Gr[k], svf[k], real_op);
-    }
-    dfl re = dfl_add(re0, re1), im = dfl_add(im0, im1);
-    cd_reduce8(re, im);
-    if (r < Nr && s8 == 0) out[row0 + r] = make_double2(dfl_to_double(re), dfl_to_double(im));
-  }
-}
-
 __device__ __forceinline__ void cd_send(uint32_t raddr, uint32_t rbar, float4 v) {
   asm volatile(
       "st.async.weak.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::
@@ -132,6 +96,47 @@ __device__ __forceinline__ void cd_load(const float4* __restrict__ M, int r, int
   }
 }
 
+// g = G b per diagonal block; the layout and grid of k_block_gemv (grid = 2 P,
+// block = 256, 8 lanes per row, Q >= ceil(Nr / 8) columns per lane, all loaded before the
+// Dot2 steps).  Dynamic shared memory: Nr float4.
+template <int Q>
+__global__ void __launch_bounds__(256) k_block_gemv_df(DevGeom g, const long* __restrict__ chain_off,
+                                                       const float4* __restrict__ G,
+                                                       const double2* __restrict__ rhs,
+                                                       double2* __restrict__ out) {
+  extern __shared__ float4 svf[];
+  const int Nr = g.Nr, P = g.P;
+  const int p = blockIdx.x >> 1, fld = blockIdx.x & 1;
+  const int m = g.pair_m[p], a = m / g.Ms, i = g.pair_l[p] - m;
+  const int cls = (fld == 0) ? (i & 1) : 1 - (i & 1);
+  const float4* Gi = G + (chain_off[2 * a + cls] + i) * (long)Nr * Nr;
+  const long row0 = ((long)fld * P + p) * Nr;
+  for (int k = threadIdx.x; k < Nr; k += blockDim.x) svf[k] = cd_split(rhs[row0 + k]);
+  __syncthreads();
+  const int s8 = threadIdx.x & 7;
+  const int rows_per_pass = blockDim.x >> 3;
+  const bool real_op = (m == 0);
+  for (int r = threadIdx.x >> 3; r < Nr + ((rows_per_pass - Nr % rows_per_pass) % rows_per_pass);
+       r += rows_per_pass) {
+    float4 a[Q];
+    cd_load<Q>(Gi, r, s8, 0, Nr, r < Nr, a);
+    dfl re0 = dfl_zero(), im0 = dfl_zero(), re1 = dfl_zero(), im1 = dfl_zero();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int k = s8 + 8 * q;
+      if (k < Nr) {
+        if (q & 1)
+          cd_cmac(re1, im1, a[q], svf[k], real_op);
+        else
+          cd_cmac(re0, im0, a[q], svf[k], real_op);
+      }
+    }
+    dfl re = dfl_add(re0, re1), im = dfl_add(im0, im1);
+    cd_reduce8(re, im);
+    if (r < Nr && s8 == 0) out[row0 + r] = make_double2(dfl_to_double(re), dfl_to_double(im));
+  }
+}
+
 // Row sum of this lane's row over all NS column parts (the h = 0 warp gathers the others'
 // partial sums from shared memory).
 template <int NS>
@@ -150,6 +155,15 @@ __device__ __forceinline__ float4 cd_sub(double2 v, dfl re, dfl im) {
   const dfl b = dfl_norm(dfl_add(dfl_from_double(v.y), dfl_neg(im)));
   return make_float4(a.s, b.s, a.c, b.c);
 }
+
+// Blocks prefetched ahead of the one being swept (a shift register of PD x QH float4 per
+// lane).  One is enough: deeper prefetch (4 blocks) measured slower on GB300 (28.9 -> 30.8
+// ms per Newton iteration at L = 127, N_r = 64, and fewer co-resident CTAs), so a block
+// step is bound by the cluster exchange, not by the HBM round trip of its rows.
+template <int QH>
+struct CdDepth {
+  static constexpr int PD = 1;
+};
 
 // Shared memory: v[2][Nr], part[NS-1][RPC], hist[steps][RPC] (float4), two mbarriers: the
 // byte layout of k_chain_half_async.  grid = 2 * 2 * nm * CS (clusters of CS),
@@ -182,24 +196,35 @@ __global__ void k_chain_half_df(DevGeom g, const long* __restrict__ chain_off,
   }
   for (int k = threadIdx.x; k < Nr; k += blockDim.x)
     v[k] = has ? cd_split(out[ci.row(first) + k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 mc[QH], mn[QH];
-  double2 gn = {0, 0};
-  if (count > 0) {
-    cd_load<QH>(H + (ci.boff + first + step) * ci.blk, c.r, c.s, c.q0, Nr, c.active, mn);
-    if (c.active) gn = out[ci.row(first + step) + c.r];
+  constexpr int PD = CdDepth<QH>::PD;
+  float4 mc[QH], mb[PD][QH];   // mb[q]: rows of block t + q (t the next step)
+  double2 gb[PD];
+#pragma unroll
+  for (int q = 0; q < PD; ++q) {
+    gb[q] = make_double2(0, 0);
+    if (q + 1 <= count) {
+      cd_load<QH>(H + (ci.boff + first + (q + 1) * step) * ci.blk, c.r, c.s, c.q0, Nr, c.active, mb[q]);
+      if (c.active) gb[q] = out[ci.row(first + (q + 1) * step) + c.r];
+    }
   }
   cluster.sync();   // barriers initialised and v[0] loaded everywhere before any st.async
   bool ok = true;
   for (int t = 1; t <= count; ++t) {
-    const int i = first + t * step;
     const int b = t & 1;
     if (threadIdx.x == 0) ca_expect(bar0 + 8 * b, (uint32_t)Nr * 16u);
 #pragma unroll
-    for (int q = 0; q < QH; ++q) mc[q] = mn[q];
-    const double2 gc = gn;
-    if (t < count) {
-      cd_load<QH>(H + (ci.boff + i + step) * ci.blk, c.r, c.s, c.q0, Nr, c.active, mn);
-      if (c.active) gn = out[ci.row(i + step) + c.r];
+    for (int q = 0; q < QH; ++q) mc[q] = mb[0][q];
+    const double2 gc = gb[0];
+#pragma unroll
+    for (int d = 0; d + 1 < PD; ++d) {
+#pragma unroll
+      for (int q = 0; q < QH; ++q) mb[d][q] = mb[d + 1][q];
+      gb[d] = gb[d + 1];
+    }
+    if (t + PD <= count) {
+      const int ip = first + (t + PD) * step;
+      cd_load<QH>(H + (ci.boff + ip) * ci.blk, c.r, c.s, c.q0, Nr, c.active, mb[PD - 1]);
+      if (c.active) gb[PD - 1] = out[ci.row(ip) + c.r];
     }
     dfl re, im;
     cd_dot<QH>(mc, v + (b ^ 1) * Nr, c.s, c.q0, Nr, real_op, re, im);
@@ -267,7 +292,9 @@ __global__ void k_chain_out_df(DevGeom g, const long* __restrict__ chain_off,
     zdn[k] = cd_split(mc0[Nr + k]);
   }
   __syncthreads();
-  float4 mc[QH], mn[QH];
+  constexpr int PD = CdDepth<QH>::PD;
+  float4 mc[QH], mb[PD][QH];   // mb[q]: rows of block km + (t + q) step (t the next step)
+  double2 yb[PD];
   // middle block: x_k = g_k - H_k y_{k-1} - W_k z_{k+1}
   dfl are = dfl_zero(), aim = dfl_zero();
   if (km > 0) {
@@ -286,10 +313,13 @@ __global__ void k_chain_out_df(DevGeom g, const long* __restrict__ chain_off,
   }
   const int step = ci.dir == 0 ? -1 : 1;
   const int count = ci.dir == 0 ? km : nb - 1 - km;
-  double2 yn = {0, 0};
-  if (count > 0) {
-    cd_load<QH>(W + (ci.boff + km + step) * ci.blk, c.r, c.s, c.q0, Nr, c.active, mn);
-    if (c.active) yn = out[ci.row(km + step) + c.r];
+#pragma unroll
+  for (int q = 0; q < PD; ++q) {
+    yb[q] = make_double2(0, 0);
+    if (q + 1 <= count) {
+      cd_load<QH>(W + (ci.boff + km + (q + 1) * step) * ci.blk, c.r, c.s, c.q0, Nr, c.active, mb[q]);
+      if (c.active) yb[q] = out[ci.row(km + (q + 1) * step) + c.r];
+    }
   }
   if (c.h > 0 && c.s == 0 && c.active)
     part[(c.h - 1) * c.RPC + c.lr] = make_float4(are.s, aim.s, are.c, aim.c);
@@ -307,15 +337,21 @@ __global__ void k_chain_out_df(DevGeom g, const long* __restrict__ chain_off,
   if (!ca_wait(bar0, 0u)) ok = false;
   // outward: top i = km-1 .. 0 with W_i x_{i+1}; bottom i = km+1 .. nb-1 with W_i x_{i-1}
   for (int t = 1; t <= count; ++t) {
-    const int i = km + t * step;
     const int b = t & 1;
     if (threadIdx.x == 0) ca_expect(bar0 + 8 * b, (uint32_t)Nr * 16u);
 #pragma unroll
-    for (int q = 0; q < QH; ++q) mc[q] = mn[q];
-    const double2 yc = yn;
-    if (t < count) {
-      cd_load<QH>(W + (ci.boff + i + step) * ci.blk, c.r, c.s, c.q0, Nr, c.active, mn);
-      if (c.active) yn = out[ci.row(i + step) + c.r];
+    for (int q = 0; q < QH; ++q) mc[q] = mb[0][q];
+    const double2 yc = yb[0];
+#pragma unroll
+    for (int d = 0; d + 1 < PD; ++d) {
+#pragma unroll
+      for (int q = 0; q < QH; ++q) mb[d][q] = mb[d + 1][q];
+      yb[d] = yb[d + 1];
+    }
+    if (t + PD <= count) {
+      const int ip = km + (t + PD) * step;
+      cd_load<QH>(W + (ci.boff + ip) * ci.blk, c.r, c.s, c.q0, Nr, c.active, mb[PD - 1]);
+      if (c.active) yb[PD - 1] = out[ci.row(ip) + c.r];
     }
     dfl re, im;
     cd_dot<QH>(mc, v + (b ^ 1) * Nr, c.s, c.q0, Nr, real_op, re, im);

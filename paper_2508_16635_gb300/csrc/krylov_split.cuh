@@ -20,6 +20,11 @@
 
 namespace rsc {
 
+// Warm L2 with the line of p (a hint: no register, no wait; p must lie inside the basis).
+__device__ __forceinline__ void ks_prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // out = s * in and outs = split48(out); s = 1 / sqrt(nrm2[0]) when nrm2 is given (1 when
 // nrm2[0] <= 0, a breakdown the host detects), else the argument.  in may equal out.
 __global__ void k_scale_split(const double* in, double* out, float2* __restrict__ outs, long n,
@@ -127,6 +132,10 @@ __global__ void __launch_bounds__(256) k_axpy_norm_s(const float2* __restrict__ 
 #pragma unroll
       for (int u = 0; u < 8; ++u)
         v[u] = reinterpret_cast<const float4*>(Vs + (long)(j + u) * ld)[i2];
+      // the next group's lines, while this group is summed
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j + 8 + u < nv) ks_prefetch_l2(reinterpret_cast<const float4*>(Vs + (long)(j + 8 + u) * ld) + i2);
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
         const float2 c0 = hs[j + u], c1 = hs[j + u + 1];
