@@ -220,8 +220,9 @@ FP64_KERNELS = {"radial_eval", "rhs_assemble", "chain_gemv", "chain_sweep", "tem
 NCU_TRAFFIC_MB = {
     # k_chain_half_async: 95.3 + 2.9 MB; k_chain_out_async: 101.1 + 3.3 MB (mean per launch)
     ("chain_sweep", "fp64"): 101.3,
-    # the double-float sweeps: 95.3 + 3.0 and 101.1 + 3.2 MB per launch were captured on the
-    # two-warp variant (chain_df = 2); the tuner now also picks four warps, so no figure here
+    # k_chain_half_df<2, 4>: 95.3 + 3.3 MB; k_chain_out_df<2, 4>: 101.1 + 3.3 MB (the two-warp
+    # variant reads the same: 95.3 + 3.0 and 101.1 + 3.2 MB)
+    ("chain_sweep", "df"): 101.5,
 }
 
 

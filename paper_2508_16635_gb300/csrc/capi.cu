@@ -1301,7 +1301,7 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
       {
         KSpan sp(ctx, RSC_K_DOTS, 8.0 * n * (k + 3), 4.0 * n * (k + 1));
         if (split)
-          k_dots_pair_s<<<dim3(nchunk, (k + 1 + 15) / 16), 256, 0, ctx->s>>>(
+          k_dots_pair_s<<<dim3(nchunk, (k + 1 + 15) / 16), 512, 0, ctx->s>>>(
               Vs, ld, k + 1, w, Vs + (long)k * ld, ctx->partial);
         else
           k_dots_pair<<<dim3(nchunk, (k + 1 + 15) / 16), 256, 0, ctx->s>>>(V, ld, k + 1, w, vk,

@@ -53,9 +53,10 @@ __global__ void k_scale_split(const double* in, double* out, float2* __restrict_
 // First MGS pass on the split basis: partial[j * nchunk + c] = Vs_j . w and
 // partial[(nv + j) * nchunk + c] = Vs_j . q over chunk c (1024 elements).  w is FP64 (the
 // fresh Jacobian action, split while staging), q = Vs_k already split.
-// grid = (ld / 1024, ceil(nv / 16)), block = 256: warp u streams vectors 16 g + u and
-// 16 g + 8 + u (16 float4 loads per lane in flight).
-__global__ void __launch_bounds__(256) k_dots_pair_s(const float2* __restrict__ Vs, long ld,
+// grid = (ld / 1024, ceil(nv / 16)), block = 512: warp u streams vector 16 g + u over the
+// chunk, its 16 float4 loads per lane issued together (one vector per warp, so no warp waits
+// out the load latency twice).
+__global__ void __launch_bounds__(512) k_dots_pair_s(const float2* __restrict__ Vs, long ld,
                                                      int nv, const double* __restrict__ w,
                                                      const float2* __restrict__ qs,
                                                      double* __restrict__ partial) {
@@ -75,33 +76,30 @@ __global__ void __launch_bounds__(256) k_dots_pair_s(const float2* __restrict__ 
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunk = gridDim.x;
-#pragma unroll 1
-  for (int r = 0; r < 2; ++r) {
-    const int j = blockIdx.y * 16 + warp + 8 * r;
-    if (j >= nv) break;
-    const float4* v4 = reinterpret_cast<const float4*>(Vs + (long)j * ld) + b2 + lane;
-    float4 vv[PER];
+  const int j = blockIdx.y * 16 + warp;
+  if (j >= nv) return;
+  const float4* v4 = reinterpret_cast<const float4*>(Vs + (long)j * ld) + b2 + lane;
+  float4 vv[PER];
 #pragma unroll
-    for (int u = 0; u < PER; ++u) vv[u] = __ldcs(v4 + u * 32);
-    dfl a0 = dfl_zero(), a1 = dfl_zero(), b0 = dfl_zero(), b1 = dfl_zero();
+  for (int u = 0; u < PER; ++u) vv[u] = __ldcs(v4 + u * 32);
+  dfl a0 = dfl_zero(), a1 = dfl_zero(), b0 = dfl_zero(), b1 = dfl_zero();
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const float4 x = ws[u * 32 + lane], y = qsh[u * 32 + lane];
-      dfl_fma(a0, vv[u].x, vv[u].y, x.x, x.y);
-      dfl_fma(a1, vv[u].z, vv[u].w, x.z, x.w);
-      dfl_fma(b0, vv[u].x, vv[u].y, y.x, y.y);
-      dfl_fma(b1, vv[u].z, vv[u].w, y.z, y.w);
-    }
-    dfl a = dfl_add(a0, a1), b = dfl_add(b0, b1);
+  for (int u = 0; u < PER; ++u) {
+    const float4 x = ws[u * 32 + lane], y = qsh[u * 32 + lane];
+    dfl_fma(a0, vv[u].x, vv[u].y, x.x, x.y);
+    dfl_fma(a1, vv[u].z, vv[u].w, x.z, x.w);
+    dfl_fma(b0, vv[u].x, vv[u].y, y.x, y.y);
+    dfl_fma(b1, vv[u].z, vv[u].w, y.z, y.w);
+  }
+  dfl a = dfl_add(a0, a1), b = dfl_add(b0, b1);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a = dfl_add(a, dfl_shfl_xor(a, o));
-      b = dfl_add(b, dfl_shfl_xor(b, o));
-    }
-    if (lane == 0) {
-      partial[(long)j * nchunk + blockIdx.x] = dfl_to_double(a);
-      partial[(long)(nv + j) * nchunk + blockIdx.x] = dfl_to_double(b);
-    }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = dfl_add(a, dfl_shfl_xor(a, o));
+    b = dfl_add(b, dfl_shfl_xor(b, o));
+  }
+  if (lane == 0) {
+    partial[(long)j * nchunk + blockIdx.x] = dfl_to_double(a);
+    partial[(long)(nv + j) * nchunk + blockIdx.x] = dfl_to_double(b);
   }
 }
 
