@@ -75,6 +75,8 @@ struct rsc_ctx {
   // workspace (sized for FP64; the FP32 path uses the front part)
   void *SR = nullptr, *FC = nullptr, *FCU = nullptr, *FA = nullptr, *AR = nullptr;
   void* AR0 = nullptr;   // analysed products of x^n during a second-order step
+  void* UG = nullptr;    // grid values of the cached base state, [9][Nd][nlat][nphi]
+  int ug_prec = 0;       // precision UG holds for the current FCU: 0 none, 1 FP64, 2 FP32
   double2* rhs = nullptr;
   double2* mid = nullptr;   // chain sweep staging, [2 nm][3][Nr]
   double* xtmp = nullptr;
@@ -565,17 +567,22 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
   const int LPW = ctx->lpw[sizeof(R) == 4 ? 1 : 0];
   dim3 grid(d.Nd, (d.nlat + WPB * LPW - 1) / (WPB * LPW));
   const double npts = (double)d.Nd * d.nlat * d.nphi;
+  // Jacobian actions read the base state's grid values (k_base_grid) when they are cached
+  const bool ug = lin && ctx->ug_prec == (sizeof(R) == 4 ? 2 : 1);
+  const int nft = ug ? 9 : NF;   // fields transformed
   {
-  KSpan sp(ctx, RSC_K_PRODUCTS, (double)(NF + 4) * d.Nd * K1 * d.nlat * sizeof(V),
-           npts * (4.0 * NF * d.K + (lin ? 60.0 : 30.0) + 16.0 * K1));
+  KSpan sp(ctx, RSC_K_PRODUCTS,
+           (double)(nft + 4) * d.Nd * K1 * d.nlat * sizeof(V) + (ug ? 9.0 * npts * sizeof(R) : 0.0),
+           npts * (4.0 * nft * d.K + (lin ? 60.0 : 30.0) + 16.0 * K1));
   if (lin)
     k_products<R, true><<<grid, 32 * WPB, smem, ctx->s>>>(
         g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC),
-        reinterpret_cast<const V*>(ctx->FCU), reinterpret_cast<V*>(ctx->FA), LPW);
+        reinterpret_cast<const V*>(ctx->FCU), reinterpret_cast<V*>(ctx->FA), LPW,
+        ug ? reinterpret_cast<const R*>(ctx->UG) : nullptr);
   else
     k_products<R, false><<<grid, 32 * WPB, smem, ctx->s>>>(
         g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC), nullptr,
-        reinterpret_cast<V*>(ctx->FA), LPW);
+        reinterpret_cast<V*>(ctx->FA), LPW, nullptr);
   CK(cudaGetLastError());
   }
   {
@@ -1061,9 +1068,33 @@ rsc_status step_any(rsc_ctx* ctx, double* U, double C, double dt, bool fp32) {
   return fp32 ? do_step<float>(ctx, U, C, dt) : do_step<double>(ctx, U, C, dt);
 }
 
-// Base-state grid coefficients for Jacobian actions.
+// The base state's grid values UG from FCU (once per base state).
+template <typename R>
+rsc_status base_grid(rsc_ctx* ctx) {
+  using V = typename C2<R>::T;
+  const Dims& d = ctx->d;
+  const int K1 = d.K + 1, WPB = 8;
+  KSpan sp(ctx, RSC_K_PRODUCTS,
+           9.0 * d.Nd * K1 * d.nlat * sizeof(V) + 9.0 * d.Nd * d.nlat * d.nphi * sizeof(R),
+           (double)d.Nd * d.nlat * d.nphi * 36.0 * K1);
+  k_base_grid<R><<<dim3(d.Nd, (d.nlat + WPB - 1) / WPB), 32 * WPB,
+                   (size_t)WPB * 9 * K1 * sizeof(V), ctx->s>>>(
+      ctx->geom(), leg<R>(ctx).view(), reinterpret_cast<const V*>(ctx->FCU),
+      reinterpret_cast<R*>(ctx->UG));
+  CK(cudaGetLastError());
+  ctx->ug_prec = sizeof(R) == 4 ? 2 : 1;
+  return RSC_OK;
+}
+
+// Base-state grid coefficients (and grid values) for Jacobian actions.
 rsc_status cache_base(rsc_ctx* ctx, const double* U, bool fp32) {
-  return fp32 ? stage_synth<float>(ctx, U, ctx->FCU) : stage_synth<double>(ctx, U, ctx->FCU);
+  ctx->ug_prec = 0;
+  if (fp32) {
+    CKS(stage_synth<float>(ctx, U, ctx->FCU));
+    return base_grid<float>(ctx);
+  }
+  CKS(stage_synth<double>(ctx, U, ctx->FCU));
+  return base_grid<double>(ctx);
 }
 
 // out = (B_U - I) u with the drift unknown in slot J (Sec. 3.4); base cached.
@@ -1512,7 +1543,9 @@ rsc_status tune_precision(rsc_ctx* ctx, rsc_tuning& t, cudaEvent_t e0, cudaEvent
     return st == RSC_OK ? ms / 3.0 : 1e30;
   };
   CKS(stage_synth<R>(ctx, ctx->rtmp, ctx->FC));
+  ctx->ug_prec = 0;
   CKS(stage_synth<R>(ctx, ctx->rtmp, ctx->FCU));
+  CKS(base_grid<R>(ctx));
   auto pa = [&] { return stage_products_analysis<R>(ctx, true); };
   // products: warps per block x latitudes per warp
   double best = 1e30;
@@ -1823,6 +1856,8 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = alloc(&ctx->SR, (size_t)d.P * d.Nd * 8 * c16)) != RSC_OK) return fail(st);
   if ((st = alloc(&ctx->FC, 9 * (size_t)d.Nd * K1 * d.nlat * c16)) != RSC_OK) return fail(st);
   if ((st = alloc(&ctx->FCU, 9 * (size_t)d.Nd * K1 * d.nlat * c16)) != RSC_OK) return fail(st);
+  if ((st = alloc(&ctx->UG, 9 * (size_t)d.Nd * d.nlat * d.nphi * sizeof(double))) != RSC_OK)
+    return fail(st);
   if ((st = alloc(&ctx->FA, 4 * (size_t)d.Nd * K1 * d.nlat * c16)) != RSC_OK) return fail(st);
   if ((st = alloc(&ctx->AR, (size_t)d.P * d.Nd * 4 * c16)) != RSC_OK) return fail(st);
   if ((st = alloc(&ctx->AR0, (size_t)d.P * d.Nd * 4 * c16)) != RSC_OK) return fail(st);
@@ -1859,7 +1894,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
   void* bufs[] = {(void*)ctx->d_slots, ctx->d_cslot, ctx->jvp_y, ctx->tc_tiles, ctx->tc_off, ctx->tc_kpad, ctx->d_status, ctx->d_EcT1, ctx->d_m_of, ctx->d_pstart, ctx->d_pair_l, ctx->d_pair_m, ctx->d_leg_off,
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
-                  ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->FA,
+                  ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->UG, ctx->FA,
                   ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->Vs, ctx->partial,
                   ctx->dots, ctx->AR0, ctx->ta_tiles, ctx->ta_off, ctx->cont_hist, ctx->cont_cond, ctx->amax_v, ctx->amax_i, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
   for (void* b : bufs) cudaFree(b);

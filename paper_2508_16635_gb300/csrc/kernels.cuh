@@ -269,12 +269,14 @@ __global__ void k_synth(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __
 // lane a sums its wavenumber over the nphi longitudes (twiddles stored [j][a]).
 // LIN = false: F = Ek U x omega, N = U.grad T from FC.
 // LIN = true : F = Ek (U x omega_u + u x omega_U), N = U.grad tau + u.grad T
-//              with U from FCU and u from FC.
+//              with U from FCU and u from FC; when UG is given, U's grid values are read
+//              from it (k_base_grid, once per base state) instead of transformed again.
 template <typename R, bool LIN>
 __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
                            const typename C2<R>::T* __restrict__ FC,
                            const typename C2<R>::T* __restrict__ FCU,
-                           typename C2<R>::T* __restrict__ FA, int LPW) {
+                           typename C2<R>::T* __restrict__ FA, int LPW,
+                           const R* __restrict__ UG) {
   using V = typename C2<R>::T;
   constexpr int NF = LIN ? 18 : 9;
   extern __shared__ unsigned char sh_raw[];
@@ -307,8 +309,10 @@ __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
   for (int rep = 0; rep < LPW; ++rep) {
     const int th = th0 + w + WPB * rep;
     if (th >= nlat) break;
+    const bool cached = LIN && UG != nullptr;
+    const int nfl = cached ? 9 : NF;   // fields transformed here
     __syncwarp();
-    for (int idx = lane; idx < NF * K1; idx += 32) {
+    for (int idx = lane; idx < nfl * K1; idx += 32) {
       const int a = idx % K1;
       const int f = idx / K1;
       const V* src = (f < 9) ? FC : FCU;
@@ -326,9 +330,15 @@ __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
         const R c = twc[a * nphi + j], sn = tws[a * nphi + j];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-          const V cf = cw[f * K1 + a];
-          val[f] += cf.x * c - cf.y * sn;
+          if (f < 9 || !cached) {
+            const V cf = cw[f * K1 + a];
+            val[f] += cf.x * c - cf.y * sn;
+          }
         }
+      }
+      if (cached) {
+#pragma unroll
+        for (int f = 0; f < 9; ++f) val[(f + 9) % NF] = UG[(((long)f * Nd + i) * nlat + th) * nphi + j];
       }
       R Fr, Ft, Fp, N;
       if (!LIN) {
@@ -366,6 +376,47 @@ __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
       for (int q = 0; q < 4; ++q)
         FA[(((long)q * Nd + i) * K1 + a) * nlat + th] = mk<R>(sr[q], si[q]);
     }
+  }
+}
+
+// The base state's nine grid fields UG[f][i][th][j] (f: u_r, u_th, u_ph, w_r, w_th, w_ph,
+// T_r, T_th, T_ph) from its Fourier coefficients FCU, with the inverse DFT of k_products;
+// computed once per base state so that every Jacobian action transforms only the
+// perturbation.  grid = (Nd, ceil(nlat / WPB)), block = 32 WPB (a warp per latitude),
+// dynamic shared memory WPB 9 (K+1) complex.
+template <typename R>
+__global__ void k_base_grid(DevGeom g, DevLegendre<R> T, const typename C2<R>::T* __restrict__ FCU,
+                            R* __restrict__ UG) {
+  using V = typename C2<R>::T;
+  extern __shared__ unsigned char sh_raw[];
+  const int K1 = g.K + 1, nphi = g.nphi, nlat = g.nlat, Nd = g.Nd;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  V* cw = reinterpret_cast<V*>(sh_raw) + w * 9 * K1;
+  const int i = blockIdx.x;
+  const int th = blockIdx.y * (blockDim.x >> 5) + w;
+  if (th >= nlat) return;
+  for (int idx = lane; idx < 9 * K1; idx += 32) {
+    const int a = idx % K1, f = idx / K1;
+    V v = FCU[(((long)f * Nd + i) * K1 + a) * nlat + th];
+    if (a == 0) v.y = 0;
+    cw[f * K1 + a] = v;
+  }
+  __syncwarp();
+  for (int j = lane; j < nphi; j += 32) {
+    R val[9];
+#pragma unroll
+    for (int f = 0; f < 9; ++f) val[f] = 0;
+    for (int a = 0; a < K1; ++a) {
+      const R fa = a ? (R)2 : (R)1;
+      const R c = fa * T.twc[a * nphi + j], sn = fa * T.tws[a * nphi + j];
+#pragma unroll
+      for (int f = 0; f < 9; ++f) {
+        const V cf = cw[f * K1 + a];
+        val[f] += cf.x * c - cf.y * sn;
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < 9; ++f) UG[(((long)f * Nd + i) * nlat + th) * nphi + j] = val[f];
   }
 }
 
