@@ -10,9 +10,9 @@
 // The operations use the _rn intrinsics so that the compiler never contracts a product and
 // a sum into one multiply-add (which would break the error-free transformations).
 //
-// split48 is host/device code (a host test checks it): it cuts a double into hi + lo with
-// integer operations only (conversions between double and float would run on the FP64
-// pipe).
+// Everything but the warp shuffle is host/device code, checked on the host by
+// tests/test_dfloat_split.py; split48 cuts a double into hi + lo with integer operations
+// only (conversions between double and float would run on the FP64 pipe).
 #pragma once
 
 #include <stdint.h>
@@ -58,59 +58,70 @@ RSC_HD void split48(double d, float& hi, float& lo) {
   lo = lf;
 }
 
-#if defined(__CUDACC__)
+// Correctly rounded FP32 operations that the compiler may not contract: the _rn intrinsics
+// on the device; on the host (tests) volatile stores, with an ISO C++ mode (no contraction
+// across statements) and IEEE single precision.
+#if defined(__CUDA_ARCH__)
+__device__ __forceinline__ float df_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float df_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float df_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+#else
+inline float df_add(float a, float b) { volatile float r = a + b; return r; }
+inline float df_mul(float a, float b) { volatile float r = a * b; return r; }
+inline float df_fma(float a, float b, float c) { volatile float r = __builtin_fmaf(a, b, c); return r; }
+#endif
 
 // A double-float accumulator: the value is s + c.
 struct dfl {
   float s, c;
 };
 
-__device__ __forceinline__ dfl dfl_zero() { return dfl{0.0f, 0.0f}; }
+RSC_HD dfl dfl_zero() { return dfl{0.0f, 0.0f}; }
 
 // a += (xh + xl)(yh + yl), the xl yl term (2^-48 relative) dropped.
-__device__ __forceinline__ void dfl_fma(dfl& a, float xh, float xl, float yh, float yl) {
-  const float p = __fmul_rn(xh, yh);
-  const float e = __fmaf_rn(xh, yh, -p);
-  const float t = __fadd_rn(a.s, p);
-  const float z = __fadd_rn(t, -a.s);
-  const float err = __fadd_rn(__fadd_rn(a.s, -__fadd_rn(t, -z)), __fadd_rn(p, -z));
-  const float cross = __fmaf_rn(xh, yl, __fmul_rn(xl, yh));
-  a.c = __fadd_rn(a.c, __fadd_rn(err, __fadd_rn(e, cross)));
+RSC_HD void dfl_fma(dfl& a, float xh, float xl, float yh, float yl) {
+  const float p = df_mul(xh, yh);
+  const float e = df_fma(xh, yh, -p);
+  const float t = df_add(a.s, p);
+  const float z = df_add(t, -a.s);
+  const float err = df_add(df_add(a.s, -df_add(t, -z)), df_add(p, -z));
+  const float cross = df_fma(xh, yl, df_mul(xl, yh));
+  a.c = df_add(a.c, df_add(err, df_add(e, cross)));
   a.s = t;
 }
 
 // a + b
-__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
-  const float t = __fadd_rn(a.s, b.s);
-  const float z = __fadd_rn(t, -a.s);
-  const float err = __fadd_rn(__fadd_rn(a.s, -__fadd_rn(t, -z)), __fadd_rn(b.s, -z));
-  return dfl{t, __fadd_rn(__fadd_rn(a.c, b.c), err)};
+RSC_HD dfl dfl_add(dfl a, dfl b) {
+  const float t = df_add(a.s, b.s);
+  const float z = df_add(t, -a.s);
+  const float err = df_add(df_add(a.s, -df_add(t, -z)), df_add(b.s, -z));
+  return dfl{t, df_add(df_add(a.c, b.c), err)};
 }
 
-__device__ __forceinline__ dfl dfl_neg(dfl a) { return dfl{-a.s, -a.c}; }
+RSC_HD dfl dfl_neg(dfl a) { return dfl{-a.s, -a.c}; }
 
 // (s, c) -> (s', c') with s' = fl(s + c) and s' + c' = s + c exactly (TwoSum: after a
 // cancellation |c| may exceed |s|, where the cheaper Fast2Sum would not be exact).  The
 // pair then satisfies |c'| <= ulp(s') / 2, which the products of dfl_fma rely on when they
 // drop the lo * lo term and round the cross terms.
-__device__ __forceinline__ dfl dfl_norm(dfl a) {
-  const float t = __fadd_rn(a.s, a.c);
-  const float z = __fadd_rn(t, -a.s);
-  return dfl{t, __fadd_rn(__fadd_rn(a.s, -__fadd_rn(t, -z)), __fadd_rn(a.c, -z))};
+RSC_HD dfl dfl_norm(dfl a) {
+  const float t = df_add(a.s, a.c);
+  const float z = df_add(t, -a.s);
+  return dfl{t, df_add(df_add(a.s, -df_add(t, -z)), df_add(a.c, -z))};
 }
 
-__device__ __forceinline__ dfl dfl_shfl_xor(dfl a, int o) {
-  return dfl{__shfl_xor_sync(0xffffffffu, a.s, o), __shfl_xor_sync(0xffffffffu, a.c, o)};
-}
+RSC_HD double dfl_to_double(dfl a) { return (double)a.s + (double)a.c; }
 
-__device__ __forceinline__ double dfl_to_double(dfl a) { return (double)a.s + (double)a.c; }
-
-__device__ __forceinline__ dfl dfl_from_double(double d) {
+RSC_HD dfl dfl_from_double(double d) {
   dfl a;
   split48(d, a.s, a.c);
   return a;
 }
 
+#if defined(__CUDACC__)
+__device__ __forceinline__ dfl dfl_shfl_xor(dfl a, int o) {
+  return dfl{__shfl_xor_sync(0xffffffffu, a.s, o), __shfl_xor_sync(0xffffffffu, a.c, o)};
+}
 #endif
 
 }  // namespace rsc
