@@ -21,7 +21,7 @@ the advective term follows Eq. Navier-Stokes) and -U.grad T for T.
 Boundary conditions replace rows (Sec. 3.1): e, T at r_j = r_out, r_in;
 f and df/dr at the two end points and their neighbours.
 
-Readings of the paper taken here (each listed in the design doc):
+Readings of the paper taken here (where it is silent or ambiguous):
   * collocation at Gauss-Lobatto radii, BC rows replacing the rows at the
     walls (and, for f, their neighbours);
   * radial de-aliasing: products on N_d = ceil(3 N_r/2) Gauss-Lobatto radii,
@@ -499,7 +499,7 @@ class Shell:
         x[2, self.pair_index(0, 0)] = np.linalg.solve(D, b)
         return self.to_real(x)
 
-    # ---- physical diagnostics (definitions stated in the design doc) ---------------------
+    # ---- physical diagnostics (the paper plots them without defining them) ------------
     def kinetic_energy(self, vec, nquad=None):
         """KE density (1/V) int |U|^2/2 dV (the kinetic energy of the bifurcation diagrams,
         Secs. 4-5; V = 4 pi (r_out^3 - r_in^3)/3).  The velocity of Sec. 2.1 is synthesised on

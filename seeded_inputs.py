@@ -5,7 +5,7 @@ and lays them out in the canonical state order
     [field e, f, T][pair (m, l): m = 0, Ms, ... <= L, l = m..L][k < Nr][re, im].
 Both the oracle and the CUDA library receive the same arrays.
 
-Perturbation recipe (stated in the design doc): amplitude
+Perturbation recipe: amplitude
     amp * exp(-l/8) * exp(-k/6) * N(0, 1)
 on the real and imaginary part of every allowed coefficient; imaginary parts
 of m = 0 coefficients and the absent e_00, f_00 are zero.
