@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-rw", action="store_true", help="skip the time-to-rotating-wave run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances run")
+    ap.add_argument("--chain-parts", type=int, default=1,
+                    help="parts per chain of the mixed path's double-float solve after "
+                         "autotuning (1: unpartitioned, the faster at RW12)")
     ap.add_argument("--tuning", default=None,
                     help="launch shapes as JSON (the line's `tuning`) instead of autotuning, so "
                          "that a profiled run uses the shapes of a measured one")
@@ -728,6 +731,10 @@ def run_gpu(args):
         tuning = sh.tuning()
     else:
         tuning = sh.autotune()  # launch shapes picked by timing, before any measurement
+        if args.precision == "mixed" and args.chain_parts > 1:
+            # partitioned chains for the double-float solve (factorised in the warm-up)
+            sh.set_tuning(dict(tuning, chain_parts=args.chain_parts))
+            tuning = sh.tuning()
     U0 = sh.conductive_state() + torch.tensor(
         si.perturbation(w["L"], w["Ms"], w["Nr"], seed=3000 + rank), device="cuda")
     # phase slot: Im of the T coefficient (l = m = 12, k*) with k* = argmax |Re|

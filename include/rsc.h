@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RSC_ABI_VERSION 4
+#define RSC_ABI_VERSION 5
 
 typedef struct rsc_ctx rsc_ctx;
 
@@ -341,6 +341,13 @@ typedef struct {
                               and orthogonalises in double-float arithmetic (inner
                               products within about 1e-14 of FP64); 0: FP64 passes.
                               Not changed by rsc_autotune.                             */
+  int chain_parts;         /* 1 to 4: parts per chain of the double-float solve (parts of
+                              at least 8 blocks): the parts are swept concurrently and
+                              joined through spikes and a reduced system per chain
+                              (SPIKE-type), which cuts the sweeps' sequential depth; the
+                              factorisation then also computes the spikes on the host.
+                              Changing it rebuilds the factorisations.  Not changed by
+                              rsc_autotune.                                            */
   double ms[6];            /* after rsc_autotune: best times (ms) of products +
                               analysis (mixed), FP64 synthesis, RHS (mixed), FP64 chain
                               solve, double-float chain solve (0 if none ran); zero

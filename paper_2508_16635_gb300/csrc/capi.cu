@@ -30,6 +30,7 @@ using namespace rsc;
 namespace {
 
 constexpr int kMaxKrylov = 2048;
+constexpr int kMaxChainParts = 4;   // parts per chain of the partitioned double-float solve
 
 struct DevFactor {
   double dt = std::nan("");
@@ -42,6 +43,19 @@ struct DevFactor {
   float4* Gs = nullptr;
   float4* Hs = nullptr;
   float4* Ws = nullptr;
+  // partitioned chains of the double-float solve (chain_parts > 1; HostFactor): part table,
+  // spikes, reduced inverses and their index tables, and the reduced solution z
+  int npart = 0, nz = 0, nu_max = 0;
+  long* parts = nullptr;
+  float4* Vsp = nullptr;
+  float4* Wsp = nullptr;
+  float4* red = nullptr;
+  long* red_off = nullptr;
+  int* red_nu = nullptr;
+  int* zoff = nullptr;
+  long* unk_row = nullptr;
+  int* blk_z = nullptr;
+  double2* zbuf = nullptr;
   bool valid = false;
 };
 
@@ -100,6 +114,7 @@ struct rsc_ctx {
   int chain_df = 0;       // mixed path: 2 / 4 = double-float chain solve with that many warps
                           // per row group (chain_df.cuh), 0 = the FP64 kernels
   int cluster_df = 8;     // CTAs per cluster of the double-float sweeps
+  int chain_parts = 1;    // parts per chain of the double-float solve (1: unpartitioned)
   // second stream: the temperature solve runs beside the e/f chain solve
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -270,6 +285,9 @@ void free_factor(DevFactor& f) {
   cudaFree(f.Gs);
   cudaFree(f.Hs);
   cudaFree(f.Ws);
+  void* extra[] = {f.parts, f.Vsp, f.Wsp, f.red, f.red_off, f.red_nu, f.zoff, f.unk_row, f.blk_z,
+                   f.zbuf};
+  for (void* b : extra) cudaFree(b);
   f = DevFactor();
 }
 
@@ -481,9 +499,36 @@ rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
       }
       return upload(ctx, dst, t.data(), t.size());
     };
-    CKS(split_upload(hf.G, &f.Gs));
-    CKS(split_upload(hf.H, &f.Hs));
-    CKS(split_upload(hf.W, &f.Ws));
+    if (ctx->chain_parts > 1) {
+      // the double-float solve on partitioned chains: its own factorisation
+      HostFactor hp;
+      if (build_factor(ctx->p, ctx->d, ctx->t, dt, hp, ctx->chain_parts)) {
+        ctx->err = "singular block in the partitioned implicit operator";
+        return RSC_ESINGULAR;
+      }
+      CKS(split_upload(hp.G, &f.Gs));
+      CKS(split_upload(hp.H, &f.Hs));
+      CKS(split_upload(hp.W, &f.Ws));
+      if (!hp.parts.empty() && !hp.unk_row.empty()) {
+        f.npart = (int)(hp.parts.size() / 6);
+        f.nz = (int)hp.unk_row.size();
+        for (int v : hp.red_nu) f.nu_max = std::max(f.nu_max, v);
+        CKS(split_upload(hp.V, &f.Vsp));
+        CKS(split_upload(hp.Wsp, &f.Wsp));
+        CKS(split_upload(hp.red, &f.red));
+        CKS(upload(ctx, &f.parts, hp.parts.data(), hp.parts.size()));
+        CKS(upload(ctx, &f.red_off, hp.red_off.data(), hp.red_off.size()));
+        CKS(upload(ctx, &f.red_nu, hp.red_nu.data(), hp.red_nu.size()));
+        CKS(upload(ctx, &f.zoff, hp.zoff.data(), hp.zoff.size()));
+        CKS(upload(ctx, &f.unk_row, hp.unk_row.data(), hp.unk_row.size()));
+        CKS(upload(ctx, &f.blk_z, hp.blk_z.data(), hp.blk_z.size()));
+        CK(cudaMalloc(&f.zbuf, (size_t)f.nz * ctx->d.Nr * sizeof(double2)));
+      }
+    } else {
+      CKS(split_upload(hf.G, &f.Gs));
+      CKS(split_upload(hf.H, &f.Hs));
+      CKS(split_upload(hf.W, &f.Ws));
+    }
   }
   f.dt = dt;
   f.valid = true;
@@ -723,7 +768,7 @@ cudaError_t launch_chain_df_q(rsc_ctx* ctx, const DevFactor* f, double* out, boo
   const int CS = ctx->cluster_df;
   const int RPC = (d.Nr + CS - 1) / CS;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * 2 * d.nm * CS);
+  cfg.gridDim = dim3(2 * (f->npart ? f->npart : 2 * d.nm) * CS);
   cfg.blockDim = dim3(32 * NS * ((RPC + 3) / 4));
   cfg.dynamicSmemBytes = chain_smem_async(d, CS, outward, NS);
   cfg.stream = ctx->s;
@@ -739,10 +784,12 @@ cudaError_t launch_chain_df_q(rsc_ctx* ctx, const DevFactor* f, double* out, boo
     return cudaLaunchKernelEx(&cfg, k_chain_out_df<Q / NS, NS>, ctx->geom(),
                               (const long*)f->chain_off, (const float4*)f->Hs,
                               (const float4*)f->Ws, reinterpret_cast<double2*>(out),
-                              (const double2*)ctx->mid, CS, cap, ctx->d_status);
+                              (const double2*)ctx->mid, CS, cap, ctx->d_status,
+                              (const long*)f->parts);
   return cudaLaunchKernelEx(&cfg, k_chain_half_df<Q / NS, NS>, ctx->geom(),
                             (const long*)f->chain_off, (const float4*)f->Hs,
-                            reinterpret_cast<double2*>(out), ctx->mid, CS, cap, ctx->d_status);
+                            reinterpret_cast<double2*>(out), ctx->mid, CS, cap, ctx->d_status,
+                            (const long*)f->parts);
 }
 
 template <int Q>
@@ -818,6 +865,27 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = 
     KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
     CK(df ? launch_chain_df(ctx, f, out, true) : launch_chain(ctx, f, out, true));
+  }
+  if (df && f->npart && !ctx->p.explicit_coriolis) {
+    // partitioned chains: reduced systems, then the correction of every part
+    KSpan sp(ctx, RSC_K_CHAIN, 16.0 * f->nz * f->nu_max * d.Nr * d.Nr + 4.0 * f->nz * d.Nr * 16.0 +
+                                   2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
+             8.0 * f->nz * f->nu_max * d.Nr * d.Nr + 2.0 * d.P * d.Nr * d.Nr * 8.0);
+    k_spike_reduce_df<<<dim3((f->nu_max * d.Nr + 31) / 32, 2 * d.nm), 256,
+                        (size_t)f->nu_max * d.Nr * sizeof(float4), ctx->s>>>(
+        f->unk_row, f->zoff, f->red_nu, f->red_off, f->red, reinterpret_cast<const double2*>(out),
+        f->zbuf, d.Nr);
+    CK(cudaGetLastError());
+    const size_t sm = 2 * (size_t)d.Nr * sizeof(float4);
+    double2* o = reinterpret_cast<double2*>(out);
+    switch (chain_maxq(d.Nr)) {
+      case 2: k_spike_correct_df<2><<<2 * d.P, 256, sm, ctx->s>>>(ctx->geom(), f->chain_off, f->blk_z, f->Vsp, f->Wsp, f->zbuf, o); break;
+      case 4: k_spike_correct_df<4><<<2 * d.P, 256, sm, ctx->s>>>(ctx->geom(), f->chain_off, f->blk_z, f->Vsp, f->Wsp, f->zbuf, o); break;
+      case 8: k_spike_correct_df<8><<<2 * d.P, 256, sm, ctx->s>>>(ctx->geom(), f->chain_off, f->blk_z, f->Vsp, f->Wsp, f->zbuf, o); break;
+      case 12: k_spike_correct_df<12><<<2 * d.P, 256, sm, ctx->s>>>(ctx->geom(), f->chain_off, f->blk_z, f->Vsp, f->Wsp, f->zbuf, o); break;
+      default: k_spike_correct_df<16><<<2 * d.P, 256, sm, ctx->s>>>(ctx->geom(), f->chain_off, f->blk_z, f->Vsp, f->Wsp, f->zbuf, o); break;
+    }
+    CK(cudaGetLastError());
   }
   if (fork) {
     CK(cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0));
@@ -1478,6 +1546,7 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
     return false;
   if (t.analysis_tc != 0 && t.analysis_tc != 1) return false;
   if (t.krylov_split != 0 && t.krylov_split != 1) return false;
+  if (t.chain_parts < 1 || t.chain_parts > kMaxChainParts) return false;
   if (!chain_df_ok(d, t.chain_df_cluster, t.chain_df)) return false;
   return chain_config_ok(d, t.chain_cluster, t.chain_async);
 }
@@ -1502,6 +1571,7 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
   t->chain_df = ctx->chain_df;
   t->chain_df_cluster = ctx->cluster_df;
   t->krylov_split = ctx->krylov_split;
+  t->chain_parts = ctx->chain_parts;
   for (int q = 0; q < 6; ++q) t->ms[q] = ctx->tune_ms[q];
 }
 
@@ -1520,6 +1590,12 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
   ctx->chain_df = t.chain_df;
   ctx->cluster_df = t.chain_df_cluster;
   ctx->krylov_split = t.krylov_split;
+  if (t.chain_parts != ctx->chain_parts) {
+    // another partition of the double-float solve: both factorisation slots are rebuilt
+    ctx->chain_parts = t.chain_parts;
+    cudaStreamSynchronize(ctx->s);
+    for (auto& f : ctx->fac) free_factor(f);
+  }
   if (ctx->jvp_exec) {   // the captured Jacobian action embeds the old launch shapes
     cudaGraphExecDestroy(ctx->jvp_exec);
     ctx->jvp_exec = nullptr;
@@ -1862,7 +1938,8 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = alloc(&ctx->AR, (size_t)d.P * d.Nd * 4 * c16)) != RSC_OK) return fail(st);
   if ((st = alloc(&ctx->AR0, (size_t)d.P * d.Nd * 4 * c16)) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->rhs, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
-  if ((st = alloc((void**)&ctx->mid, (size_t)2 * d.nm * 3 * d.Nr * c16)) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->mid, (size_t)2 * d.nm * kMaxChainParts * 3 * d.Nr * c16)) != RSC_OK)
+    return fail(st);
   if ((st = alloc((void**)&ctx->d_slots, 2 * sizeof(double*))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->d_cslot, sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->jvp_y, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);

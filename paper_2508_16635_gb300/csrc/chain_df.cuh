@@ -156,6 +156,27 @@ __device__ __forceinline__ float4 cd_sub(double2 v, dfl re, dfl im) {
   return make_float4(a.s, b.s, a.c, b.c);
 }
 
+// Geometry of part c of a partitioned chain (cluster pair blockIdx.x / CS / 2), from the
+// part table [p0, cls, nb, boff, m, chain] per part: the sweeps treat a part as a chain.
+__device__ __forceinline__ ChainInfo chain_info_part(const DevGeom& g, const long* __restrict__ parts,
+                                                     int CS) {
+  ChainInfo ci;
+  const int cl = blockIdx.x / CS;
+  ci.c = cl >> 1;
+  ci.dir = cl & 1;
+  const long* q = parts + (long)ci.c * 6;
+  ci.p0 = (int)q[0];
+  ci.cls = (int)q[1];
+  ci.nb = (int)q[2];
+  ci.boff = q[3];
+  ci.m = (int)q[4];
+  ci.km = (ci.nb - 1) / 2;
+  ci.P = g.P;
+  ci.Nr = g.Nr;
+  ci.blk = (long)g.Nr * g.Nr;
+  return ci;
+}
+
 // Blocks prefetched ahead of the one being swept (a shift register of PD x QH float4 per
 // lane).  One is enough: deeper prefetch (4 blocks) measured slower on GB300 (28.9 -> 30.8
 // ms per Newton iteration at L = 127, N_r = 64, and fewer co-resident CTAs), so a block
@@ -172,11 +193,11 @@ template <int QH, int NS>
 __global__ void k_chain_half_df(DevGeom g, const long* __restrict__ chain_off,
                                 const float4* __restrict__ H, double2* __restrict__ out,
                                 double2* __restrict__ mid, int CS, int steps_cap,
-                                int* __restrict__ status) {
+                                int* __restrict__ status, const long* __restrict__ parts) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ float4 cd_sh[];
-  const ChainInfo ci = chain_info(g, chain_off, CS);
+  const ChainInfo ci = parts ? chain_info_part(g, parts, CS) : chain_info(g, chain_off, CS);
   const int Nr = ci.Nr;
   const CaLane c = ca_lane<QH, NS>(Nr, CS, (int)cluster.block_rank());
   float4* v = cd_sh;                        // [2][Nr]
@@ -265,11 +286,12 @@ template <int QH, int NS>
 __global__ void k_chain_out_df(DevGeom g, const long* __restrict__ chain_off,
                                const float4* __restrict__ H, const float4* __restrict__ W,
                                double2* __restrict__ out, const double2* __restrict__ mid,
-                               int CS, int steps_cap, int* __restrict__ status) {
+                               int CS, int steps_cap, int* __restrict__ status,
+                               const long* __restrict__ parts) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ float4 cd_sh[];
-  const ChainInfo ci = chain_info(g, chain_off, CS);
+  const ChainInfo ci = parts ? chain_info_part(g, parts, CS) : chain_info(g, chain_off, CS);
   const int Nr = ci.Nr;
   const CaLane c = ca_lane<QH, NS>(Nr, CS, (int)cluster.block_rank());
   float4* v = cd_sh;
@@ -374,6 +396,93 @@ __global__ void k_chain_out_df(DevGeom g, const long* __restrict__ chain_off,
     if (r < Nr) out[ci.row(km + t * step) + r] = cd_join(hist[idx]);
   }
   cluster.sync();
+}
+
+// Reduced system of partitioned chains: z = (I + K)^-1 xl_z per chain, xl_z the part-local
+// solutions at the blocks that couple parts (unk_row: their element offsets in a state).
+// grid = (ceil(nu_max Nr / 32), chains), block = 256 (8 lanes per row of the inverse),
+// dynamic shared memory nu_max Nr float4.
+__global__ void __launch_bounds__(256) k_spike_reduce_df(const long* __restrict__ unk_row,
+                                                         const int* __restrict__ zoff,
+                                                         const int* __restrict__ red_nu,
+                                                         const long* __restrict__ red_off,
+                                                         const float4* __restrict__ red,
+                                                         const double2* __restrict__ out,
+                                                         double2* __restrict__ zbuf, int Nr) {
+  extern __shared__ float4 rv[];
+  const int c = blockIdx.y;
+  const int n = red_nu[c] * Nr;
+  if (blockIdx.x * 32 >= n) return;   // the whole block: no unknown rows here
+  const int z0 = zoff[c];
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x)
+    rv[idx] = cd_split(out[unk_row[z0 + idx / Nr] + idx % Nr]);
+  __syncthreads();
+  const int s8 = threadIdx.x & 7;
+  const int r = blockIdx.x * 32 + (threadIdx.x >> 3);
+  dfl re0 = dfl_zero(), im0 = dfl_zero(), re1 = dfl_zero(), im1 = dfl_zero();
+  if (r < n) {
+    const float4* Mr = red + red_off[c] + (long)r * n;
+    int k = s8;
+    for (; k + 8 < n; k += 16) {
+      cd_cmac(re0, im0, Mr[k], rv[k], false);
+      cd_cmac(re1, im1, Mr[k + 8], rv[k + 8], false);
+    }
+    if (k < n) cd_cmac(re0, im0, Mr[k], rv[k], false);
+  }
+  dfl re = dfl_add(re0, re1), im = dfl_add(im0, im1);
+  cd_reduce8(re, im);
+  if (r < n && s8 == 0)
+    zbuf[(long)(z0 + r / Nr) * Nr + r % Nr] = make_double2(dfl_to_double(re), dfl_to_double(im));
+}
+
+// Correction of partitioned chains: x_i = xl_i - V_i z(T) - Wsp_i z(B) in place, for the
+// blocks of the parts that have a next (T) or a previous (B) part (blk_z: their z blocks,
+// -1 for none).  The layout and grid of k_block_gemv_df (grid = 2 P, block = 256, Q >=
+// ceil(Nr / 8) columns per lane); dynamic shared memory 2 Nr float4.
+template <int Q>
+__global__ void __launch_bounds__(256) k_spike_correct_df(DevGeom g, const long* __restrict__ chain_off,
+                                                          const int* __restrict__ blk_z,
+                                                          const float4* __restrict__ V,
+                                                          const float4* __restrict__ Wsp,
+                                                          const double2* __restrict__ zbuf,
+                                                          double2* __restrict__ out) {
+  extern __shared__ float4 zs[];
+  const int Nr = g.Nr, P = g.P;
+  const int p = blockIdx.x >> 1, fld = blockIdx.x & 1;
+  const int m = g.pair_m[p], a = m / g.Ms, i = g.pair_l[p] - m;
+  const int cls = (fld == 0) ? (i & 1) : 1 - (i & 1);
+  const long gb = chain_off[2 * a + cls] + i;
+  const int zT = blk_z[2 * gb], zB = blk_z[2 * gb + 1];
+  if (zT < 0 && zB < 0) return;   // the whole block: a chain without parts
+  const long row0 = ((long)fld * P + p) * Nr;
+  for (int k = threadIdx.x; k < Nr; k += blockDim.x) {
+    zs[k] = zT >= 0 ? cd_split(zbuf[(long)zT * Nr + k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    zs[Nr + k] = zB >= 0 ? cd_split(zbuf[(long)zB * Nr + k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  const int s8 = threadIdx.x & 7;
+  const int rows_per_pass = blockDim.x >> 3;
+  const bool real_op = (m == 0);
+  const float4* Vi = V + gb * (long)Nr * Nr;
+  const float4* Wi = Wsp + gb * (long)Nr * Nr;
+  for (int r = threadIdx.x >> 3; r < Nr + ((rows_per_pass - Nr % rows_per_pass) % rows_per_pass);
+       r += rows_per_pass) {
+    float4 av[Q], aw[Q];
+    cd_load<Q>(Vi, r, s8, 0, Nr, r < Nr && zT >= 0, av);
+    cd_load<Q>(Wi, r, s8, 0, Nr, r < Nr && zB >= 0, aw);
+    dfl re0 = dfl_zero(), im0 = dfl_zero(), re1 = dfl_zero(), im1 = dfl_zero();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int k = s8 + 8 * q;
+      if (k < Nr) {
+        cd_cmac(re0, im0, av[q], zs[k], real_op);
+        cd_cmac(re1, im1, aw[q], zs[Nr + k], real_op);
+      }
+    }
+    dfl re = dfl_add(re0, re1), im = dfl_add(im0, im1);
+    cd_reduce8(re, im);
+    if (r < Nr && s8 == 0) out[row0 + r] = cd_join(cd_sub(out[row0 + r], re, im));
+  }
 }
 
 }  // namespace rsc

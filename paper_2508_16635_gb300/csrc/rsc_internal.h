@@ -52,13 +52,28 @@ struct HostFactor {
   std::vector<long> chain_off;        // first block of each chain
   std::vector<cplx> G, H, W;          // per block Nr x Nr, row-major
   std::vector<double> Tinv;           // per l: Nr x Nr inverse of the T operator
+  // Partitioned chains (nparts > 1): every chain is cut into parts, each factorised on its
+  // own (G, H, W above, same slots); the parts are coupled through spikes and a reduced
+  // system for the first and last blocks of the parts (a SPIKE-type solve):
+  //   x_i = xl_i - V_i x(first block of the next part) - Wsp_i x(last block of the previous),
+  // xl the part-local solution.
+  std::vector<long> parts;            // per part: p0, cls, nb, boff, m, chain
+  std::vector<cplx> V, Wsp;           // spikes per block, Nr x Nr (zero where absent)
+  std::vector<long> red_off;          // per chain: offset of its reduced inverse in red
+  std::vector<int> red_nu, zoff;      // per chain: unknown blocks, first z block
+  std::vector<cplx> red;              // per chain: (nu Nr)^2 inverse of I + K, row-major
+  std::vector<long> unk_row;          // per z block: element offset of that block in a state
+  std::vector<int> unk_chain;         // per z block: its chain
+  std::vector<int> blk_z;             // per block: z block of the next part's first block
+                                      // and of the previous part's last block (-1: none)
 };
 
 void build_dims(const rsc_params& p, Dims& d);
 void build_tables(const rsc_params& p, const Dims& d, HostTables& t);
 // Returns 0 on success, or 1 + chain index of a singular block.
+// nparts > 1: partitioned chains (parts of at least 8 blocks, at most nparts per chain).
 int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double dt,
-                 HostFactor& f);
+                 HostFactor& f, int nparts = 1);
 // Gauss-Legendre nodes (descending from +1) and weights on [-1, 1].
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 void conductive_T00(const rsc_params& p, const Dims& d, const HostTables& t,

@@ -386,8 +386,154 @@ void lu_solve(int n, const std::vector<T>& LU, const std::vector<int>& piv, int 
 
 }  // namespace
 
+// Spikes, reduced systems and index tables of partitioned chains (a SPIKE-type solve,
+// HostFactor).  Part q of a chain has blocks s_q..e_q-1; its part-local factors are in
+// G, H, W.  V_q = A_q^-1 [0; ...; C] is its response to the coupling of its last block to
+// the next part's first block, Wsp_q = A_q^-1 [A; 0; ...] to the coupling of its first block
+// to the previous part's last block.  With xl the part-local solution, every block obeys
+//   x_i = xl_i - V_i x(s_{q+1}) - Wsp_i x(e_{q-1} - 1),
+// and these relations at the blocks that couple parts (B_q = x(e_q - 1), T_{q+1} = x(s_{q+1}))
+// form (I + K) z = xl_z, whose inverse is stored per chain.
+static bool partition_extras(const Dims& d, const HostTables& t, const Ops& ops,
+                             const std::vector<std::vector<int>>& cuts, HostFactor& f) {
+  const int Nr = d.Nr;
+  const size_t blk = (size_t)Nr * Nr;
+  const int nchains = 2 * d.nm;
+  const long nblk = f.chain_off[nchains];
+  f.V.assign(nblk * blk, cplx(0.0));
+  f.Wsp.assign(nblk * blk, cplx(0.0));
+  f.blk_z.assign(nblk * 2, -1);
+  f.parts.clear();
+  f.red_off.assign(nchains, 0);
+  f.red_nu.assign(nchains, 0);
+  f.zoff.assign(nchains, 0);
+  f.unk_row.clear();
+  f.unk_chain.clear();
+  long roff = 0;
+  int z = 0;
+  for (int c = 0; c < nchains; ++c) {
+    const int a = c / 2, cls = c % 2, m = t.m_of[a];
+    const int Pc = (int)cuts[c].size() - 1;
+    for (int q = 0; q < Pc; ++q) {
+      const int s = cuts[c][q], e = cuts[c][q + 1];
+      f.parts.insert(f.parts.end(), {(long)(t.pstart[a] + s), (long)((cls + s) & 1), (long)(e - s),
+                                     f.chain_off[c] + s, (long)m, (long)c});
+    }
+    const int nu = 2 * (Pc - 1);
+    f.red_nu[c] = nu;
+    f.zoff[c] = z;
+    f.red_off[c] = roff;
+    for (int u = 0; u < nu; ++u) {   // B_q (u = 2q): last block of part q; T_{q+1} (u = 2q+1)
+      const int i = (u % 2 == 0) ? cuts[c][u / 2 + 1] - 1 : cuts[c][u / 2 + 1];
+      const int fld = (i + cls) & 1;
+      f.unk_row.push_back(((long)fld * d.P + t.pstart[a] + i) * Nr);
+      f.unk_chain.push_back(c);
+    }
+    for (int q = 0; q < Pc; ++q)
+      for (int i = cuts[c][q]; i < cuts[c][q + 1]; ++i) {
+        const long g = f.chain_off[c] + i;
+        f.blk_z[g * 2 + 0] = (q < Pc - 1) ? z + 2 * q + 1 : -1;
+        f.blk_z[g * 2 + 1] = (q > 0) ? z + 2 * (q - 1) : -1;
+      }
+    z += nu;
+    roff += (long)nu * Nr * nu * Nr;
+  }
+  f.red.assign(roff, cplx(0.0));
+
+  auto mm_sub = [&](const cplx* A, const std::vector<cplx>& X, std::vector<cplx>& Y) {
+    for (int r = 0; r < Nr; ++r)
+      for (int k = 0; k < Nr; ++k) {
+        const cplx x = A[(size_t)r * Nr + k];
+        if (x == cplx(0.0)) continue;
+        for (int q = 0; q < Nr; ++q) Y[(size_t)r * Nr + q] -= x * X[(size_t)k * Nr + q];
+      }
+  };
+  auto mm = [&](const cplx* A, std::vector<cplx>& X) {   // X <- A X
+    std::vector<cplx> Y(blk, cplx(0.0));
+    for (int r = 0; r < Nr; ++r)
+      for (int k = 0; k < Nr; ++k) {
+        const cplx x = A[(size_t)r * Nr + k];
+        if (x == cplx(0.0)) continue;
+        for (int q = 0; q < Nr; ++q) Y[(size_t)r * Nr + q] += x * X[(size_t)k * Nr + q];
+      }
+    X.swap(Y);
+  };
+  // X[i - s] <- (part-local operator)^-1 X[i - s] with the part's twisted factors (the
+  // order of the GPU sweeps: g = G b, half sweeps from both ends, middle, outward sweeps)
+  auto part_solve = [&](int c, int s, int e, std::vector<std::vector<cplx>>& X) {
+    const int km = s + (e - s - 1) / 2;
+    auto at = [&](const std::vector<cplx>& v, int i) { return &v[(f.chain_off[c] + i) * blk]; };
+    for (int i = s; i < e; ++i) mm(at(f.G, i), X[i - s]);
+    for (int i = s + 1; i < km; ++i) mm_sub(at(f.H, i), X[i - 1 - s], X[i - s]);
+    for (int i = e - 2; i > km; --i) mm_sub(at(f.H, i), X[i + 1 - s], X[i - s]);
+    if (km > s) mm_sub(at(f.H, km), X[km - 1 - s], X[km - s]);
+    if (km < e - 1) mm_sub(at(f.W, km), X[km + 1 - s], X[km - s]);
+    for (int i = km - 1; i >= s; --i) mm_sub(at(f.W, i), X[i + 1 - s], X[i - s]);
+    for (int i = km + 1; i < e; ++i) mm_sub(at(f.W, i), X[i - 1 - s], X[i - s]);
+  };
+  std::vector<int> bad(nchains, 0);
+  auto work = [&](int c) {
+    const int a = c / 2, cls = c % 2, m = t.m_of[a];
+    const int Pc = (int)cuts[c].size() - 1;
+    if (Pc < 2) return;
+    auto field_of = [&](int i) { return ((i + cls) % 2 == 0) ? 0 : 1; };
+    std::vector<cplx> B;
+    for (int q = 0; q < Pc; ++q) {
+      const int s = cuts[c][q], e = cuts[c][q + 1];
+      for (int side = 0; side < 2; ++side) {
+        if ((side == 0 && q == Pc - 1) || (side == 1 && q == 0)) continue;
+        std::vector<std::vector<cplx>> X(e - s, std::vector<cplx>(blk, cplx(0.0)));
+        if (side == 0) {   // coupling of block e-1 to block e (the next part's first)
+          ops.coupling(field_of(e - 1), m + e - 1, m, +1, B);
+          X[e - 1 - s] = B;
+        } else {           // coupling of block s to block s-1 (the previous part's last)
+          ops.coupling(field_of(s), m + s, m, -1, B);
+          X[0] = B;
+        }
+        part_solve(c, s, e, X);
+        std::vector<cplx>& dst = side == 0 ? f.V : f.Wsp;
+        for (int i = s; i < e; ++i)
+          std::copy(X[i - s].begin(), X[i - s].end(), &dst[(f.chain_off[c] + i) * blk]);
+      }
+    }
+    // (I + K) z = xl_z over the nu unknown blocks, inverted
+    const int nu = f.red_nu[c], n = nu * Nr;
+    std::vector<cplx> M((size_t)n * n, cplx(0.0)), I((size_t)n * n, cplx(0.0));
+    for (int r = 0; r < n; ++r) M[(size_t)r * n + r] = I[(size_t)r * n + r] = 1.0;
+    for (int u = 0; u < nu; ++u) {
+      const int q = (u % 2 == 0) ? u / 2 : u / 2 + 1;     // the part of unknown u
+      const int i = (u % 2 == 0) ? cuts[c][u / 2 + 1] - 1 : cuts[c][u / 2 + 1];
+      const long g = f.chain_off[c] + i;
+      for (int side = 0; side < 2; ++side) {
+        const int uc = side == 0 ? (q < Pc - 1 ? 2 * q + 1 : -1) : (q > 0 ? 2 * (q - 1) : -1);
+        if (uc < 0) continue;
+        const cplx* S = &(side == 0 ? f.V : f.Wsp)[g * blk];
+        for (int r = 0; r < Nr; ++r)
+          for (int k = 0; k < Nr; ++k) M[(size_t)(u * Nr + r) * n + uc * Nr + k] += S[(size_t)r * Nr + k];
+      }
+    }
+    std::vector<int> piv;
+    if (!lu_factor(n, M, piv)) {
+      bad[c] = 1;
+      return;
+    }
+    lu_solve(n, M, piv, n, I);
+    std::copy(I.begin(), I.end(), f.red.begin() + f.red_off[c]);
+  };
+  const int nth = std::max(1, std::min<int>(nchains, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nth; ++w)
+    pool.emplace_back([&, w]() {
+      for (int c = w; c < nchains; c += nth) work(c);
+    });
+  for (auto& th : pool) th.join();
+  for (int c = 0; c < nchains; ++c)
+    if (bad[c]) return false;
+  return true;
+}
+
 int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double dt,
-                 HostFactor& f) {
+                 HostFactor& f, int nparts) {
   const int Nr = d.Nr;
   const size_t blk = (size_t)Nr * Nr;
   Ops ops{d, t, p.Ek, p.Pr, std::isfinite(dt) ? 1.0 / dt : 0.0, Nr, p.explicit_coriolis != 0};
@@ -404,15 +550,23 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
   f.H.assign(off * blk, cplx(0.0));
   f.W.assign(off * blk, cplx(0.0));
   std::vector<int> bad(nchains, 0);
+  // part boundaries of each chain: Pc parts of at least 8 blocks (one part: the whole chain)
+  std::vector<std::vector<int>> cuts(nchains);
+  for (int c = 0; c < nchains; ++c) {
+    const int nb = d.L - t.m_of[c / 2] + 1;
+    const int Pc = std::max(1, std::min(std::max(1, nparts), nb / 8));
+    for (int q = 0; q <= Pc; ++q) cuts[c].push_back((int)((long)q * nb / Pc));
+  }
 
-  // Twisted block factorisation of each chain: blocks 0..k-1 are eliminated
-  // top-down (block Thomas), blocks k+1..n-1 bottom-up, and the middle block
-  // k = (n-1)/2 closes the system, so the forward sweeps run from both ends at
-  // once and meet in the middle.  Per block three matrices are stored:
+  // Twisted block factorisation of the blocks s..e-1 of a chain (the whole chain, or one
+  // part of it): blocks s..k-1 are eliminated top-down (block Thomas), blocks k+1..e-1
+  // bottom-up, and the middle block k = s + (e-s-1)/2 closes the system, so the forward
+  // sweeps run from both ends at once and meet in the middle.  Per block three matrices
+  // are stored:
   //   top    i < k : G = D'^-1, H = D'^-1 A, W = D'^-1 C
   //   bottom i > k : G = E'^-1, H = E'^-1 C, W = E'^-1 A
   //   middle i = k : G = Z, H = Z A, W = Z C,  Z = (D - A W_{k-1} - C W_{k+1})^-1
-  // with A (C) the Coriolis coupling to block i-1 (i+1).
+  // with A (C) the Coriolis coupling to block i-1 (i+1) inside the range.
   auto sub_prod = [&](std::vector<cplx>& Dm, const std::vector<cplx>& X, const cplx* Y) {
     for (int r = 0; r < Nr; ++r)
       for (int q = 0; q < Nr; ++q) {
@@ -421,11 +575,10 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
         for (int k = 0; k < Nr; ++k) Dm[(size_t)r * Nr + k] -= x * Y[(size_t)q * Nr + k];
       }
   };
-  auto work = [&](int c) {
+  auto factor_range = [&](int c, int s, int e) -> bool {
     const int a = c / 2, cls = c % 2;
     const int m = t.m_of[a];
-    const int nb = d.L - m + 1;
-    const int km = (nb - 1) / 2;
+    const int km = s + (e - s - 1) / 2;
     auto field_of = [&](int i) { return ((i + cls) % 2 == 0) ? 0 : 1; };
     auto slot = [&](std::vector<cplx>& v, int i) { return &v[(f.chain_off[c] + i) * blk]; };
     std::vector<cplx> D, A, C, tmp;
@@ -436,16 +589,16 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
       lu_solve(Nr, D, piv, Nr, tmp);
       std::copy(tmp.begin(), tmp.end(), slot(f.G, i));
     };
-    for (int i = 0; i < km; ++i) {  // top-down
+    for (int i = s; i < km; ++i) {  // top-down
       const int l = m + i, fld = field_of(i);
       ops.diag(fld, l, m, D);
-      if (i > 0) {
+      if (i > s) {
         ops.coupling(fld, l, m, -1, A);
         sub_prod(D, A, slot(f.W, i - 1));
       }
-      if (!lu_factor(Nr, D, piv)) { bad[c] = 1; return; }
+      if (!lu_factor(Nr, D, piv)) return false;
       invert_into(i);
-      if (i > 0) {
+      if (i > s) {
         lu_solve(Nr, D, piv, Nr, A);
         std::copy(A.begin(), A.end(), slot(f.H, i));
       }
@@ -453,16 +606,16 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
       lu_solve(Nr, D, piv, Nr, C);
       std::copy(C.begin(), C.end(), slot(f.W, i));
     }
-    for (int i = nb - 1; i > km; --i) {  // bottom-up
+    for (int i = e - 1; i > km; --i) {  // bottom-up
       const int l = m + i, fld = field_of(i);
       ops.diag(fld, l, m, D);
-      if (i < nb - 1) {
+      if (i < e - 1) {
         ops.coupling(fld, l, m, +1, C);
         sub_prod(D, C, slot(f.W, i + 1));
       }
-      if (!lu_factor(Nr, D, piv)) { bad[c] = 1; return; }
+      if (!lu_factor(Nr, D, piv)) return false;
       invert_into(i);
-      if (i < nb - 1) {
+      if (i < e - 1) {
         lu_solve(Nr, D, piv, Nr, C);
         std::copy(C.begin(), C.end(), slot(f.H, i));
       }
@@ -473,25 +626,33 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
     {  // middle
       const int i = km, l = m + i, fld = field_of(i);
       ops.diag(fld, l, m, D);
-      if (i > 0) {
+      if (i > s) {
         ops.coupling(fld, l, m, -1, A);
         sub_prod(D, A, slot(f.W, i - 1));
       }
-      if (i < nb - 1) {
+      if (i < e - 1) {
         ops.coupling(fld, l, m, +1, C);
         sub_prod(D, C, slot(f.W, i + 1));
       }
-      if (!lu_factor(Nr, D, piv)) { bad[c] = 1; return; }
+      if (!lu_factor(Nr, D, piv)) return false;
       invert_into(i);
-      if (i > 0) {
+      if (i > s) {
         lu_solve(Nr, D, piv, Nr, A);
         std::copy(A.begin(), A.end(), slot(f.H, i));
       }
-      if (i < nb - 1) {
+      if (i < e - 1) {
         lu_solve(Nr, D, piv, Nr, C);
         std::copy(C.begin(), C.end(), slot(f.W, i));
       }
     }
+    return true;
+  };
+  auto work = [&](int c) {
+    for (size_t q = 0; q + 1 < cuts[c].size(); ++q)
+      if (!factor_range(c, cuts[c][q], cuts[c][q + 1])) {
+        bad[c] = 1;
+        return;
+      }
   };
   const int nth = std::max(1, std::min<int>(nchains, (int)std::thread::hardware_concurrency()));
   std::vector<std::thread> pool;
@@ -502,6 +663,7 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
   for (auto& th : pool) th.join();
   for (int c = 0; c < nchains; ++c)
     if (bad[c]) return 1 + c;
+  if (nparts > 1 && !partition_extras(d, t, ops, cuts, f)) return 1 + nchains;
   // Temperature: real inverse per l.
   f.Tinv.assign((size_t)(d.L + 1) * blk, 0.0);
   std::vector<double> D, I;

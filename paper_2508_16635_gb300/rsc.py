@@ -53,7 +53,7 @@ class Tuning(ctypes.Structure):
                 ("chain_cluster", ctypes.c_int), ("analysis_tc", ctypes.c_int),
                 ("chain_async", ctypes.c_int), ("chain_df", ctypes.c_int),
                 ("chain_df_cluster", ctypes.c_int), ("krylov_split", ctypes.c_int),
-                ("ms", ctypes.c_double * 6)]
+                ("chain_parts", ctypes.c_int), ("ms", ctypes.c_double * 6)]
 
     def as_dict(self):
         return {"products_warps": list(self.products_warps),
@@ -63,7 +63,8 @@ class Tuning(ctypes.Structure):
                 "rhs_pairs": list(self.rhs_pairs), "chain_cluster": self.chain_cluster,
                 "analysis_tc": self.analysis_tc, "chain_async": self.chain_async,
                 "chain_df": self.chain_df, "chain_df_cluster": self.chain_df_cluster,
-                "krylov_split": self.krylov_split, "ms": list(self.ms)}
+                "krylov_split": self.krylov_split, "chain_parts": self.chain_parts,
+                "ms": list(self.ms)}
 
 
 class ContinuationOpts(ctypes.Structure):
@@ -378,6 +379,7 @@ class RotatingShell:
         t.chain_df = d.get("chain_df", cur["chain_df"])
         t.chain_df_cluster = d.get("chain_df_cluster", cur["chain_df_cluster"])
         t.krylov_split = d.get("krylov_split", cur["krylov_split"])
+        t.chain_parts = d.get("chain_parts", cur["chain_parts"])
         self._check(self.lib.rsc_set_tuning(self._ctx, ctypes.byref(t)))
 
     def continue_ra(self, U, C, J, Ra0, Ra1, Ra_end, n_opt=4, gamma=20.0, max_points=8,
