@@ -18,7 +18,8 @@ shell   the discretised Boussinesq model: explicit terms, implicit operator
         IMEX Euler step (Eq. discrete), the Jacobian action with the phase
         trick (Secs. 3.3-3.4).
 krylov  MGS-GMRES and the Newton iteration for rotating waves (Secs. 3.3-3.4).
-onset   linear stability of the conductive state (critical Rayleigh number).
+continuation  natural-parameter continuation in Ra and in log10 Ek, spectral-tail
+        refinement and zero-fill regridding (Secs. 4.3-4.4).
 
 Parity status of each function is stated in its docstring; functions without
 an independent pin say "parity unpinned".

@@ -29,14 +29,14 @@ class SphereGrid:
         self.nlat = basis.nlat_for(L)
         self.nphi = basis.nphi_for(L, Ms)
         self.x, self.w = basis.gauss_legendre(self.nlat)
-        self.sin = np.sqrt(1.0 - self.x ** 2)
+        self.sin = basis.gauss_legendre_sin(self.nlat)
         # Per m: P = N P_l^m, dP = d/dtheta of it, Ps = P / sin(theta); rows l = m..L.
         self.P, self.dP, self.Ps = [], [], []
         for m in self.ms:
             f = basis.ylm_norm_factor(m)
-            p = f * basis.plm_bar(L, m, self.x)
+            p = f * basis.plm_bar(L, m, self.x, self.sin)
             self.P.append(p)
-            self.dP.append(f * basis.dplm_bar_dtheta(L, m, self.x))
+            self.dP.append(f * basis.dplm_bar_dtheta(L, m, self.x, self.sin))
             self.Ps.append(p / self.sin[None, :])
         # Azimuthal DFT matrices over the sector: phi_j = 2 pi j / (Ms nphi),
         # so m phi_j = 2 pi k j / nphi for m = k Ms.

@@ -83,67 +83,83 @@ static void cheb_table(int npts, int nk, int order, double r_in, double r_out,
   }
 }
 
+// Gauss-Legendre rule, north (x ~ +1) first.  Newton's method on P_n runs in
+// long double (64- or 113-bit significand) and the node and weight are rounded
+// to double at the end: in double arithmetic, P_n' is so large near the poles
+// that the rounding of x alone puts 1e-10 relative errors into those weights
+// at n = 384.  Weight w = 2 (1 - x^2) / (n P_{n-1}(x))^2, valid at a root.
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.resize(n);
   w.resize(n);
-  for (int i = 0; i < n; ++i) {
-    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));  // i = 0 nearest x = +1
-    double dp = 1.0;
-    for (int it = 0; it < 200; ++it) {
-      double p0 = 1.0, p1 = z;
-      for (int k = 2; k <= n; ++k) {
-        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      dp = n * (z * p1 - p0) / (z * z - 1.0);
-      const double dz = p1 / dp;
-      z -= dz;
-      if (std::fabs(dz) < 1e-17) break;
-    }
-    double p0 = 1.0, p1 = z;
-    for (int k = 2; k <= n; ++k) {
-      const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+  auto bonnet = [n](long double z, long double& pn, long double& pm) {
+    long double p0 = 1.0L, p1 = z;
+    for (int k = 1; k < n; ++k) {
+      const long double p2 = ((2.0L * k + 1.0L) * z * p1 - (long double)k * p0) / (k + 1.0L);
       p0 = p1;
       p1 = p2;
     }
-    dp = n * (z * p1 - p0) / (z * z - 1.0);
-    x[i] = z;
-    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    pn = p1;
+    pm = p0;
+  };
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    long double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    long double pn = 0.0L, pm = 0.0L;
+    for (int it = 0; it < 100; ++it) {
+      bonnet(z, pn, pm);
+      const long double dp = n * (pm - z * pn) / ((1.0L - z) * (1.0L + z));
+      const long double dz = pn / dp;
+      z -= dz;
+      if (std::fabs((double)dz) < 1e-30) break;
+    }
+    bonnet(z, pn, pm);
+    const long double wi = 2.0L * (1.0L - z) * (1.0L + z) / ((n * pm) * (n * pm));
+    x[i] = (double)z;
+    w[i] = (double)wi;
+    x[n - 1 - i] = -x[i];
+    w[n - 1 - i] = w[i];
   }
+  if (n % 2) x[n / 2] = 0.0;
 }
 
 // Normalised P_l^m (Eq. Ylm_norm, no Condon-Shortley phase) for l = m..lmax at
-// one node, with an extended exponent so that high m near the poles underflow
-// gracefully instead of zeroing the whole recursion.
-static void legendre_column(int lmax, int m, double x, std::vector<double>& out) {
+// one node x with s = sqrt(1 - x^2).  The start s^m prod sqrt((2k+1)/2k) leaves
+// the double range near the poles for large m, so the recursion carries an
+// extra exponent: values are rescaled by exact powers 2^+-500 and put back
+// with ldexp, which gives 0 where the true value is below the double range
+// and full precision elsewhere.
+static void legendre_column(int lmax, int m, double x, double s, std::vector<double>& out) {
   out.assign(lmax - m + 1, 0.0);
-  const double s = std::sqrt(std::max(0.0, 1.0 - x * x));
-  double lg = 0.0;  // log2 of pbar_m^m
-  for (int k = 1; k <= m; ++k) lg += 0.5 * std::log2((2.0 * k + 1.0) / (2.0 * k));
-  lg += m * std::log2(s);
-  long E = (long)std::floor(lg);
-  double v0 = 0.0, v1 = std::exp2(lg - (double)E);
   const double norm = (m > 0) ? std::sqrt(2.0) : 1.0;
-  out[0] = norm * std::ldexp(v1, (int)E);
+  long E = 0;  // true value = stored * 2^E
+  double v1 = 1.0;
+  for (int k = 1; k <= m; ++k) {
+    v1 *= s * std::sqrt((2.0 * k + 1.0) / (2.0 * k));
+    if (v1 != 0.0 && std::fabs(v1) < 0x1p-500) {
+      v1 = std::ldexp(v1, 500);
+      E -= 500;
+    }
+  }
+  auto put = [&](int q, double v) {
+    out[q] = (E < -2200) ? 0.0 : norm * std::ldexp(v, (int)E);
+  };
+  put(0, v1);
   if (lmax == m) return;
-  double v2 = x * std::sqrt(2.0 * m + 3.0) * v1;
-  v0 = v1;
-  v1 = v2;
-  out[1] = norm * std::ldexp(v1, (int)E);
+  double v0 = v1;
+  v1 = x * std::sqrt(2.0 * m + 3.0) * v0;
+  put(1, v1);
   for (int l = m + 2; l <= lmax; ++l) {
     const double a = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
     const double b = std::sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) /
                                (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
-    v2 = a * (x * v1 - b * v0);
+    const double v2 = a * (x * v1 - b * v0);
     v0 = v1;
     v1 = v2;
-    if (std::fabs(v1) > 0x1p500) {
+    if (E < 0 && std::fabs(v1) > 0x1p500) {
       v0 = std::ldexp(v0, -500);
       v1 = std::ldexp(v1, -500);
       E += 500;
     }
-    out[l - m] = norm * std::ldexp(v1, (int)std::min<long>(E, INT_MAX));
+    put(l - m, v1);
   }
 }
 
@@ -213,8 +229,8 @@ void build_tables(const rsc_params& p, const Dims& d, HostTables& t) {
     const double nrm = 2.0 * (m > 0 ? 2.0 : 1.0);  // int P^2 dx with Eq. Ylm_norm
     for (int tt = 0; tt < d.nlat2; ++tt) {
       const double x = t.xlat[tt];
-      const double s = std::sqrt(1.0 - x * x);
-      legendre_column(d.L + 1, m, x, col);  // rows l = m..L+1
+      const double s = std::sqrt((1.0 - x) * (1.0 + x));
+      legendre_column(d.L + 1, m, x, s, col);  // rows l = m..L+1
       for (int q = 0; q < nl; ++q) {
         const int l = m + q;
         const double cl = std::sqrt(((double)l * l - (double)m * m) / (4.0 * l * l - 1.0));
@@ -575,57 +591,92 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
         for (int k = 0; k < Nr; ++k) Dm[(size_t)r * Nr + k] -= x * Y[(size_t)q * Nr + k];
       }
   };
+  // Row equilibration: every row of a block row is divided by its largest entry over the
+  // diagonal block and both Coriolis couplings before the block is factorised, and the
+  // factors absorb the scaling (G = (S D')^-1 S, H = (S D')^-1 S A, W = (S D')^-1 S C are
+  // the same matrices as without it).  The rows of one block span thirteen orders of
+  // magnitude (boundary rows ~1, fourth-order rows ~1e13 at N_r = 64); pivoting on the
+  // unscaled rows costs the boundary rows up to 1e-9 of their accuracy.
+  auto row_scale = [&](int fld, int l, int m, int i, int nb, const std::vector<cplx>& Dm,
+                       std::vector<double>& S) {
+    std::vector<cplx> B;
+    S.assign(Nr, 0.0);
+    for (int r = 0; r < Nr; ++r)
+      for (int k = 0; k < Nr; ++k) S[r] = std::max(S[r], std::abs(Dm[(size_t)r * Nr + k]));
+    for (int side = -1; side <= 1; side += 2) {
+      if ((side < 0 && i == 0) || (side > 0 && i == nb - 1)) continue;
+      ops.coupling(fld, l, m, side, B);
+      for (int r = 0; r < Nr; ++r)
+        for (int k = 0; k < Nr; ++k) S[r] = std::max(S[r], std::abs(B[(size_t)r * Nr + k]));
+    }
+    for (int r = 0; r < Nr; ++r) S[r] = 1.0 / S[r];
+  };
+  auto scale_rows = [&](std::vector<cplx>& Mx, const std::vector<double>& S) {
+    for (int r = 0; r < Nr; ++r)
+      for (int k = 0; k < Nr; ++k) Mx[(size_t)r * Nr + k] *= S[r];
+  };
   auto factor_range = [&](int c, int s, int e) -> bool {
     const int a = c / 2, cls = c % 2;
     const int m = t.m_of[a];
+    const int nb = d.L - m + 1;
     const int km = s + (e - s - 1) / 2;
     auto field_of = [&](int i) { return ((i + cls) % 2 == 0) ? 0 : 1; };
     auto slot = [&](std::vector<cplx>& v, int i) { return &v[(f.chain_off[c] + i) * blk]; };
     std::vector<cplx> D, A, C, tmp;
+    std::vector<double> S;
     std::vector<int> piv;
     auto invert_into = [&](int i) {
       tmp.assign(blk, cplx(0.0));
-      for (int r = 0; r < Nr; ++r) tmp[(size_t)r * Nr + r] = 1.0;
+      for (int r = 0; r < Nr; ++r) tmp[(size_t)r * Nr + r] = S[r];
       lu_solve(Nr, D, piv, Nr, tmp);
       std::copy(tmp.begin(), tmp.end(), slot(f.G, i));
     };
     for (int i = s; i < km; ++i) {  // top-down
       const int l = m + i, fld = field_of(i);
       ops.diag(fld, l, m, D);
+      row_scale(fld, l, m, i, nb, D, S);
       if (i > s) {
         ops.coupling(fld, l, m, -1, A);
         sub_prod(D, A, slot(f.W, i - 1));
       }
+      scale_rows(D, S);
       if (!lu_factor(Nr, D, piv)) return false;
       invert_into(i);
       if (i > s) {
+        scale_rows(A, S);
         lu_solve(Nr, D, piv, Nr, A);
         std::copy(A.begin(), A.end(), slot(f.H, i));
       }
       ops.coupling(fld, l, m, +1, C);
+      scale_rows(C, S);
       lu_solve(Nr, D, piv, Nr, C);
       std::copy(C.begin(), C.end(), slot(f.W, i));
     }
     for (int i = e - 1; i > km; --i) {  // bottom-up
       const int l = m + i, fld = field_of(i);
       ops.diag(fld, l, m, D);
+      row_scale(fld, l, m, i, nb, D, S);
       if (i < e - 1) {
         ops.coupling(fld, l, m, +1, C);
         sub_prod(D, C, slot(f.W, i + 1));
       }
+      scale_rows(D, S);
       if (!lu_factor(Nr, D, piv)) return false;
       invert_into(i);
       if (i < e - 1) {
+        scale_rows(C, S);
         lu_solve(Nr, D, piv, Nr, C);
         std::copy(C.begin(), C.end(), slot(f.H, i));
       }
       ops.coupling(fld, l, m, -1, A);
+      scale_rows(A, S);
       lu_solve(Nr, D, piv, Nr, A);
       std::copy(A.begin(), A.end(), slot(f.W, i));
     }
     {  // middle
       const int i = km, l = m + i, fld = field_of(i);
       ops.diag(fld, l, m, D);
+      row_scale(fld, l, m, i, nb, D, S);
       if (i > s) {
         ops.coupling(fld, l, m, -1, A);
         sub_prod(D, A, slot(f.W, i - 1));
@@ -634,13 +685,16 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
         ops.coupling(fld, l, m, +1, C);
         sub_prod(D, C, slot(f.W, i + 1));
       }
+      scale_rows(D, S);
       if (!lu_factor(Nr, D, piv)) return false;
       invert_into(i);
       if (i > s) {
+        scale_rows(A, S);
         lu_solve(Nr, D, piv, Nr, A);
         std::copy(A.begin(), A.end(), slot(f.H, i));
       }
       if (i < e - 1) {
+        scale_rows(C, S);
         lu_solve(Nr, D, piv, Nr, C);
         std::copy(C.begin(), C.end(), slot(f.W, i));
       }
@@ -668,11 +722,18 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
   f.Tinv.assign((size_t)(d.L + 1) * blk, 0.0);
   std::vector<double> D, I;
   std::vector<int> piv;
+  std::vector<double> St(Nr);
   for (int l = 0; l <= d.L; ++l) {
     ops.temp(l, D);
+    for (int r = 0; r < Nr; ++r) {  // row equilibration, as for the chains
+      double mx = 0.0;
+      for (int k = 0; k < Nr; ++k) mx = std::max(mx, std::fabs(D[(size_t)r * Nr + k]));
+      St[r] = 1.0 / mx;
+      for (int k = 0; k < Nr; ++k) D[(size_t)r * Nr + k] *= St[r];
+    }
     if (!lu_factor(Nr, D, piv)) return 1 + nchains;
     I.assign(blk, 0.0);
-    for (int r = 0; r < Nr; ++r) I[(size_t)r * Nr + r] = 1.0;
+    for (int r = 0; r < Nr; ++r) I[(size_t)r * Nr + r] = St[r];
     lu_solve(Nr, D, piv, Nr, I);
     std::copy(I.begin(), I.end(), f.Tinv.begin() + (size_t)l * blk);
   }

@@ -58,6 +58,22 @@ def test_gauss_legendre_exact_on_monomials(n):
         assert abs((w * x ** k).sum() - exact) < 1e-13
 
 
+@pytest.mark.parametrize("n", [192, 384])
+def test_gauss_legendre_weights_at_large_n(n):
+    """Sum_j w_j P_k(x_j) = 2 delta_k0 for every k < 2n, with P_k from scipy.
+
+    Double-precision Newton (as in numpy's leggauss) misses this by 2-4e-14
+    because the weights near the poles carry 1e-10 relative errors; the
+    oracle's nodes and weights meet it at the rounding level.
+    """
+    x, w = basis.gauss_legendre(n)
+    s = basis.gauss_legendre_sin(n)
+    assert np.abs(s * s + x * x - 1.0).max() < 4e-16
+    for k in range(2 * n):
+        v = (w * sp.eval_legendre(k, x)).sum() - (2.0 if k == 0 else 0.0)
+        assert abs(v) < 3e-15, k
+
+
 def _n_lm(l, m):
     return math.sqrt((2.0 - (m == 0)) * (2 * l + 1)
                      * math.exp(math.lgamma(l - m + 1) - math.lgamma(l + m + 1)))
@@ -80,6 +96,82 @@ def test_discrete_orthogonality():
         p = basis.ylm_norm_factor(m) * basis.plm_bar(L, m, x)
         G = (p * w) @ p.T
         assert np.abs(G - 2.0 * (2.0 - (m == 0)) * np.eye(L - m + 1)).max() < 5e-13
+
+
+@pytest.mark.parametrize("L,Ms", [(127, 12), (255, 8)])
+def test_discrete_orthogonality_large_truncations(L, Ms):
+    n = basis.nlat_for(L)
+    x, w = basis.gauss_legendre(n)
+    s = basis.gauss_legendre_sin(n)
+    for m in range(0, L + 1, Ms):
+        p = basis.ylm_norm_factor(m) * basis.plm_bar(L, m, x, s)
+        G = (p * w) @ p.T / (2.0 * (2.0 - (m == 0)))
+        assert np.abs(G - np.eye(L - m + 1)).max() < 5e-14, m
+
+
+def test_unsold_sum_rule_at_L255():
+    """Unsold's theorem: sum_m |Y_l^m|^2 = (2l+1)/(4 pi), i.e.
+    sum_{m=0..l} (2 - delta_m0) pbar_l^m(x)^2 = 2l + 1 at every x."""
+    L = 255
+    n = basis.nlat_for(L)
+    x = basis.gauss_legendre(n)[0]
+    s = basis.gauss_legendre_sin(n)
+    acc = np.zeros((L + 1, n))
+    for m in range(L + 1):
+        acc[m:] += (2.0 - (m == 0)) * basis.plm_bar(L, m, x, s) ** 2
+    ref = (2.0 * np.arange(L + 1) + 1.0)[:, None]
+    assert np.abs(acc / ref - 1.0).max() < 2e-13
+
+
+def _pbar_rodrigues(l, m, t):
+    """pbar_l^m at s = 2t/(1+t^2), x = (1-t^2)/(1+t^2) (t rational), from
+    P_l^m = (1-x^2)^{m/2} d^m/dx^m P_l(x) with the explicit coefficients of P_l,
+    all in exact rational arithmetic; only the normalisation's square root is
+    taken in 60-digit decimal arithmetic.  Returns a Decimal."""
+    import decimal
+    from fractions import Fraction
+    x = (1 - t * t) / (1 + t * t)
+    s = 2 * t / (1 + t * t)
+    # P_l(x) = 2^-l sum_k (-1)^k C(l,k) C(2l-2k, l) x^(l-2k)
+    total = Fraction(0)
+    for k in range(l // 2 + 1):
+        deg = l - 2 * k
+        if deg < m:
+            continue
+        c = Fraction((-1) ** k * math.comb(l, k) * math.comb(2 * l - 2 * k, l), 2 ** l)
+        c *= math.perm(deg, m)            # d^m/dx^m x^deg = deg!/(deg-m)! x^(deg-m)
+        total += c * x ** (deg - m)
+    val = total * s ** m
+    with decimal.localcontext() as ctx:
+        ctx.prec = 60
+        ctx.Emin, ctx.Emax = -999999, 999999
+        norm = (decimal.Decimal((2 * l + 1) * math.factorial(l - m))
+                / decimal.Decimal(math.factorial(l + m))).sqrt()
+        return norm * decimal.Decimal(val.numerator) / decimal.Decimal(val.denominator)
+
+
+def test_plm_scaled_start_against_rodrigues():
+    """Near the pole the start pbar_m^m ~ s^m is far below the double range, but
+    pbar_l^m grows back into it for large l: the scaled start must reproduce
+    the exact values there, and entries that stay below the range must be 0."""
+    from fractions import Fraction
+    import decimal
+    t = Fraction(1, 2000)                      # s ~ 1e-3
+    m, lmax = 120, 420
+    s = float(2 * t / (1 + t * t))
+    x = float((1 - t * t) / (1 + t * t))
+    tab = basis.plm_bar(lmax, m, np.array([x]), np.array([s]))[:, 0]
+    assert tab[0] == 0.0                       # s^120 ~ 1e-360: below the range
+    for l in (346, 360, 400, 420):
+        ref = _pbar_rodrigues(l, m, t)
+        assert abs(decimal.Decimal(tab[l - m]) / ref - 1) < decimal.Decimal("1e-13"), l
+    # mid-latitude: every row against the closed form
+    t2 = Fraction(1, 3)
+    s2, x2 = float(2 * t2 / (1 + t2 * t2)), float((1 - t2 * t2) / (1 + t2 * t2))
+    tab2 = basis.plm_bar(60, 17, np.array([x2]), np.array([s2]))[:, 0]
+    for l in (17, 18, 30, 60):
+        ref = _pbar_rodrigues(l, 17, t2)
+        assert abs(decimal.Decimal(tab2[l - 17]) - ref) < decimal.Decimal("1e-13") * (1 + abs(ref))
 
 
 def test_recursions_of_the_paper_hold_on_the_grid():

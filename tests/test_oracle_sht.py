@@ -16,7 +16,7 @@ def _random_coeffs(g, rng, lmin=0, extra=()):
     return out
 
 
-@pytest.mark.parametrize("L,Ms", [(31, 4), (15, 1), (24, 3), (63, 8)])
+@pytest.mark.parametrize("L,Ms", [(31, 4), (15, 1), (24, 3), (63, 8), (127, 12), (255, 8)])
 def test_scalar_round_trip(L, Ms):
     g = sht.SphereGrid(L, Ms)
     a = _random_coeffs(g, np.random.default_rng(L), extra=(3,))
@@ -27,7 +27,7 @@ def test_scalar_round_trip(L, Ms):
     assert num / den < 1e-13      # relative 2-norm over all coefficients
 
 
-@pytest.mark.parametrize("L,Ms", [(31, 4), (15, 1), (63, 8)])
+@pytest.mark.parametrize("L,Ms", [(31, 4), (15, 1), (63, 8), (127, 12), (255, 8)])
 def test_vector_round_trip(L, Ms):
     g = sht.SphereGrid(L, Ms)
     rng = np.random.default_rng(100 + L)
