@@ -10,10 +10,11 @@ GMRES is the Saad-Schultz method with modified Gram-Schmidt, zero initial
 guess, no restart, stopped when the least-squares residual falls below
 tol * ||b|| (Sec. 3.3 accepts at relative 1e-10).
 
-Pins (tests/test_oracle_krylov.py): GMRES against a dense LU solve of the
-assembled operator; quadratic convergence of Newton onto the conductive
-state; independence of the converged rotating wave from the pseudo-timestep
-(Eq. finalrhs); the drift speed of Table 1.
+Pins: tests/test_oracle_krylov.py (GMRES against a dense LU solve of the
+assembled Jacobian with the drift unknown; the converged rotating wave is the
+same at pseudo-timesteps 200 and 20 (Eq. finalrhs); quadratic convergence of
+Newton onto the wave) and tests/test_oracle_paper_values.py (the drift speeds
+of Table 1).
 """
 import numpy as np
 
