@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RSC_ABI_VERSION 5
+#define RSC_ABI_VERSION 6
 
 typedef struct rsc_ctx rsc_ctx;
 
@@ -63,8 +63,15 @@ typedef enum {
 
 typedef enum {
   RSC_FP64 = 0,        /* every stage in FP64                                 */
-  RSC_MIXED = 1        /* transforms and products in FP32; RHS, block solves,
-                          GMRES and Newton update in FP64                      */
+  RSC_MIXED = 1        /* transforms and products in FP32 (Legendre sums on
+                          tcgen05 tensor cores, 3xTF32); right-hand side,
+                          temperature solve, Newton residual and update in FP64;
+                          the e/f chain solve of Jacobian actions and steps
+                          and the GMRES orthogonalisation in double-float
+                          arithmetic (FP32 hi + lo pairs, 48-bit significand)
+                          unless rsc_tuning chain_df / krylov_split = 0 select
+                          the FP64 kernels; the Newton residual step always
+                          solves in FP64                                       */
 } rsc_precision;
 
 /* Physical parameters and truncation (Sec. 2.1 parameters; Sec. 3.1 grids).
@@ -151,6 +158,20 @@ rsc_status rsc_step_host(rsc_ctx* ctx, double* U_host, double C, double dt, int 
  * T-rows -U.grad T (Sec. 3.2, Eq. defineFimp).  Boundary rows hold the
  * unprojected values.  A diagnostic of the transform pipeline.             */
 rsc_status rsc_explicit_terms(rsc_ctx* ctx, const double* U, double* N);
+
+/* The implicit solve of one step on its own: x = (M/dt + K)^{-1} rhs, with K the
+ * implicit operator of Sec. 3.2 (diffusion and, unless explicit_coriolis, the
+ * Coriolis terms of Eqs. impcor_e_final / impcor_f_final, coupling l to l +- 1
+ * in two block-tridiagonal chains per m, Fig. blocks) and M the mass operators
+ * (Sec. 3.3).  rhs and x are device vectors in the state layout whose entries
+ * are values at the Nr collocation radii (not Chebyshev coefficients): row k
+ * of a pair is the equation at radius r_k; the boundary rows (k = 0, Nr - 1
+ * for e and T; also 1, Nr - 2 for f) hold the boundary-condition values, the
+ * rows of e_00 and f_00 hold 0, and x receives Chebyshev coefficients.  rhs
+ * and x may be the same buffer.  On a mixed-precision context the e/f chains
+ * are solved like its Jacobian actions (chain_df).  Factorises dt on first
+ * use.  Returns RSC_EINVAL for a null pointer or dt <= 0.                   */
+rsc_status rsc_implicit_solve(rsc_ctx* ctx, const double* rhs, double* x, double dt);
 
 /* Jacobian action of Sec. 3.3-3.4 for `count` directions:
  *   out_i = (B_U - I) u_i with the drift unknown c = u_i[J] (Sec. 3.4):
@@ -270,7 +291,8 @@ rsc_status rsc_regrid(const rsc_ctx* src, const double* U_src, rsc_ctx* dst, dou
 rsc_status rsc_refine_params(const rsc_params* p, double cheb_tail, double sh_tail,
                              double threshold, double growth, rsc_params* out, int* refined);
 
-/* Newton-GMRES on a HOST state (copies in and out inside the call).        */
+/* Newton-GMRES on a HOST state (copies in and out inside the call, through a
+ * device buffer the context allocated at creation: nothing is allocated).   */
 rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
                               const rsc_newton_opts* opts, rsc_newton_report* report);
 
@@ -424,7 +446,11 @@ rsc_status rsc_norm2(rsc_ctx* ctx, const double* v, size_t n, double* out);
  * (16 KiB) in device memory, held by every GPU that loads the library until
  * the process exits.  The first call on a device looks the array up (once
  * per device, with that device current), so make that first call before any
- * stream capture.  All calls on a device share the array: calls whose
+ * stream capture.  The looked-up address belongs to the device's primary
+ * context: after cudaDeviceReset (or anything else that destroys that
+ * context) it is stale, and a later call would write through it, so do not
+ * use this entry point in a process that resets its devices.  All calls on
+ * a device share the array: calls whose
  * kernels overlap on the GPU (other streams, other host threads) race and
  * may return wrong sums; serialise them.  Returns RSC_EINVAL when v or out
  * is NULL or n > RSC_NORM2_NOALLOC_MAX_N, RSC_ECUDA when the look-up or

@@ -96,6 +96,7 @@ struct rsc_ctx {
   double* xtmp = nullptr;
   double* vtmp = nullptr;
   double* rtmp = nullptr;
+  double* ustate = nullptr;   // device copy of the state of the *_host calls
   // factorisations, two slots (time stepping dt and Newton dt)
   DevFactor fac[2];
   int fac_next = 0;
@@ -1946,6 +1947,7 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = alloc((void**)&ctx->xtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->vtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->rtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->ustate, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   ctx->nblk_dot = (int)std::max<long>((n + 1023) / 1024, 152L * 8);   // pass-A chunks, pass-B blocks
   if ((st = alloc((void**)&ctx->partial, (size_t)ctx->nblk_dot * (2 * kMaxKrylov + 4) * sizeof(double))) != RSC_OK)
     return fail(st);
@@ -1972,7 +1974,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->UG, ctx->FA,
-                  ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->V, ctx->Vs, ctx->partial,
+                  ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->ustate, ctx->V, ctx->Vs, ctx->partial,
                   ctx->dots, ctx->AR0, ctx->ta_tiles, ctx->ta_off, ctx->cont_hist, ctx->cont_cond, ctx->amax_v, ctx->amax_i, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
   for (void* b : bufs) cudaFree(b);
   for (int q = 0; q < 8; ++q) {
@@ -2053,9 +2055,9 @@ rsc_status rsc_step2(rsc_ctx* ctx, double* U, double dt, int nsteps) {
 rsc_status rsc_step_host(rsc_ctx* ctx, double* U_host, double C, double dt, int nsteps) {
   if (!ctx || !U_host) return RSC_EINVAL;
   const long n = ctx->d.n();
-  CK(cudaMemcpyAsync(ctx->vtmp, U_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
-  CKS(rsc_step(ctx, ctx->vtmp, C, dt, nsteps));
-  CK(cudaMemcpyAsync(U_host, ctx->vtmp, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaMemcpyAsync(ctx->ustate, U_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+  CKS(rsc_step(ctx, ctx->ustate, C, dt, nsteps));
+  CK(cudaMemcpyAsync(U_host, ctx->ustate, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
   return RSC_OK;
 }
@@ -2215,18 +2217,26 @@ rsc_status rsc_newton_rw(rsc_ctx* ctx, double* U, double* C, long J, const rsc_n
 
 rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
                               const rsc_newton_opts* o, rsc_newton_report* rep) {
-  if (!ctx || !U_host) return RSC_EINVAL;
+  if (!ctx || !U_host || !C) return RSC_EINVAL;
   const long n = ctx->d.n();
-  double* Ud = nullptr;
-  CK(cudaMalloc(&Ud, n * sizeof(double)));
-  cudaMemcpyAsync(Ud, U_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->s);
-  rsc_status st = rsc_newton_rw(ctx, Ud, C, J, o, rep);
-  cudaMemcpyAsync(U_host, Ud, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
-  cudaStreamSynchronize(ctx->s);
-  cudaFree(Ud);
+  // the device copy lives in a buffer the context allocated at creation
+  CK(cudaMemcpyAsync(ctx->ustate, U_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+  const rsc_status st = rsc_newton_rw(ctx, ctx->ustate, C, J, o, rep);
+  if (st != RSC_OK && st != RSC_ENOCONV) return st;
+  CK(cudaMemcpyAsync(U_host, ctx->ustate, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
   return st;
 }
 
+rsc_status rsc_implicit_solve(rsc_ctx* ctx, const double* rhs, double* x, double dt) {
+  if (!ctx || !rhs || !x || !(dt > 0) || !std::isfinite(dt)) return RSC_EINVAL;
+  DevFactor* f = nullptr;
+  CKS(get_factor(ctx, dt, &f));
+  CK(cudaMemcpyAsync(ctx->rhs, rhs, (size_t)ctx->d.n() * sizeof(double), cudaMemcpyDeviceToDevice,
+                     ctx->s));
+  CKS(stage_solve(ctx, f, x, ctx->p.precision == RSC_MIXED));
+  return RSC_OK;
+}
 
 rsc_status rsc_autotune(rsc_ctx* ctx, rsc_tuning* out) {
   if (!ctx) return RSC_EINVAL;

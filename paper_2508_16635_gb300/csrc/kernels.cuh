@@ -1342,14 +1342,6 @@ __global__ void k_axpby(double a, const double* __restrict__ x, double b, double
     y[idx] = a * x[idx] + b * y[idx];
 }
 
-// out = y - u, except out[J] = y[J] (u_J is the drift unknown, Sec. 3.4)
-__global__ void k_sub_frozen(const double* __restrict__ y, const double* __restrict__ u, long J,
-                             double* __restrict__ out, long n) {
-  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-       idx += (long)gridDim.x * blockDim.x)
-    out[idx] = (idx == J) ? y[idx] : y[idx] - u[idx];
-}
-
 // Graph-replayed Jacobian action: the input and output vectors are reached
 // through pointers held in device memory (set by k_set_ptrs before each replay).
 __global__ void k_set_ptrs(const double** slots, const double* u, double* out) {

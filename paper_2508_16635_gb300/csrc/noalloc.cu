@@ -91,7 +91,19 @@ extern "C" rsc_status rsc_norm2_noalloc(const double* v, size_t n, double* out, 
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int nblk = (int)((n + kChunk - 1) / kChunk);
-  if (nblk > 0) k_sumsq_partials<<<nblk, kThreads, 0, s>>>(v, (long)n, scratch);
-  k_sumsq_finish<<<1, kThreads, 0, s>>>(scratch, nblk, out);
-  return cudaGetLastError() == cudaSuccess ? RSC_OK : RSC_ECUDA;
+  // Each launch is checked through its own return code: cudaGetLastError would also
+  // return (and clear) an error that unrelated code left pending on this thread.
+  long nl = (long)n;
+  if (nblk > 0) {
+    void* args1[] = {(void*)&v, (void*)&nl, (void*)&scratch};
+    if (cudaLaunchKernel((const void*)k_sumsq_partials, dim3(nblk), dim3(kThreads), args1, 0, s) !=
+        cudaSuccess)
+      return RSC_ECUDA;
+  }
+  int nb = nblk;
+  void* args2[] = {(void*)&scratch, (void*)&nb, (void*)&out};
+  if (cudaLaunchKernel((const void*)k_sumsq_finish, dim3(1), dim3(kThreads), args2, 0, s) !=
+      cudaSuccess)
+    return RSC_ECUDA;
+  return RSC_OK;
 }

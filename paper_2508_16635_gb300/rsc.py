@@ -27,7 +27,8 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_batch_create", "rsc_batch_destroy", "rsc_batch_size", "rsc_batch_context",
            "rsc_batch_last_error", "rsc_batch_apply_jacobian", "rsc_batch_newton_rw",
            "rsc_autotune", "rsc_get_tuning", "rsc_set_tuning", "rsc_batch_autotune",
-           "rsc_continue_ek", "rsc_spectral_tail", "rsc_regrid", "rsc_refine_params")
+           "rsc_continue_ek", "rsc_spectral_tail", "rsc_regrid", "rsc_refine_params",
+           "rsc_implicit_solve")
 NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
            "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
@@ -143,6 +144,7 @@ def load_library(path=LIB_PATH):
         "rsc_step": ([P, P, D, D, I], I),
         "rsc_step_host": ([P, P, D, D, I], I),
         "rsc_explicit_terms": ([P, P, P], I),
+        "rsc_implicit_solve": ([P, P, P, D], I),
         "rsc_apply_jacobian": ([P, P, D, ctypes.c_long, P, P, I, D], I),
         "rsc_newton_rw": ([P, P, ctypes.POINTER(D), ctypes.c_long, ctypes.POINTER(NewtonOpts),
                            ctypes.POINTER(NewtonReport)], I),
@@ -293,6 +295,14 @@ class RotatingShell:
         N = self.new_state()
         self._check(self.lib.rsc_explicit_terms(self._ctx, self._vec(U), _ptr(N)))
         return N
+
+    def implicit_solve(self, rhs, dt, out=None):
+        """x = (M/dt + K)^-1 rhs (rsc_implicit_solve); rhs holds values at the collocation
+        radii in the state layout, x Chebyshev coefficients."""
+        if out is None:
+            out = self.torch.empty_like(rhs)
+        self._check(self.lib.rsc_implicit_solve(self._ctx, self._vec(rhs), self._vec(out), dt))
+        return out
 
     def apply_jacobian(self, U, C, J, u, dt, out=None):
         count = u.numel() // self.n
@@ -505,6 +515,14 @@ class Batch:
 
     def synchronize(self):
         self.torch.cuda.synchronize(self.device)
+
+    def implicit_solve(self, rhs, dt, out=None):
+        """x = (M/dt + K)^-1 rhs (rsc_implicit_solve); rhs holds values at the collocation
+        radii in the state layout, x Chebyshev coefficients."""
+        if out is None:
+            out = self.torch.empty_like(rhs)
+        self._check(self.lib.rsc_implicit_solve(self._ctx, self._vec(rhs), self._vec(out), dt))
+        return out
 
     def apply_jacobian(self, U, C, J, u, dt, out=None):
         """Jacobian actions of every instance in one graph launch: u[i] holds `count`

@@ -54,3 +54,11 @@ def test_a_kernel_without_a_capture_reports_no_traffic():
     r = bench.roofline(prof, PEAKS, "mixed", {"chain_df": 4, "krylov_split": 1})
     assert r["traffic"] is None and r["traffic_source"] is None
     assert r["arithmetic"] == "FP32" and r["peak"] in (70.0, 6800.0)
+
+
+def test_dtype_label_says_what_ran():
+    assert bench.dtype_label("fp64", {"chain_df": 4, "krylov_split": 1}) == "f64"
+    lab = bench.dtype_label("mixed", {"chain_df": 2, "krylov_split": 1})
+    assert "double-float e/f chain solve" in lab and "double-float Krylov basis" in lab
+    lab = bench.dtype_label("mixed", {"chain_df": 0, "krylov_split": 0})
+    assert "f64 e/f chain solve" in lab and "f64 Krylov basis" in lab

@@ -35,14 +35,24 @@ def test_norm2_noalloc_matches_context_norm_on_two_calls(torch):
     rng = np.random.default_rng(77)
     # a ragged length spanning several blocks, then a second, shorter call that
     # must not see the first call's partial sums
-    for n in (3_000_001, 70_000):
-        v = torch.tensor(rng.standard_normal(n), device="cuda")
-        st = lib.rsc_norm2_noalloc(ctypes.c_void_p(v.data_ptr()), n,
+    vs = [torch.tensor(rng.standard_normal(n), device="cuda") for n in (3_000_001, 70_000)]
+    refs = [gpu.norm2(v) for v in vs]
+    # warm-up call: the first call on a device looks up the scratch array's address
+    assert lib.rsc_norm2_noalloc(ctypes.c_void_p(vs[1].data_ptr()), vs[1].numel(),
+                                 ctypes.c_void_p(out.data_ptr()), stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for v, ref in zip(vs, refs):
+        st = lib.rsc_norm2_noalloc(ctypes.c_void_p(v.data_ptr()), v.numel(),
                                    ctypes.c_void_p(out.data_ptr()), stream)
         assert st == 0
         torch.cuda.synchronize()
-        ref = gpu.norm2(v)
         assert abs(out.item() - ref) <= 1e-12 * ref
+    # the calls allocated no device memory (driver free bytes and torch's allocator)
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    v = vs[0]
     # sizes beyond the fixed scratch are rejected before any launch
     st = lib.rsc_norm2_noalloc(ctypes.c_void_p(v.data_ptr()), NORM2_NOALLOC_MAX_N + 1,
                                ctypes.c_void_p(out.data_ptr()), stream)
