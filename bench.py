@@ -311,6 +311,24 @@ def fp64_arm(torch, RotatingShell, w, K, nsteps=2):
             "ms_per_newton_iteration": tot_ms / nsteps, "tuning": tuning}
 
 
+def factor_timing(torch, RotatingShell, w, dt=200.0):
+    """Wall time of one factorisation of the implicit operator at dt (Sec. 3.2; Sec. 4.4
+    refactorises at every new Ek) on the GPU (FP64 block LU kernels) and on the host."""
+    out = {}
+    for where, flag in (("gpu", 1), ("host", 0)):
+        sh = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"])
+        sh.set_tuning(dict(sh.tuning(), factor_gpu=flag))
+        z = sh.new_state()
+        sh.implicit_solve(z, dt)
+        torch.cuda.synchronize()
+        sec, on_gpu = sh.factor_time()
+        out[where + "_s"] = sec
+        out[where + "_ran_on_gpu"] = on_gpu
+        sh.close()
+    out["host_cores"] = os.cpu_count()
+    return out
+
+
 def roofline(prof, peaks, precision, tuning):
     name = max(prof, key=lambda k: prof[k]["ms"])   # the only kernel timed in this pass
     p = prof[name]
@@ -936,6 +954,7 @@ def run_gpu(args):
             "clocks": clk.summary(),
             "wall_s_timed_region": wall,
         }
+        line["factorisation"] = factor_timing(torch, RotatingShell, w)
         if args.precision == "mixed":
             line["fp64_path"] = fp64_arm(torch, RotatingShell, w, K)
             line["mixed_over_fp64_jvps"] = value / world / line["fp64_path"]["jvps_per_s"]

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RSC_ABI_VERSION 6
+#define RSC_ABI_VERSION 7
 
 typedef struct rsc_ctx rsc_ctx;
 
@@ -172,6 +172,19 @@ rsc_status rsc_explicit_terms(rsc_ctx* ctx, const double* U, double* N);
  * are solved like its Jacobian actions (chain_df).  Factorises dt on first
  * use.  Returns RSC_EINVAL for a null pointer or dt <= 0.                   */
 rsc_status rsc_implicit_solve(rsc_ctx* ctx, const double* rhs, double* x, double dt);
+
+/* One block of the factorisation of dt (built first if needed), copied to the host
+ * (synchronous).  which = 0, 1, 2: G, H, W of block `index` (chains in the order
+ * (m index, class), blocks l = m .. L inside a chain; Nr x Nr complex row-major, 2 Nr^2
+ * doubles): the twisted block Thomas factors of Sec. 3.2 with G = D'^-1, H = D'^-1 A,
+ * W = D'^-1 C above the middle block of a chain, G = E'^-1, H = E'^-1 C, W = E'^-1 A
+ * below it, and G = Z, H = Z A, W = Z C at the middle block (A, C the couplings to
+ * l - 1, l + 1).  which = 3: the inverse of the temperature operator of degree
+ * l = index (Nr^2 doubles).  For checks of the factorisation.                     */
+rsc_status rsc_factor_block(rsc_ctx* ctx, double dt, int which, long index, double* out_host);
+
+/* Wall time (s) of the context's last factorisation and whether it ran on the GPU. */
+rsc_status rsc_factor_time(const rsc_ctx* ctx, double* seconds, int* on_gpu);
 
 /* Jacobian action of Sec. 3.3-3.4 for `count` directions:
  *   out_i = (B_U - I) u_i with the drift unknown c = u_i[J] (Sec. 3.4):
@@ -370,6 +383,11 @@ typedef struct {
                               factorisation then also computes the spikes on the host.
                               Changing it rebuilds the factorisations.  Not changed by
                               rsc_autotune.                                            */
+  int factor_gpu;          /* 1 (default): factorise the implicit operator on the GPU
+                              (FP64 block LU with row equilibration and partial
+                              pivoting inside each block, Sec. 3.2) when Nr <= 96 and
+                              chain_parts = 1; 0: on the host CPU (the same factors to
+                              rounding).  Changing it rebuilds the factorisations.     */
   double ms[6];            /* after rsc_autotune: best times (ms) of products +
                               analysis (mixed), FP64 synthesis, RHS (mixed), FP64 chain
                               solve, double-float chain solve (0 if none ran); zero

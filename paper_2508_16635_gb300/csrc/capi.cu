@@ -23,6 +23,7 @@
 #include "legendre_tc_analysis.cuh"
 #include "krylov_split.cuh"
 #include "chain_df.cuh"
+#include "factor_gpu.cuh"
 #include "rsc_internal.h"
 
 using namespace rsc;
@@ -97,6 +98,10 @@ struct rsc_ctx {
   double* vtmp = nullptr;
   double* rtmp = nullptr;
   double* ustate = nullptr;   // device copy of the state of the *_host calls
+  double* d_Ef[4] = {nullptr, nullptr, nullptr, nullptr};   // E0, E1, E2, E4 row-major [j][k]
+  int factor_gpu = 1;          // 1: factorise on the GPU (k_factor_*), 0: on the host
+  double factor_s = 0.0;       // wall time of the last factorisation (s)
+  int factor_on_gpu = 0;       // where the last factorisation ran
   // factorisations, two slots (time stepping dt and Newton dt)
   DevFactor fac[2];
   int fac_next = 0;
@@ -462,6 +467,89 @@ rsc_status set_smem_limits(rsc_ctx* ctx) {
   return RSC_OK;
 }
 
+// Whether the factorisation runs on the device: the GPU kernels hold one block of up to
+// kFacMaxNr rows in shared memory and build unpartitioned chains (the spikes of partitioned
+// chains come from the host routine).
+bool factor_on_device(const rsc_ctx* ctx) {
+  return ctx->factor_gpu && ctx->d.Nr <= kFacMaxNr && ctx->chain_parts == 1;
+}
+
+// The factors of one dt on the device (factor_gpu.cuh), FP64, and their double-float
+// copies on a mixed-precision context.
+rsc_status gpu_factor(rsc_ctx* ctx, double dt, DevFactor& f) {
+  const Dims& d = ctx->d;
+  const int nchains = 2 * d.nm;
+  std::vector<long> off(nchains + 1);
+  long o = 0;
+  for (int c = 0; c < nchains; ++c) {
+    off[c] = o;
+    o += d.L - ctx->t.m_of[c / 2] + 1;
+  }
+  off[nchains] = o;
+  const size_t blk = (size_t)d.Nr * d.Nr;
+  const size_t nent = (size_t)o * blk;
+  CKS(upload(ctx, &f.chain_off, off.data(), off.size()));
+  CK(cudaMalloc(&f.G, nent * sizeof(double2)));
+  CK(cudaMalloc(&f.H, nent * sizeof(double2)));
+  CK(cudaMalloc(&f.W, nent * sizeof(double2)));
+  CK(cudaMalloc(&f.Tinv, (size_t)(d.L + 1) * blk * sizeof(double)));
+  CK(cudaMemsetAsync(f.H, 0, nent * sizeof(double2), ctx->s));   // H of the end blocks stays 0
+  CK(cudaMemsetAsync(f.W, 0, nent * sizeof(double2), ctx->s));
+  int* status = nullptr;
+  CK(cudaMalloc(&status, (nchains + 1) * sizeof(int)));
+  CK(cudaMemsetAsync(status, 0, (nchains + 1) * sizeof(int), ctx->s));
+  FacGeom g;
+  g.Nr = d.Nr;
+  g.L = d.L;
+  g.nm = d.nm;
+  g.m_of = ctx->d_m_of;
+  g.chain_off = f.chain_off;
+  g.rc = ctx->d_rc;
+  g.E0 = ctx->d_Ef[0];
+  g.E1 = ctx->d_Ef[1];
+  g.E2 = ctx->d_Ef[2];
+  g.E4 = ctx->d_Ef[3];
+  g.Ek = ctx->p.Ek;
+  g.Pr = ctx->p.Pr;
+  g.inv_dt = std::isfinite(dt) ? 1.0 / dt : 0.0;
+  g.explicit_coriolis = ctx->p.explicit_coriolis ? 1 : 0;
+  const size_t smem = fac_smem_bytes(d.Nr);
+  for (const void* fn : {(const void*)k_factor_half, (const void*)k_factor_mid, (const void*)k_factor_temp})
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  double2* G = reinterpret_cast<double2*>(f.G);
+  double2* H = reinterpret_cast<double2*>(f.H);
+  double2* W = reinterpret_cast<double2*>(f.W);
+  k_factor_temp<<<d.L + 1, kFacThreads, smem, ctx->s>>>(g, f.Tinv, status + nchains);
+  CK(cudaGetLastError());
+  k_factor_half<<<2 * nchains, kFacThreads, smem, ctx->s>>>(g, G, H, W, status);
+  CK(cudaGetLastError());
+  k_factor_mid<<<nchains, kFacThreads, smem, ctx->s>>>(g, G, H, W, status);
+  CK(cudaGetLastError());
+  ctx->launches += 3;
+  if (ctx->p.precision == RSC_MIXED) {
+    CK(cudaMalloc(&f.Gs, nent * sizeof(float4)));
+    CK(cudaMalloc(&f.Hs, nent * sizeof(float4)));
+    CK(cudaMalloc(&f.Ws, nent * sizeof(float4)));
+    const int nb = (int)std::min<size_t>((nent + 255) / 256, 152 * 32);
+    k_split_factor<<<nb, 256, 0, ctx->s>>>(G, f.Gs, (long)nent);
+    k_split_factor<<<nb, 256, 0, ctx->s>>>(H, f.Hs, (long)nent);
+    k_split_factor<<<nb, 256, 0, ctx->s>>>(W, f.Ws, (long)nent);
+    CK(cudaGetLastError());
+    ctx->launches += 3;
+  }
+  std::vector<int> hs(nchains + 1);
+  CK(cudaMemcpyAsync(hs.data(), status, hs.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  cudaFree(status);
+  for (int c = 0; c <= nchains; ++c)
+    if (hs[c]) {
+      ctx->err = c < nchains ? "singular block in the implicit operator (chain " + std::to_string(c) + ")"
+                             : std::string("singular temperature block");
+      return RSC_ESINGULAR;
+    }
+  return RSC_OK;
+}
+
 rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
   for (auto& f : ctx->fac)
     if (f.valid && f.dt == dt) {
@@ -476,6 +564,16 @@ rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
     ctx->jvp_exec = nullptr;
   }
   free_factor(f);
+  const auto t_fac0 = std::chrono::steady_clock::now();
+  if (factor_on_device(ctx)) {
+    CKS(gpu_factor(ctx, dt, f));
+    ctx->factor_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_fac0).count();
+    ctx->factor_on_gpu = 1;
+    f.dt = dt;
+    f.valid = true;
+    *out = &f;
+    return RSC_OK;
+  }
   HostFactor hf;
   const int bad = build_factor(ctx->p, ctx->d, ctx->t, dt, hf);
   if (bad) {
@@ -531,6 +629,8 @@ rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
       CKS(split_upload(hf.W, &f.Ws));
     }
   }
+  ctx->factor_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_fac0).count();
+  ctx->factor_on_gpu = 0;
   f.dt = dt;
   f.valid = true;
   *out = &f;
@@ -1548,6 +1648,7 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
   if (t.analysis_tc != 0 && t.analysis_tc != 1) return false;
   if (t.krylov_split != 0 && t.krylov_split != 1) return false;
   if (t.chain_parts < 1 || t.chain_parts > kMaxChainParts) return false;
+  if (t.factor_gpu != 0 && t.factor_gpu != 1) return false;
   if (!chain_df_ok(d, t.chain_df_cluster, t.chain_df)) return false;
   return chain_config_ok(d, t.chain_cluster, t.chain_async);
 }
@@ -1573,6 +1674,7 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
   t->chain_df_cluster = ctx->cluster_df;
   t->krylov_split = ctx->krylov_split;
   t->chain_parts = ctx->chain_parts;
+  t->factor_gpu = ctx->factor_gpu;
   for (int q = 0; q < 6; ++q) t->ms[q] = ctx->tune_ms[q];
 }
 
@@ -1591,6 +1693,12 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
   ctx->chain_df = t.chain_df;
   ctx->cluster_df = t.chain_df_cluster;
   ctx->krylov_split = t.krylov_split;
+  if (t.factor_gpu != ctx->factor_gpu) {
+    // the factorisations are rebuilt where the new setting says
+    ctx->factor_gpu = t.factor_gpu;
+    cudaStreamSynchronize(ctx->s);
+    for (auto& f : ctx->fac) free_factor(f);
+  }
   if (t.chain_parts != ctx->chain_parts) {
     // another partition of the double-float solve: both factorisation slots are rebuilt
     ctx->chain_parts = t.chain_parts;
@@ -1877,6 +1985,10 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
     auto e0 = transpose(t.Ec[0], d.Nr, d.Nr), e2 = transpose(t.Ec[2], d.Nr, d.Nr);
     auto e1 = transpose(t.Ec[1], d.Nr, d.Nr);
     UP(ctx->d_EcT1, e1);
+    UP(ctx->d_Ef[0], t.Ec[0]);
+    UP(ctx->d_Ef[1], t.Ec[1]);
+    UP(ctx->d_Ef[2], t.Ec[2]);
+    UP(ctx->d_Ef[3], t.Ec[4]);
     auto d0 = transpose(t.Ed[0], d.Nd, d.Nr), d1 = transpose(t.Ed[1], d.Nd, d.Nr),
          d2 = transpose(t.Ed[2], d.Nd, d.Nr);
     auto r0 = transpose(t.R0, d.Nr, d.Nd), r1 = transpose(t.R1, d.Nr, d.Nd);
@@ -1974,7 +2086,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->UG, ctx->FA,
-                  ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->ustate, ctx->V, ctx->Vs, ctx->partial,
+                  ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->ustate, ctx->d_Ef[0], ctx->d_Ef[1], ctx->d_Ef[2], ctx->d_Ef[3], ctx->V, ctx->Vs, ctx->partial,
                   ctx->dots, ctx->AR0, ctx->ta_tiles, ctx->ta_off, ctx->cont_hist, ctx->cont_cond, ctx->amax_v, ctx->amax_i, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
   for (void* b : bufs) cudaFree(b);
   for (int q = 0; q < 8; ++q) {
@@ -2226,6 +2338,35 @@ rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
   CK(cudaMemcpyAsync(U_host, ctx->ustate, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
   return st;
+}
+
+rsc_status rsc_factor_block(rsc_ctx* ctx, double dt, int which, long index, double* out_host) {
+  if (!ctx || !out_host || which < 0 || which > 3 || index < 0 || !(dt > 0) || !std::isfinite(dt))
+    return RSC_EINVAL;
+  const Dims& d = ctx->d;
+  const size_t blk = (size_t)d.Nr * d.Nr;
+  long nblk = 0;
+  for (int a = 0; a < d.nm; ++a) nblk += 2L * (d.L - ctx->t.m_of[a] + 1);
+  if ((which < 3 && index >= nblk) || (which == 3 && index > d.L)) return RSC_EINVAL;
+  DevFactor* f = nullptr;
+  CKS(get_factor(ctx, dt, &f));
+  if (which == 3)
+    CK(cudaMemcpyAsync(out_host, f->Tinv + index * blk, blk * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->s));
+  else {
+    const double2* src = which == 0 ? f->G : which == 1 ? f->H : f->W;
+    CK(cudaMemcpyAsync(out_host, src + index * blk, blk * sizeof(double2), cudaMemcpyDeviceToHost,
+                       ctx->s));
+  }
+  CK(cudaStreamSynchronize(ctx->s));
+  return RSC_OK;
+}
+
+rsc_status rsc_factor_time(const rsc_ctx* ctx, double* seconds, int* on_gpu) {
+  if (!ctx) return RSC_EINVAL;
+  if (seconds) *seconds = ctx->factor_s;
+  if (on_gpu) *on_gpu = ctx->factor_on_gpu;
+  return RSC_OK;
 }
 
 rsc_status rsc_implicit_solve(rsc_ctx* ctx, const double* rhs, double* x, double dt) {

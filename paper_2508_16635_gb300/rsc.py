@@ -28,7 +28,7 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_batch_last_error", "rsc_batch_apply_jacobian", "rsc_batch_newton_rw",
            "rsc_autotune", "rsc_get_tuning", "rsc_set_tuning", "rsc_batch_autotune",
            "rsc_continue_ek", "rsc_spectral_tail", "rsc_regrid", "rsc_refine_params",
-           "rsc_implicit_solve")
+           "rsc_implicit_solve", "rsc_factor_block", "rsc_factor_time")
 NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
            "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
@@ -54,7 +54,8 @@ class Tuning(ctypes.Structure):
                 ("chain_cluster", ctypes.c_int), ("analysis_tc", ctypes.c_int),
                 ("chain_async", ctypes.c_int), ("chain_df", ctypes.c_int),
                 ("chain_df_cluster", ctypes.c_int), ("krylov_split", ctypes.c_int),
-                ("chain_parts", ctypes.c_int), ("ms", ctypes.c_double * 6)]
+                ("chain_parts", ctypes.c_int), ("factor_gpu", ctypes.c_int),
+                ("ms", ctypes.c_double * 6)]
 
     def as_dict(self):
         return {"products_warps": list(self.products_warps),
@@ -65,7 +66,7 @@ class Tuning(ctypes.Structure):
                 "analysis_tc": self.analysis_tc, "chain_async": self.chain_async,
                 "chain_df": self.chain_df, "chain_df_cluster": self.chain_df_cluster,
                 "krylov_split": self.krylov_split, "chain_parts": self.chain_parts,
-                "ms": list(self.ms)}
+                "factor_gpu": self.factor_gpu, "ms": list(self.ms)}
 
 
 class ContinuationOpts(ctypes.Structure):
@@ -145,6 +146,8 @@ def load_library(path=LIB_PATH):
         "rsc_step_host": ([P, P, D, D, I], I),
         "rsc_explicit_terms": ([P, P, P], I),
         "rsc_implicit_solve": ([P, P, P, D], I),
+        "rsc_factor_block": ([P, D, I, ctypes.c_long, P], I),
+        "rsc_factor_time": ([P, ctypes.POINTER(D), ctypes.POINTER(I)], I),
         "rsc_apply_jacobian": ([P, P, D, ctypes.c_long, P, P, I, D], I),
         "rsc_newton_rw": ([P, P, ctypes.POINTER(D), ctypes.c_long, ctypes.POINTER(NewtonOpts),
                            ctypes.POINTER(NewtonReport)], I),
@@ -304,6 +307,25 @@ class RotatingShell:
         self._check(self.lib.rsc_implicit_solve(self._ctx, self._vec(rhs), self._vec(out), dt))
         return out
 
+    def factor_block(self, dt, which, index):
+        """One factor block as a numpy array (rsc_factor_block): which in "G", "H", "W"
+        (complex Nr x Nr, block `index` over all chains) or "T" (real, degree `index`)."""
+        import numpy as np
+        w = {"G": 0, "H": 1, "W": 2, "T": 3}[which]
+        Nr = self.Nr
+        buf = np.empty(Nr * Nr * (1 if w == 3 else 2))
+        self._check(self.lib.rsc_factor_block(self._ctx, dt, w, index,
+                                              ctypes.c_void_p(buf.ctypes.data)))
+        if w == 3:
+            return buf.reshape(Nr, Nr)
+        return (buf[0::2] + 1j * buf[1::2]).reshape(Nr, Nr)
+
+    def factor_time(self):
+        """(seconds, on_gpu) of the last factorisation (rsc_factor_time)."""
+        sec, on = ctypes.c_double(), ctypes.c_int()
+        self._check(self.lib.rsc_factor_time(self._ctx, ctypes.byref(sec), ctypes.byref(on)))
+        return sec.value, bool(on.value)
+
     def apply_jacobian(self, U, C, J, u, dt, out=None):
         count = u.numel() // self.n
         if out is None:
@@ -390,6 +412,7 @@ class RotatingShell:
         t.chain_df_cluster = d.get("chain_df_cluster", cur["chain_df_cluster"])
         t.krylov_split = d.get("krylov_split", cur["krylov_split"])
         t.chain_parts = d.get("chain_parts", cur["chain_parts"])
+        t.factor_gpu = d.get("factor_gpu", cur["factor_gpu"])
         self._check(self.lib.rsc_set_tuning(self._ctx, ctypes.byref(t)))
 
     def continue_ra(self, U, C, J, Ra0, Ra1, Ra_end, n_opt=4, gamma=20.0, max_points=8,
@@ -523,6 +546,25 @@ class Batch:
             out = self.torch.empty_like(rhs)
         self._check(self.lib.rsc_implicit_solve(self._ctx, self._vec(rhs), self._vec(out), dt))
         return out
+
+    def factor_block(self, dt, which, index):
+        """One factor block as a numpy array (rsc_factor_block): which in "G", "H", "W"
+        (complex Nr x Nr, block `index` over all chains) or "T" (real, degree `index`)."""
+        import numpy as np
+        w = {"G": 0, "H": 1, "W": 2, "T": 3}[which]
+        Nr = self.Nr
+        buf = np.empty(Nr * Nr * (1 if w == 3 else 2))
+        self._check(self.lib.rsc_factor_block(self._ctx, dt, w, index,
+                                              ctypes.c_void_p(buf.ctypes.data)))
+        if w == 3:
+            return buf.reshape(Nr, Nr)
+        return (buf[0::2] + 1j * buf[1::2]).reshape(Nr, Nr)
+
+    def factor_time(self):
+        """(seconds, on_gpu) of the last factorisation (rsc_factor_time)."""
+        sec, on = ctypes.c_double(), ctypes.c_int()
+        self._check(self.lib.rsc_factor_time(self._ctx, ctypes.byref(sec), ctypes.byref(on)))
+        return sec.value, bool(on.value)
 
     def apply_jacobian(self, U, C, J, u, dt, out=None):
         """Jacobian actions of every instance in one graph launch: u[i] holds `count`

@@ -706,6 +706,47 @@ def test_implicit_solve_backward_error_double_float(torch, name, L, Ms, Nr, Ek, 
 
 
 @pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES_C3)
+@pytest.mark.parametrize("dt", [2e-3, 200.0])
+def test_gpu_factorisation_matches_the_host_factors(torch, name, L, Ms, Nr, Ek, Ra, dt):
+    """The FP64 block factorisation on the GPU (factor_gpu = 1, the default) against the
+    host routine (factor_gpu = 0), block by block: G, H, W of every chain block and the
+    temperature inverses.  The two sum in different orders; the factors' sensitivity to
+    rounding is the condition number of the equilibrated blocks D' (up to about 1e6 at
+    L = 127, N_r = 64), so blocks agree to 1e-9 of their largest entry and the temperature
+    inverses (condition about 1e4) to 1e-11; both factorisations then pass the solve's
+    backward-error check."""
+    from paper_2508_16635_gb300 import RotatingShell
+    s = _shell(L, Ms, Nr, Ek, Ra)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra)
+    host = RotatingShell(L, Ms, Nr, Ek, Ra)
+    host.set_tuning(dict(host.tuning(), factor_gpu=0))
+    assert gpu.tuning()["factor_gpu"] == 1
+    nblk = 2 * s.P
+    worst = {"G": 0.0, "H": 0.0, "W": 0.0}
+    for b in range(nblk):
+        for w in ("G", "H", "W"):
+            a, h = gpu.factor_block(dt, w, b), host.factor_block(dt, w, b)
+            scale = np.abs(h).max()
+            if scale == 0.0:
+                assert np.abs(a).max() == 0.0, (w, b)
+                continue
+            worst[w] = max(worst[w], float(np.abs(a - h).max() / scale))
+    assert gpu.factor_time()[1] and not host.factor_time()[1]
+    assert max(worst.values()) < 1e-9, worst
+    for l in range(L + 1):
+        a, h = gpu.factor_block(dt, "T", l), host.factor_block(dt, "T", l)
+        assert np.abs(a - h).max() < 1e-11 * np.abs(h).max(), l
+    b = _random_rhs(s, 99 + L)
+    for ctx in (gpu, host):
+        x = s.to_complex(ctx.implicit_solve(torch.tensor(s.to_real(b), device="cuda"), dt)
+                         .cpu().numpy())
+        eta, fwd, fwd_T = _solve_errors(s, dt, b, x)
+        assert eta < 64 * U64 and fwd < 1e-11 and fwd_T < 1e-12, (eta / U64, fwd, fwd_T)
+    gpu.close()
+    host.close()
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES_C3)
 def test_double_float_chain_solve_against_the_oracle(torch, name, L, Ms, Nr, Ek, Ra):
     """The mixed Jacobian action with the double-float chain solve against the FP64 oracle, at
     the mixed-path bound (the FP32 transforms dominate): 5e-5 per field."""
