@@ -388,6 +388,14 @@ typedef struct {
                               pivoting inside each block, Sec. 3.2) when Nr <= 96 and
                               chain_parts = 1; 0: on the host CPU (the same factors to
                               rounding).  Changing it rebuilds the factorisations.     */
+  int refine;              /* 0 to 2 (default 1): steps of iterative refinement after every
+                              FP64 e/f chain solve (steps, Newton residuals, Jacobian actions
+                              of the FP64 path, rsc_implicit_solve on an FP64 context):
+                              r = b - (M/dt + K) x in FP64, x += solve(r).  The sweeps
+                              multiply by explicit block inverses, which at Ek = 1e-5 leaves
+                              relative errors up to 1e-8 in the small poloidal field of
+                              the m = 0 chains; one step removes them.  The double-float
+                              solve of the mixed path is not refined.                  */
   double ms[6];            /* after rsc_autotune: best times (ms) of products +
                               analysis (mixed), FP64 synthesis, RHS (mixed), FP64 chain
                               solve, double-float chain solve (0 if none ran); zero

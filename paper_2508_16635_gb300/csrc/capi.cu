@@ -100,6 +100,8 @@ struct rsc_ctx {
   double* ustate = nullptr;   // device copy of the state of the *_host calls
   double* d_Ef[4] = {nullptr, nullptr, nullptr, nullptr};   // E0, E1, E2, E4 row-major [j][k]
   int factor_gpu = 1;          // 1: factorise on the GPU (k_factor_*), 0: on the host
+  int refine = 1;              // iterative-refinement steps of every FP64 e/f chain solve
+  double* ref_tmp = nullptr;   // correction of a refinement step
   double factor_s = 0.0;       // wall time of the last factorisation (s)
   int factor_on_gpu = 0;       // where the last factorisation ran
   // factorisations, two slots (time stepping dt and Newton dt)
@@ -926,12 +928,13 @@ void launch_gemv_df(rsc_ctx* ctx, const DevFactor* f, double* out) {
 
 // df: the double-float GEMV and sweeps (mixed path, when the context has double-float tables
 // and chain_df is on); otherwise the FP64 kernels.
-rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = false) {
+rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = false,
+                       bool temp = true) {
   df = df && f->Gs && f->Hs && f->Ws && ctx->chain_df != 0;
   const Dims& d = ctx->d;
   // the temperature solve depends only on the right-hand side: it runs on a second stream
   // beside the e/f chain solve (sequentially while tracing, so that every launch is timed)
-  const bool fork = !ctx->prof_on;
+  const bool fork = !ctx->prof_on && temp;
   if (fork) {
     if (!ctx->s2) {
       CK(cudaStreamCreateWithFlags(&ctx->s2, cudaStreamNonBlocking));
@@ -992,12 +995,75 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = 
     CK(cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0));
     return RSC_OK;
   }
+  if (!temp) return RSC_OK;
   KSpan sp(ctx, RSC_K_TEMP, (double)(d.L + 1) * d.Nr * d.Nr * 8.0 + 2.0 * d.P * d.Nr * 16.0,
            4.0 * d.P * d.Nr * d.Nr);
   k_temp_solve<<<d.P, round32(d.Nr), (size_t)d.Nr * sizeof(double2), ctx->s>>>(
       ctx->geom(), f->Tinv, ctx->rhs, reinterpret_cast<double2*>(out));
   CK(cudaGetLastError());
   return RSC_OK;
+}
+
+rsc_status launch_1d_grid(long n, int* blocks) {
+  *blocks = (int)std::min<long>((n + 255) / 256, 152L * 8);
+  return RSC_OK;
+}
+
+FacGeom fac_geom(const rsc_ctx* ctx, double dt) {
+  FacGeom g;
+  g.Nr = ctx->d.Nr;
+  g.L = ctx->d.L;
+  g.nm = ctx->d.nm;
+  g.m_of = ctx->d_m_of;
+  g.chain_off = nullptr;
+  g.rc = ctx->d_rc;
+  g.E0 = ctx->d_Ef[0];
+  g.E1 = ctx->d_Ef[1];
+  g.E2 = ctx->d_Ef[2];
+  g.E4 = ctx->d_Ef[3];
+  g.Ek = ctx->p.Ek;
+  g.Pr = ctx->p.Pr;
+  g.inv_dt = std::isfinite(dt) ? 1.0 / dt : 0.0;
+  g.explicit_coriolis = ctx->p.explicit_coriolis ? 1 : 0;
+  return g;
+}
+
+// The FP64 chain solve followed by ctx->refine steps of iterative refinement of the e/f
+// chains: r = b - (M/dt + K) x with b in ctx->rhs (overwritten by r), x += solve(r).  The
+// block Thomas sweeps multiply by explicit inverses of the equilibrated blocks; one step
+// with an FP64 residual restores the accuracy of a pivoted LU (factor_gpu.cuh).
+rsc_status stage_solve_fp64(rsc_ctx* ctx, const DevFactor* f, double* out) {
+  CKS(stage_solve(ctx, f, out, false));
+  const Dims& d = ctx->d;
+  const long nef = 4L * d.P * d.Nr;   // doubles of the e and f fields
+  int nb;
+  launch_1d_grid(nef, &nb);
+  for (int it = 0; it < ctx->refine; ++it) {
+    {
+      KSpan sp(ctx, RSC_K_CHAIN, 3.0 * d.n() * 8.0 + 4.0 * d.Nr * d.Nr * 8.0,
+               2.0 * d.P * d.Nr * d.Nr * 12.0);
+      k_chain_residual<<<d.P, dim3(round32(d.Nr), 2), 6 * (size_t)d.Nr * sizeof(double2), ctx->s>>>(
+          fac_geom(ctx, f->dt), ctx->d_pair_l, ctx->d_pair_m, d.P,
+          reinterpret_cast<const double2*>(out), ctx->rhs);
+      CK(cudaGetLastError());
+    }
+    CKS(stage_solve(ctx, f, ctx->ref_tmp, false, false));
+    {
+      KSpan sp(ctx, RSC_K_BLAS, 24.0 * nef, 2.0 * nef);
+      k_axpby<<<nb, 256, 0, ctx->s>>>(1.0, ctx->ref_tmp, 1.0, out, nef);
+      CK(cudaGetLastError());
+    }
+  }
+  return RSC_OK;
+}
+
+// The solve of a step or Jacobian action in transform precision R: the refined FP64 solve
+// for R = double, the solve of the mixed path (double-float chains unless chain_df = 0)
+// for R = float.
+template <typename R>
+rsc_status stage_solve_path(rsc_ctx* ctx, const DevFactor* f, double* out) {
+  if (sizeof(R) == 8) return stage_solve_fp64(ctx, f, out);
+  return stage_solve(ctx, f, out, true);
 }
 
 bool cluster_ok_pair(const Dims& d, int CS, int NS, const void* const (&fns)[2]);
@@ -1169,14 +1235,11 @@ rsc_status do_step(rsc_ctx* ctx, double* U, double C, double dt) {
   CKS(stage_synth<R>(ctx, U, ctx->FC));
   CKS(stage_products_analysis<R>(ctx, false));
   CKS(stage_rhs<R>(ctx, make_rp(ctx, dt, C, 0), U, nullptr, nullptr, ctx->rhs));
-  CKS(stage_solve(ctx, f, U, sizeof(R) == 4));
+  CKS(stage_solve_path<R>(ctx, f, U));
   return RSC_OK;
 }
 
-rsc_status launch_1d_grid(long n, int* blocks) {
-  *blocks = (int)std::min<long>((n + 255) / 256, 152L * 8);
-  return RSC_OK;
-}
+
 
 // One second-order step in the laboratory frame, in place (Crank-Nicolson for the
 // implicit operator, Heun's predictor-corrector for the explicit terms; the time-stepping
@@ -1202,7 +1265,7 @@ rsc_status do_step2(rsc_ctx* ctx, double* U, double dt) {
   CKS(stage_products_analysis<R>(ctx, false));
   CK(cudaMemcpyAsync(ctx->AR0, ctx->AR, nar * sizeof(V), cudaMemcpyDeviceToDevice, ctx->s));
   CKS(stage_rhs<R>(ctx, rp, U, nullptr, nullptr, ctx->rhs));
-  CKS(stage_solve(ctx, f, ctx->vtmp, sizeof(R) == 4));
+  CKS(stage_solve_path<R>(ctx, f, ctx->vtmp));
   {
     KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
     k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, U, 2.0, ctx->vtmp, n);
@@ -1224,7 +1287,7 @@ rsc_status do_step2(rsc_ctx* ctx, double* U, double dt) {
     CK(cudaGetLastError());
   }
   CKS(stage_rhs<R>(ctx, rp, U, nullptr, nullptr, ctx->rhs, ctx->xtmp));
-  CKS(stage_solve(ctx, f, ctx->vtmp, sizeof(R) == 4));
+  CKS(stage_solve_path<R>(ctx, f, ctx->vtmp));
   {
     KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
     k_axpby<<<nb, 256, 0, ctx->s>>>(2.0, ctx->vtmp, -1.0, U, n);
@@ -1283,7 +1346,7 @@ rsc_status do_jvp_eager(rsc_ctx* ctx, const double* U, double C, long J, const d
   RhsParams rp = make_rp(ctx, dt, C, 1);
   rp.J = J;  // c = u[J] is read on the device
   CKS(stage_rhs<R>(ctx, rp, ctx->xtmp, U, u, ctx->rhs));
-  CKS(stage_solve(ctx, f, out, sizeof(R) == 4));
+  CKS(stage_solve_path<R>(ctx, f, out));
   {
     KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
     k_axpby<<<nb, 256, 0, ctx->s>>>(-1.0, ctx->xtmp, 1.0, out, n);
@@ -1309,7 +1372,7 @@ rsc_status jvp_body_indirect(rsc_ctx* ctx, const double* U, double C, long J, De
   RhsParams rp = make_rp(ctx, dt, C, 1);
   rp.J = J >= 0 ? 0 : -1;  // c is read from d_cslot[0]
   CKS(stage_rhs<R>(ctx, rp, ctx->xtmp, U, ctx->d_cslot, ctx->rhs));
-  CKS(stage_solve(ctx, f, ctx->jvp_y, sizeof(R) == 4));
+  CKS(stage_solve_path<R>(ctx, f, ctx->jvp_y));
   {
     KSpan sp(ctx, RSC_K_BLAS, 24.0 * n, 2.0 * n);
     k_finish_ind<<<nb, 256, 0, ctx->s>>>(ctx->d_slots, ctx->jvp_y, ctx->xtmp, n);
@@ -1649,6 +1712,7 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
   if (t.krylov_split != 0 && t.krylov_split != 1) return false;
   if (t.chain_parts < 1 || t.chain_parts > kMaxChainParts) return false;
   if (t.factor_gpu != 0 && t.factor_gpu != 1) return false;
+  if (t.refine < 0 || t.refine > 2) return false;
   if (!chain_df_ok(d, t.chain_df_cluster, t.chain_df)) return false;
   return chain_config_ok(d, t.chain_cluster, t.chain_async);
 }
@@ -1675,6 +1739,7 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
   t->krylov_split = ctx->krylov_split;
   t->chain_parts = ctx->chain_parts;
   t->factor_gpu = ctx->factor_gpu;
+  t->refine = ctx->refine;
   for (int q = 0; q < 6; ++q) t->ms[q] = ctx->tune_ms[q];
 }
 
@@ -1693,6 +1758,7 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
   ctx->chain_df = t.chain_df;
   ctx->cluster_df = t.chain_df_cluster;
   ctx->krylov_split = t.krylov_split;
+  ctx->refine = t.refine;
   if (t.factor_gpu != ctx->factor_gpu) {
     // the factorisations are rebuilt where the new setting says
     ctx->factor_gpu = t.factor_gpu;
@@ -2060,6 +2126,7 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
   if ((st = alloc((void**)&ctx->vtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->rtmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   if ((st = alloc((void**)&ctx->ustate, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
+  if ((st = alloc((void**)&ctx->ref_tmp, (size_t)n * sizeof(double))) != RSC_OK) return fail(st);
   ctx->nblk_dot = (int)std::max<long>((n + 1023) / 1024, 152L * 8);   // pass-A chunks, pass-B blocks
   if ((st = alloc((void**)&ctx->partial, (size_t)ctx->nblk_dot * (2 * kMaxKrylov + 4) * sizeof(double))) != RSC_OK)
     return fail(st);
@@ -2086,7 +2153,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
                   ctx->d_rc, ctx->d_rd, ctx->d_EcT0, ctx->d_EcT2, ctx->d_EdT0, ctx->d_EdT1,
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->UG, ctx->FA,
-                  ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->ustate, ctx->d_Ef[0], ctx->d_Ef[1], ctx->d_Ef[2], ctx->d_Ef[3], ctx->V, ctx->Vs, ctx->partial,
+                  ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->ustate, ctx->ref_tmp, ctx->d_Ef[0], ctx->d_Ef[1], ctx->d_Ef[2], ctx->d_Ef[3], ctx->V, ctx->Vs, ctx->partial,
                   ctx->dots, ctx->AR0, ctx->ta_tiles, ctx->ta_off, ctx->cont_hist, ctx->cont_cond, ctx->amax_v, ctx->amax_i, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
   for (void* b : bufs) cudaFree(b);
   for (int q = 0; q < 8; ++q) {
@@ -2375,7 +2442,10 @@ rsc_status rsc_implicit_solve(rsc_ctx* ctx, const double* rhs, double* x, double
   CKS(get_factor(ctx, dt, &f));
   CK(cudaMemcpyAsync(ctx->rhs, rhs, (size_t)ctx->d.n() * sizeof(double), cudaMemcpyDeviceToDevice,
                      ctx->s));
-  CKS(stage_solve(ctx, f, x, ctx->p.precision == RSC_MIXED));
+  if (ctx->p.precision == RSC_MIXED)
+    CKS(stage_solve(ctx, f, x, true));
+  else
+    CKS(stage_solve_fp64(ctx, f, x));
   return RSC_OK;
 }
 

@@ -457,6 +457,97 @@ __global__ void __launch_bounds__(kFacThreads) k_factor_temp(FacGeom g, double* 
   }
 }
 
+// Residual of the e/f chains, for iterative refinement of the FP64 chain solve:
+// r = b - (M/dt + K) x on the e and f rows (the operator of fac_diag / fac_coupling_row
+// applied to x through the Chebyshev tables: D x needs E0 x, E1 x, E2 x, E4 x of the
+// pair's own coefficients, the couplings E0 x and E1 x of the other potential at l - 1 and
+// l + 1), in place over rb (b on entry, r on exit); the temperature rows are set to 0.
+// The block Thomas sweeps multiply by explicit block inverses, which is not backward
+// stable: at Ek = 1e-5 the small poloidal field f of the m = 0 chains can carry relative
+// errors of 1e-8.  One refinement step x += solve(r) with this FP64 residual brings the
+// solution to the accuracy of a pivoted banded LU (1e-15 on the same chains).
+// grid = P (one CTA per pair), block = (round32(Nr), 2): threadIdx.y = field e / f.
+__global__ void k_chain_residual(FacGeom g, const int* __restrict__ pair_l,
+                                 const int* __restrict__ pair_m, int P,
+                                 const double2* __restrict__ x, double2* __restrict__ rb) {
+  extern __shared__ double2 xs_[];   // [fld][pair offset -1, 0, +1][Nr]
+  const int Nr = g.Nr, p = blockIdx.x;
+  const int l = pair_l[p], m = pair_m[p];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  for (int idx = tid; idx < 6 * Nr; idx += nt) {
+    const int fld = idx / (3 * Nr), o = (idx / Nr) % 3 - 1, k = idx % Nr;
+    const int l2 = l + o;
+    double2 v = make_double2(0.0, 0.0);
+    if (l2 >= m && l2 <= g.L) v = x[((long)fld * P + p + o) * Nr + k];
+    xs_[idx] = v;
+  }
+  __syncthreads();
+  const int j = threadIdx.x, fld = threadIdx.y;
+  if (j >= Nr) return;
+  const long row = ((long)fld * P + p) * Nr + j;
+  if (fld == 0) rb[((long)2 * P + p) * Nr + j] = make_double2(0.0, 0.0);
+  const double2* xo = xs_ + (fld * 3 + 1) * Nr;   // own coefficients at l
+  double2 Ax;
+  if (l == 0) {
+    Ax = xo[j];
+  } else {
+    double2 e0 = {0, 0}, e1 = {0, 0}, e2 = {0, 0}, e4 = {0, 0};
+    // rows of the tables: interior rows use row j; the boundary rows their wall rows
+    const bool bc = (j == 0 || j == Nr - 1) || (fld == 1 && (j == 1 || j == Nr - 2));
+    const int jr = (j <= 1) ? 0 : (j >= Nr - 2 ? Nr - 1 : j);
+    const int rr = bc ? jr : j;
+    for (int k = 0; k < Nr; ++k) {
+      const size_t rk = (size_t)rr * Nr + k;
+      const double2 v = xo[k];
+      const double c0 = g.E0[rk], c1 = g.E1[rk];
+      e0.x = fma(c0, v.x, e0.x); e0.y = fma(c0, v.y, e0.y);
+      e1.x = fma(c1, v.x, e1.x); e1.y = fma(c1, v.y, e1.y);
+      if (!bc) {
+        const double c2 = g.E2[rk], c4 = g.E4[rk];
+        e2.x = fma(c2, v.x, e2.x); e2.y = fma(c2, v.y, e2.y);
+        e4.x = fma(c4, v.x, e4.x); e4.y = fma(c4, v.y, e4.y);
+      }
+    }
+    if (bc) {
+      Ax = (j == 0 || j == Nr - 1) ? e0 : e1;   // f: rows 1, Nr - 2 hold d_r f at the walls
+    } else {
+      const double r = g.rc[j], r2 = r * r, lam = l * (l + 1.0), mk = lam * g.Ek / r2;
+      const double2 Ll = make_double2(e2.x - lam / r2 * e0.x, e2.y - lam / r2 * e0.y);
+      if (fld == 0) {
+        const double cm = g.explicit_coriolis ? 0.0 : -2.0 * m / r2;   // times i e
+        Ax = make_double2(mk * g.inv_dt * e0.x - mk * Ll.x - cm * e0.y,
+                          mk * g.inv_dt * e0.y - mk * Ll.y + cm * e0.x);
+      } else {
+        const double c2 = -2.0 * lam / r2, c1 = 4.0 * lam / (r2 * r), c0 = (lam * lam - 6.0 * lam) / (r2 * r2);
+        const double2 LL = make_double2(e4.x + c2 * e2.x + c1 * e1.x + c0 * e0.x,
+                                        e4.y + c2 * e2.y + c1 * e1.y + c0 * e0.y);
+        const double cm = g.explicit_coriolis ? 0.0 : 2.0 * m / r2;     // times i Ll f
+        Ax = make_double2(-mk * g.inv_dt * Ll.x + mk * LL.x - cm * Ll.y,
+                          -mk * g.inv_dt * Ll.y + mk * LL.y + cm * Ll.x);
+      }
+      // Coriolis couplings to the other potential at l - 1 and l + 1
+      for (int side = -1; side <= 1; side += 2) {
+        if ((side < 0 && l - 1 < m) || (side > 0 && l + 1 > g.L)) continue;
+        double a2, al;
+        fac_coupling_row(g, fld, l, m, side, j, a2, al);
+        if (a2 == 0.0) continue;
+        const double2* xn = xs_ + ((1 - fld) * 3 + 1 + side) * Nr;
+        double2 n0 = {0, 0}, n1 = {0, 0};
+        for (int k = 0; k < Nr; ++k) {
+          const size_t jk = (size_t)j * Nr + k;
+          const double c0 = g.E0[jk], c1 = g.E1[jk];
+          n0.x = fma(c0, xn[k].x, n0.x); n0.y = fma(c0, xn[k].y, n0.y);
+          n1.x = fma(c1, xn[k].x, n1.x); n1.y = fma(c1, xn[k].y, n1.y);
+        }
+        Ax.x += a2 * (al * n0.x - n1.x);
+        Ax.y += a2 * (al * n0.y - n1.y);
+      }
+    }
+  }
+  const double2 b = rb[row];
+  rb[row] = make_double2(b.x - Ax.x, b.y - Ax.y);
+}
+
 // Double-float copies of the factors for the mixed path: hi = the entry rounded to FP32,
 // lo = the remainder rounded to FP32 (as the host split).
 __global__ void k_split_factor(const double2* __restrict__ src, float4* __restrict__ dst, long n) {
