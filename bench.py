@@ -64,6 +64,8 @@ def parse():
                          "mixed batched Newton)")
     ap.add_argument("--coriolis-study", action="store_true",
                     help="only run the implicit vs explicit Coriolis comparison (Sec. 5)")
+    ap.add_argument("--resolution-study", action="store_true",
+                    help="only run the resolution study of the RW12 drift (Table 1 row 3)")
     return ap.parse_args()
 
 
@@ -499,6 +501,8 @@ def batch_measure(torch, Batch, count=16, reps=5):
     ms_list = [4, 6, 8, 10, 12]
     inst = [dict(L=95, Ms=ms_list[i % 5], Nr=48, Ek=Ek, Ra=float(f * Rac), precision="mixed")
             for i, f in enumerate(np.linspace(1.05, 2.0, 32))]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     t0 = time.perf_counter()
     b = Batch(inst)
     t_create = time.perf_counter() - t0
@@ -520,6 +524,7 @@ def batch_measure(torch, Batch, count=16, reps=5):
     b.apply_jacobian(U, C, J, u, 200.0, out=out)     # factorisations and graph capture
     b.synchronize()
     t_first = time.perf_counter() - t0
+    mem_gb = (free0 - torch.cuda.mem_get_info()[0]) / 1e9
     b.apply_jacobian(U, C, J, u, 200.0, out=out)
     b.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -547,7 +552,9 @@ def batch_measure(torch, Batch, count=16, reps=5):
             "jvps_per_s_batched": n_act / t_graph, "jvps_per_s_sequential": n_act / t_seq,
             "batching_speedup": t_seq / t_graph, "create_s": t_create, "autotune_s": t_tune,
             "tuning_by_Ms": {inst[i]["Ms"]: tuning[i] for i in range(5)},
-            "first_launch_s_including_factorisation_and_capture": t_first}
+            "first_launch_s_including_factorisation_and_capture": t_first,
+            "device_memory_gb_after_first_launch": mem_gb,
+            "factor_sets_per_dt": len(ms_list)}
 
 
 def _wave_from_seed(torch, RotatingShell, c, precision="mixed", max_steps=60000):
@@ -669,6 +676,47 @@ def dt_study(torch, RotatingShell, rows=(0, 1, 2)):
         row["seconds"] = time.perf_counter() - t0
         out.append(row)
         print(json.dumps({"dt_study_row": row}), flush=True)
+    return out
+
+
+def resolution_study(torch, RotatingShell):
+    """Table 1 row 3 (RW12, Ek = 1e-5, Ra = 140) at several truncations: the wave is
+    converged on the FP64 path at L = 127, N_r = 64 from a time-stepped m = 12 seed, then
+    carried by zero-fill regridding (rsc_regrid) to every (L, N_r) of the grid and converged
+    again by FP64 Newton-GMRES (residual 1e-10).  The drift C, kinetic energy and Nusselt
+    numbers show whether C settles with resolution, and where the paper's resolution
+    (N_r = 76, N_theta = 136: L = 89) sits."""
+    w = dict(WORKLOAD)
+    c = dict(L=127, Ms=12, Nr=64, Ek=w["Ek"], Ra=w["Ra"], seed_dt=2e-5)
+    guess, C0, J, seed_steps = _wave_from_seed(torch, RotatingShell, c)
+    base = RotatingShell(127, 12, 64, w["Ek"], w["Ra"])
+    Ub = guess.clone()
+    Cb, rep, st = base.newton_rw(Ub, C0, J, tol=1e-10, max_newton=20, kmax=600, gmres_tol=1e-10)
+    out = {"seed_steps": seed_steps, "base": {"L": 127, "Nr": 64, "C": Cb, "status": st,
+                                              "residual": rep["residual"]}, "points": []}
+    grid = [(89, 64), (89, 76), (89, 96), (107, 76), (127, 64), (127, 76), (127, 96),
+            (159, 64), (159, 76), (159, 96), (191, 96)]
+    for L, Nr in grid:
+        t0 = time.perf_counter()
+        sh = RotatingShell(L, 12, Nr, w["Ek"], w["Ra"])
+        U = sh.regrid_from(base, Ub)
+        x = U.view(3, sh.P, Nr, 2)
+        pM = L + 1
+        kstar = int(torch.argmax(torch.abs(x[2, pM, :, 0])).item())
+        Jt = sh.phase_slot(12, kstar)
+        C, rep, st = sh.newton_rw(U, Cb, Jt, tol=1e-10, max_newton=20, kmax=600,
+                                  gmres_tol=1e-10)
+        ke, nui, nuo = sh.diagnostics(U)
+        cheb, shs = sh.spectral_tail(U)
+        row = {"L": L, "Nr": Nr, "C": C, "KE": ke, "Nu_in": nui, "Nu_out": nuo,
+               "status": st, "residual": rep["residual"], "newton_iterations": rep["iterations"],
+               "jacobian_actions": rep["gmres_total"], "cheb_tail": cheb, "sh_tail": shs,
+               "seconds": time.perf_counter() - t0}
+        out["points"].append(row)
+        print(json.dumps({"resolution_point": row}), flush=True)
+        sh.close()
+    base.close()
+    out["paper_C_exact"] = 51.2817
     return out
 
 
@@ -810,6 +858,11 @@ def run_gpu(args):
     if args.coriolis_study:
         if rank == 0:
             print(json.dumps({"coriolis_study": coriolis_study(torch, RotatingShell)}), flush=True)
+        return 0
+    if args.resolution_study:
+        if rank == 0:
+            print(json.dumps({"resolution_study": resolution_study(torch, RotatingShell)}),
+                  flush=True)
         return 0
     peaks = measured_peaks(torch)
     sh = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],

@@ -320,7 +320,12 @@ rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
  * Newton-GMRES at once (one host thread per instance, each on its stream).
  * The streams of the instances are ordered after `stream` only inside
  * rsc_batch_apply_jacobian; synchronise the contexts (rsc_batch_context)
- * before reading their results otherwise.                                   */
+ * before reading their results otherwise.  Instances with the same operator
+ * (L, Ms, Nr, Ek, Pr, eta, precision, Coriolis treatment; Ra may differ, since
+ * it enters only the explicit part) share one set of factorisations per time
+ * step (Sec. 3.2: the factors depend on Ek and dt, not on Ra), built by the
+ * first instance that needs it; an instance whose Ek changes (rsc_set_params)
+ * or that uses partitioned chains factorises on its own.                    */
 typedef struct rsc_batch rsc_batch;
 
 rsc_status rsc_batch_create(const rsc_params* params, int n, void* stream, rsc_batch** out);
@@ -396,6 +401,11 @@ typedef struct {
                               relative errors up to 1e-8 in the small poloidal field of
                               the m = 0 chains; one step removes them.  The double-float
                               solve of the mixed path is not refined.                  */
+  int chain_ring;          /* double-float sweeps: 0 = the next block's rows prefetched into
+                              registers one block step ahead; 2 to 16 = a shared-memory ring
+                              of that many blocks, filled by bulk copies (cp.async.bulk)
+                              ahead of the sweep.  Same arithmetic and order of sums.
+                              Unpartitioned chains only.                               */
   double ms[6];            /* after rsc_autotune: best times (ms) of products +
                               analysis (mixed), FP64 synthesis, RHS (mixed), FP64 chain
                               solve, double-float chain solve (0 if none ran); zero

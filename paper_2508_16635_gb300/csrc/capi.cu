@@ -13,6 +13,8 @@
 #include <new>
 #include <string>
 #include <cstdint>
+#include <memory>
+#include <mutex>
 #include <thread>
 #include <type_traits>
 #include <vector>
@@ -24,6 +26,7 @@
 #include "krylov_split.cuh"
 #include "chain_df.cuh"
 #include "factor_gpu.cuh"
+#include "chain_ring.cuh"
 #include "rsc_internal.h"
 
 using namespace rsc;
@@ -68,6 +71,8 @@ struct LegDev {
   }
 };
 
+struct FactorShare;
+
 }  // namespace
 
 struct rsc_ctx {
@@ -107,6 +112,9 @@ struct rsc_ctx {
   // factorisations, two slots (time stepping dt and Newton dt)
   DevFactor fac[2];
   int fac_next = 0;
+  // factorisations shared with the other instances of a batch that have the same operator
+  // (truncation, Ek, Pr, eta, precision, Coriolis treatment); null for a lone context
+  std::shared_ptr<FactorShare> share;
   // Krylov
   double* V = nullptr;
   float2* Vs = nullptr;   // the same basis as (hi, lo) float pairs (krylov_split)
@@ -123,6 +131,8 @@ struct rsc_ctx {
                           // per row group (chain_df.cuh), 0 = the FP64 kernels
   int cluster_df = 8;     // CTAs per cluster of the double-float sweeps
   int chain_parts = 1;    // parts per chain of the double-float solve (1: unpartitioned)
+  int chain_ring = 0;     // double-float sweeps: 0 = one block prefetched in registers,
+                          // D >= 2 = a shared-memory ring of D blocks filled by bulk copies
   // second stream: the temperature solve runs beside the e/f chain solve
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -298,6 +308,22 @@ void free_factor(DevFactor& f) {
   for (void* b : extra) cudaFree(b);
   f = DevFactor();
 }
+
+// Factorisations of one operator shared by several contexts (the instances of a batch with
+// the same truncation, Ek, Pr, eta, precision and Coriolis treatment; Sec. 3.2: the factors
+// depend on (Ek, dt) and the truncation only, not on Ra).  One slot per dt, built by the
+// first context that needs it and kept until the last sharing context is destroyed.
+struct FactorShare {
+  static constexpr int kMaxSlots = 4;
+  std::mutex mu;
+  std::vector<DevFactor*> slots;
+  ~FactorShare() {
+    for (DevFactor* f : slots) {
+      free_factor(*f);
+      delete f;
+    }
+  }
+};
 
 template <typename R>
 rsc_status upload_legendre(rsc_ctx* ctx, LegDev<R>& L) {
@@ -552,20 +578,9 @@ rsc_status gpu_factor(rsc_ctx* ctx, double dt, DevFactor& f) {
   return RSC_OK;
 }
 
-rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
-  for (auto& f : ctx->fac)
-    if (f.valid && f.dt == dt) {
-      *out = &f;
-      return RSC_OK;
-    }
-  DevFactor& f = ctx->fac[ctx->fac_next];
-  ctx->fac_next ^= 1;
-  CK(cudaStreamSynchronize(ctx->s));
-  if (ctx->jvp_exec) {   // the captured Jacobian action may point into the slot being replaced
-    cudaGraphExecDestroy(ctx->jvp_exec);
-    ctx->jvp_exec = nullptr;
-  }
-  free_factor(f);
+// Factorise dt into f (FP64 factors, their double-float copies on a mixed context, the
+// partitioned extras when chain_parts > 1).
+rsc_status build_factor_into(rsc_ctx* ctx, double dt, DevFactor& f) {
   const auto t_fac0 = std::chrono::steady_clock::now();
   if (factor_on_device(ctx)) {
     CKS(gpu_factor(ctx, dt, f));
@@ -573,7 +588,6 @@ rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
     ctx->factor_on_gpu = 1;
     f.dt = dt;
     f.valid = true;
-    *out = &f;
     return RSC_OK;
   }
   HostFactor hf;
@@ -635,6 +649,48 @@ rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
   ctx->factor_on_gpu = 0;
   f.dt = dt;
   f.valid = true;
+  return RSC_OK;
+}
+
+
+rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
+  for (auto& f : ctx->fac)
+    if (f.valid && f.dt == dt) {
+      *out = &f;
+      return RSC_OK;
+    }
+  if (ctx->share && ctx->chain_parts == 1) {
+    FactorShare& sh = *ctx->share;
+    std::lock_guard<std::mutex> lock(sh.mu);
+    for (DevFactor* f : sh.slots)
+      if (f->valid && f->dt == dt) {
+        *out = f;
+        return RSC_OK;
+      }
+    if ((int)sh.slots.size() < FactorShare::kMaxSlots) {
+      DevFactor* f = new (std::nothrow) DevFactor();
+      if (!f) return RSC_ENOMEM;
+      CK(cudaStreamSynchronize(ctx->s));
+      const rsc_status st = build_factor_into(ctx, dt, *f);
+      if (st != RSC_OK) {
+        free_factor(*f);
+        delete f;
+        return st;
+      }
+      sh.slots.push_back(f);
+      *out = f;
+      return RSC_OK;
+    }
+  }
+  DevFactor& f = ctx->fac[ctx->fac_next];
+  ctx->fac_next ^= 1;
+  CK(cudaStreamSynchronize(ctx->s));
+  if (ctx->jvp_exec) {   // the captured Jacobian action may point into the slot being replaced
+    cudaGraphExecDestroy(ctx->jvp_exec);
+    ctx->jvp_exec = nullptr;
+  }
+  free_factor(f);
+  CKS(build_factor_into(ctx, dt, f));
   *out = &f;
   return RSC_OK;
 }
@@ -866,7 +922,36 @@ cudaError_t launch_chain(rsc_ctx* ctx, const DevFactor* f, double* out, bool out
 // Double-float sweeps (chain_df.cuh): NS = ctx->chain_df warps per row group, clusters of
 // ctx->cluster_df CTAs; the shared-memory layout of the asynchronous FP64 sweeps.
 template <int Q, int NS>
+cudaError_t launch_chain_ring_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
+  const Dims& d = ctx->d;
+  const int CS = ctx->cluster_df, D = ctx->chain_ring;
+  const int RPC = (d.Nr + CS - 1) / CS;
+  const int cap = chain_steps_cap(d);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * 2 * d.nm * CS);
+  cfg.blockDim = dim3(32 * NS * ((RPC + 3) / 4));
+  cfg.dynamicSmemBytes = cr_layout(d.Nr, RPC, NS, cap, D, outward).total;
+  cfg.stream = ctx->s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (outward)
+    return cudaLaunchKernelEx(&cfg, k_chain_out_ring<Q / NS, NS>, ctx->geom(),
+                              (const long*)f->chain_off, (const float4*)f->Hs,
+                              (const float4*)f->Ws, reinterpret_cast<double2*>(out),
+                              (const double2*)ctx->mid, CS, cap, D, ctx->d_status);
+  return cudaLaunchKernelEx(&cfg, k_chain_half_ring<Q / NS, NS>, ctx->geom(),
+                            (const long*)f->chain_off, (const float4*)f->Hs,
+                            reinterpret_cast<double2*>(out), ctx->mid, CS, cap, D, ctx->d_status);
+}
+
+template <int Q, int NS>
 cudaError_t launch_chain_df_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
+  if (ctx->chain_ring > 0 && !f->npart) return launch_chain_ring_q<Q, NS>(ctx, f, out, outward);
   const Dims& d = ctx->d;
   const int CS = ctx->cluster_df;
   const int RPC = (d.Nr + CS - 1) / CS;
@@ -1188,6 +1273,63 @@ bool chain_df_ok_q(const Dims& d, int CS, int ns) {
   if (ns == 2) return cluster_ok_df<Q, 2>(d, CS);
   if constexpr (Q % 4 == 0) return ns == 4 && cluster_ok_df<Q, 4>(d, CS);
   return false;
+}
+
+// The ring sweeps (chain_ring.cuh) with ns warps per row group, clusters of CS, depth D.
+template <int Q, int NS>
+bool cluster_ok_ring(const Dims& d, int CS, int D) {
+  const void* const fns[2] = {(const void*)k_chain_half_ring<Q / NS, NS>,
+                              (const void*)k_chain_out_ring<Q / NS, NS>};
+  const int RPC = (d.Nr + CS - 1) / CS;
+  for (int w = 0; w < 2; ++w) {
+    cudaFuncSetAttribute(fns[w], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaGetLastError();
+    const size_t smem = cr_layout(d.Nr, RPC, NS, chain_steps_cap(d), D, w == 1).total;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fns[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * 2 * d.nm * CS);
+    cfg.blockDim = dim3(32 * NS * ((RPC + 3) / 4));
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cfg.blockDim.x > 1024 || cudaOccupancyMaxActiveClusters(&n, fns[w], &cfg) != cudaSuccess ||
+        n <= 0) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  return true;
+}
+
+template <int Q>
+bool chain_ring_ok_q(const Dims& d, int CS, int ns, int D) {
+  if (ns == 2) return cluster_ok_ring<Q, 2>(d, CS, D);
+  if constexpr (Q % 4 == 0) return ns == 4 && cluster_ok_ring<Q, 4>(d, CS, D);
+  return false;
+}
+
+// Ring depth D of the double-float sweeps (0: the register-prefetch kernels).
+bool chain_ring_ok(const Dims& d, int CS, int ns, int D) {
+  if (D == 0) return true;
+  if (D < 2 || D > 16 || ns == 0 || CS < 1 || CS > d.Nr) return false;
+  switch (chain_maxq(d.Nr)) {
+    case 2: return chain_ring_ok_q<2>(d, CS, ns, D);
+    case 4: return chain_ring_ok_q<4>(d, CS, ns, D);
+    case 8: return chain_ring_ok_q<8>(d, CS, ns, D);
+    case 12: return chain_ring_ok_q<12>(d, CS, ns, D);
+    default: return chain_ring_ok_q<16>(d, CS, ns, D);
+  }
 }
 
 // Double-float sweeps with ns warps per row group on clusters of CS (ns = 0: off).
@@ -1713,6 +1855,7 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
   if (t.chain_parts < 1 || t.chain_parts > kMaxChainParts) return false;
   if (t.factor_gpu != 0 && t.factor_gpu != 1) return false;
   if (t.refine < 0 || t.refine > 2) return false;
+  if (!chain_ring_ok(d, t.chain_df_cluster, t.chain_df, t.chain_ring)) return false;
   if (!chain_df_ok(d, t.chain_df_cluster, t.chain_df)) return false;
   return chain_config_ok(d, t.chain_cluster, t.chain_async);
 }
@@ -1740,6 +1883,7 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
   t->chain_parts = ctx->chain_parts;
   t->factor_gpu = ctx->factor_gpu;
   t->refine = ctx->refine;
+  t->chain_ring = ctx->chain_ring;
   for (int q = 0; q < 6; ++q) t->ms[q] = ctx->tune_ms[q];
 }
 
@@ -1759,6 +1903,7 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
   ctx->cluster_df = t.chain_df_cluster;
   ctx->krylov_split = t.krylov_split;
   ctx->refine = t.refine;
+  ctx->chain_ring = t.chain_ring;
   if (t.factor_gpu != ctx->factor_gpu) {
     // the factorisations are rebuilt where the new setting says
     ctx->factor_gpu = t.factor_gpu;
@@ -1911,26 +2056,37 @@ rsc_status autotune(rsc_ctx* ctx, rsc_tuning* out) {
     // mixed path: the double-float chain solve against the best FP64 one
     if (st == RSC_OK && f->Gs) {
       double best_df = 1e30;
-      int bn = 0, bcs = t.chain_df_cluster;
-      for (int ns : {2, 4}) {
-        for (int cs : {16, 8, 4, 2}) {
-          if (st != RSC_OK) break;
-          if (!chain_df_ok(ctx->d, cs, ns)) continue;
-          ctx->chain_df = ns;
-          ctx->cluster_df = cs;
-          st = stage_solve(ctx, f, ctx->xtmp, true);
-          cudaEventRecord(e0, ctx->s);
-          for (int r = 0; r < 3 && st == RSC_OK; ++r) st = stage_solve(ctx, f, ctx->xtmp, true);
-          cudaEventRecord(e1, ctx->s);
-          if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
-          float ms = 0;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (st == RSC_OK && ms / 3.0 < best_df) { best_df = ms / 3.0; bn = ns; bcs = cs; }
+      int bn = 0, bcs = t.chain_df_cluster, bring = 0;
+      for (int ring : {0, 4, 8}) {
+        for (int ns : {2, 4}) {
+          for (int cs : {16, 8, 4, 2}) {
+            if (st != RSC_OK) break;
+            if (!chain_df_ok(ctx->d, cs, ns) || (!f->npart && !chain_ring_ok(ctx->d, cs, ns, ring)) ||
+                (f->npart && ring))
+              continue;
+            ctx->chain_df = ns;
+            ctx->cluster_df = cs;
+            ctx->chain_ring = ring;
+            st = stage_solve(ctx, f, ctx->xtmp, true);
+            cudaEventRecord(e0, ctx->s);
+            for (int r = 0; r < 3 && st == RSC_OK; ++r) st = stage_solve(ctx, f, ctx->xtmp, true);
+            cudaEventRecord(e1, ctx->s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == RSC_OK && ms / 3.0 < best_df) {
+              best_df = ms / 3.0;
+              bn = ns;
+              bcs = cs;
+              bring = ring;
+            }
+          }
         }
       }
       if (st == RSC_OK) st = check_status(ctx);
       t.chain_df = best_df < best ? bn : 0;
       t.chain_df_cluster = bcs;
+      t.chain_ring = best_df < best ? bring : 0;
       ctx->tune_ms[5] = best_df < 1e30 ? best_df : 0.0;
     }
   }
@@ -2185,8 +2341,10 @@ rsc_status rsc_set_params(rsc_ctx* ctx, const rsc_params* params) {
   }
   CK(cudaStreamSynchronize(ctx->s));
   ctx->p = *params;
-  if (refactor)
+  if (refactor) {
     for (auto& f : ctx->fac) free_factor(f);
+    ctx->share.reset();   // another operator: this context factorises on its own
+  }
   if (ctx->jvp_exec) {   // captured launches embed parameters and factor pointers
     cudaGraphExecDestroy(ctx->jvp_exec);
     ctx->jvp_exec = nullptr;
@@ -2828,6 +2986,24 @@ rsc_status rsc_batch_create(const rsc_params* params, int n, void* stream, rsc_b
   if (st != RSC_OK) {
     batch_free(b);
     return st;
+  }
+  // instances with the same operator share one set of factorisations
+  auto same_operator = [&](const rsc_params& a, const rsc_params& c) {
+    return a.L == c.L && a.Ms == c.Ms && a.Nr == c.Nr && a.Ek == c.Ek && a.Pr == c.Pr &&
+           a.eta == c.eta && a.precision == c.precision &&
+           a.explicit_coriolis == c.explicit_coriolis;
+  };
+  for (int i = 0; i < n; ++i) {
+    if (b->ctx[i]->share) continue;
+    std::shared_ptr<FactorShare> sh;
+    for (int j = i + 1; j < n; ++j)
+      if (!b->ctx[j]->share && same_operator(params[i], params[j])) {
+        if (!sh) {
+          sh = std::make_shared<FactorShare>();
+          b->ctx[i]->share = sh;
+        }
+        b->ctx[j]->share = sh;
+      }
   }
   *out = b;
   return RSC_OK;

@@ -421,6 +421,46 @@ def test_batch_jacobian_parity(torch):
     b.close()
 
 
+def test_batch_instances_share_factorisations(torch):
+    """Instances with the same operator (here three Rayleigh numbers at one Ek) share one
+    factorisation per dt, an instance at another Ek has its own: every instance's Jacobian
+    actions equal those of a lone context bit for bit, and the shared batch holds less
+    device memory than the same instances with separate factorisations."""
+    from paper_2508_16635_gb300 import Batch, RotatingShell
+    L, Ms, Nr = 31, 4, 24
+    inst = [dict(L=L, Ms=Ms, Nr=Nr, Ek=1e-3, Ra=Ra) for Ra in (100.0, 120.0, 140.0)]
+    inst.append(dict(L=L, Ms=Ms, Nr=Nr, Ek=2e-3, Ra=120.0))
+    s = _shell(L, Ms, Nr, 1e-3, 100.0)
+    U = [torch.tensor(s.conductive_state() + si.perturbation(L, Ms, Nr, seed=80 + i, amp=3e-2),
+                      device="cuda") for i in range(len(inst))]
+    u = [torch.tensor(si.random_vector(L, Ms, Nr, seed=90 + i), device="cuda")
+         for i in range(len(inst))]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    b = Batch(inst)
+    out = [torch.empty_like(x) for x in u]
+    b.apply_jacobian(U, [0.3] * 4, [None] * 4, u, 200.0, out=out)
+    b.synchronize()
+    used_shared = free0 - torch.cuda.mem_get_info()[0]
+    for i, d in enumerate(inst):
+        lone = RotatingShell(L, Ms, Nr, d["Ek"], d["Ra"])
+        ref = lone.apply_jacobian(U[i], 0.3, None, u[i], 200.0)
+        assert torch.equal(ref, out[i]), i
+        lone.close()
+    b.close()
+    torch.cuda.synchronize()
+    # the same four instances as lone contexts (four factorisations instead of two)
+    free1 = torch.cuda.mem_get_info()[0]
+    lones = [RotatingShell(L, Ms, Nr, d["Ek"], d["Ra"]) for d in inst]
+    for i, g in enumerate(lones):
+        g.apply_jacobian(U[i], 0.3, None, u[i], 200.0)
+    torch.cuda.synchronize()
+    used_lone = free1 - torch.cuda.mem_get_info()[0]
+    for g in lones:
+        g.close()
+    assert used_shared < used_lone, (used_shared, used_lone)
+
+
 def test_batch_newton_matches_single_instance_solves(torch):
     """rsc_batch_newton_rw (instances concurrently) gives bit-identical waves to the
     single-context solves (whose parity with the oracle is tested above)."""
@@ -670,15 +710,25 @@ def test_implicit_solve_backward_error_double_float(torch, name, L, Ms, Nr, Ek, 
     for ns in (2, 4):
         for cs in (16, 8, 4, 2):
             try:
-                gpu.set_tuning(dict(t0, chain_df=ns, chain_df_cluster=cs, chain_parts=1))
+                gpu.set_tuning(dict(t0, chain_df=ns, chain_df_cluster=cs, chain_parts=1,
+                                    chain_ring=0))
             except Exception:
                 continue
             ran += 1
-            x = s.to_complex(gpu.implicit_solve(B, dt).cpu().numpy())
+            xr = gpu.implicit_solve(B, dt).cpu().numpy()
+            x = s.to_complex(xr)
             eta, fwd, fwd_T = _solve_errors(s, dt, b, x)
             assert eta < 64 * U48, (ns, cs, eta / U48)
             assert fwd < 32 * 1e-11, (ns, cs, fwd)
             assert fwd_T < 1e-12, (ns, cs, fwd_T)
+            # the shared-memory ring sweeps: same arithmetic in the same order, bitwise
+            for ring in (2, 4, 8):
+                try:
+                    gpu.set_tuning(dict(t0, chain_df=ns, chain_df_cluster=cs, chain_parts=1,
+                                        chain_ring=ring))
+                except Exception:
+                    continue
+                assert np.array_equal(gpu.implicit_solve(B, dt).cpu().numpy(), xr), (ns, cs, ring)
     assert ran >= 2
     # partitioned chains (SPIKE-type): only where the longest chain splits into parts of at
     # least 8 blocks; a failing set_tuning is an error here
