@@ -66,6 +66,9 @@ def parse():
                     help="only run the implicit vs explicit Coriolis comparison (Sec. 5)")
     ap.add_argument("--resolution-study", action="store_true",
                     help="only run the resolution study of the RW12 drift (Table 1 row 3)")
+    ap.add_argument("--c5", action="store_true",
+                    help="only run the large single instance (L = 255, N_r = 96): 1000 time "
+                         "steps and one Newton iteration of 100 Jacobian actions per precision")
     return ap.parse_args()
 
 
@@ -720,6 +723,56 @@ def resolution_study(torch, RotatingShell):
     return out
 
 
+def c5_run(torch, RotatingShell, nsteps=1000, krylov=100):
+    """The large single instance (Ek = 3e-6, Pr = 1, r_in/r_out = 0.35, L = 255, M_s = 8,
+    N_r = 96, dt = 2e-6): from the m = 8 seed, `nsteps` IMEX Euler steps timed with CUDA
+    events, then one Newton iteration (FP64 residual at dt = 200, GMRES with `krylov`
+    Jacobian actions, update, FP64 residual) on the stepped state, for the mixed and the
+    FP64 path, each autotuned; and the per-kernel time of one traced Newton iteration."""
+    c = si.config("C5")
+    out = {"config": "C5: Ek=3e-6, L=255, Ms=8, Nr=96, dt=2e-6", "n": None}
+    for prec in ("mixed", "fp64"):
+        sh = RotatingShell(c["L"], 8, c["Nr"], c["Ek"], c["Ra"], precision=prec)
+        tuning = sh.autotune()
+        U = sh.conductive_state() + torch.tensor(
+            si.mode_seed(c["L"], 8, c["Nr"], 8, seed=5000, amp=1e-2), device="cuda")
+        sh.step(U, 0.0, c["dt"], nsteps=3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        sh.step(U, 0.0, c["dt"], nsteps=nsteps)
+        e1.record()
+        torch.cuda.synchronize()
+        t_steps = e0.elapsed_time(e1) * 1e-3
+        J = sh.phase_slot(8, 1)
+        U1 = U.clone()
+        sh.newton_rw(U1, 0.0, J, tol=0.0, max_newton=1, kmax=krylov, gmres_tol=0.0)  # warm-up
+        U1 = U.clone()
+        torch.cuda.synchronize()
+        e0.record()
+        _, rep, _ = sh.newton_rw(U1, 0.0, J, tol=0.0, max_newton=1, kmax=krylov, gmres_tol=0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        t_newton = e0.elapsed_time(e1) * 1e-3
+        sh.profile(True)
+        U1 = U.clone()
+        sh.newton_rw(U1, 0.0, J, tol=0.0, max_newton=1, kmax=krylov, gmres_tol=0.0)
+        prof = {k: round(v["ms"], 3) for k, v in sh.profile_report().items() if v["launches"]}
+        sh.profile(False)
+        ke, nui, nuo = sh.diagnostics(U)
+        out["n"] = sh.n
+        out[prec] = {"timesteps_per_s": nsteps / t_steps, "seconds_1000_steps": t_steps,
+                     "newton_iteration_s": t_newton, "jvps_per_s": rep["gmres_total"] / t_newton,
+                     "jacobian_actions": rep["gmres_total"], "residual_after": rep["residual"],
+                     "KE_after_steps": ke, "kernel_ms_per_newton_iteration": prof,
+                     "tuning": tuning}
+        sh.close()
+        print(json.dumps({"c5_" + prec: out[prec]}), flush=True)
+    out["mixed_over_fp64"] = {"timesteps": out["mixed"]["timesteps_per_s"] / out["fp64"]["timesteps_per_s"],
+                              "jvps": out["mixed"]["jvps_per_s"] / out["fp64"]["jvps_per_s"]}
+    return out
+
+
 def _throughput(torch, RotatingShell, c, precision, krylov, nsteps):
     """Time steps/s (IMEX Euler, lab frame) and Jacobian actions/s (one Newton iteration with
     `krylov` actions) of one configuration, after autotuning; CUDA events, 2 warm-ups."""
@@ -858,6 +911,10 @@ def run_gpu(args):
     if args.coriolis_study:
         if rank == 0:
             print(json.dumps({"coriolis_study": coriolis_study(torch, RotatingShell)}), flush=True)
+        return 0
+    if args.c5:
+        if rank == 0:
+            print(json.dumps({"c5": c5_run(torch, RotatingShell)}), flush=True)
         return 0
     if args.resolution_study:
         if rank == 0:
