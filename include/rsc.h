@@ -401,11 +401,6 @@ typedef struct {
                               relative errors up to 1e-8 in the small poloidal field of
                               the m = 0 chains; one step removes them.  The double-float
                               solve of the mixed path is not refined.                  */
-  int chain_ring;          /* double-float sweeps: 0 = the next block's rows prefetched into
-                              registers one block step ahead; 2 to 16 = a shared-memory ring
-                              of that many blocks, filled by bulk copies (cp.async.bulk)
-                              ahead of the sweep.  Same arithmetic and order of sums.
-                              Unpartitioned chains only.                               */
   double ms[6];            /* after rsc_autotune: best times (ms) of products +
                               analysis (mixed), FP64 synthesis, RHS (mixed), FP64 chain
                               solve, double-float chain solve (0 if none ran); zero

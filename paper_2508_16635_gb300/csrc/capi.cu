@@ -26,7 +26,6 @@
 #include "krylov_split.cuh"
 #include "chain_df.cuh"
 #include "factor_gpu.cuh"
-#include "chain_ring.cuh"
 #include "rsc_internal.h"
 
 using namespace rsc;
@@ -131,8 +130,6 @@ struct rsc_ctx {
                           // per row group (chain_df.cuh), 0 = the FP64 kernels
   int cluster_df = 8;     // CTAs per cluster of the double-float sweeps
   int chain_parts = 1;    // parts per chain of the double-float solve (1: unpartitioned)
-  int chain_ring = 0;     // double-float sweeps: 0 = one block prefetched in registers,
-                          // D >= 2 = a shared-memory ring of D blocks filled by bulk copies
   // second stream: the temperature solve runs beside the e/f chain solve
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -922,36 +919,7 @@ cudaError_t launch_chain(rsc_ctx* ctx, const DevFactor* f, double* out, bool out
 // Double-float sweeps (chain_df.cuh): NS = ctx->chain_df warps per row group, clusters of
 // ctx->cluster_df CTAs; the shared-memory layout of the asynchronous FP64 sweeps.
 template <int Q, int NS>
-cudaError_t launch_chain_ring_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
-  const Dims& d = ctx->d;
-  const int CS = ctx->cluster_df, D = ctx->chain_ring;
-  const int RPC = (d.Nr + CS - 1) / CS;
-  const int cap = chain_steps_cap(d);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * 2 * d.nm * CS);
-  cfg.blockDim = dim3(32 * NS * ((RPC + 3) / 4));
-  cfg.dynamicSmemBytes = cr_layout(d.Nr, RPC, NS, cap, D, outward).total;
-  cfg.stream = ctx->s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (outward)
-    return cudaLaunchKernelEx(&cfg, k_chain_out_ring<Q / NS, NS>, ctx->geom(),
-                              (const long*)f->chain_off, (const float4*)f->Hs,
-                              (const float4*)f->Ws, reinterpret_cast<double2*>(out),
-                              (const double2*)ctx->mid, CS, cap, D, ctx->d_status);
-  return cudaLaunchKernelEx(&cfg, k_chain_half_ring<Q / NS, NS>, ctx->geom(),
-                            (const long*)f->chain_off, (const float4*)f->Hs,
-                            reinterpret_cast<double2*>(out), ctx->mid, CS, cap, D, ctx->d_status);
-}
-
-template <int Q, int NS>
 cudaError_t launch_chain_df_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
-  if (ctx->chain_ring > 0 && !f->npart) return launch_chain_ring_q<Q, NS>(ctx, f, out, outward);
   const Dims& d = ctx->d;
   const int CS = ctx->cluster_df;
   const int RPC = (d.Nr + CS - 1) / CS;
@@ -1273,63 +1241,6 @@ bool chain_df_ok_q(const Dims& d, int CS, int ns) {
   if (ns == 2) return cluster_ok_df<Q, 2>(d, CS);
   if constexpr (Q % 4 == 0) return ns == 4 && cluster_ok_df<Q, 4>(d, CS);
   return false;
-}
-
-// The ring sweeps (chain_ring.cuh) with ns warps per row group, clusters of CS, depth D.
-template <int Q, int NS>
-bool cluster_ok_ring(const Dims& d, int CS, int D) {
-  const void* const fns[2] = {(const void*)k_chain_half_ring<Q / NS, NS>,
-                              (const void*)k_chain_out_ring<Q / NS, NS>};
-  const int RPC = (d.Nr + CS - 1) / CS;
-  for (int w = 0; w < 2; ++w) {
-    cudaFuncSetAttribute(fns[w], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaGetLastError();
-    const size_t smem = cr_layout(d.Nr, RPC, NS, chain_steps_cap(d), D, w == 1).total;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(fns[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * 2 * d.nm * CS);
-    cfg.blockDim = dim3(32 * NS * ((RPC + 3) / 4));
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cfg.blockDim.x > 1024 || cudaOccupancyMaxActiveClusters(&n, fns[w], &cfg) != cudaSuccess ||
-        n <= 0) {
-      cudaGetLastError();
-      return false;
-    }
-  }
-  return true;
-}
-
-template <int Q>
-bool chain_ring_ok_q(const Dims& d, int CS, int ns, int D) {
-  if (ns == 2) return cluster_ok_ring<Q, 2>(d, CS, D);
-  if constexpr (Q % 4 == 0) return ns == 4 && cluster_ok_ring<Q, 4>(d, CS, D);
-  return false;
-}
-
-// Ring depth D of the double-float sweeps (0: the register-prefetch kernels).
-bool chain_ring_ok(const Dims& d, int CS, int ns, int D) {
-  if (D == 0) return true;
-  if (D < 2 || D > 16 || ns == 0 || CS < 1 || CS > d.Nr) return false;
-  switch (chain_maxq(d.Nr)) {
-    case 2: return chain_ring_ok_q<2>(d, CS, ns, D);
-    case 4: return chain_ring_ok_q<4>(d, CS, ns, D);
-    case 8: return chain_ring_ok_q<8>(d, CS, ns, D);
-    case 12: return chain_ring_ok_q<12>(d, CS, ns, D);
-    default: return chain_ring_ok_q<16>(d, CS, ns, D);
-  }
 }
 
 // Double-float sweeps with ns warps per row group on clusters of CS (ns = 0: off).
@@ -1855,7 +1766,6 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
   if (t.chain_parts < 1 || t.chain_parts > kMaxChainParts) return false;
   if (t.factor_gpu != 0 && t.factor_gpu != 1) return false;
   if (t.refine < 0 || t.refine > 2) return false;
-  if (!chain_ring_ok(d, t.chain_df_cluster, t.chain_df, t.chain_ring)) return false;
   if (!chain_df_ok(d, t.chain_df_cluster, t.chain_df)) return false;
   return chain_config_ok(d, t.chain_cluster, t.chain_async);
 }
@@ -1883,7 +1793,6 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
   t->chain_parts = ctx->chain_parts;
   t->factor_gpu = ctx->factor_gpu;
   t->refine = ctx->refine;
-  t->chain_ring = ctx->chain_ring;
   for (int q = 0; q < 6; ++q) t->ms[q] = ctx->tune_ms[q];
 }
 
@@ -1903,7 +1812,6 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
   ctx->cluster_df = t.chain_df_cluster;
   ctx->krylov_split = t.krylov_split;
   ctx->refine = t.refine;
-  ctx->chain_ring = t.chain_ring;
   if (t.factor_gpu != ctx->factor_gpu) {
     // the factorisations are rebuilt where the new setting says
     ctx->factor_gpu = t.factor_gpu;
@@ -2056,37 +1964,26 @@ rsc_status autotune(rsc_ctx* ctx, rsc_tuning* out) {
     // mixed path: the double-float chain solve against the best FP64 one
     if (st == RSC_OK && f->Gs) {
       double best_df = 1e30;
-      int bn = 0, bcs = t.chain_df_cluster, bring = 0;
-      for (int ring : {0, 4, 8}) {
-        for (int ns : {2, 4}) {
-          for (int cs : {16, 8, 4, 2}) {
-            if (st != RSC_OK) break;
-            if (!chain_df_ok(ctx->d, cs, ns) || (!f->npart && !chain_ring_ok(ctx->d, cs, ns, ring)) ||
-                (f->npart && ring))
-              continue;
-            ctx->chain_df = ns;
-            ctx->cluster_df = cs;
-            ctx->chain_ring = ring;
-            st = stage_solve(ctx, f, ctx->xtmp, true);
-            cudaEventRecord(e0, ctx->s);
-            for (int r = 0; r < 3 && st == RSC_OK; ++r) st = stage_solve(ctx, f, ctx->xtmp, true);
-            cudaEventRecord(e1, ctx->s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (st == RSC_OK && ms / 3.0 < best_df) {
-              best_df = ms / 3.0;
-              bn = ns;
-              bcs = cs;
-              bring = ring;
-            }
-          }
+      int bn = 0, bcs = t.chain_df_cluster;
+      for (int ns : {2, 4}) {
+        for (int cs : {16, 8, 4, 2}) {
+          if (st != RSC_OK) break;
+          if (!chain_df_ok(ctx->d, cs, ns)) continue;
+          ctx->chain_df = ns;
+          ctx->cluster_df = cs;
+          st = stage_solve(ctx, f, ctx->xtmp, true);
+          cudaEventRecord(e0, ctx->s);
+          for (int r = 0; r < 3 && st == RSC_OK; ++r) st = stage_solve(ctx, f, ctx->xtmp, true);
+          cudaEventRecord(e1, ctx->s);
+          if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (st == RSC_OK && ms / 3.0 < best_df) { best_df = ms / 3.0; bn = ns; bcs = cs; }
         }
       }
       if (st == RSC_OK) st = check_status(ctx);
       t.chain_df = best_df < best ? bn : 0;
       t.chain_df_cluster = bcs;
-      t.chain_ring = best_df < best ? bring : 0;
       ctx->tune_ms[5] = best_df < 1e30 ? best_df : 0.0;
     }
   }

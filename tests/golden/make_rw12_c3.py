@@ -51,14 +51,15 @@ def main():
     nu_in, nu_out = s.nusselt(Uw)
     ke = s.kinetic_energy(Uw)
     res = hist[-1]["residual"]
-    out = os.path.join(HERE, "rw12_c3_oracle.txt")
+    out = os.environ.get("RSC_GOLDEN_OUT", os.path.join(HERE, "rw12_c3_oracle.txt"))
     with open(out, "w") as f:
         f.write("# The oracle's RW12 wave at L = 127, Ms = 12, N_r = 64, Ek = 1e-5, Ra = 140 (Table 1\n")
         f.write("# row 3 parameters at the benchmark truncation), written by make_rw12_c3.py from\n")
         f.write(f"# seeded_inputs.mode_seed(seed=4000, amp=1e-2), {steps} oracle steps of dt = {DT},\n")
         f.write(f"# Newton-GMRES at dt = 200: {len(hist) - 1} iterations, final ||B(U) - U|| = {res:.3e}.\n")
         f.write("# key value\n")
-        f.write(f"C {C!r}\nKE {ke!r}\nNu_in {nu_in!r}\nNu_out {nu_out!r}\nresidual {res!r}\n")
+        f.write(f"C {float(C)!r}\nKE {float(ke)!r}\nNu_in {float(nu_in)!r}\n"
+                f"Nu_out {float(nu_out)!r}\nresidual {float(res)!r}\n")
         f.write(f"phase_slot {J}\nnewton_iterations {len(hist) - 1}\n")
     print(f"wrote {out} after {time.time() - t0:.0f} s", flush=True)
 
