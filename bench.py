@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-rw", action="store_true", help="skip the time-to-rotating-wave run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances run")
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="skip the FP64-path and factorisation timings (profiling runs)")
     ap.add_argument("--chain-parts", type=int, default=1,
                     help="parts per chain of the mixed path's double-float solve after "
                          "autotuning (1: unpartitioned, the faster at RW12)")
@@ -1064,8 +1066,9 @@ def run_gpu(args):
             "clocks": clk.summary(),
             "wall_s_timed_region": wall,
         }
-        line["factorisation"] = factor_timing(torch, RotatingShell, w)
-        if args.precision == "mixed":
+        if not args.no_fp64_arm:
+            line["factorisation"] = factor_timing(torch, RotatingShell, w)
+        if args.precision == "mixed" and not args.no_fp64_arm:
             line["fp64_path"] = fp64_arm(torch, RotatingShell, w, K)
             line["mixed_over_fp64_jvps"] = value / world / line["fp64_path"]["jvps_per_s"]
         if not args.no_rw:
