@@ -22,7 +22,6 @@
 #pragma once
 
 #include "dfloat.h"
-#include "dfloat2.cuh"
 
 namespace rsc {
 
@@ -35,17 +34,6 @@ __device__ __forceinline__ float4 cd_split(double2 v) {
 
 __device__ __forceinline__ double2 cd_join(float4 q) {
   return make_double2((double)q.x + (double)q.z, (double)q.y + (double)q.w);
-}
-
-// acc += a b for complex double-float a (factor entry), b (vector entry): the re and im
-// sums of cd_cmac in one packed accumulator (a real when real_op: the im parts of the table
-// are zero at m = 0 and skipped).
-__device__ __forceinline__ void cd_cmac2(cdfl& acc, float4 a, float4 b, bool real_op) {
-  cdfl_fma(acc, make_float2(a.x, a.x), make_float2(a.z, a.z), make_float2(b.x, b.y),
-           make_float2(b.z, b.w));
-  if (!real_op)
-    cdfl_fma(acc, make_float2(-a.y, a.y), make_float2(-a.w, a.w), make_float2(b.y, b.x),
-             make_float2(b.w, b.z));
 }
 
 // acc (re, im) += a b for complex double-float a, b (a real when real_op: im parts of the
@@ -68,11 +56,6 @@ __device__ __forceinline__ void cd_reduce8(dfl& re, dfl& im) {
   }
 }
 
-__device__ __forceinline__ void cd_reduce8(cdfl& a) {
-#pragma unroll
-  for (int o = 4; o > 0; o >>= 1) a = cdfl_add(a, cdfl_shfl_xor(a, o));
-}
-
 __device__ __forceinline__ void cd_send(uint32_t raddr, uint32_t rbar, float4 v) {
   asm volatile(
       "st.async.weak.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::
@@ -87,21 +70,20 @@ __device__ __forceinline__ void cd_send(uint32_t raddr, uint32_t rbar, float4 v)
 template <int QH>
 __device__ __forceinline__ void cd_dot(const float4 (&reg)[QH], const float4* v, int s, int q0,
                                        int Nr, bool real_op, dfl& re, dfl& im) {
-  cdfl a0 = cdfl_zero(), a1 = cdfl_zero();
+  dfl r0 = dfl_zero(), i0 = dfl_zero(), r1 = dfl_zero(), i1 = dfl_zero();
 #pragma unroll
   for (int q = 0; q < QH; ++q) {
     const int k = s + 8 * (q0 + q);
     if (k < Nr) {
       if (q & 1)
-        cd_cmac2(a1, reg[q], v[k], real_op);
+        cd_cmac(r1, i1, reg[q], v[k], real_op);
       else
-        cd_cmac2(a0, reg[q], v[k], real_op);
+        cd_cmac(r0, i0, reg[q], v[k], real_op);
     }
   }
-  cdfl a = cdfl_add(a0, a1);
-  cd_reduce8(a);
-  re = dfl{a.s.x, a.c.x};
-  im = dfl{a.s.y, a.c.y};
+  re = dfl_add(r0, r1);
+  im = dfl_add(i0, i1);
+  cd_reduce8(re, im);
 }
 
 template <int QH>
@@ -138,21 +120,20 @@ __global__ void __launch_bounds__(256) k_block_gemv_df(DevGeom g, const long* __
        r += rows_per_pass) {
     float4 a[Q];
     cd_load<Q>(Gi, r, s8, 0, Nr, r < Nr, a);
-    cdfl a0 = cdfl_zero(), a1 = cdfl_zero();
+    dfl re0 = dfl_zero(), im0 = dfl_zero(), re1 = dfl_zero(), im1 = dfl_zero();
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int k = s8 + 8 * q;
       if (k < Nr) {
         if (q & 1)
-          cd_cmac2(a1, a[q], svf[k], real_op);
+          cd_cmac(re1, im1, a[q], svf[k], real_op);
         else
-          cd_cmac2(a0, a[q], svf[k], real_op);
+          cd_cmac(re0, im0, a[q], svf[k], real_op);
       }
     }
-    cdfl acc = cdfl_add(a0, a1);
-    cd_reduce8(acc);
-    if (r < Nr && s8 == 0)
-      out[row0 + r] = make_double2(dfl_to_double(dfl{acc.s.x, acc.c.x}), dfl_to_double(dfl{acc.s.y, acc.c.y}));
+    dfl re = dfl_add(re0, re1), im = dfl_add(im0, im1);
+    cd_reduce8(re, im);
+    if (r < Nr && s8 == 0) out[row0 + r] = make_double2(dfl_to_double(re), dfl_to_double(im));
   }
 }
 

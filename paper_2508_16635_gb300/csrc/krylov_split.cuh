@@ -17,7 +17,6 @@
 #pragma once
 
 #include "dfloat.h"
-#include "dfloat2.cuh"
 
 namespace rsc {
 
@@ -83,22 +82,24 @@ __global__ void __launch_bounds__(512) k_dots_pair_s(const float2* __restrict__ 
   float4 vv[PER];
 #pragma unroll
   for (int u = 0; u < PER; ++u) vv[u] = __ldcs(v4 + u * 32);
-  // (Vs_j . w, Vs_j . q) as one packed pair of Dot2 sums, even and odd elements apart
-  cdfl e = cdfl_zero(), o = cdfl_zero();
+  dfl a0 = dfl_zero(), a1 = dfl_zero(), b0 = dfl_zero(), b1 = dfl_zero();
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const float4 x = ws[u * 32 + lane], y = qsh[u * 32 + lane];
-    cdfl_fma(e, make_float2(vv[u].x, vv[u].x), make_float2(vv[u].y, vv[u].y),
-             make_float2(x.x, y.x), make_float2(x.y, y.y));
-    cdfl_fma(o, make_float2(vv[u].z, vv[u].z), make_float2(vv[u].w, vv[u].w),
-             make_float2(x.z, y.z), make_float2(x.w, y.w));
+    dfl_fma(a0, vv[u].x, vv[u].y, x.x, x.y);
+    dfl_fma(a1, vv[u].z, vv[u].w, x.z, x.w);
+    dfl_fma(b0, vv[u].x, vv[u].y, y.x, y.y);
+    dfl_fma(b1, vv[u].z, vv[u].w, y.z, y.w);
   }
-  cdfl ab = cdfl_add(e, o);
+  dfl a = dfl_add(a0, a1), b = dfl_add(b0, b1);
 #pragma unroll
-  for (int sh = 16; sh > 0; sh >>= 1) ab = cdfl_add(ab, cdfl_shfl_xor(ab, sh));
+  for (int o = 16; o > 0; o >>= 1) {
+    a = dfl_add(a, dfl_shfl_xor(a, o));
+    b = dfl_add(b, dfl_shfl_xor(b, o));
+  }
   if (lane == 0) {
-    partial[(long)j * nchunk + blockIdx.x] = cdfl_to_double_x(ab);
-    partial[(long)(nv + j) * nchunk + blockIdx.x] = cdfl_to_double_y(ab);
+    partial[(long)j * nchunk + blockIdx.x] = dfl_to_double(a);
+    partial[(long)(nv + j) * nchunk + blockIdx.x] = dfl_to_double(b);
   }
 }
 
@@ -122,8 +123,7 @@ __global__ void __launch_bounds__(256) k_axpy_norm_s(const float2* __restrict__ 
   double ss = 0.0;
   for (long i2 = (long)blockIdx.x * blockDim.x + threadIdx.x; i2 < n2;
        i2 += (long)gridDim.x * blockDim.x) {
-    // (x, y) components of the pair as packed Dot2 sums s (even j) and t (odd j)
-    cdfl sv = cdfl_zero(), tv = cdfl_zero();
+    dfl sx = dfl_zero(), sy = dfl_zero(), tx = dfl_zero(), ty = dfl_zero();
     int j = 0;
     for (; j + 8 <= nv; j += 8) {
       float4 v[8];
@@ -137,22 +137,21 @@ __global__ void __launch_bounds__(256) k_axpy_norm_s(const float2* __restrict__ 
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
         const float2 c0 = hs[j + u], c1 = hs[j + u + 1];
-        cdfl_fma(sv, make_float2(c0.x, c0.x), make_float2(c0.y, c0.y),
-                 make_float2(v[u].x, v[u].z), make_float2(v[u].y, v[u].w));
-        cdfl_fma(tv, make_float2(c1.x, c1.x), make_float2(c1.y, c1.y),
-                 make_float2(v[u + 1].x, v[u + 1].z), make_float2(v[u + 1].y, v[u + 1].w));
+        dfl_fma(sx, c0.x, c0.y, v[u].x, v[u].y);
+        dfl_fma(sy, c0.x, c0.y, v[u].z, v[u].w);
+        dfl_fma(tx, c1.x, c1.y, v[u + 1].x, v[u + 1].y);
+        dfl_fma(ty, c1.x, c1.y, v[u + 1].z, v[u + 1].w);
       }
     }
     for (; j < nv; ++j) {
       const float4 v = reinterpret_cast<const float4*>(Vs + (long)j * ld)[i2];
       const float2 c = hs[j];
-      cdfl_fma(sv, make_float2(c.x, c.x), make_float2(c.y, c.y), make_float2(v.x, v.z),
-               make_float2(v.y, v.w));
+      dfl_fma(sx, c.x, c.y, v.x, v.y);
+      dfl_fma(sy, c.x, c.y, v.z, v.w);
     }
-    const cdfl st = cdfl_add(sv, tv);
     double2 o = w2[i2];
-    o.x -= cdfl_to_double_x(st);
-    o.y -= cdfl_to_double_y(st);
+    o.x -= dfl_to_double(dfl_add(sx, tx));
+    o.y -= dfl_to_double(dfl_add(sy, ty));
     w2[i2] = o;
     ss = fma(o.x, o.x, fma(o.y, o.y, ss));
   }
@@ -183,8 +182,7 @@ __global__ void __launch_bounds__(256) k_multi_axpy_s(const float2* __restrict__
   double2* x2 = reinterpret_cast<double2*>(x);
   for (long i2 = (long)blockIdx.x * blockDim.x + threadIdx.x; i2 < n2;
        i2 += (long)gridDim.x * blockDim.x) {
-    // (x, y) components of the pair as packed Dot2 sums s (even j) and t (odd j)
-    cdfl sv = cdfl_zero(), tv = cdfl_zero();
+    dfl sx = dfl_zero(), sy = dfl_zero(), tx = dfl_zero(), ty = dfl_zero();
     int j = 0;
     for (; j + 8 <= nv; j += 8) {
       float4 v[8];
@@ -194,22 +192,21 @@ __global__ void __launch_bounds__(256) k_multi_axpy_s(const float2* __restrict__
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
         const float2 c0 = cs[j + u], c1 = cs[j + u + 1];
-        cdfl_fma(sv, make_float2(c0.x, c0.x), make_float2(c0.y, c0.y),
-                 make_float2(v[u].x, v[u].z), make_float2(v[u].y, v[u].w));
-        cdfl_fma(tv, make_float2(c1.x, c1.x), make_float2(c1.y, c1.y),
-                 make_float2(v[u + 1].x, v[u + 1].z), make_float2(v[u + 1].y, v[u + 1].w));
+        dfl_fma(sx, c0.x, c0.y, v[u].x, v[u].y);
+        dfl_fma(sy, c0.x, c0.y, v[u].z, v[u].w);
+        dfl_fma(tx, c1.x, c1.y, v[u + 1].x, v[u + 1].y);
+        dfl_fma(ty, c1.x, c1.y, v[u + 1].z, v[u + 1].w);
       }
     }
     for (; j < nv; ++j) {
       const float4 v = reinterpret_cast<const float4*>(Vs + (long)j * ld)[i2];
       const float2 c = cs[j];
-      cdfl_fma(sv, make_float2(c.x, c.x), make_float2(c.y, c.y), make_float2(v.x, v.z),
-               make_float2(v.y, v.w));
+      dfl_fma(sx, c.x, c.y, v.x, v.y);
+      dfl_fma(sy, c.x, c.y, v.z, v.w);
     }
-    const cdfl st = cdfl_add(sv, tv);
     double2 o = x2[i2];
-    o.x += cdfl_to_double_x(st);
-    o.y += cdfl_to_double_y(st);
+    o.x += dfl_to_double(dfl_add(sx, tx));
+    o.y += dfl_to_double(dfl_add(sy, ty));
     x2[i2] = o;
   }
 }
