@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--c5-steps", type=int, default=1000, help="time steps of --c5")
     ap.add_argument("--c5-krylov", type=int, default=100, help="Jacobian actions of --c5")
     ap.add_argument("--c5-precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--c5-wave", action="store_true",
+                    help="with --c5: also converge the m = 8 rotating wave (time stepping from "
+                         "the m = 8 seed until it settles, then Newton-GMRES to 1e-10) on "
+                         "the mixed path and time it")
     return ap.parse_args()
 
 
@@ -497,17 +501,17 @@ def coriolis_study(torch, RotatingShell):
 def batch_measure(torch, Batch, count=16, reps=5):
     """Batched uneven instances: 32 continuation points at Ek = 3e-5 with azimuthal
     symmetries M_s = 4, 6, 8, 10, 12 (instance i has M_s = [4, 6, 8, 10, 12][i % 5], so 24, 16,
-    12, 10 and 8 active m), L = 95, N_r = 48, Ra_i = linspace(1.05, 2.0, 32)_i x Ra_c with the
-    onset estimate Ra_c = 2.7 Ek^(-1/3) (the paper prints no onset values; RW12 exists at
-    Ek = 1e-5, Ra = 126 = 2.7 Ek^(-1/3), and the throughput does not depend on Ra).
+    12, 10 and 8 active m), L = 95, N_r = 48, Ra_i = linspace(1.05, 2.0, 32)_i x Ra_c(M_i),
+    the linear onset of mode m = M_i at this truncation (seeded_inputs.ONSET_RA, from the
+    oracle's linear analysis; the paper prints no onset values).
     16 Jacobian actions (Newton pseudo-step dt = 200) per instance per launch, all instances
     in one CUDA graph (rsc_batch_apply_jacobian), against the same actions issued instance
     by instance."""
     import numpy as np
     Ek = 3e-5
-    Rac = 2.7 * Ek ** (-1.0 / 3.0)
     ms_list = [4, 6, 8, 10, 12]
-    inst = [dict(L=95, Ms=ms_list[i % 5], Nr=48, Ek=Ek, Ra=float(f * Rac), precision="mixed")
+    inst = [dict(L=95, Ms=ms_list[i % 5], Nr=48, Ek=Ek,
+                 Ra=float(f * si.ONSET_RA[f"C4_m{ms_list[i % 5]}"]), precision="mixed")
             for i, f in enumerate(np.linspace(1.05, 2.0, 32))]
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
@@ -555,7 +559,9 @@ def batch_measure(torch, Batch, count=16, reps=5):
     n_act = len(inst) * count
     b.close()
     return {"config": "32 instances, Ek=3e-5, L=95, Nr=48, Ms=[4,6,8,10,12][i%5], "
-                      "Ra=linspace(1.05,2,32) x 2.7 Ek^(-1/3), 16 actions each, mixed precision",
+                      "Ra=linspace(1.05,2,32) x Ra_c(Ms) (linear onset of m = Ms), "
+                      "16 actions each, mixed precision",
+            "onset_Ra_by_Ms": {M: si.ONSET_RA[f"C4_m{M}"] for M in ms_list},
             "actions_per_launch": n_act, "graph_ms_per_launch": t_graph * 1e3,
             "jvps_per_s_batched": n_act / t_graph, "jvps_per_s_sequential": n_act / t_seq,
             "batching_speedup": t_seq / t_graph, "create_s": t_create, "autotune_s": t_tune,
@@ -728,14 +734,19 @@ def resolution_study(torch, RotatingShell):
     return out
 
 
-def c5_run(torch, RotatingShell, nsteps=1000, krylov=100, precisions=("mixed", "fp64")):
+def c5_run(torch, RotatingShell, nsteps=1000, krylov=100, precisions=("mixed", "fp64"),
+           wave=False):
     """The large single instance (Ek = 3e-6, Pr = 1, r_in/r_out = 0.35, L = 255, M_s = 8,
-    N_r = 96, dt = 2e-6): from the m = 8 seed, `nsteps` IMEX Euler steps timed with CUDA
-    events, then one Newton iteration (FP64 residual at dt = 200, GMRES with `krylov`
-    Jacobian actions, update, FP64 residual) on the stepped state, for the mixed and the
-    FP64 path, each autotuned; and the per-kernel time of one traced Newton iteration."""
+    N_r = 96, dt = 2e-6, Ra = 1.1 Ra_c of m = 8): from the m = 8 seed, `nsteps` IMEX Euler
+    steps timed with CUDA events, then one Newton iteration (FP64 residual at dt = 200, GMRES
+    with `krylov` Jacobian actions, update, FP64 residual) on the stepped state, for the
+    mixed and the FP64 path, each autotuned; and the per-kernel time of one traced Newton
+    iteration.  wave: the m = 8 rotating wave converged on the mixed path (time stepping at
+    dt = 2e-5 from the seed until the m = 8 temperature amplitude settles, then Newton-GMRES
+    to a residual of 1e-10), with the time of each part."""
     c = si.config("C5")
-    out = {"config": "C5: Ek=3e-6, L=255, Ms=8, Nr=96, dt=2e-6", "n": None}
+    out = {"config": f"C5: Ek=3e-6, L=255, Ms=8, Nr=96, dt=2e-6, Ra={c['Ra']:.4f} "
+                     f"(1.1 x onset of m = 8, {si.ONSET_RA['C5']:.4f})", "n": None}
     for prec in precisions:
         sh = RotatingShell(c["L"], 8, c["Nr"], c["Ek"], c["Ra"], precision=prec)
         tuning = sh.autotune()
@@ -775,6 +786,29 @@ def c5_run(torch, RotatingShell, nsteps=1000, krylov=100, precisions=("mixed", "
                      "tuning": tuning}
         sh.close()
         print(json.dumps({"c5_" + prec: out[prec]}), flush=True)
+    if wave:
+        cw = dict(L=c["L"], Ms=8, Nr=c["Nr"], Ek=c["Ek"], Ra=c["Ra"], seed_dt=2e-5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        guess, C0, J, steps = _wave_from_seed(torch, RotatingShell, cw, "mixed", max_steps=150000)
+        torch.cuda.synchronize()
+        t_seed = time.perf_counter() - t0
+        sh = RotatingShell(c["L"], 8, c["Nr"], c["Ek"], c["Ra"], precision="mixed")
+        sh.autotune()
+        U = guess.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        C, rep, st = sh.newton_rw(U, C0, J, tol=1e-10, max_newton=12, kmax=400, gmres_tol=1e-10)
+        torch.cuda.synchronize()
+        t_newton = time.perf_counter() - t0
+        ke, nui, nuo = sh.diagnostics(U)
+        out["wave"] = {"seed_dt": 2e-5, "seed_steps": steps, "seed_s": t_seed, "C_seed": C0,
+                       "newton_s": t_newton, "status": st, "C": C, "KE": ke, "Nu_in": nui,
+                       "Nu_out": nuo, "newton_iterations": rep["newton_iterations"],
+                       "jacobian_actions": rep["gmres_total"], "residual": rep["residual"],
+                       "time_to_wave_s": t_seed + t_newton}
+        sh.close()
+        print(json.dumps({"c5_wave": out["wave"]}), flush=True)
     if "mixed" in out and "fp64" in out:
         out["mixed_over_fp64"] = {
             "timesteps": out["mixed"]["timesteps_per_s"] / out["fp64"]["timesteps_per_s"],
@@ -925,7 +959,7 @@ def run_gpu(args):
         if rank == 0:
             precs = ("mixed", "fp64") if args.c5_precision == "both" else (args.c5_precision,)
             print(json.dumps({"c5": c5_run(torch, RotatingShell, args.c5_steps, args.c5_krylov,
-                                           precs)}), flush=True)
+                                           precs, wave=args.c5_wave)}), flush=True)
         return 0
     if args.resolution_study:
         if rank == 0:
@@ -1057,6 +1091,8 @@ def run_gpu(args):
             "dtype": dtype_label(args.precision, tuning),
             "data": "synthetic (seeded perturbation of the conductive state)",
             "config": {"workload": w["name"], "precision": args.precision,
+                       "onset_Ra": si.ONSET_RA["C3"],
+                       "Ra_over_onset": w["Ra"] / si.ONSET_RA["C3"],
                        "step": f"1 Newton iteration: FP64 residual, GMRES with {K} Jacobian "
                                f"actions (one-reduction MGS), update, FP64 residual",
                        "krylov_per_iteration": K, "parallelism": f"replicas x{world}",

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RSC_ABI_VERSION 7
+#define RSC_ABI_VERSION 8
 
 typedef struct rsc_ctx rsc_ctx;
 
@@ -401,6 +401,11 @@ typedef struct {
                               relative errors up to 1e-8 in the small poloidal field of
                               the m = 0 chains; one step removes them.  The double-float
                               solve of the mixed path is not refined.                  */
+  int synth_pipe;          /* tensor-core synthesis (mixed path): 1 = the table tile and
+                              operand of the next (parity, table) phase are staged while
+                              the MMAs of the current one run (two tile stages; only
+                              where they fit in shared memory, padded K <= 72); 0 = the
+                              phases one after another.  Same arithmetic.              */
   double ms[6];            /* after rsc_autotune: best times (ms) of products +
                               analysis (mixed), FP64 synthesis, RHS (mixed), FP64 chain
                               solve, double-float chain solve (0 if none ran); zero

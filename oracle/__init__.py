@@ -18,6 +18,9 @@ shell   the discretised Boussinesq model: explicit terms, implicit operator
         IMEX Euler step (Eq. discrete), the Jacobian action with the phase
         trick (Secs. 3.3-3.4).
 krylov  MGS-GMRES and the Newton iteration for rotating waves (Secs. 3.3-3.4).
+onset   the linear onset of convection about the conductive state: the pencil of the
+        linearised operator per (m, symmetry class), its rightmost eigenvalue, and the
+        critical Rayleigh number and drift of each mode (Secs. 2.2, 4.4).
 continuation  natural-parameter continuation in Ra and in log10 Ek, spectral-tail
         refinement and zero-fill regridding (Secs. 4.3-4.4).
 

@@ -148,7 +148,8 @@ struct rsc_ctx {
   long* tc_off = nullptr;
   int* tc_kpad = nullptr;
   int tc_nmt = 1;
-  size_t tc_smem = 0;
+  int tc_kmax = 0;          // largest padded K of the synthesis tiles
+  int synth_pipe = 0;       // 1: two-stage tensor-core synthesis (where it fits)
   int* d_status = nullptr;
   // tracing: launch counter, per-kernel CUDA-event timing and algorithmic traffic
   long launches = 0;
@@ -348,6 +349,9 @@ rsc_status upload_legendre(rsc_ctx* ctx, LegDev<R>& L) {
 // A tiles of the tensor-core synthesis: for each (m, parity s, table w, latitude tile),
 // 128 latitudes x Kpad degrees of the class in the K-major core-matrix layout,
 // TF32 hi part then lo part.
+// The two-stage tensor-core synthesis fits in the opt-in shared memory of a CTA.
+bool synth_pipe_fits(int kmax) { return kmax > 0 && tc_synth_smem(kmax, true) <= 227 * 1024; }
+
 rsc_status build_tc_tables(rsc_ctx* ctx) {
   const Dims& d = ctx->d;
   const HostTables& t = ctx->t;
@@ -396,7 +400,8 @@ rsc_status build_tc_tables(rsc_ctx* ctx) {
   ctx->tc_nmt = nmt;
   int kmax = 0;
   for (int k : kpad) kmax = std::max(kmax, k);
-  ctx->tc_smem = (2 * 128 * (size_t)kmax + 2 * (size_t)kTcNV * kmax) * sizeof(float) + 64;
+  ctx->tc_kmax = kmax;
+  ctx->synth_pipe = synth_pipe_fits(kmax) ? 1 : 0;
   return RSC_OK;
 }
 
@@ -486,7 +491,8 @@ rsc_status set_smem_limits(rsc_ctx* ctx) {
   CK(cudaFuncSetAttribute(k_analysis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_rhs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_rhs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+  CK(cudaFuncSetAttribute(k_synth_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+  CK(cudaFuncSetAttribute(k_synth_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
   CK(cudaFuncSetAttribute(k_analysis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ta_smem()));
   CK(cudaFuncSetAttribute(k_dots_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * (kMaxKrylov + 2) * 8));
   return RSC_OK;
@@ -714,9 +720,15 @@ rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
            52.0 * d.P * d.nlat2 * d.Nd);
   if (sizeof(R) == 4) {
     TcTables tt{ctx->tc_tiles, ctx->tc_off, ctx->tc_kpad, ctx->tc_nmt, ctx->d_status};
-    k_synth_tc<<<dim3(d.nm, (d.Nd + kTcRadii - 1) / kTcRadii, ctx->tc_nmt), 128, ctx->tc_smem,
-                 ctx->s>>>(g, tt, reinterpret_cast<const float2*>(ctx->SR),
-                           reinterpret_cast<float2*>(FCout));
+    const dim3 grid(d.nm, (d.Nd + kTcRadii - 1) / kTcRadii, ctx->tc_nmt);
+    const bool pipe = ctx->synth_pipe != 0;
+    const size_t smem = tc_synth_smem(ctx->tc_kmax, pipe);
+    if (pipe)
+      k_synth_tc<true><<<grid, 128, smem, ctx->s>>>(g, tt, reinterpret_cast<const float2*>(ctx->SR),
+                                                    reinterpret_cast<float2*>(FCout));
+    else
+      k_synth_tc<false><<<grid, 128, smem, ctx->s>>>(g, tt, reinterpret_cast<const float2*>(ctx->SR),
+                                                     reinterpret_cast<float2*>(FCout));
     CK(cudaGetLastError());
   } else {
     const int RT = ctx->rt_synth[0];
@@ -735,7 +747,7 @@ size_t products_smem(const Dims& d, bool lin, int wpb) {
   using V = typename C2<R>::T;
   const int K1 = d.K + 1, NF = lin ? 18 : 9;
   return (size_t)wpb * NF * K1 * sizeof(V) + 4 * (size_t)K1 * d.nphi * sizeof(R) +
-         (size_t)wpb * 4 * d.nphi * sizeof(R);
+         (size_t)wpb * 4 * (d.nphi + 1) * sizeof(R);
 }
 
 // Shared memory of the Legendre analysis for RT radii per block and TC staged latitudes.
@@ -1766,6 +1778,8 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
   if (t.chain_parts < 1 || t.chain_parts > kMaxChainParts) return false;
   if (t.factor_gpu != 0 && t.factor_gpu != 1) return false;
   if (t.refine < 0 || t.refine > 2) return false;
+  if (t.synth_pipe != 0 && t.synth_pipe != 1) return false;
+  if (t.synth_pipe == 1 && !synth_pipe_fits(ctx->tc_kmax)) return false;
   if (!chain_df_ok(d, t.chain_df_cluster, t.chain_df)) return false;
   return chain_config_ok(d, t.chain_cluster, t.chain_async);
 }
@@ -1793,6 +1807,7 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
   t->chain_parts = ctx->chain_parts;
   t->factor_gpu = ctx->factor_gpu;
   t->refine = ctx->refine;
+  t->synth_pipe = ctx->synth_pipe;
   for (int q = 0; q < 6; ++q) t->ms[q] = ctx->tune_ms[q];
 }
 
@@ -1812,6 +1827,7 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
   ctx->cluster_df = t.chain_df_cluster;
   ctx->krylov_split = t.krylov_split;
   ctx->refine = t.refine;
+  ctx->synth_pipe = t.synth_pipe;
   if (t.factor_gpu != ctx->factor_gpu) {
     // the factorisations are rebuilt where the new setting says
     ctx->factor_gpu = t.factor_gpu;
@@ -1891,6 +1907,19 @@ rsc_status tune_precision(rsc_ctx* ctx, rsc_tuning& t, cudaEvent_t e0, cudaEvent
     if (ms < best) best = ms;
   }
   if (p == 1) ctx->tune_ms[0] = best;   // products + analysis of the mixed path
+  // tensor-core synthesis (mixed path): two-stage schedule against one phase at a time
+  if (p == 1 && synth_pipe_fits(ctx->tc_kmax)) {
+    double bt = 1e30;
+    int bpipe = 0;
+    for (int pipe : {0, 1}) {
+      ctx->synth_pipe = pipe;
+      const double ms = timeit([&] { return stage_synth<float>(ctx, ctx->rtmp, ctx->FC); });
+      CKS(st);
+      CKS(check_status(ctx));
+      if (ms < bt) { bt = ms; bpipe = pipe; }
+    }
+    ctx->synth_pipe = t.synth_pipe = bpipe;
+  }
   // synthesis (CUDA-core FP64 path): radii per block
   if (p == 0) {
     best = 1e30;

@@ -287,7 +287,7 @@ __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
   R* tws = twc + K1 * nphi;
   R* twcT = tws + K1 * nphi;                              // [nphi][K1] / nphi
   R* twsT = twcT + K1 * nphi;
-  R* prod = twsT + K1 * nphi;                             // [WPB][4][nphi]
+  R* prod = twsT + K1 * nphi;                             // [WPB][4][nphi + 1]
   const int i = blockIdx.x;
   const R inv = (R)1 / (R)nphi;
   for (int idx = threadIdx.x; idx < K1 * nphi; idx += blockDim.x) {
@@ -302,7 +302,8 @@ __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   V* cw = coef + w * NF * K1;
-  R* pw = prod + w * 4 * nphi;
+  const int pst = nphi + 1;   // padded row: the four products of one j sit in four banks
+  R* pw = prod + w * 4 * pst;
   // warp w takes latitudes th0 + w, th0 + w + WPB, ... (LPW of them): the twiddles staged
   // above serve all of them
   const int th0 = blockIdx.y * WPB * LPW;
@@ -355,26 +356,24 @@ __global__ void k_products(DevGeom g, DevLegendre<R> T, R Ek,
         Fp = Ek * ((U[0] * u[4] - U[1] * u[3]) + (u[0] * U[4] - u[1] * U[3]));
         N = U[0] * u[6] + U[1] * u[7] + U[2] * u[8] + u[0] * U[6] + u[1] * U[7] + u[2] * U[8];
       }
-      pw[0 * nphi + j] = Fr;
-      pw[1 * nphi + j] = Ft;
-      pw[2 * nphi + j] = Fp;
-      pw[3 * nphi + j] = N;
+      pw[0 * pst + j] = Fr;
+      pw[1 * pst + j] = Ft;
+      pw[2 * pst + j] = Fp;
+      pw[3 * pst + j] = N;
     }
     __syncwarp();
-    for (int a = lane; a < K1; a += 32) {
-      R sr[4] = {0, 0, 0, 0}, si[4] = {0, 0, 0, 0};
+    // forward DFT: one (product q, wavenumber a) output per lane, 4 (K + 1) outputs per
+    // latitude (a lane per wavenumber left 32 - (K + 1) lanes idle)
+    for (int t = lane; t < 4 * K1; t += 32) {
+      const int q = t / K1, a = t - q * K1;
+      const R* pq = pw + q * pst;
+      R sr = 0, si = 0;
       for (int j = 0; j < nphi; ++j) {
-        const R c = twcT[j * K1 + a], sn = twsT[j * K1 + a];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const R v = pw[q * nphi + j];
-          sr[q] += v * c;
-          si[q] -= v * sn;
-        }
+        const R v = pq[j];
+        sr += v * twcT[j * K1 + a];
+        si -= v * twsT[j * K1 + a];
       }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        FA[(((long)q * Nd + i) * K1 + a) * nlat + th] = mk<R>(sr[q], si[q]);
+      FA[(((long)q * Nd + i) * K1 + a) * nlat + th] = mk<R>(sr, si);
     }
   }
 }

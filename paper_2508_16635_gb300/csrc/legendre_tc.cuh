@@ -93,7 +93,109 @@ __device__ __forceinline__ void tc_ld<2>(uint32_t taddr, float (&v)[2]) {
   v[1] = __uint_as_float(r1);
 }
 
-// grid = (nm, ceil(Nd / 8), nmt); block = 128; dynamic smem from tc_synth_smem().
+// B operand of phase (s, w): columns n = (radius, component, re/im), K-major core-matrix
+// layout; eight independent gathers per thread are in flight before the first store.
+// (Consecutive threads take consecutive columns of one degree, whose sources lie in one
+// 512-byte span of the radial values; a lane-per-core-matrix-entry mapping measured 17 %
+// slower.)
+__device__ __forceinline__ void tc_gather_b(const float2* __restrict__ SR, int p0, int nl, int i0,
+                                            int Nd, int Kp, int s, int w, float* sBh, float* sBl,
+                                            int tid) {
+  const int NC = (w == 0) ? 3 : 5;          // components of this table type
+  const int NW = (w == 0) ? kTcNP : kTcNV;  // N of the GEMM (padded)
+  const int total = NW * Kp;
+  for (int base = tid; base < total; base += 128 * 8) {
+    float vals[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + 128 * u;
+      const int k = idx / NW;
+      const int n = idx - k * NW;
+      const int q = s + 2 * k;
+      const int rr = n / (2 * NC);
+      const int rem = n - rr * 2 * NC;
+      const int c = rem >> 1, ri = rem & 1;
+      const int i = i0 + rr;
+      float v = 0.f;
+      if (idx < total && q < nl && rr < kTcRadii && i < Nd) {
+        const int comp = (w == 0) ? (c == 0 ? 0 : (c == 1 ? 3 : 6))
+                                  : (c < 2 ? c + 1 : (c < 4 ? c + 2 : 7));   // 1, 2, 4, 5, 7
+        const float* z = reinterpret_cast<const float*>(SR + ((long)(p0 + q) * Nd + i) * 8 + comp);
+        v = __ldg(z + ri);
+      }
+      vals[u] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + 128 * u;
+      if (idx < total) {
+        const int k = idx / NW;
+        const int n = idx - k * NW;
+        const float v = vals[u];
+        const float h = tf32_hi(v);
+        const int off = (n >> 3) * (Kp / 4) * 32 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
+        sBh[off] = h;
+        sBl[off] = v - h;
+      }
+    }
+  }
+}
+
+// Bulk copy of the hi and lo A tiles of one phase (one thread), completing on `bar`.
+__device__ __forceinline__ void tc_copy_a(uint32_t bar, float* sAh, float* sAl, const float* src,
+                                          int Kp) {
+  const uint32_t bytes = (uint32_t)(128 * Kp * 4);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc_smem(sAh)),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc_smem(sAl)),
+      "l"(src + 128 * Kp), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// The 3xTF32 MMAs of one phase into accumulator columns `col` (one thread), committed to `bar`.
+__device__ __forceinline__ void tc_mma_phase(uint32_t tmem, uint32_t col, const float* sAh,
+                                             const float* sAl, const float* sBh, const float* sBl,
+                                             int NW, int Kp, uint32_t bar) {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t sbo = (uint32_t)(Kp / 4) * 128u;
+  const uint32_t idesc = tc_idesc(NW);
+  for (int t = 0; t < Kp / 8; ++t) {
+    const uint32_t ko = (uint32_t)t * 256u;   // two core matrices of 128 B per k-step
+    const uint64_t ah = tc_desc(tc_smem(sAh) + ko, 128, sbo);
+    const uint64_t al = tc_desc(tc_smem(sAl) + ko, 128, sbo);
+    const uint64_t bh = tc_desc(tc_smem(sBh) + ko, 128, sbo);
+    const uint64_t bl = tc_desc(tc_smem(sBl) + ko, 128, sbo);
+    tc_mma(tmem + col, ah, bh, idesc, t > 0 ? 1u : 0u);
+    tc_mma(tmem + col, ah, bl, idesc, 1u);
+    tc_mma(tmem + col, al, bh, idesc, 1u);
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// Shared memory of the synthesis for padded K `kmax`: one A stage and one B buffer (PIPE =
+// false), or two A stages and separate B buffers for the P-type and the vector-type phases
+// (PIPE = true), plus four mbarriers and the tensor-memory slot.
+__host__ __device__ constexpr size_t tc_synth_smem(int kmax, bool pipe) {
+  return pipe ? (4 * 128 * (size_t)kmax + 2 * (size_t)(kTcNP + kTcNV) * kmax) * sizeof(float) + 64
+              : (2 * 128 * (size_t)kmax + 2 * (size_t)kTcNV * kmax) * sizeof(float) + 64;
+}
+
+// Six phases (s, w): parity class outer, table type inner, so that the B operand of w = 2
+// (P/sin) is the one already staged for w = 1 (dP/dtheta): the same columns.
+// PIPE = false: each phase copies its A tile, gathers its B operand, runs its MMAs and
+// waits for them before the next phase starts.  PIPE = true: the A tile and B operand of
+// phase p + 1 are staged (second A stage, the other B buffer) while the MMAs of phase p run;
+// a buffer is refilled only after the MMAs that read it have completed.
+// grid = (nm, ceil(Nd / 8), nmt); block = 128; dynamic smem tc_synth_smem(kmax, PIPE).
+template <bool PIPE>
 __global__ void __launch_bounds__(128) k_synth_tc(DevGeom g, TcTables tt, const float2* __restrict__ SR,
                                                   float2* __restrict__ FC) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
@@ -106,14 +208,28 @@ __global__ void __launch_bounds__(128) k_synth_tc(DevGeom g, TcTables tt, const 
   const int Kp = tt.kpad[a];
   const int Nd = g.Nd;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // shared memory: A hi | A lo (128 x Kp each), B hi | B lo (kTcNV x Kp each), barriers
-  float* sAh = reinterpret_cast<float*>(tc_raw);
-  float* sAl = sAh + 128 * Kp;
-  float* sBh = sAl + 128 * Kp;
-  float* sBl = sBh + kTcNV * Kp;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sBl + kTcNV * Kp);   // [0] copies, [1] MMAs
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
-  const uint32_t bar_copy = tc_smem(&bar[0]), bar_mma = tc_smem(&bar[1]);
+  // shared memory: A (hi | lo, 128 x Kp each; two stages when PIPE), B (hi | lo; one buffer
+  // of kTcNV columns, or kTcNP- and kTcNV-column buffers when PIPE), barriers
+  // (pointers chosen with selects, not arrays, so that nothing lands in local memory)
+  float *sA0, *sA1, *sBh0, *sBl0, *sBh1, *sBl1;
+  uint64_t* bar;
+  if constexpr (PIPE) {
+    sA0 = reinterpret_cast<float*>(tc_raw);
+    sA1 = sA0 + 2 * 128 * Kp;
+    sBh0 = sA1 + 2 * 128 * Kp;
+    sBl0 = sBh0 + kTcNP * Kp;
+    sBh1 = sBl0 + kTcNP * Kp;
+    sBl1 = sBh1 + kTcNV * Kp;
+    bar = reinterpret_cast<uint64_t*>(sBl1 + kTcNV * Kp);   // copy[2], mma[2]
+  } else {
+    sA0 = sA1 = reinterpret_cast<float*>(tc_raw);
+    sBh0 = sBh1 = sA0 + 2 * 128 * Kp;
+    sBl0 = sBl1 = sBh0 + kTcNV * Kp;
+    bar = reinterpret_cast<uint64_t*>(sBl0 + kTcNV * Kp);
+  }
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 4);
+  const uint32_t bc0 = tc_smem(&bar[0]), bc1 = tc_smem(&bar[1]);
+  const uint32_t bm0 = tc_smem(&bar[2]), bm1 = tc_smem(&bar[3]);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(tslot)),
                  "r"(kTcAlloc)
@@ -121,8 +237,8 @@ __global__ void __launch_bounds__(128) k_synth_tc(DevGeom g, TcTables tt, const 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_copy), "r"(1) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_mma), "r"(1) : "memory");
+    for (uint32_t b : {bc0, bc1, bm0, bm1})
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -130,101 +246,88 @@ __global__ void __launch_bounds__(128) k_synth_tc(DevGeom g, TcTables tt, const 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
   bool ok = true;
-  const uint32_t sbo = (uint32_t)(Kp / 4) * 128u;
-  const int nks = Kp / 8;
-  uint32_t ph = 0;
-  // phases (s, w): parity class outer, table type inner, so that the B operand of
-  // w = 2 (P/sin) is the one already staged for w = 1 (dP/dtheta): the same columns
-  for (int s = 0; s < 2 && ok; ++s) {
-    for (int w = 0; w < 3 && ok; ++w) {
-    const int NC = (w == 0) ? 3 : 5;          // components of this table type
-    const int NW = (w == 0) ? kTcNP : kTcNV;  // N of the GEMM (padded)
-    {
-      // (1) tables: bulk copy of the hi and lo tiles
-      if (tid == 0) {
-        const float* src = tt.tiles + tt.off[((a * 2 + s) * 3 + w) * tt.nmt + mt];
-        const uint32_t bytes = (uint32_t)(128 * Kp * 4);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_copy),
-                     "r"(2 * bytes)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                tc_smem(sAh)),
-            "l"(src), "r"(bytes), "r"(bar_copy)
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                tc_smem(sAl)),
-            "l"(src + 128 * Kp), "r"(bytes), "r"(bar_copy)
-            : "memory");
-      }
-      // (2) B: columns n = (radius, component, re/im), K-major core-matrix layout; eight
-      // independent gathers per thread are in flight before the first store
-      const int vi[5] = {1, 2, 4, 5, 7};
-      const int total = (w == 2) ? 0 : NW * Kp;   // w = 2 reuses the operand of w = 1
-      for (int base = tid; base < total; base += 128 * 8) {
-        float vals[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int idx = base + 128 * u;
-          const int k = idx / NW;
-          const int n = idx - k * NW;
-          const int q = s + 2 * k;
-          const int rr = n / (2 * NC);
-          const int rem = n - rr * 2 * NC;
-          const int c = rem >> 1, ri = rem & 1;
-          const int i = i0 + rr;
-          float v = 0.f;
-          if (idx < total && q < nl && rr < kTcRadii && i < Nd) {
-            const int comp = (w == 0) ? (c == 0 ? 0 : (c == 1 ? 3 : 6)) : vi[c];
-            const float* z = reinterpret_cast<const float*>(SR + ((long)(p0 + q) * Nd + i) * 8 + comp);
-            v = __ldg(z + ri);
-          }
-          vals[u] = v;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int idx = base + 128 * u;
-          if (idx < total) {
-            const int k = idx / NW;
-            const int n = idx - k * NW;
-            const float v = vals[u];
-            const float h = tf32_hi(v);
-            const int off = (n >> 3) * (Kp / 4) * 32 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
-            sBh[off] = h;
-            sBl[off] = v - h;
-          }
-        }
-      }
+  auto tile = [&](int p) {
+    return tt.tiles + tt.off[((a * 2 + p / 3) * 3 + p % 3) * tt.nmt + mt];
+  };
+  auto col_of = [&](int p) -> uint32_t {
+    const int s = p / 3, w = p % 3;
+    return (w == 0) ? s * kTcNP : 2 * kTcNP + ((w - 1) * 2 + s) * kTcNV;
+  };
+  if constexpr (!PIPE) {
+    uint32_t ph = 0;
+    for (int p = 0; p < 6 && ok; ++p) {
+      const int s = p / 3, w = p % 3;
+      // (1) tables: bulk copy of the hi and lo tiles; (2) B (w = 2 reuses the operand of w = 1)
+      if (tid == 0) tc_copy_a(bc0, sA0, sA0 + 128 * Kp, tile(p), Kp);
+      if (w != 2) tc_gather_b(SR, p0, nl, i0, Nd, Kp, s, w, sBh0, sBl0, tid);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-      ok = tc_wait(bar_copy, ph);
+      ok = tc_wait(bc0, ph);
       // (3) the MMAs, issued by one thread
-      if (tid == 0 && ok) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t col = (w == 0) ? s * kTcNP : 2 * kTcNP + ((w - 1) * 2 + s) * kTcNV;
-        const uint32_t idesc = tc_idesc(NW);
-        for (int t = 0; t < nks; ++t) {
-          const uint32_t ko = (uint32_t)t * 256u;   // two core matrices of 128 B per k-step
-          const uint64_t ah = tc_desc(tc_smem(sAh) + ko, 128, sbo);
-          const uint64_t al = tc_desc(tc_smem(sAl) + ko, 128, sbo);
-          const uint64_t bh = tc_desc(tc_smem(sBh) + ko, 128, sbo);
-          const uint64_t bl = tc_desc(tc_smem(sBl) + ko, 128, sbo);
-          tc_mma(tmem + col, ah, bh, idesc, t > 0 ? 1u : 0u);
-          tc_mma(tmem + col, ah, bl, idesc, 1u);
-          tc_mma(tmem + col, al, bh, idesc, 1u);
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         bar_mma)
-                     : "memory");
-      }
+      if (tid == 0 && ok)
+        tc_mma_phase(tmem, col_of(p), sA0, sA0 + 128 * Kp, sBh0, sBl0, (w == 0) ? kTcNP : kTcNV,
+                     Kp, bm0);
       // shared operands are reused by the next phase: wait for the MMAs
-      const bool mma_ok = ok ? tc_wait(bar_mma, ph) : false;
+      const bool mma_ok = ok ? tc_wait(bm0, ph) : false;
       ok = ok && mma_ok;
       ph ^= 1u;
       __syncthreads();
     }
+  } else {
+    // bit b of `ph`: parity of the next wait on barrier b (copy 0, copy 1, MMA 0, MMA 1);
+    // bit b of `pend`: an operation completing on barrier b not yet waited for (every exit
+    // path waits for it)
+    uint32_t ph = 0u, pend = 0u;
+    auto bar_of = [&](int b) { return b == 0 ? bc0 : b == 1 ? bc1 : b == 2 ? bm0 : bm1; };
+    auto wait_bar = [&](int b) {
+      const bool done = tc_wait(bar_of(b), (ph >> b) & 1u);
+      if (done) {
+        ph ^= 1u << b;
+        pend &= ~(1u << b);
+      }
+      return done;
+    };
+    if (tid == 0) tc_copy_a(bc0, sA0, sA0 + 128 * Kp, tile(0), Kp);
+    pend |= 1u;
+    tc_gather_b(SR, p0, nl, i0, Nd, Kp, 0, 0, sBh0, sBl0, tid);
+    for (int p = 0; p < 6; ++p) {
+      const int st = p & 1, w = p % 3;
+      float* A = st ? sA1 : sA0;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();   // B of phase p stored by every thread
+      const bool got = wait_bar(st);
+      ok = __syncthreads_and(got ? 1 : 0) != 0;   // one decision for the whole CTA
+      if (!ok) break;
+      if (tid == 0)
+        tc_mma_phase(tmem, col_of(p), A, A + 128 * Kp, w == 0 ? sBh0 : sBh1, w == 0 ? sBl0 : sBl1,
+                     (w == 0) ? kTcNP : kTcNV, Kp, st ? bm1 : bm0);
+      pend |= 1u << (2 + st);
+      if (p + 1 < 6) {
+        const int nst = st ^ 1;
+        // phase p + 1 refills A stage nst, last read by the MMAs of phase p - 1, and (when
+        // it gathers) the B buffer of its table type, last read by phase p - 1 or earlier
+        if (pend & (1u << (2 + nst))) {
+          const bool done = wait_bar(2 + nst);
+          ok = __syncthreads_and(done ? 1 : 0) != 0;
+          if (!ok) break;
+        }
+        float* An = nst ? sA1 : sA0;
+        if (tid == 0) tc_copy_a(nst ? bc1 : bc0, An, An + 128 * Kp, tile(p + 1), Kp);
+        pend |= 1u << nst;
+        const int w1 = (p + 1) % 3;
+        if (w1 != 2)
+          tc_gather_b(SR, p0, nl, i0, Nd, Kp, (p + 1) / 3, w1, w1 == 0 ? sBh0 : sBh1,
+                      w1 == 0 ? sBl0 : sBl1, tid);
+      }
     }
+    // the last MMAs (and, after a timeout, every copy and MMA still in flight: a wait that
+    // gave up is retried once more, bounded, before the tensor memory is released)
+    for (int b = 3; b >= 0; --b)
+      if (pend & (1u << b)) {
+        const bool done = wait_bar(b);
+        ok = ok && done;
+      }
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
   }
   if (!ok && tid == 0) atomicExch(tt.status, 7);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

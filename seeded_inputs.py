@@ -56,6 +56,23 @@ def random_vector(L, Ms, Nr, seed, amp=1.0):
     return perturbation(L, Ms, Nr, seed, amp=amp)
 
 
+# Linear onset Ra_c of each workload's rotating wave (mode m = M, equatorially symmetric,
+# Pr = 1, r_in/r_out = 0.35) at the workload's own truncation: the values that
+# tests/golden/make_onset.py wrote to tests/golden/onset_workloads.txt from the oracle's
+# linear analysis (tests/test_oracle_onset.py checks that the two tables agree).  The
+# paper prints no onset values.
+ONSET_RA = {
+    "C1": 55.9041816078,
+    "C2": 69.5958906601,
+    "C3": 111.2929193930,
+    "C4_m4": 118.4463565448,
+    "C4_m6": 100.8089645706,
+    "C4_m8": 90.3601771719,
+    "C4_m10": 85.2962306339,
+    "C4_m12": 85.8781358929,
+}
+
+
 def config(name):
     """Truncation and physical parameters of the named workloads.
 

@@ -893,3 +893,93 @@ def test_rw12_wave_against_the_oracle_wave(torch, precision):
     print(precision, errs)
     assert max(errs.values()) < 1e-8, errs
     gpu.close()
+
+
+# ---- linear onset (oracle/onset.py; Secs. 2.2, 4.4) ----------------------------------------
+def _golden_onset():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "onset_workloads.txt")
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            rows[f[0]] = dict(Ek=float(f[1]), m=int(f[2]), L=int(f[3]), Nr=int(f[4]),
+                              Ra=float(f[5]), omega=float(f[6]), C=float(f[7]))
+    return rows
+
+
+@functools.lru_cache(maxsize=None)
+def _onset_mode(name):
+    """The oracle's neutral mode of a workload at its stored onset (make_onset.py): Arnoldi
+    near i omega on the pencil at Ra_c; (state vector, sigma, row)."""
+    from oracle import onset as on
+    g = _golden_onset()[name]
+    pen = on.Pencil(Shell(g["L"], g["m"], g["Nr"], g["Ek"], 1.0), g["m"], 1)
+    sig, V = on.eig_near(pen, g["Ra"], 1j * g["omega"], k=4)
+    j = int(np.argmin(np.abs(sig - 1j * g["omega"])))
+    return pen.state(V[:, j] / np.linalg.norm(V[:, j])), complex(sig[j]), g
+
+
+@pytest.mark.parametrize("name", ["C1", "C2"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_linearised_step_fixes_the_onset_mode(torch, name, precision):
+    """At the workload's onset (Ra_c) with the onset drift C_c = -omega/m in the explicit
+    part, the GPU's linearised step at the conductive state leaves the oracle's neutral mode
+    unchanged: |(B_U - I) u| / |u| below 1e-10 in FP64 (below 1e-4 on the mixed path, whose
+    FP32 transforms move a Jacobian action by about 2e-5), at the Newton pseudo-timestep and
+    at a short one.  Off onset (Ra = 0.9 Ra_c) it does not."""
+    from paper_2508_16635_gb300 import RotatingShell
+    u, sig, g = _onset_mode(name)
+    M = g["m"]
+    C = -sig.imag / M
+    bound = 1e-10 if precision == "fp64" else 1e-4
+    gpu = RotatingShell(g["L"], M, g["Nr"], g["Ek"], g["Ra"], precision=precision)
+    U = gpu.conductive_state()
+    ut = torch.tensor(u, device="cuda")
+    for dt in (200.0, 1e-3):
+        r = gpu.apply_jacobian(U, C, None, ut, dt).cpu().numpy()
+        assert np.linalg.norm(r) < bound * np.linalg.norm(u), (dt, np.linalg.norm(r))
+    gpu.set_params(Ra=0.9 * g["Ra"])
+    r = gpu.apply_jacobian(gpu.conductive_state(), C, None, ut, 200.0).cpu().numpy()
+    assert np.linalg.norm(r) > 1e-3 * np.linalg.norm(u)
+    gpu.close()
+
+
+def test_rw_branch_meets_the_onset_on_the_gpu(torch):
+    """The nonlinear branch against the linear onset: RW4 (Ek = 1e-3) followed down in Ra by
+    the GPU's Newton-GMRES from Table 1's Ra = 120 to 1.01 Ra_c.  Near a supercritical onset
+    the kinetic energy grows like Ra - Ra_c and the drift tends to the onset drift, so the
+    linear extrapolation of KE and C from 1.01 and 1.02 Ra_c gives Ra_c within 5e-4 and C_c
+    within 2e-4 of the oracle's pencil (L = 23, N_r = 16; the oracle's own branch lands
+    within 1.0e-4 and 2.1e-5)."""
+    from oracle import krylov
+    from oracle import onset as on
+    from paper_2508_16635_gb300 import RotatingShell
+    L, Ms, Nr, Ek, M = 23, 4, 16, 1e-3, 4
+    lin = on.critical_rayleigh(on.Pencil(Shell(L, M, Nr, Ek, 1.0), M, 1), (40.0, 80.0),
+                               shift="auto")
+    s = Shell(L, Ms, Nr, Ek, 120.0)
+    U0, C0, J = _rw_initial_guess(s, M)
+    gpu = RotatingShell(L, Ms, Nr, Ek, 120.0)
+    U = torch.tensor(U0, device="cuda")
+    Uc = gpu.conductive_state()
+    C, rep, st = gpu.newton_rw(U, C0, J, tol=1e-11, max_newton=14, kmax=150)
+    assert st == 0, rep
+    Ra_prev = 120.0
+    pts = []
+    for f in (1.6, 1.3, 1.15, 1.07, 1.04, 1.02, 1.01):
+        Ra = f * lin["Ra"]
+        # weakly nonlinear predictor: the amplitude scales like sqrt(Ra - Ra_c)
+        U.copy_(Uc + (U - Uc) * np.sqrt((Ra - lin["Ra"]) / (Ra_prev - lin["Ra"])))
+        gpu.set_params(Ra=Ra)
+        C, rep, st = gpu.newton_rw(U, C, J, tol=1e-11, max_newton=20, kmax=200)
+        assert st == 0 and rep["residual"] < 1e-11, (f, rep)
+        pts.append((Ra, gpu.diagnostics(U)[0], C))
+        Ra_prev = Ra
+    (Ra2, k2, c2), (Ra1, k1, c1) = pts[-2], pts[-1]
+    Ra_ext = Ra1 - k1 * (Ra2 - Ra1) / (k2 - k1)
+    C_ext = c1 + (c2 - c1) * (Ra_ext - Ra1) / (Ra2 - Ra1)
+    print("onset", lin["Ra"], Ra_ext, lin["C"], C_ext)
+    assert abs(Ra_ext - lin["Ra"]) < 5e-4 * lin["Ra"]
+    assert abs(C_ext - lin["C"]) < 2e-4 * abs(lin["C"])
+    gpu.close()
