@@ -70,6 +70,7 @@ ONSET_RA = {
     "C4_m8": 90.3601771719,
     "C4_m10": 85.2962306339,
     "C4_m12": 85.8781358929,
+    "C5": 219.0622885318,
 }
 
 
@@ -85,7 +86,8 @@ def config(name):
         "C1": dict(L=31, Ms=4, Nr=24, Ek=1e-3, dt=1e-4, Ra=120.0),
         "C2": dict(L=63, Ms=8, Nr=48, Ek=1e-4, dt=2e-5, Ra=130.0),
         "C3": dict(L=127, Ms=12, Nr=64, Ek=1e-5, dt=5e-6, Ra=140.0),
-        "C5": dict(L=255, Ms=8, Nr=96, Ek=3e-6, dt=2e-6, Ra=200.0),
+        # C5 at 1.1 x the onset of its m = 8 wave
+        "C5": dict(L=255, Ms=8, Nr=96, Ek=3e-6, dt=2e-6, Ra=1.1 * ONSET_RA["C5"]),
     }
     d = dict(table[name])
     d.update(Pr=1.0, eta=0.35)
