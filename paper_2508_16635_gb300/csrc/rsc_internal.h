@@ -68,12 +68,35 @@ struct HostFactor {
                                       // and of the previous part's last block (-1: none)
 };
 
+// One level of odd-even (cyclic) reduction of every e/f chain, for the double-float solve
+// of the mixed path.  With D_i, A_i, C_i the diagonal block of block row i and its
+// couplings to blocks i - 1 and i + 1, the odd blocks are eliminated:
+//   x_i = D_i^-1 (b_i - A_i x_{i-1} - C_i x_{i+1}),   i odd,
+// which leaves a block-tridiagonal chain of half the length on the even blocks j = 2t:
+//   D'_t = D_j - A_j D_{j-1}^-1 C_{j-1} - C_j D_{j+1}^-1 A_{j+1},
+//   A'_t = -A_j D_{j-1}^-1 A_{j-1},   C'_t = -C_j D_{j+1}^-1 C_{j+1},
+//   b'_t = b_j - A_j D_{j-1}^-1 b_{j-1} - C_j D_{j+1}^-1 b_{j+1}.
+// The reduced chains carry the twisted block factors of HostFactor (G, H, W; middle block
+// t = (nr - 1) / 2 of nr = (nb + 1) / 2), so the solve is: u_i = D_i^-1 b_i (odd), b'
+// (even), the twisted sweeps over the reduced chains, then the odd blocks from their
+// neighbours.  Terms that reach past a chain end are absent.
+struct HostFactorCR {
+  double dt = 0;
+  std::vector<long> odd_off;   // per chain (+1 total): first odd block in Dinv
+  std::vector<long> red_off;   // per chain (+1 total): first reduced block in G, H, W
+  std::vector<cplx> Dinv;      // per odd block i = 1, 3, ...: D_i^-1, Nr x Nr row-major
+  std::vector<cplx> G, H, W;   // twisted factors of the reduced chains, as HostFactor
+};
+
 void build_dims(const rsc_params& p, Dims& d);
 void build_tables(const rsc_params& p, const Dims& d, HostTables& t);
 // Returns 0 on success, or 1 + chain index of a singular block.
 // nparts > 1: partitioned chains (parts of at least 8 blocks, at most nparts per chain).
 int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double dt,
                  HostFactor& f, int nparts = 1);
+// Returns 0 on success, or 1 + chain index of a singular block (implicit Coriolis only).
+int build_factor_cr(const rsc_params& p, const Dims& d, const HostTables& t, double dt,
+                    HostFactorCR& f);
 // Gauss-Legendre nodes (descending from +1) and weights on [-1, 1].
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 void conductive_T00(const rsc_params& p, const Dims& d, const HostTables& t,

@@ -740,6 +740,162 @@ int build_factor(const rsc_params& p, const Dims& d, const HostTables& t, double
   return 0;
 }
 
+// One level of odd-even reduction of every e/f chain (HostFactorCR): the inverses of the
+// odd diagonal blocks, the reduced chains on the even blocks, and the twisted block factors
+// of the reduced chains (the conventions of build_factor on a range 0..nr-1, with row
+// equilibration over the reduced block row).
+int build_factor_cr(const rsc_params& p, const Dims& d, const HostTables& t, double dt,
+                    HostFactorCR& f) {
+  const int Nr = d.Nr;
+  const size_t blk = (size_t)Nr * Nr;
+  Ops ops{d, t, p.Ek, p.Pr, std::isfinite(dt) ? 1.0 / dt : 0.0, Nr, p.explicit_coriolis != 0};
+  f.dt = dt;
+  const int nchains = 2 * d.nm;
+  f.odd_off.resize(nchains + 1);
+  f.red_off.resize(nchains + 1);
+  long no = 0, nr = 0;
+  for (int c = 0; c < nchains; ++c) {
+    const int nb = d.L - t.m_of[c / 2] + 1;
+    f.odd_off[c] = no;
+    f.red_off[c] = nr;
+    no += nb / 2;
+    nr += (nb + 1) / 2;
+  }
+  f.odd_off[nchains] = no;
+  f.red_off[nchains] = nr;
+  f.Dinv.assign(no * blk, cplx(0.0));
+  f.G.assign(nr * blk, cplx(0.0));
+  f.H.assign(nr * blk, cplx(0.0));
+  f.W.assign(nr * blk, cplx(0.0));
+  // Cm -= Am Bm (row-major Nr x Nr)
+  auto sub_prod = [&](cplx* Cm, const cplx* Am, const cplx* Bm) {
+    for (int r = 0; r < Nr; ++r)
+      for (int q = 0; q < Nr; ++q) {
+        const cplx a = Am[(size_t)r * Nr + q];
+        if (a == cplx(0.0)) continue;
+        const cplx* br = Bm + (size_t)q * Nr;
+        cplx* cr = Cm + (size_t)r * Nr;
+        for (int k = 0; k < Nr; ++k) cr[k] -= a * br[k];
+      }
+  };
+  auto row_max = [&](const cplx* Mx, std::vector<double>& S) {
+    for (int r = 0; r < Nr; ++r)
+      for (int k = 0; k < Nr; ++k) S[r] = std::max(S[r], std::abs(Mx[(size_t)r * Nr + k]));
+  };
+  auto scale_rows = [&](cplx* Mx, const std::vector<double>& S) {
+    for (int r = 0; r < Nr; ++r)
+      for (int k = 0; k < Nr; ++k) Mx[(size_t)r * Nr + k] *= S[r];
+  };
+  std::vector<int> bad(nchains, 0);
+  auto work = [&](int c) -> bool {
+    const int a = c / 2, cls = c % 2, m = t.m_of[a];
+    const int nb = d.L - m + 1, nodd = nb / 2, nred = (nb + 1) / 2;
+    auto field_of = [&](int i) { return ((i + cls) % 2 == 0) ? 0 : 1; };
+    std::vector<cplx> D, A, C, tmp;
+    std::vector<double> S(Nr);
+    std::vector<int> piv;
+    // odd blocks i = 2q + 1: D_i^-1, Pq = D_i^-1 A_i, Qq = D_i^-1 C_i
+    std::vector<cplx> Pm((size_t)nodd * blk, cplx(0.0)), Qm((size_t)nodd * blk, cplx(0.0));
+    for (int q = 0; q < nodd; ++q) {
+      const int i = 2 * q + 1, l = m + i, fld = field_of(i);
+      ops.diag(fld, l, m, D);
+      std::fill(S.begin(), S.end(), 0.0);
+      row_max(D.data(), S);
+      for (int r = 0; r < Nr; ++r) S[r] = 1.0 / S[r];
+      scale_rows(D.data(), S);
+      if (!lu_factor(Nr, D, piv)) return false;
+      tmp.assign(blk, cplx(0.0));
+      for (int r = 0; r < Nr; ++r) tmp[(size_t)r * Nr + r] = S[r];
+      lu_solve(Nr, D, piv, Nr, tmp);
+      std::copy(tmp.begin(), tmp.end(), &f.Dinv[(f.odd_off[c] + q) * blk]);
+      ops.coupling(fld, l, m, -1, A);
+      scale_rows(A.data(), S);
+      lu_solve(Nr, D, piv, Nr, A);
+      std::copy(A.begin(), A.end(), &Pm[(size_t)q * blk]);
+      if (i + 1 < nb) {
+        ops.coupling(fld, l, m, +1, C);
+        scale_rows(C.data(), S);
+        lu_solve(Nr, D, piv, Nr, C);
+        std::copy(C.begin(), C.end(), &Qm[(size_t)q * blk]);
+      }
+    }
+    // reduced chain on the even blocks j = 2 tt
+    std::vector<cplx> Dr((size_t)nred * blk, cplx(0.0)), Ar((size_t)nred * blk, cplx(0.0)),
+        Cr((size_t)nred * blk, cplx(0.0));
+    for (int tt = 0; tt < nred; ++tt) {
+      const int j = 2 * tt, l = m + j, fld = field_of(j);
+      ops.diag(fld, l, m, D);
+      cplx* dr = &Dr[(size_t)tt * blk];
+      std::copy(D.begin(), D.end(), dr);
+      if (j >= 1) {
+        ops.coupling(fld, l, m, -1, A);
+        sub_prod(dr, A.data(), &Qm[(size_t)(tt - 1) * blk]);
+        if (j >= 2) sub_prod(&Ar[(size_t)tt * blk], A.data(), &Pm[(size_t)(tt - 1) * blk]);
+      }
+      if (j + 1 < nb) {
+        ops.coupling(fld, l, m, +1, C);
+        sub_prod(dr, C.data(), &Pm[(size_t)tt * blk]);
+        if (j + 2 < nb) sub_prod(&Cr[(size_t)tt * blk], C.data(), &Qm[(size_t)tt * blk]);
+      }
+    }
+    // twisted block factors of the reduced chain
+    const int km = (nred - 1) / 2;
+    auto slot = [&](std::vector<cplx>& v, int tt) { return &v[(f.red_off[c] + tt) * blk]; };
+    auto factor_block = [&](int tt, bool up, bool down) -> bool {
+      // up: subtract A' W_{tt-1}; down: subtract C' W_{tt+1}
+      const bool hasA = tt > 0, hasC = tt < nred - 1;
+      std::fill(S.begin(), S.end(), 0.0);
+      row_max(&Dr[(size_t)tt * blk], S);
+      if (hasA) row_max(&Ar[(size_t)tt * blk], S);
+      if (hasC) row_max(&Cr[(size_t)tt * blk], S);
+      for (int r = 0; r < Nr; ++r) S[r] = 1.0 / S[r];
+      D.assign(Dr.begin() + (size_t)tt * blk, Dr.begin() + (size_t)(tt + 1) * blk);
+      if (up) sub_prod(D.data(), &Ar[(size_t)tt * blk], slot(f.W, tt - 1));
+      if (down) sub_prod(D.data(), &Cr[(size_t)tt * blk], slot(f.W, tt + 1));
+      scale_rows(D.data(), S);
+      if (!lu_factor(Nr, D, piv)) return false;
+      tmp.assign(blk, cplx(0.0));
+      for (int r = 0; r < Nr; ++r) tmp[(size_t)r * Nr + r] = S[r];
+      lu_solve(Nr, D, piv, Nr, tmp);
+      std::copy(tmp.begin(), tmp.end(), slot(f.G, tt));
+      // top / middle: H = D'^-1 A', W = D'^-1 C';  bottom: H = E'^-1 C', W = E'^-1 A'
+      const bool bottom = tt > km;
+      const std::vector<cplx>& Hsrc = bottom ? Cr : Ar;
+      const std::vector<cplx>& Wsrc = bottom ? Ar : Cr;
+      const bool hasH = bottom ? hasC : hasA, hasW = bottom ? hasA : hasC;
+      if (hasH) {
+        A.assign(Hsrc.begin() + (size_t)tt * blk, Hsrc.begin() + (size_t)(tt + 1) * blk);
+        scale_rows(A.data(), S);
+        lu_solve(Nr, D, piv, Nr, A);
+        std::copy(A.begin(), A.end(), slot(f.H, tt));
+      }
+      if (hasW) {
+        C.assign(Wsrc.begin() + (size_t)tt * blk, Wsrc.begin() + (size_t)(tt + 1) * blk);
+        scale_rows(C.data(), S);
+        lu_solve(Nr, D, piv, Nr, C);
+        std::copy(C.begin(), C.end(), slot(f.W, tt));
+      }
+      return true;
+    };
+    for (int tt = 0; tt < km; ++tt)
+      if (!factor_block(tt, tt > 0, false)) return false;
+    for (int tt = nred - 1; tt > km; --tt)
+      if (!factor_block(tt, false, tt < nred - 1)) return false;
+    return factor_block(km, km > 0, km < nred - 1);
+  };
+  const int nth = std::max(1, std::min<int>(nchains, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nth; ++w)
+    pool.emplace_back([&, w]() {
+      for (int c = w; c < nchains; c += nth)
+        if (!work(c)) bad[c] = 1;
+    });
+  for (auto& th : pool) th.join();
+  for (int c = 0; c < nchains; ++c)
+    if (bad[c]) return 1 + c;
+  return 0;
+}
+
 void conductive_T00(const rsc_params& p, const Dims& d, const HostTables& t,
                     std::vector<double>& coef) {
   const int Nr = d.Nr;
