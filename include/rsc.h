@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define RSC_ABI_VERSION 8
+#define RSC_ABI_VERSION 9
 
 typedef struct rsc_ctx rsc_ctx;
 
@@ -406,6 +406,16 @@ typedef struct {
                               the MMAs of the current one run (two tile stages; only
                               where they fit in shared memory, padded K <= 72); 0 = the
                               phases one after another.  Same arithmetic.              */
+  int chain_cr;            /* double-float solve of the mixed path: 1 = one level of
+                              odd-even (cyclic) reduction of every chain first (the odd
+                              blocks eliminated with their inverses D_i^-1, the reduced
+                              chain of the even blocks swept as the full chains are;
+                              the couplings applied from the Chebyshev tables), which
+                              halves the sequential depth of the sweeps and reads 2.5
+                              instead of 3 factor blocks per block pair; its factors are
+                              computed on the host on first use (chain_parts = 1 and
+                              implicit Coriolis only).  0 = the unreduced chains.
+                              Changes the order of the arithmetic.                     */
   double ms[6];            /* after rsc_autotune: best times (ms) of products +
                               analysis (mixed), FP64 synthesis, RHS (mixed), FP64 chain
                               solve, double-float chain solve (0 if none ran); zero

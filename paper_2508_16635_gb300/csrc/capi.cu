@@ -25,6 +25,7 @@
 #include "legendre_tc_analysis.cuh"
 #include "krylov_split.cuh"
 #include "chain_df.cuh"
+#include "chain_cr.cuh"
 #include "factor_gpu.cuh"
 #include "rsc_internal.h"
 
@@ -59,6 +60,15 @@ struct DevFactor {
   long* unk_row = nullptr;
   int* blk_z = nullptr;
   double2* zbuf = nullptr;
+  // odd-even reduced chains of the double-float solve (chain_cr; HostFactorCR): inverses of
+  // the odd diagonal blocks and the twisted factors of the reduced chains, float4 pairs
+  long* cr_odd_off = nullptr;
+  long* cr_red_off = nullptr;
+  float4* Ds = nullptr;
+  float4* Gr = nullptr;
+  float4* Hr = nullptr;
+  float4* Wr = nullptr;
+  double cr_s = 0.0;   // host time of their factorisation (s)
   bool valid = false;
 };
 
@@ -130,6 +140,13 @@ struct rsc_ctx {
                           // per row group (chain_df.cuh), 0 = the FP64 kernels
   int cluster_df = 8;     // CTAs per cluster of the double-float sweeps
   int chain_parts = 1;    // parts per chain of the double-float solve (1: unpartitioned)
+  int chain_cr = 0;       // 1: the double-float solve on odd-even reduced chains (chain_cr.cuh)
+  int* d_cr_pairs = nullptr;   // pairs with odd l - m (n_cr_odd), then even (n_cr_even)
+  int n_cr_odd = 0, n_cr_even = 0;
+  float4* d_E01 = nullptr;     // [j][k] {E0 hi, E0 lo, E1 hi, E1 lo} at the collocation radii
+  float4* d_cr_rowf = nullptr;    // [j] {2 / r^3 hi, lo, 2 / r^2 hi, lo}
+  float4* d_cr_pairf = nullptr;   // [p][2] {a l, a}, {c (l + 1), c} (coupling coefficients)
+  float4* cr_w = nullptr;      // E0 u, E1 u of the odd blocks, [2][2 P Nr]
   // second stream: the temperature solve runs beside the e/f chain solve
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -302,7 +319,7 @@ void free_factor(DevFactor& f) {
   cudaFree(f.Hs);
   cudaFree(f.Ws);
   void* extra[] = {f.parts, f.Vsp, f.Wsp, f.red, f.red_off, f.red_nu, f.zoff, f.unk_row, f.blk_z,
-                   f.zbuf};
+                   f.zbuf, f.cr_odd_off, f.cr_red_off, f.Ds, f.Gr, f.Hr, f.Wr};
   for (void* b : extra) cudaFree(b);
   f = DevFactor();
 }
@@ -656,7 +673,99 @@ rsc_status build_factor_into(rsc_ctx* ctx, double dt, DevFactor& f) {
 }
 
 
+// The double-float solve runs on odd-even reduced chains (chain_cr.cuh) on this context.
+bool cr_wanted(const rsc_ctx* ctx) {
+  return ctx->p.precision == RSC_MIXED && ctx->chain_cr && ctx->chain_parts == 1 &&
+         !ctx->p.explicit_coriolis;
+}
+
+// Double-float copy of complex FP64 blocks: hi = the entry rounded to FP32, lo = the
+// remainder rounded to FP32.
+rsc_status upload_split(rsc_ctx* ctx, const std::vector<cplx>& src, float4** dst) {
+  std::vector<float4> t(src.size());
+  for (size_t i = 0; i < src.size(); ++i) {
+    const double re = src[i].real(), im = src[i].imag();
+    const float rh = (float)re, ih = (float)im;
+    t[i] = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+  }
+  return upload(ctx, dst, t.data(), t.size());
+}
+
+// The reduced-chain tables of the context (pair lists, E0 / E1 as double-float pairs, the
+// w buffer) on first use, and the reduced factors of f (host factorisation) if it has none.
+rsc_status ensure_cr(rsc_ctx* ctx, DevFactor* f) {
+  const Dims& d = ctx->d;
+  if (!ctx->d_E01) {
+    std::vector<int> pairs;
+    for (int parity = 1; parity >= 0; --parity) {
+      for (int p = 0; p < d.P; ++p)
+        if (((ctx->t.pair_l[p] - ctx->t.pair_m[p]) & 1) == parity) pairs.push_back(p);
+      if (parity == 1) ctx->n_cr_odd = (int)pairs.size();
+    }
+    ctx->n_cr_even = (int)pairs.size() - ctx->n_cr_odd;
+    CKS(upload(ctx, &ctx->d_cr_pairs, pairs.data(), pairs.size()));
+    std::vector<float4> e((size_t)d.Nr * d.Nr);
+    for (size_t i = 0; i < e.size(); ++i) {
+      const double a = ctx->t.Ec[0][i], b = ctx->t.Ec[1][i];
+      const float ah = (float)a, bh = (float)b;
+      e[i] = make_float4(ah, (float)(a - (double)ah), bh, (float)(b - (double)bh));
+    }
+    CKS(upload(ctx, &ctx->d_E01, e.data(), e.size()));
+    auto pair_of = [](double a, double b) {
+      const float ah = (float)a, bh = (float)b;
+      return make_float4(ah, (float)(a - (double)ah), bh, (float)(b - (double)bh));
+    };
+    std::vector<float4> rowf(d.Nr), pairf(2 * (size_t)d.P);
+    for (int j = 0; j < d.Nr; ++j) {
+      const double r = ctx->t.rc[j], sc = 2.0 / (r * r);
+      rowf[j] = pair_of(sc / r, sc);
+    }
+    // normalised coefficients of the couplings to l - 1 and l + 1 (Eqs. impcor_e_final /
+    // impcor_f_final, the N_l^m ratio folded in)
+    for (int p = 0; p < d.P; ++p) {
+      const double l = ctx->t.pair_l[p], m = ctx->t.pair_m[p], l1 = l + 1.0;
+      const double a = l == 0 ? 0.0 : (l * l - 1.0) * std::sqrt((l * l - m * m) / (4.0 * l * l - 1.0));
+      const double c = l == 0 ? 0.0 : l * (l + 2.0) * std::sqrt((l1 * l1 - m * m) / (4.0 * l1 * l1 - 1.0));
+      pairf[2 * p] = pair_of(a * l, a);
+      pairf[2 * p + 1] = pair_of(c * l1, c);
+    }
+    CKS(upload(ctx, &ctx->d_cr_rowf, rowf.data(), rowf.size()));
+    CKS(upload(ctx, &ctx->d_cr_pairf, pairf.data(), pairf.size()));
+    CK(cudaMalloc(&ctx->cr_w, (size_t)2 * 2 * d.P * d.Nr * sizeof(float4)));
+  }
+  if (f->Ds) return RSC_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  HostFactorCR hc;
+  const int bad = build_factor_cr(ctx->p, d, ctx->t, f->dt, hc);
+  if (bad) {
+    ctx->err = "singular block in the reduced implicit operator (chain " + std::to_string(bad - 1) + ")";
+    return RSC_ESINGULAR;
+  }
+  CKS(upload(ctx, &f->cr_odd_off, hc.odd_off.data(), hc.odd_off.size()));
+  CKS(upload(ctx, &f->cr_red_off, hc.red_off.data(), hc.red_off.size()));
+  CKS(upload_split(ctx, hc.Dinv, &f->Ds));
+  CKS(upload_split(ctx, hc.G, &f->Gr));
+  CKS(upload_split(ctx, hc.H, &f->Hr));
+  CKS(upload_split(ctx, hc.W, &f->Wr));
+  f->cr_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return RSC_OK;
+}
+
+rsc_status ensure_cr_locked(rsc_ctx* ctx, DevFactor* f) {
+  if (!ctx->share) return ensure_cr(ctx, f);
+  std::lock_guard<std::mutex> lock(ctx->share->mu);
+  return ensure_cr(ctx, f);
+}
+
+rsc_status get_factor_slot(rsc_ctx* ctx, double dt, DevFactor** out);
+
+// A shared slot gains its reduced factors under the share's lock.
 rsc_status get_factor(rsc_ctx* ctx, double dt, DevFactor** out) {
+  CKS(get_factor_slot(ctx, dt, out));
+  return cr_wanted(ctx) ? ensure_cr_locked(ctx, *out) : RSC_OK;
+}
+
+rsc_status get_factor_slot(rsc_ctx* ctx, double dt, DevFactor** out) {
   for (auto& f : ctx->fac)
     if (f.valid && f.dt == dt) {
       *out = &f;
@@ -930,13 +1039,15 @@ cudaError_t launch_chain(rsc_ctx* ctx, const DevFactor* f, double* out, bool out
 
 // Double-float sweeps (chain_df.cuh): NS = ctx->chain_df warps per row group, clusters of
 // ctx->cluster_df CTAs; the shared-memory layout of the asynchronous FP64 sweeps.
+// cr: the reduced chains of the odd-even reduced solve (every second block; chain_cr.cuh).
 template <int Q, int NS>
-cudaError_t launch_chain_df_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
+cudaError_t launch_chain_df_q(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward,
+                              bool cr) {
   const Dims& d = ctx->d;
   const int CS = ctx->cluster_df;
   const int RPC = (d.Nr + CS - 1) / CS;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * (f->npart ? f->npart : 2 * d.nm) * CS);
+  cfg.gridDim = dim3(2 * (cr || !f->npart ? 2 * d.nm : f->npart) * CS);
   cfg.blockDim = dim3(32 * NS * ((RPC + 3) / 4));
   cfg.dynamicSmemBytes = chain_smem_async(d, CS, outward, NS);
   cfg.stream = ctx->s;
@@ -948,33 +1059,70 @@ cudaError_t launch_chain_df_q(rsc_ctx* ctx, const DevFactor* f, double* out, boo
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const int cap = chain_steps_cap(d);
+  const long* off = cr ? f->cr_red_off : f->chain_off;
+  const float4* H = cr ? f->Hr : f->Hs;
+  const float4* W = cr ? f->Wr : f->Ws;
+  const long* parts = cr ? nullptr : f->parts;
+  const int bs = cr ? 2 : 1;
   if (outward)
-    return cudaLaunchKernelEx(&cfg, k_chain_out_df<Q / NS, NS>, ctx->geom(),
-                              (const long*)f->chain_off, (const float4*)f->Hs,
-                              (const float4*)f->Ws, reinterpret_cast<double2*>(out),
-                              (const double2*)ctx->mid, CS, cap, ctx->d_status,
-                              (const long*)f->parts);
-  return cudaLaunchKernelEx(&cfg, k_chain_half_df<Q / NS, NS>, ctx->geom(),
-                            (const long*)f->chain_off, (const float4*)f->Hs,
+    return cudaLaunchKernelEx(&cfg, k_chain_out_df<Q / NS, NS>, ctx->geom(), off, H, W,
+                              reinterpret_cast<double2*>(out), (const double2*)ctx->mid, CS,
+                              cap, ctx->d_status, parts, bs);
+  return cudaLaunchKernelEx(&cfg, k_chain_half_df<Q / NS, NS>, ctx->geom(), off, H,
                             reinterpret_cast<double2*>(out), ctx->mid, CS, cap, ctx->d_status,
-                            (const long*)f->parts);
+                            parts, bs);
 }
 
 template <int Q>
-cudaError_t launch_chain_df_ns(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
-  if (ctx->chain_df == 2) return launch_chain_df_q<Q, 2>(ctx, f, out, outward);
+cudaError_t launch_chain_df_ns(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward,
+                               bool cr) {
+  if (ctx->chain_df == 2) return launch_chain_df_q<Q, 2>(ctx, f, out, outward, cr);
   if constexpr (Q % 4 == 0)
-    if (ctx->chain_df == 4) return launch_chain_df_q<Q, 4>(ctx, f, out, outward);
+    if (ctx->chain_df == 4) return launch_chain_df_q<Q, 4>(ctx, f, out, outward, cr);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_chain_df(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward) {
+cudaError_t launch_chain_df(rsc_ctx* ctx, const DevFactor* f, double* out, bool outward,
+                            bool cr = false) {
   switch (chain_maxq(ctx->d.Nr)) {
-    case 2: return launch_chain_df_ns<2>(ctx, f, out, outward);
-    case 4: return launch_chain_df_ns<4>(ctx, f, out, outward);
-    case 8: return launch_chain_df_ns<8>(ctx, f, out, outward);
-    case 12: return launch_chain_df_ns<12>(ctx, f, out, outward);
-    default: return launch_chain_df_ns<16>(ctx, f, out, outward);
+    case 2: return launch_chain_df_ns<2>(ctx, f, out, outward, cr);
+    case 4: return launch_chain_df_ns<4>(ctx, f, out, outward, cr);
+    case 8: return launch_chain_df_ns<8>(ctx, f, out, outward, cr);
+    case 12: return launch_chain_df_ns<12>(ctx, f, out, outward, cr);
+    default: return launch_chain_df_ns<16>(ctx, f, out, outward, cr);
+  }
+}
+
+// The passes of the odd-even reduced solve that run over every block (chain_cr.cuh):
+// pass 0 = u and E0 u, E1 u of the odd blocks, 1 = b' and G' b' of the even blocks,
+// 2 = the odd blocks from their neighbours.
+template <int Q>
+void launch_cr_pass_q(rsc_ctx* ctx, const DevFactor* f, double* out, int pass) {
+  const Dims& d = ctx->d;
+  const size_t v = (size_t)d.Nr * sizeof(float4);
+  const int* odd = ctx->d_cr_pairs;
+  const int* even = ctx->d_cr_pairs + ctx->n_cr_odd;
+  double2* o = reinterpret_cast<double2*>(out);
+  if (pass == 0)
+    k_cr_odd_df<Q><<<2 * ctx->n_cr_odd, 256, 2 * v, ctx->s>>>(
+        ctx->geom(), odd, f->cr_odd_off, f->Ds, ctx->d_E01, ctx->rhs, ctx->cr_w);
+  else if (pass == 1)
+    k_cr_even_df<Q><<<2 * ctx->n_cr_even, 256, 2 * v, ctx->s>>>(
+        ctx->geom(), even, f->cr_red_off, f->Gr, ctx->d_cr_rowf, ctx->d_cr_pairf, ctx->rhs,
+        ctx->cr_w, o);
+  else
+    k_cr_back_df<Q><<<2 * ctx->n_cr_odd, 256, 5 * v, ctx->s>>>(
+        ctx->geom(), odd, f->cr_odd_off, f->Ds, ctx->d_E01, ctx->d_cr_rowf, ctx->d_cr_pairf,
+        ctx->rhs, o);
+}
+
+void launch_cr_pass(rsc_ctx* ctx, const DevFactor* f, double* out, int pass) {
+  switch (chain_maxq(ctx->d.Nr)) {
+    case 2: launch_cr_pass_q<2>(ctx, f, out, pass); break;
+    case 4: launch_cr_pass_q<4>(ctx, f, out, pass); break;
+    case 8: launch_cr_pass_q<8>(ctx, f, out, pass); break;
+    case 12: launch_cr_pass_q<12>(ctx, f, out, pass); break;
+    default: launch_cr_pass_q<16>(ctx, f, out, pass); break;
   }
 }
 
@@ -996,6 +1144,7 @@ void launch_gemv_df(rsc_ctx* ctx, const DevFactor* f, double* out) {
 rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = false,
                        bool temp = true) {
   df = df && f->Gs && f->Hs && f->Ws && ctx->chain_df != 0;
+  const bool cr = df && cr_wanted(ctx) && f->Ds && ctx->d_E01;
   const Dims& d = ctx->d;
   // the temperature solve depends only on the right-hand side: it runs on a second stream
   // beside the e/f chain solve (sequentially while tracing, so that every launch is timed)
@@ -1014,7 +1163,34 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = 
     CK(cudaGetLastError());
     CK(cudaEventRecord(ctx->ev_join, ctx->s2));
   }
-  {
+  if (cr) {
+    // odd-even reduced chains: odd blocks, reduced right-hand side, sweeps over the reduced
+    // chains, odd blocks; blocks and vectors counted once per pass (the tables E0, E1 once)
+    const double nr2 = (double)d.Nr * d.Nr, bo = 2.0 * ctx->n_cr_odd, be = 2.0 * ctx->n_cr_even;
+    const double tab = nr2 * 16.0;
+    {
+      KSpan sp(ctx, RSC_K_CHAIN, bo * nr2 * 16.0 + bo * d.Nr * 16.0 * 3.0 + tab,
+               bo * nr2 * 8.0 + bo * nr2 * 4.0);
+      launch_cr_pass(ctx, f, out, 0);
+      CK(cudaGetLastError());
+    }
+    {
+      KSpan sp(ctx, RSC_K_CHAIN, be * nr2 * 16.0 + be * d.Nr * 16.0 * 6.0, be * nr2 * 8.0);
+      launch_cr_pass(ctx, f, out, 1);
+      CK(cudaGetLastError());
+    }
+    for (int outward = 0; outward < 2; ++outward) {
+      KSpan sp(ctx, RSC_K_CHAIN_SEQ, be * nr2 * 16.0 + 2.0 * be * d.Nr * 16.0, be * nr2 * 8.0);
+      CK(launch_chain_df(ctx, f, out, outward != 0, true));
+    }
+    {
+      KSpan sp(ctx, RSC_K_CHAIN, bo * nr2 * 16.0 + bo * d.Nr * 16.0 * 4.0 + tab,
+               bo * nr2 * 8.0 + bo * nr2 * 4.0);
+      launch_cr_pass(ctx, f, out, 2);
+      CK(cudaGetLastError());
+    }
+  }
+  if (!cr) {
     KSpan sp(ctx, RSC_K_CHAIN, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
     if (df)
@@ -1024,13 +1200,13 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = 
           ctx->geom(), f->chain_off, f->G, ctx->rhs, reinterpret_cast<double2*>(out));
     CK(cudaGetLastError());
   }
-  if (!ctx->p.explicit_coriolis) {
+  if (!cr && !ctx->p.explicit_coriolis) {
     // forward half-sweeps read H of about half the blocks each way, outward sweeps W
     KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
     CK(df ? launch_chain_df(ctx, f, out, false) : launch_chain(ctx, f, out, false));
   }
-  if (!ctx->p.explicit_coriolis) {
+  if (!cr && !ctx->p.explicit_coriolis) {
     KSpan sp(ctx, RSC_K_CHAIN_SEQ, 2.0 * d.P * d.Nr * d.Nr * 16.0 + 4.0 * d.P * d.Nr * 16.0,
              2.0 * d.P * d.Nr * d.Nr * 8.0);
     CK(df ? launch_chain_df(ctx, f, out, true) : launch_chain(ctx, f, out, true));
@@ -1779,6 +1955,7 @@ bool tuning_ok(rsc_ctx* ctx, const rsc_tuning& t) {
   if (t.factor_gpu != 0 && t.factor_gpu != 1) return false;
   if (t.refine < 0 || t.refine > 2) return false;
   if (t.synth_pipe != 0 && t.synth_pipe != 1) return false;
+  if (t.chain_cr != 0 && t.chain_cr != 1) return false;
   if (t.synth_pipe == 1 && !synth_pipe_fits(ctx->tc_kmax)) return false;
   if (!chain_df_ok(d, t.chain_df_cluster, t.chain_df)) return false;
   return chain_config_ok(d, t.chain_cluster, t.chain_async);
@@ -1808,6 +1985,7 @@ void get_tuning(const rsc_ctx* ctx, rsc_tuning* t) {
   t->factor_gpu = ctx->factor_gpu;
   t->refine = ctx->refine;
   t->synth_pipe = ctx->synth_pipe;
+  t->chain_cr = ctx->chain_cr;
   for (int q = 0; q < 6; ++q) t->ms[q] = ctx->tune_ms[q];
 }
 
@@ -1828,6 +2006,7 @@ void set_tuning(rsc_ctx* ctx, const rsc_tuning& t) {
   ctx->krylov_split = t.krylov_split;
   ctx->refine = t.refine;
   ctx->synth_pipe = t.synth_pipe;
+  ctx->chain_cr = t.chain_cr;   // the reduced factors are added to a slot on its next use
   if (t.factor_gpu != ctx->factor_gpu) {
     // the factorisations are rebuilt where the new setting says
     ctx->factor_gpu = t.factor_gpu;
@@ -1993,26 +2172,39 @@ rsc_status autotune(rsc_ctx* ctx, rsc_tuning* out) {
     // mixed path: the double-float chain solve against the best FP64 one
     if (st == RSC_OK && f->Gs) {
       double best_df = 1e30;
-      int bn = 0, bcs = t.chain_df_cluster;
-      for (int ns : {2, 4}) {
-        for (int cs : {16, 8, 4, 2}) {
-          if (st != RSC_OK) break;
-          if (!chain_df_ok(ctx->d, cs, ns)) continue;
-          ctx->chain_df = ns;
-          ctx->cluster_df = cs;
-          st = stage_solve(ctx, f, ctx->xtmp, true);
-          cudaEventRecord(e0, ctx->s);
-          for (int r = 0; r < 3 && st == RSC_OK; ++r) st = stage_solve(ctx, f, ctx->xtmp, true);
-          cudaEventRecord(e1, ctx->s);
-          if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
-          float ms = 0;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (st == RSC_OK && ms / 3.0 < best_df) { best_df = ms / 3.0; bn = ns; bcs = cs; }
+      int bn = 0, bcs = t.chain_df_cluster, bcr = 0;
+      const int saved_cr = ctx->chain_cr;
+      for (int cr : {0, 1}) {   // the unreduced chains, then the odd-even reduced ones
+        ctx->chain_cr = cr;
+        if (cr && (st != RSC_OK || !cr_wanted(ctx))) break;
+        if (cr) st = ensure_cr_locked(ctx, f);
+        for (int ns : {2, 4}) {
+          for (int cs : {16, 8, 4, 2}) {
+            if (st != RSC_OK) break;
+            if (!chain_df_ok(ctx->d, cs, ns)) continue;
+            ctx->chain_df = ns;
+            ctx->cluster_df = cs;
+            st = stage_solve(ctx, f, ctx->xtmp, true);
+            cudaEventRecord(e0, ctx->s);
+            for (int r = 0; r < 3 && st == RSC_OK; ++r) st = stage_solve(ctx, f, ctx->xtmp, true);
+            cudaEventRecord(e1, ctx->s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = RSC_ECUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == RSC_OK && ms / 3.0 < best_df) {
+              best_df = ms / 3.0;
+              bn = ns;
+              bcs = cs;
+              bcr = cr;
+            }
+          }
         }
       }
+      ctx->chain_cr = saved_cr;
       if (st == RSC_OK) st = check_status(ctx);
       t.chain_df = best_df < best ? bn : 0;
       t.chain_df_cluster = bcs;
+      t.chain_cr = best_df < best ? bcr : 0;
       ctx->tune_ms[5] = best_df < 1e30 ? best_df : 0.0;
     }
   }
@@ -2236,7 +2428,7 @@ rsc_status rsc_destroy(rsc_ctx* ctx) {
                   ctx->d_EdT2, ctx->d_R0T, ctx->d_R1T, ctx->f_EdT0, ctx->f_EdT1,
                   ctx->f_EdT2, ctx->f_R0T, ctx->f_R1T, ctx->f_rd, ctx->f_EcT0, ctx->f_EcT2, ctx->SR, ctx->FC, ctx->FCU, ctx->UG, ctx->FA,
                   ctx->AR, ctx->rhs, ctx->mid, ctx->xtmp, ctx->vtmp, ctx->rtmp, ctx->ustate, ctx->ref_tmp, ctx->d_Ef[0], ctx->d_Ef[1], ctx->d_Ef[2], ctx->d_Ef[3], ctx->V, ctx->Vs, ctx->partial,
-                  ctx->dots, ctx->AR0, ctx->ta_tiles, ctx->ta_off, ctx->cont_hist, ctx->cont_cond, ctx->amax_v, ctx->amax_i, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag};
+                  ctx->dots, ctx->AR0, ctx->ta_tiles, ctx->ta_off, ctx->cont_hist, ctx->cont_cond, ctx->amax_v, ctx->amax_i, ctx->d_keT, ctx->d_kedT, ctx->d_ker, ctx->d_kew, ctx->d_diag, ctx->d_cr_pairs, ctx->d_E01, ctx->cr_w, ctx->d_cr_rowf, ctx->d_cr_pairf};
   for (void* b : bufs) cudaFree(b);
   for (int q = 0; q < 8; ++q) {
     cudaFree(ctx->leg64.buf[q]);

@@ -170,6 +170,7 @@ __device__ __forceinline__ ChainInfo chain_info_part(const DevGeom& g, const lon
   ci.nb = (int)q[2];
   ci.boff = q[3];
   ci.m = (int)q[4];
+  ci.bs = 1;
   ci.km = (ci.nb - 1) / 2;
   ci.P = g.P;
   ci.Nr = g.Nr;
@@ -188,16 +189,18 @@ struct CdDepth {
 
 // Shared memory: v[2][Nr], part[NS-1][RPC], hist[steps][RPC] (float4), two mbarriers: the
 // byte layout of k_chain_half_async.  grid = 2 * 2 * nm * CS (clusters of CS),
-// block = 32 NS ceil(RPC / 4).
+// block = 32 NS ceil(RPC / 4).  bs = 2 sweeps the reduced chains of chain_cr.cuh (chain_off
+// their first blocks in H), 1 the full chains.
 template <int QH, int NS>
 __global__ void k_chain_half_df(DevGeom g, const long* __restrict__ chain_off,
                                 const float4* __restrict__ H, double2* __restrict__ out,
                                 double2* __restrict__ mid, int CS, int steps_cap,
-                                int* __restrict__ status, const long* __restrict__ parts) {
+                                int* __restrict__ status, const long* __restrict__ parts,
+                                int bs) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ float4 cd_sh[];
-  const ChainInfo ci = parts ? chain_info_part(g, parts, CS) : chain_info(g, chain_off, CS);
+  const ChainInfo ci = parts ? chain_info_part(g, parts, CS) : chain_info(g, chain_off, CS, bs);
   const int Nr = ci.Nr;
   const CaLane c = ca_lane<QH, NS>(Nr, CS, (int)cluster.block_rank());
   float4* v = cd_sh;                        // [2][Nr]
@@ -287,11 +290,11 @@ __global__ void k_chain_out_df(DevGeom g, const long* __restrict__ chain_off,
                                const float4* __restrict__ H, const float4* __restrict__ W,
                                double2* __restrict__ out, const double2* __restrict__ mid,
                                int CS, int steps_cap, int* __restrict__ status,
-                               const long* __restrict__ parts) {
+                               const long* __restrict__ parts, int bs) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ float4 cd_sh[];
-  const ChainInfo ci = parts ? chain_info_part(g, parts, CS) : chain_info(g, chain_off, CS);
+  const ChainInfo ci = parts ? chain_info_part(g, parts, CS) : chain_info(g, chain_off, CS, bs);
   const int Nr = ci.Nr;
   const CaLane c = ca_lane<QH, NS>(Nr, CS, (int)cluster.block_rank());
   float4* v = cd_sh;

@@ -859,16 +859,20 @@ struct ChainLane {
   }
 };
 
+// bs = 2: the chain of every second block (the reduced chains of chain_cr.cuh), block i of
+// it being block bs i of the full chain.
 struct ChainInfo {
-  int c, dir, cls, p0, nb, km, P, Nr, m;
+  int c, dir, cls, p0, nb, km, P, Nr, m, bs;
   long boff, blk;
   __device__ __forceinline__ long row(int i) const {
-    const int fld = ((i + cls) & 1) ? 1 : 0;
-    return ((long)fld * P + p0 + i) * Nr;
+    const int ib = i * bs;
+    const int fld = ((ib + cls) & 1) ? 1 : 0;
+    return ((long)fld * P + p0 + ib) * Nr;
   }
 };
 
-__device__ __forceinline__ ChainInfo chain_info(const DevGeom& g, const long* chain_off, int CS) {
+__device__ __forceinline__ ChainInfo chain_info(const DevGeom& g, const long* chain_off, int CS,
+                                                int bs = 1) {
   ChainInfo ci;
   const int cl = blockIdx.x / CS;
   ci.c = cl >> 1;
@@ -878,7 +882,8 @@ __device__ __forceinline__ ChainInfo chain_info(const DevGeom& g, const long* ch
   const int m = g.m_of[a];
   ci.m = m;
   ci.p0 = g.pstart[a];
-  ci.nb = g.L - m + 1;
+  ci.bs = bs;
+  ci.nb = (g.L - m + bs) / bs;
   ci.km = (ci.nb - 1) / 2;
   ci.P = g.P;
   ci.Nr = g.Nr;

@@ -56,7 +56,7 @@ class Tuning(ctypes.Structure):
                 ("chain_df_cluster", ctypes.c_int), ("krylov_split", ctypes.c_int),
                 ("chain_parts", ctypes.c_int), ("factor_gpu", ctypes.c_int),
                 ("refine", ctypes.c_int), ("synth_pipe", ctypes.c_int),
-                ("ms", ctypes.c_double * 6)]
+                ("chain_cr", ctypes.c_int), ("ms", ctypes.c_double * 6)]
 
     def as_dict(self):
         return {"products_warps": list(self.products_warps),
@@ -68,7 +68,7 @@ class Tuning(ctypes.Structure):
                 "chain_df": self.chain_df, "chain_df_cluster": self.chain_df_cluster,
                 "krylov_split": self.krylov_split, "chain_parts": self.chain_parts,
                 "factor_gpu": self.factor_gpu, "refine": self.refine,
-                "synth_pipe": self.synth_pipe,
+                "synth_pipe": self.synth_pipe, "chain_cr": self.chain_cr,
                 "ms": list(self.ms)}
 
 
@@ -418,6 +418,7 @@ class RotatingShell:
         t.factor_gpu = d.get("factor_gpu", cur["factor_gpu"])
         t.refine = d.get("refine", cur["refine"])
         t.synth_pipe = d.get("synth_pipe", cur["synth_pipe"])
+        t.chain_cr = d.get("chain_cr", cur["chain_cr"])
         self._check(self.lib.rsc_set_tuning(self._ctx, ctypes.byref(t)))
 
     def continue_ra(self, U, C, J, Ra0, Ra1, Ra_end, n_opt=4, gamma=20.0, max_points=8,

@@ -35,7 +35,7 @@ def test_binding_covers_header():
 
 
 def test_version_and_status_strings(lib):
-    assert lib.rsc_abi_version() == 8
+    assert lib.rsc_abi_version() == 9
     assert lib.rsc_status_string(0) == b"RSC_OK"
     assert lib.rsc_status_string(6) == b"RSC_ESINGULAR"
 

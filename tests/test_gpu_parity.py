@@ -747,6 +747,52 @@ def test_implicit_solve_backward_error_double_float(torch, name, L, Ms, Nr, Ek, 
 
 @pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES_C3)
 @pytest.mark.parametrize("dt", [2e-3, 200.0])
+def test_implicit_solve_backward_error_reduced_chains(torch, name, L, Ms, Nr, Ek, Ra, dt):
+    """The double-float solve on odd-even reduced chains (chain_cr = 1: the odd blocks
+    eliminated with D_i^-1, the half-length chains of the even blocks swept, the odd blocks
+    recovered from their neighbours) with 2 / 4 warps per row group on every schedulable
+    cluster size, against the oracle's chains: row-scaled backward error below 64 u_df, the
+    solution within 32 x the FP64 bound of the reduced factors on the host (1e-10 at L = 127,
+    N_r = 64, dt = 200, where the odd blocks' back-substitution cancels O(1) Coriolis terms
+    against an O(Ek) diagonal; tests/test_host_factor_cr.py).  The reduced passes must run:
+    two launches more than the unreduced solve."""
+    from paper_2508_16635_gb300 import RotatingShell
+    s = _shell(L, Ms, Nr, Ek, Ra)
+    b = _random_rhs(s, 97 + L)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
+    t0 = gpu.tuning()
+    B = torch.tensor(s.to_real(b), device="cuda")
+
+    def launches(**kw):
+        gpu.set_tuning(dict(t0, **kw))
+        gpu.implicit_solve(B, dt)
+        torch.cuda.synchronize()
+        n1 = gpu.launch_count()
+        x = gpu.implicit_solve(B, dt).cpu().numpy()
+        torch.cuda.synchronize()
+        return gpu.launch_count() - n1, x
+
+    plain, _ = launches(chain_df=2, chain_cr=0)
+    ran = 0
+    for ns in (2, 4):
+        for cs in (16, 8, 4, 2):
+            try:
+                gpu.set_tuning(dict(t0, chain_df=ns, chain_df_cluster=cs, chain_cr=1))
+            except Exception:
+                continue
+            ran += 1
+            n, x = launches(chain_df=ns, chain_df_cluster=cs, chain_cr=1)
+            assert n == plain + 2, (ns, cs, n, plain)
+            eta, fwd, fwd_T = _solve_errors(s, dt, b, s.to_complex(x))
+            assert eta < 64 * U48, (ns, cs, eta / U48)
+            assert fwd < 32 * 1e-10, (ns, cs, fwd)
+            assert fwd_T < 1e-12, (ns, cs, fwd_T)
+    assert ran >= 2
+    gpu.close()
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES_C3)
+@pytest.mark.parametrize("dt", [2e-3, 200.0])
 def test_gpu_factorisation_matches_the_host_factors(torch, name, L, Ms, Nr, Ek, Ra, dt):
     """The FP64 block factorisation on the GPU (factor_gpu = 1, the default) against the
     host routine (factor_gpu = 0), block by block: G, H, W of every chain block and the
@@ -787,9 +833,11 @@ def test_gpu_factorisation_matches_the_host_factors(torch, name, L, Ms, Nr, Ek, 
 
 
 @pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES_C3)
-def test_double_float_chain_solve_against_the_oracle(torch, name, L, Ms, Nr, Ek, Ra):
-    """The mixed Jacobian action with the double-float chain solve against the FP64 oracle, at
-    the mixed-path bound (the FP32 transforms dominate): 5e-5 per field."""
+@pytest.mark.parametrize("chain_cr", [0, 1])
+def test_double_float_chain_solve_against_the_oracle(torch, name, L, Ms, Nr, Ek, Ra, chain_cr):
+    """The mixed Jacobian action with the double-float chain solve (unreduced and odd-even
+    reduced chains) against the FP64 oracle, at the mixed-path bound (the FP32 transforms
+    dominate): 5e-5 per field."""
     from paper_2508_16635_gb300 import RotatingShell
     s = _shell(L, Ms, Nr, Ek, Ra)
     x = s.conductive_state() + si.perturbation(L, Ms, Nr, seed=73, amp=1e-2)
@@ -798,6 +846,7 @@ def test_double_float_chain_solve_against_the_oracle(torch, name, L, Ms, Nr, Ek,
     want = s.jvp(x, 0.4, J, u, 200.0)
     gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
     assert gpu.tuning()["chain_df"] in (2, 4)
+    gpu.set_tuning(dict(gpu.tuning(), chain_cr=chain_cr))
     got = gpu.apply_jacobian(torch.tensor(x, device="cuda"), 0.4, J,
                              torch.tensor(u, device="cuda"), 200.0).cpu().numpy()
     errs = _maxabs_fields(s, got, want)
