@@ -180,11 +180,19 @@ rsc_status rsc_implicit_solve(rsc_ctx* ctx, const double* rhs, double* x, double
  * W = D'^-1 C above the middle block of a chain, G = E'^-1, H = E'^-1 C, W = E'^-1 A
  * below it, and G = Z, H = Z A, W = Z C at the middle block (A, C the couplings to
  * l - 1, l + 1).  which = 3: the inverse of the temperature operator of degree
- * l = index (Nr^2 doubles).  For checks of the factorisation.                     */
+ * l = index (Nr^2 doubles).  Mixed contexts with implicit Coriolis, the odd-even reduced
+ * chains of rsc_tuning chain_cr (built if needed): which = 4: D_i^-1 of odd block `index`
+ * (the odd blocks i = 1, 3, ... of every chain, chains in order); which = 5, 6, 7: G', H',
+ * W' of reduced block `index` (the even blocks of every chain), the twisted factors of
+ * the reduced chains with the conventions above; read from their double-float copies
+ * (hi + lo, about 2^-48 relative).  For checks of the factorisation.                */
 rsc_status rsc_factor_block(rsc_ctx* ctx, double dt, int which, long index, double* out_host);
 
 /* Wall time (s) of the context's last factorisation and whether it ran on the GPU. */
 rsc_status rsc_factor_time(const rsc_ctx* ctx, double* seconds, int* on_gpu);
+/* The same for the context's last factorisation of the odd-even reduced chains
+ * (rsc_tuning chain_cr; 0 s until one has run).                                  */
+rsc_status rsc_factor_time_cr(const rsc_ctx* ctx, double* seconds, int* on_gpu);
 
 /* Jacobian action of Sec. 3.3-3.4 for `count` directions:
  *   out_i = (B_U - I) u_i with the drift unknown c = u_i[J] (Sec. 3.4):

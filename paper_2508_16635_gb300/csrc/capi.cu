@@ -26,6 +26,7 @@
 #include "krylov_split.cuh"
 #include "chain_df.cuh"
 #include "chain_cr.cuh"
+#include "cr_factor_gpu.cuh"
 #include "factor_gpu.cuh"
 #include "rsc_internal.h"
 
@@ -68,7 +69,8 @@ struct DevFactor {
   float4* Gr = nullptr;
   float4* Hr = nullptr;
   float4* Wr = nullptr;
-  double cr_s = 0.0;   // host time of their factorisation (s)
+  double cr_s = 0.0;   // wall time of their factorisation (s)
+  int cr_on_gpu = 0;   // where it ran
   bool valid = false;
 };
 
@@ -118,6 +120,8 @@ struct rsc_ctx {
   double* ref_tmp = nullptr;   // correction of a refinement step
   double factor_s = 0.0;       // wall time of the last factorisation (s)
   int factor_on_gpu = 0;       // where the last factorisation ran
+  double factor_cr_s = 0.0;    // the same for the last factorisation of the reduced chains
+  int factor_cr_on_gpu = 0;
   // factorisations, two slots (time stepping dt and Newton dt)
   DevFactor fac[2];
   int fac_next = 0;
@@ -691,8 +695,113 @@ rsc_status upload_split(rsc_ctx* ctx, const std::vector<cplx>& src, float4** dst
   return upload(ctx, dst, t.data(), t.size());
 }
 
+FacGeom fac_geom(const rsc_ctx* ctx, double dt);
+
+// The reduced factors of f->dt on the device (cr_factor_gpu.cuh): FP64 block LU of the odd
+// blocks, the reduced chains' blocks, their twisted factors, then the double-float copies.
+// Needs the context's pair lists (ensure_cr).
+rsc_status gpu_factor_cr(rsc_ctx* ctx, DevFactor* f) {
+  const Dims& d = ctx->d;
+  const int nchains = 2 * d.nm;
+  std::vector<long> oo(nchains + 1), ro(nchains + 1);
+  long no = 0, nr = 0;
+  for (int c = 0; c < nchains; ++c) {
+    const int nb = d.L - ctx->t.m_of[c / 2] + 1;
+    oo[c] = no;
+    ro[c] = nr;
+    no += nb / 2;
+    nr += (nb + 1) / 2;
+  }
+  oo[nchains] = no;
+  ro[nchains] = nr;
+  CKS(upload(ctx, &f->cr_odd_off, oo.data(), oo.size()));
+  CKS(upload(ctx, &f->cr_red_off, ro.data(), ro.size()));
+  const size_t blk = (size_t)d.Nr * d.Nr;
+  const size_t eo = std::max<size_t>(1, no * blk), er = (size_t)nr * blk;
+  double2 *Di = nullptr, *Pm = nullptr, *Qm = nullptr, *Dr = nullptr, *Ar = nullptr, *Cr = nullptr;
+  double2 *G = nullptr, *H = nullptr, *W = nullptr;
+  int* status = nullptr;
+  double2** bufs[] = {&Di, &Pm, &Qm, &Dr, &Ar, &Cr, &G, &H, &W};
+  const size_t sizes[] = {eo, eo, eo, er, er, er, er, er, er};
+  auto release = [&]() {
+    for (double2** b : bufs) cudaFree(*b);
+    cudaFree(status);
+  };
+  for (int q = 0; q < 9; ++q)
+    if (cudaMalloc(bufs[q], sizes[q] * sizeof(double2)) != cudaSuccess) {
+      release();
+      ctx->err = "cudaMalloc of the reduced-chain factorisation scratch failed";
+      return RSC_ENOMEM;
+    }
+  cudaError_t e = cudaMalloc(&status, nchains * sizeof(int));
+  auto ok = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  ok(cudaMemsetAsync(status, 0, nchains * sizeof(int), ctx->s));
+  ok(cudaMemsetAsync(Qm, 0, eo * sizeof(double2), ctx->s));   // absent at a chain's last block
+  ok(cudaMemsetAsync(H, 0, er * sizeof(double2), ctx->s));    // absent at the end blocks
+  ok(cudaMemsetAsync(W, 0, er * sizeof(double2), ctx->s));
+  const FacGeom g = fac_geom(ctx, f->dt);
+  CrFacGeom cg;
+  cg.pair_l = ctx->d_pair_l;
+  cg.pair_m = ctx->d_pair_m;
+  cg.Ms = d.Ms;
+  cg.odd_off = f->cr_odd_off;
+  cg.red_off = f->cr_red_off;
+  const size_t smem = fac_smem_bytes(d.Nr);
+  for (const void* fn : {(const void*)k_cr_fac_odd, (const void*)k_cr_fac_reduce,
+                         (const void*)k_cr_fac_half, (const void*)k_cr_fac_mid})
+    ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (e == cudaSuccess && ctx->n_cr_odd > 0) {
+    cg.pairs = ctx->d_cr_pairs;
+    k_cr_fac_odd<<<2 * ctx->n_cr_odd, kFacThreads, smem, ctx->s>>>(g, cg, Di, Pm, Qm, status);
+    ok(cudaGetLastError());
+  }
+  if (e == cudaSuccess) {
+    cg.pairs = ctx->d_cr_pairs + ctx->n_cr_odd;
+    k_cr_fac_reduce<<<2 * ctx->n_cr_even, kFacThreads, smem, ctx->s>>>(g, cg, Pm, Qm, Dr, Ar, Cr);
+    ok(cudaGetLastError());
+  }
+  if (e == cudaSuccess) {
+    k_cr_fac_half<<<2 * nchains, kFacThreads, smem, ctx->s>>>(g, f->cr_red_off, Dr, Ar, Cr, G, H, W,
+                                                            status);
+    ok(cudaGetLastError());
+  }
+  if (e == cudaSuccess) {
+    k_cr_fac_mid<<<nchains, kFacThreads, smem, ctx->s>>>(g, f->cr_red_off, Dr, Ar, Cr, G, H, W,
+                                                       status);
+    ok(cudaGetLastError());
+  }
+  // double-float copies
+  float4** dsts[] = {&f->Ds, &f->Gr, &f->Hr, &f->Wr};
+  const double2* srcs[] = {Di, G, H, W};
+  const size_t ns[] = {eo, er, er, er};
+  for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+    ok(cudaMalloc(dsts[q], ns[q] * sizeof(float4)));
+    if (e != cudaSuccess) break;
+    const int nbk = (int)std::min<size_t>((ns[q] + 255) / 256, 152 * 32);
+    k_split_factor<<<nbk, 256, 0, ctx->s>>>(srcs[q], *dsts[q], (long)ns[q]);
+    ok(cudaGetLastError());
+  }
+  std::vector<int> hs(nchains, 0);
+  if (e == cudaSuccess)
+    ok(cudaMemcpyAsync(hs.data(), status, nchains * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  ok(cudaStreamSynchronize(ctx->s));
+  release();
+  ctx->launches += 8;
+  if (e != cudaSuccess) {
+    ctx->err = std::string("CUDA error in the reduced-chain factorisation: ") + cudaGetErrorString(e);
+    return RSC_ECUDA;
+  }
+  for (int c = 0; c < nchains; ++c)
+    if (hs[c]) {
+      ctx->err = "singular block in the reduced implicit operator (chain " + std::to_string(c) + ")";
+      return RSC_ESINGULAR;
+    }
+  return RSC_OK;
+}
+
 // The reduced-chain tables of the context (pair lists, E0 / E1 as double-float pairs, the
-// w buffer) on first use, and the reduced factors of f (host factorisation) if it has none.
+// w buffer) on first use, and the reduced factors of f if it has none (on the GPU where the
+// FP64 factorisation runs there, else on the host).
 rsc_status ensure_cr(rsc_ctx* ctx, DevFactor* f) {
   const Dims& d = ctx->d;
   if (!ctx->d_E01) {
@@ -735,6 +844,14 @@ rsc_status ensure_cr(rsc_ctx* ctx, DevFactor* f) {
   }
   if (f->Ds) return RSC_OK;
   const auto t0 = std::chrono::steady_clock::now();
+  if (factor_on_device(ctx)) {
+    CKS(gpu_factor_cr(ctx, f));
+    f->cr_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    f->cr_on_gpu = 1;
+    ctx->factor_cr_s = f->cr_s;
+    ctx->factor_cr_on_gpu = 1;
+    return RSC_OK;
+  }
   HostFactorCR hc;
   const int bad = build_factor_cr(ctx->p, d, ctx->t, f->dt, hc);
   if (bad) {
@@ -748,6 +865,9 @@ rsc_status ensure_cr(rsc_ctx* ctx, DevFactor* f) {
   CKS(upload_split(ctx, hc.H, &f->Hr));
   CKS(upload_split(ctx, hc.W, &f->Wr));
   f->cr_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  f->cr_on_gpu = 0;
+  ctx->factor_cr_s = f->cr_s;
+  ctx->factor_cr_on_gpu = 0;
   return RSC_OK;
 }
 
@@ -2684,15 +2804,38 @@ rsc_status rsc_newton_rw_host(rsc_ctx* ctx, double* U_host, double* C, long J,
 }
 
 rsc_status rsc_factor_block(rsc_ctx* ctx, double dt, int which, long index, double* out_host) {
-  if (!ctx || !out_host || which < 0 || which > 3 || index < 0 || !(dt > 0) || !std::isfinite(dt))
+  if (!ctx || !out_host || which < 0 || which > 7 || index < 0 || !(dt > 0) || !std::isfinite(dt))
     return RSC_EINVAL;
   const Dims& d = ctx->d;
   const size_t blk = (size_t)d.Nr * d.Nr;
-  long nblk = 0;
-  for (int a = 0; a < d.nm; ++a) nblk += 2L * (d.L - ctx->t.m_of[a] + 1);
-  if ((which < 3 && index >= nblk) || (which == 3 && index > d.L)) return RSC_EINVAL;
+  long nblk = 0, nodd = 0;
+  for (int a = 0; a < d.nm; ++a) {
+    nblk += 2L * (d.L - ctx->t.m_of[a] + 1);
+    nodd += 2L * ((d.L - ctx->t.m_of[a] + 1) / 2);
+  }
+  if ((which < 3 && index >= nblk) || (which == 3 && index > d.L) ||
+      (which == 4 && index >= nodd) || (which > 4 && index >= nblk - nodd))
+    return RSC_EINVAL;
+  if (which >= 4 && (ctx->p.precision != RSC_MIXED || ctx->p.explicit_coriolis ||
+                     ctx->chain_parts != 1)) {
+    ctx->err = "reduced-chain factors exist on mixed contexts with implicit Coriolis only";
+    return RSC_EINVAL;
+  }
   DevFactor* f = nullptr;
   CKS(get_factor(ctx, dt, &f));
+  if (which >= 4) {
+    CKS(ensure_cr_locked(ctx, f));
+    const float4* src = which == 4 ? f->Ds : which == 5 ? f->Gr : which == 6 ? f->Hr : f->Wr;
+    std::vector<float4> t(blk);
+    CK(cudaMemcpyAsync(t.data(), src + index * blk, blk * sizeof(float4), cudaMemcpyDeviceToHost,
+                       ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    for (size_t e = 0; e < blk; ++e) {
+      out_host[2 * e] = (double)t[e].x + (double)t[e].z;
+      out_host[2 * e + 1] = (double)t[e].y + (double)t[e].w;
+    }
+    return RSC_OK;
+  }
   if (which == 3)
     CK(cudaMemcpyAsync(out_host, f->Tinv + index * blk, blk * sizeof(double),
                        cudaMemcpyDeviceToHost, ctx->s));
@@ -2709,6 +2852,13 @@ rsc_status rsc_factor_time(const rsc_ctx* ctx, double* seconds, int* on_gpu) {
   if (!ctx) return RSC_EINVAL;
   if (seconds) *seconds = ctx->factor_s;
   if (on_gpu) *on_gpu = ctx->factor_on_gpu;
+  return RSC_OK;
+}
+
+rsc_status rsc_factor_time_cr(const rsc_ctx* ctx, double* seconds, int* on_gpu) {
+  if (!ctx) return RSC_EINVAL;
+  if (seconds) *seconds = ctx->factor_cr_s;
+  if (on_gpu) *on_gpu = ctx->factor_cr_on_gpu;
   return RSC_OK;
 }
 

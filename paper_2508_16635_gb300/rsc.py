@@ -28,7 +28,7 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_batch_last_error", "rsc_batch_apply_jacobian", "rsc_batch_newton_rw",
            "rsc_autotune", "rsc_get_tuning", "rsc_set_tuning", "rsc_batch_autotune",
            "rsc_continue_ek", "rsc_spectral_tail", "rsc_regrid", "rsc_refine_params",
-           "rsc_implicit_solve", "rsc_factor_block", "rsc_factor_time")
+           "rsc_implicit_solve", "rsc_factor_block", "rsc_factor_time", "rsc_factor_time_cr")
 NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
            "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
@@ -151,6 +151,7 @@ def load_library(path=LIB_PATH):
         "rsc_implicit_solve": ([P, P, P, D], I),
         "rsc_factor_block": ([P, D, I, ctypes.c_long, P], I),
         "rsc_factor_time": ([P, ctypes.POINTER(D), ctypes.POINTER(I)], I),
+        "rsc_factor_time_cr": ([P, ctypes.POINTER(D), ctypes.POINTER(I)], I),
         "rsc_apply_jacobian": ([P, P, D, ctypes.c_long, P, P, I, D], I),
         "rsc_newton_rw": ([P, P, ctypes.POINTER(D), ctypes.c_long, ctypes.POINTER(NewtonOpts),
                            ctypes.POINTER(NewtonReport)], I),
@@ -312,9 +313,11 @@ class RotatingShell:
 
     def factor_block(self, dt, which, index):
         """One factor block as a numpy array (rsc_factor_block): which in "G", "H", "W"
-        (complex Nr x Nr, block `index` over all chains) or "T" (real, degree `index`)."""
+        (complex Nr x Nr, block `index` over all chains), "T" (real, degree `index`), or the
+        odd-even reduced chains' "Dinv" (odd block `index`), "Gr", "Hr", "Wr" (reduced block
+        `index`) of a mixed context."""
         import numpy as np
-        w = {"G": 0, "H": 1, "W": 2, "T": 3}[which]
+        w = {"G": 0, "H": 1, "W": 2, "T": 3, "Dinv": 4, "Gr": 5, "Hr": 6, "Wr": 7}[which]
         Nr = self.Nr
         buf = np.empty(Nr * Nr * (1 if w == 3 else 2))
         self._check(self.lib.rsc_factor_block(self._ctx, dt, w, index,
@@ -327,6 +330,13 @@ class RotatingShell:
         """(seconds, on_gpu) of the last factorisation (rsc_factor_time)."""
         sec, on = ctypes.c_double(), ctypes.c_int()
         self._check(self.lib.rsc_factor_time(self._ctx, ctypes.byref(sec), ctypes.byref(on)))
+        return sec.value, bool(on.value)
+
+    def factor_time_cr(self):
+        """(seconds, on_gpu) of the last factorisation of the odd-even reduced chains
+        (rsc_factor_time_cr)."""
+        sec, on = ctypes.c_double(), ctypes.c_int()
+        self._check(self.lib.rsc_factor_time_cr(self._ctx, ctypes.byref(sec), ctypes.byref(on)))
         return sec.value, bool(on.value)
 
     def apply_jacobian(self, U, C, J, u, dt, out=None):
@@ -555,9 +565,11 @@ class Batch:
 
     def factor_block(self, dt, which, index):
         """One factor block as a numpy array (rsc_factor_block): which in "G", "H", "W"
-        (complex Nr x Nr, block `index` over all chains) or "T" (real, degree `index`)."""
+        (complex Nr x Nr, block `index` over all chains), "T" (real, degree `index`), or the
+        odd-even reduced chains' "Dinv" (odd block `index`), "Gr", "Hr", "Wr" (reduced block
+        `index`) of a mixed context."""
         import numpy as np
-        w = {"G": 0, "H": 1, "W": 2, "T": 3}[which]
+        w = {"G": 0, "H": 1, "W": 2, "T": 3, "Dinv": 4, "Gr": 5, "Hr": 6, "Wr": 7}[which]
         Nr = self.Nr
         buf = np.empty(Nr * Nr * (1 if w == 3 else 2))
         self._check(self.lib.rsc_factor_block(self._ctx, dt, w, index,
@@ -570,6 +582,13 @@ class Batch:
         """(seconds, on_gpu) of the last factorisation (rsc_factor_time)."""
         sec, on = ctypes.c_double(), ctypes.c_int()
         self._check(self.lib.rsc_factor_time(self._ctx, ctypes.byref(sec), ctypes.byref(on)))
+        return sec.value, bool(on.value)
+
+    def factor_time_cr(self):
+        """(seconds, on_gpu) of the last factorisation of the odd-even reduced chains
+        (rsc_factor_time_cr)."""
+        sec, on = ctypes.c_double(), ctypes.c_int()
+        self._check(self.lib.rsc_factor_time_cr(self._ctx, ctypes.byref(sec), ctypes.byref(on)))
         return sec.value, bool(on.value)
 
     def apply_jacobian(self, U, C, J, u, dt, out=None):

@@ -793,6 +793,48 @@ def test_implicit_solve_backward_error_reduced_chains(torch, name, L, Ms, Nr, Ek
 
 @pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES_C3)
 @pytest.mark.parametrize("dt", [2e-3, 200.0])
+def test_gpu_reduced_factorisation_matches_the_host(torch, name, L, Ms, Nr, Ek, Ra, dt):
+    """The factorisation of the odd-even reduced chains on the GPU (factor_gpu = 1: FP64
+    block LU of the odd blocks, the reduced blocks from the Chebyshev tables, the twisted
+    factors of the reduced chains) against the host routine (factor_gpu = 0, pinned by
+    tests/test_host_factor_cr.py), block by block: D_i^-1 of every odd block and G', H', W'
+    of every reduced block, within 1e-9 of each block's largest entry (the blocks'
+    condition numbers reach 1e6 at L = 127, N_r = 64); both then pass the backward-error
+    check of the reduced double-float solve."""
+    from paper_2508_16635_gb300 import RotatingShell
+    s = _shell(L, Ms, Nr, Ek, Ra)
+    ctxs = []
+    for flag in (1, 0):
+        c = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
+        c.set_tuning(dict(c.tuning(), factor_gpu=flag, chain_cr=1))
+        ctxs.append(c)
+    gpu, host = ctxs
+    nodd = sum(2 * ((L - m + 1) // 2) for m in s.ms)
+    nred = 2 * s.P - nodd
+    worst = {}
+    for w, n in (("Dinv", nodd), ("Gr", nred), ("Hr", nred), ("Wr", nred)):
+        worst[w] = 0.0
+        for b in range(n):
+            a, h = gpu.factor_block(dt, w, b), host.factor_block(dt, w, b)
+            scale = np.abs(h).max()
+            if scale == 0.0:
+                assert np.abs(a).max() == 0.0, (w, b)
+                continue
+            worst[w] = max(worst[w], float(np.abs(a - h).max() / scale))
+    assert gpu.factor_time_cr()[1] and not host.factor_time_cr()[1]
+    assert max(worst.values()) < 1e-9, worst
+    b = _random_rhs(s, 98 + L)
+    B = torch.tensor(s.to_real(b), device="cuda")
+    for ctx in (gpu, host):
+        x = s.to_complex(ctx.implicit_solve(B, dt).cpu().numpy())
+        eta, fwd, fwd_T = _solve_errors(s, dt, b, x)
+        assert eta < 64 * U48 and fwd < 32 * 1e-10 and fwd_T < 1e-12, (eta / U48, fwd, fwd_T)
+    gpu.close()
+    host.close()
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES_C3)
+@pytest.mark.parametrize("dt", [2e-3, 200.0])
 def test_gpu_factorisation_matches_the_host_factors(torch, name, L, Ms, Nr, Ek, Ra, dt):
     """The FP64 block factorisation on the GPU (factor_gpu = 1, the default) against the
     host routine (factor_gpu = 0), block by block: G, H, W of every chain block and the
