@@ -68,6 +68,9 @@ def parse():
                     help="only run the implicit vs explicit Coriolis comparison (Sec. 5)")
     ap.add_argument("--resolution-study", action="store_true",
                     help="only run the resolution study of the RW12 drift (Table 1 row 3)")
+    ap.add_argument("--implicit-solves", type=int, default=0,
+                    help="only run this many implicit solves (rsc_implicit_solve, dt = 200) on "
+                         "a context of the workload, for a profiler capture of the chain solve")
     ap.add_argument("--c5", action="store_true",
                     help="only run the large single instance (L = 255, N_r = 96): 1000 time "
                          "steps and one Newton iteration of 100 Jacobian actions per precision")
@@ -256,14 +259,29 @@ FP64_KERNELS = {"radial_eval", "rhs_assemble", "chain_gemv", "chain_sweep", "tem
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on this workload,
-# keyed by (kernel class, arithmetic): a figure holds only for the variant it was taken on
+# keyed by (kernel class, arithmetic and chains): a figure holds only for the variant it was
+# taken on
 NCU_TRAFFIC_MB = {
     # k_chain_half_async: 95.3 + 2.9 MB; k_chain_out_async: 101.1 + 3.3 MB (mean per launch)
     ("chain_sweep", "fp64"): 101.3,
     # k_chain_half_df<2, 4>: 95.3 + 3.3 MB; k_chain_out_df<2, 4>: 101.1 + 3.3 MB (the two-warp
     # variant reads the same: 95.3 + 3.0 and 101.1 + 3.2 MB)
     ("chain_sweep", "df"): 101.5,
+    # the sweeps over the odd-even reduced chains: k_chain_half_df<2, 4>: 45.5 + 0.0 MB,
+    # k_chain_out_df<2, 4>: 51.3 + 12.8 MB
+    ("chain_sweep", "df_cr"): 54.8,
+    # k_cr_odd_df<8>: 49.9 + 1.0 MB, k_cr_even_df<8>: 51.4 + 3.6 MB, k_cr_back_df<8>: 50.7 + 0.0 MB
+    ("chain_reduced", "df_cr"): 52.2,
 }
+
+
+def traffic_variant(name, precision, tuning, dfk):
+    """The NCU_TRAFFIC_MB variant of a kernel class under this tuning."""
+    if name not in dfk:
+        return "fp64"
+    if precision == "mixed" and tuning.get("chain_cr", 0) and name in ("chain_sweep", "chain_reduced"):
+        return "df_cr"
+    return "df"
 
 
 def double_float_kernels(precision, tuning):
@@ -272,7 +290,7 @@ def double_float_kernels(precision, tuning):
     against the split Krylov basis (krylov_split)."""
     out = set()
     if precision == "mixed" and tuning.get("chain_df", 0):
-        out |= {"chain_sweep", "chain_gemv"}
+        out |= {"chain_sweep", "chain_gemv", "chain_reduced"}
     if tuning.get("krylov_split", 0):
         out |= {"gmres_dots", "gmres_axpy"}
     return out
@@ -339,6 +357,16 @@ def factor_timing(torch, RotatingShell, w, dt=200.0):
         out[where + "_s"] = sec
         out[where + "_ran_on_gpu"] = on_gpu
         sh.close()
+        # the odd-even reduced chains of the mixed path's double-float solve
+        sm = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
+                           precision="mixed")
+        sm.set_tuning(dict(sm.tuning(), factor_gpu=flag, chain_cr=1))
+        sm.implicit_solve(sm.new_state(), dt)
+        torch.cuda.synchronize()
+        sec, on_gpu = sm.factor_time_cr()
+        out["reduced_" + where + "_s"] = sec
+        out["reduced_" + where + "_ran_on_gpu"] = on_gpu
+        sm.close()
     out["host_cores"] = os.cpu_count()
     return out
 
@@ -370,7 +398,7 @@ def roofline(prof, peaks, precision, tuning):
             out = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                    "frac": f_hbm, "peak_source": peaks["hbm_source"],
                    "arithmetic": "FP64" if fp64 else "FP32"}
-    mb = NCU_TRAFFIC_MB.get((name, "df" if name in dfk else "fp64"))
+    mb = NCU_TRAFFIC_MB.get((name, traffic_variant(name, precision, tuning, dfk)))
     out.update(kernel=name, traffic=mb * 1e6 if mb is not None else None,
                traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"
                if mb is not None else None, avg_launch_ms=t * 1e3, launches=p["launches"],
@@ -385,7 +413,7 @@ def newton_rw_measure(torch, RotatingShell, w, max_steps=40000, dt=2e-5):
     The initial guess comes from time stepping an m = M_s seed (the route of
     Sec. 2.2) until the state stops changing relative to its drift; then
     Newton-GMRES (dt = 200, Sec. 3.3) is run from that guess on the FP64 path
-    and on the mixed path, each timed end to end.
+    and on the mixed path, each autotuned first and timed end to end.
     """
     M = w["Ms"]
     sh = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
@@ -425,6 +453,7 @@ def newton_rw_measure(torch, RotatingShell, w, max_steps=40000, dt=2e-5):
         s2 = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
                            precision=prec)
         s2.step(s2.new_state(), 0.0, 200.0, nsteps=1)   # factorise dt = 200 outside the timing
+        s2.autotune()                                     # launch shapes, outside the timing
         Ur = guess.clone()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -960,6 +989,20 @@ def run_gpu(args):
             precs = ("mixed", "fp64") if args.c5_precision == "both" else (args.c5_precision,)
             print(json.dumps({"c5": c5_run(torch, RotatingShell, args.c5_steps, args.c5_krylov,
                                            precs, wave=args.c5_wave)}), flush=True)
+        return 0
+    if args.implicit_solves:
+        if rank == 0:
+            sh = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
+                               precision=args.precision)
+            if args.tuning:
+                sh.set_tuning(json.loads(args.tuning))
+            b = torch.tensor(si.random_vector(w["L"], w["Ms"], w["Nr"], seed=3003), device="cuda")
+            for _ in range(args.implicit_solves):
+                x = sh.implicit_solve(b, 200.0)
+            torch.cuda.synchronize()
+            print(json.dumps({"implicit_solves": args.implicit_solves, "tuning": sh.tuning(),
+                              "norm": float(torch.linalg.norm(x).item())}), flush=True)
+            sh.close()
         return 0
     if args.resolution_study:
         if rank == 0:

@@ -421,9 +421,10 @@ typedef struct {
                               the couplings applied from the Chebyshev tables), which
                               halves the sequential depth of the sweeps and reads 2.5
                               instead of 3 factor blocks per block pair; its factors are
-                              computed on the host on first use (chain_parts = 1 and
-                              implicit Coriolis only).  0 = the unreduced chains.
-                              Changes the order of the arithmetic.                     */
+                              computed on first use, on the GPU where factor_gpu puts
+                              the FP64 factorisation (chain_parts = 1 and implicit
+                              Coriolis only).  Default 1 on a mixed context; 0 = the
+                              unreduced chains.  Changes the order of the arithmetic.   */
   double ms[6];            /* after rsc_autotune: best times (ms) of products +
                               analysis (mixed), FP64 synthesis, RHS (mixed), FP64 chain
                               solve, double-float chain solve (0 if none ran); zero
@@ -453,7 +454,10 @@ enum {
   RSC_K_AXPY = 8,      /* GMRES multi-vector updates                          */
   RSC_K_BLAS = 9,      /* other vector operations                             */
   RSC_K_CHAIN_SEQ = 10,/* chain solve, forward / backward sweeps (clusters)   */
-  RSC_NUM_KERNELS = 11
+  RSC_K_CHAIN_RED = 11,/* odd-even reduced chain solve, the passes over every
+                          block (odd blocks, reduced right-hand side, odd blocks
+                          from their neighbours)                               */
+  RSC_NUM_KERNELS = 12
 };
 
 /* Start (mask != 0) or stop collecting per-kernel timings: CUDA events are

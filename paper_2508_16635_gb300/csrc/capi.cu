@@ -1289,13 +1289,13 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = 
     const double nr2 = (double)d.Nr * d.Nr, bo = 2.0 * ctx->n_cr_odd, be = 2.0 * ctx->n_cr_even;
     const double tab = nr2 * 16.0;
     {
-      KSpan sp(ctx, RSC_K_CHAIN, bo * nr2 * 16.0 + bo * d.Nr * 16.0 * 3.0 + tab,
+      KSpan sp(ctx, RSC_K_CHAIN_RED, bo * nr2 * 16.0 + bo * d.Nr * 16.0 * 3.0 + tab,
                bo * nr2 * 8.0 + bo * nr2 * 4.0);
       launch_cr_pass(ctx, f, out, 0);
       CK(cudaGetLastError());
     }
     {
-      KSpan sp(ctx, RSC_K_CHAIN, be * nr2 * 16.0 + be * d.Nr * 16.0 * 6.0, be * nr2 * 8.0);
+      KSpan sp(ctx, RSC_K_CHAIN_RED, be * nr2 * 16.0 + be * d.Nr * 16.0 * 6.0, be * nr2 * 8.0);
       launch_cr_pass(ctx, f, out, 1);
       CK(cudaGetLastError());
     }
@@ -1304,7 +1304,7 @@ rsc_status stage_solve(rsc_ctx* ctx, const DevFactor* f, double* out, bool df = 
       CK(launch_chain_df(ctx, f, out, outward != 0, true));
     }
     {
-      KSpan sp(ctx, RSC_K_CHAIN, bo * nr2 * 16.0 + bo * d.Nr * 16.0 * 4.0 + tab,
+      KSpan sp(ctx, RSC_K_CHAIN_RED, bo * nr2 * 16.0 + bo * d.Nr * 16.0 * 4.0 + tab,
                bo * nr2 * 8.0 + bo * nr2 * 4.0);
       launch_cr_pass(ctx, f, out, 2);
       CK(cudaGetLastError());
@@ -2491,6 +2491,7 @@ rsc_status rsc_create(const rsc_params* params, void* stream, rsc_ctx** out) {
         ctx->cluster_df = cs;
         break;
       }
+    ctx->chain_cr = 1;   // on odd-even reduced chains (used with implicit Coriolis only)
   }
   const size_t c16 = sizeof(double2);
   const size_t K1 = d.K + 1;
@@ -2667,7 +2668,8 @@ rsc_status rsc_apply_jacobian(rsc_ctx* ctx, const double* U, double C, long J, c
 
 static const char* kKernelNames[RSC_NUM_KERNELS] = {
     "radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
-    "chain_solve", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep"};
+    "chain_solve", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep",
+    "chain_reduced"};
 
 const char* rsc_kernel_name(int id) {
   return (id >= 0 && id < RSC_NUM_KERNELS) ? kKernelNames[id] : "unknown";

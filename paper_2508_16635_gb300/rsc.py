@@ -31,7 +31,8 @@ EXPORTS = ("rsc_create", "rsc_destroy", "rsc_set_params", "rsc_state_size",
            "rsc_implicit_solve", "rsc_factor_block", "rsc_factor_time", "rsc_factor_time_cr")
 NORM2_NOALLOC_MAX_N = 8388608
 KERNELS = ("radial_eval", "legendre_synth", "fft_products", "legendre_analysis", "rhs_assemble",
-           "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep")
+           "chain_gemv", "temp_solve", "gmres_dots", "gmres_axpy", "blas1", "chain_sweep",
+           "chain_reduced")
 
 
 class Params(ctypes.Structure):

@@ -21,7 +21,7 @@ def prof_of(name, ms, launches, nbytes, flops):
 
 def test_double_float_kernels_follow_the_tuning():
     t = {"chain_df": 4, "krylov_split": 1}
-    assert bench.double_float_kernels("mixed", t) == {"chain_sweep", "chain_gemv",
+    assert bench.double_float_kernels("mixed", t) == {"chain_sweep", "chain_gemv", "chain_reduced",
                                                        "gmres_dots", "gmres_axpy"}
     # the FP64 path never runs the double-float chain solve; its GMRES may use the split basis
     assert bench.double_float_kernels("fp64", t) == {"gmres_dots", "gmres_axpy"}
@@ -37,6 +37,17 @@ def test_double_float_sweeps_are_reported_against_hbm_with_their_traffic():
     assert r["frac"] == pytest.approx(r["achieved"] / 6800.0)
     assert r["traffic"] == pytest.approx(101.5e6)          # the double-float capture
     assert r["arithmetic"].startswith("double-float")
+
+
+def test_reduced_chain_sweeps_take_their_own_capture():
+    # the sweeps over the odd-even reduced chains read half the blocks: 51.5 MB in 40.4 us
+    prof = prof_of("chain_sweep", 0.0404 * 100, 100, 51.5e6, 25e6)
+    r = bench.roofline(prof, PEAKS, "mixed", {"chain_df": 4, "krylov_split": 1, "chain_cr": 1})
+    assert r["bound"] == "hbm" and r["traffic"] == pytest.approx(54.8e6)
+    assert r["frac"] == pytest.approx(51.5e6 / 40.4e-6 / 1e9 / 6800.0)
+    prof = prof_of("chain_reduced", 0.025 * 30, 30, 52e6, 33e6)
+    r = bench.roofline(prof, PEAKS, "mixed", {"chain_df": 4, "krylov_split": 1, "chain_cr": 1})
+    assert r["arithmetic"].startswith("double-float") and r["traffic"] == pytest.approx(52.2e6)
 
 
 def test_fp64_sweeps_keep_the_fp64_bound_and_their_own_traffic():

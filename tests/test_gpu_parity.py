@@ -533,7 +533,8 @@ def test_autotune_keeps_results_bitwise(torch, name, L, Ms, Nr, Ek, Ra):
         assert t["chain_cluster"] in (2, 4, 8, 16) and min(t["rhs_pairs"]) >= 1
         # the sweep variant, the tensor-core analysis and the double-float sweeps' column
         # split sum in another order (the double-float cluster size does not)
-        gpu.set_tuning(dict(t, chain_async=0, analysis_tc=0, chain_df=t0["chain_df"]))
+        gpu.set_tuning(dict(t, chain_async=0, analysis_tc=0, chain_df=t0["chain_df"],
+                            chain_cr=t0["chain_cr"]))
         a1 = gpu.apply_jacobian(U, 0.3, None, torch.tensor(u, device="cuda"), 200.0)
         s1 = gpu.step(U.clone(), 0.0, 1e-3)
         assert torch.equal(a0, a1) and torch.equal(s0, s1)
@@ -704,13 +705,14 @@ def test_implicit_solve_backward_error_double_float(torch, name, L, Ms, Nr, Ek, 
     b = _random_rhs(s, 95 + L)
     gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
     t0 = gpu.tuning()
-    assert t0["chain_df"] in (2, 4)         # the default of a mixed context
+    assert t0["chain_df"] in (2, 4) and t0["chain_cr"] == 1   # the defaults of a mixed context
     B = torch.tensor(s.to_real(b), device="cuda")
     ran = 0
     for ns in (2, 4):
         for cs in (16, 8, 4, 2):
             try:
-                gpu.set_tuning(dict(t0, chain_df=ns, chain_df_cluster=cs, chain_parts=1))
+                gpu.set_tuning(dict(t0, chain_df=ns, chain_df_cluster=cs, chain_parts=1,
+                                    chain_cr=0))
             except Exception:
                 continue
             ran += 1
@@ -725,7 +727,7 @@ def test_implicit_solve_backward_error_double_float(torch, name, L, Ms, Nr, Ek, 
     for parts in (2, 4):
         if _longest_chain(L) < 8 * parts:
             continue
-        gpu.set_tuning(dict(t0, chain_parts=1))
+        gpu.set_tuning(dict(t0, chain_parts=1, chain_cr=0))
         gpu.implicit_solve(B, dt)
         torch.cuda.synchronize()
         n1 = gpu.launch_count()
