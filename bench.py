@@ -407,13 +407,27 @@ def roofline(prof, peaks, precision, tuning):
     return out
 
 
+def oracle_wave_rw12():
+    """C, KE, Nu_in, Nu_out of the oracle's RW12 wave at L = 127, M_s = 12, N_r = 64
+    (tests/golden/rw12_c3_oracle.txt, written by tests/golden/make_rw12_c3.py from the
+    oracle alone)."""
+    vals = {}
+    with open(os.path.join(ROOT, "tests", "golden", "rw12_c3_oracle.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
 def newton_rw_measure(torch, RotatingShell, w, max_steps=40000, dt=2e-5):
     """Time-to-converged rotating wave at the workload's parameters (Table 1 row 3).
 
     The initial guess comes from time stepping an m = M_s seed (the route of
     Sec. 2.2) until the state stops changing relative to its drift; then
     Newton-GMRES (dt = 200, Sec. 3.3) is run from that guess on the FP64 path
-    and on the mixed path, each autotuned first and timed end to end.
+    and on the mixed path, each autotuned first and timed end to end; the drift, kinetic
+    energy and Nusselt numbers of both waves are compared with the oracle's wave.
     """
     M = w["Ms"]
     sh = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
@@ -449,6 +463,7 @@ def newton_rw_measure(torch, RotatingShell, w, max_steps=40000, dt=2e-5):
     sh.close()
     out = {"time_stepping": {"steps": steps, "dt": dt, "seconds": t_stepping,
                              "precision": "mixed"}, "C0": C0, "phase_slot": J}
+    ref = oracle_wave_rw12() if (w["L"], w["Ms"], w["Nr"]) == (127, 12, 64) else None
     for prec in ("fp64", "mixed"):
         s2 = RotatingShell(w["L"], w["Ms"], w["Nr"], w["Ek"], w["Ra"], w["Pr"], w["eta"],
                            precision=prec)
@@ -464,6 +479,12 @@ def newton_rw_measure(torch, RotatingShell, w, max_steps=40000, dt=2e-5):
                      "residual": rep["residual"], "newton_iterations": rep["iterations"],
                      "gmres_total": rep["gmres_total"], "gmres_per_newton": rep["gmres_history"],
                      "residual_history": rep["residual_history"]}
+        ke, nu_in, nu_out = s2.diagnostics(Ur)
+        out[prec].update(KE=ke, Nu_in=nu_in, Nu_out=nu_out)
+        if ref:   # the oracle's wave at this truncation (drift, KE and Nu are phase-free)
+            out[prec]["vs_oracle_wave"] = {
+                k: abs(v - ref[k]) / abs(ref[k])
+                for k, v in (("C", C), ("KE", ke), ("Nu_in", nu_in), ("Nu_out", nu_out))}
         out[prec + "_U"] = Ur
         s2.close()
     Uf, Um = out.pop("fp64_U"), out.pop("mixed_U")
