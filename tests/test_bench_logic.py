@@ -43,11 +43,11 @@ def test_reduced_chain_sweeps_take_their_own_capture():
     # the sweeps over the odd-even reduced chains read half the blocks: 51.5 MB in 40.4 us
     prof = prof_of("chain_sweep", 0.0404 * 100, 100, 51.5e6, 25e6)
     r = bench.roofline(prof, PEAKS, "mixed", {"chain_df": 4, "krylov_split": 1, "chain_cr": 1})
-    assert r["bound"] == "hbm" and r["traffic"] == pytest.approx(54.8e6)
+    assert r["bound"] == "hbm" and r["traffic"] == pytest.approx(57.7e6)
     assert r["frac"] == pytest.approx(51.5e6 / 40.4e-6 / 1e9 / 6800.0)
     prof = prof_of("chain_reduced", 0.025 * 30, 30, 52e6, 33e6)
     r = bench.roofline(prof, PEAKS, "mixed", {"chain_df": 4, "krylov_split": 1, "chain_cr": 1})
-    assert r["arithmetic"].startswith("double-float") and r["traffic"] == pytest.approx(52.2e6)
+    assert r["arithmetic"].startswith("double-float") and r["traffic"] == pytest.approx(52.1e6)
 
 
 def test_fp64_sweeps_keep_the_fp64_bound_and_their_own_traffic():
