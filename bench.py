@@ -785,7 +785,7 @@ def resolution_study(torch, RotatingShell):
 
 
 def c5_run(torch, RotatingShell, nsteps=1000, krylov=100, precisions=("mixed", "fp64"),
-           wave=False):
+           wave=False, tuning=None):
     """The large single instance (Ek = 3e-6, Pr = 1, r_in/r_out = 0.35, L = 255, M_s = 8,
     N_r = 96, dt = 2e-6, Ra = 1.1 Ra_c of m = 8): from the m = 8 seed, `nsteps` IMEX Euler
     steps timed with CUDA events, then one Newton iteration (FP64 residual at dt = 200, GMRES
@@ -793,13 +793,18 @@ def c5_run(torch, RotatingShell, nsteps=1000, krylov=100, precisions=("mixed", "
     mixed and the FP64 path, each autotuned; and the per-kernel time of one traced Newton
     iteration.  wave: the m = 8 rotating wave converged on the mixed path (time stepping at
     dt = 2e-5 from the seed until the m = 8 temperature amplitude settles, then Newton-GMRES
-    to a residual of 1e-10), with the time of each part."""
+    to a residual of 1e-10), with the time of each part.  tuning: fixed launch shapes (JSON)
+    instead of autotuning, so that a profiled run holds only the measured work."""
     c = si.config("C5")
     out = {"config": f"C5: Ek=3e-6, L=255, Ms=8, Nr=96, dt=2e-6, Ra={c['Ra']:.4f} "
                      f"(1.1 x onset of m = 8, {si.ONSET_RA['C5']:.4f})", "n": None}
     for prec in precisions:
         sh = RotatingShell(c["L"], 8, c["Nr"], c["Ek"], c["Ra"], precision=prec)
-        tuning = sh.autotune()
+        if tuning:
+            sh.set_tuning(json.loads(tuning))
+            tun = sh.tuning()
+        else:
+            tun = sh.autotune()
         U = sh.conductive_state() + torch.tensor(
             si.mode_seed(c["L"], 8, c["Nr"], 8, seed=5000, amp=1e-2), device="cuda")
         sh.step(U, 0.0, c["dt"], nsteps=3)
@@ -833,7 +838,7 @@ def c5_run(torch, RotatingShell, nsteps=1000, krylov=100, precisions=("mixed", "
                      "jacobian_actions": rep["gmres_total"], "residual_after": rep["residual"],
                      "KE_after_steps": ke, "kernel_ms_per_newton_iteration": prof,
                      "last_factorisation_s": fac_s, "factorisation_on_gpu": fac_gpu,
-                     "tuning": tuning}
+                     "tuning": tun}
         sh.close()
         print(json.dumps({"c5_" + prec: out[prec]}), flush=True)
     if wave:
@@ -1009,7 +1014,8 @@ def run_gpu(args):
         if rank == 0:
             precs = ("mixed", "fp64") if args.c5_precision == "both" else (args.c5_precision,)
             print(json.dumps({"c5": c5_run(torch, RotatingShell, args.c5_steps, args.c5_krylov,
-                                           precs, wave=args.c5_wave)}), flush=True)
+                                           precs, wave=args.c5_wave, tuning=args.tuning)}),
+                  flush=True)
         return 0
     if args.implicit_solves:
         if rank == 0:
