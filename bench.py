@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--c5-steps", type=int, default=1000, help="time steps of --c5")
     ap.add_argument("--c5-krylov", type=int, default=100, help="Jacobian actions of --c5")
     ap.add_argument("--c5-precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--c5-wave-krylov", type=int, default=1000,
+                    help="Jacobian actions per Newton iteration at most, for --c5-wave")
     ap.add_argument("--c5-wave", action="store_true",
                     help="with --c5: also converge the m = 8 rotating wave (time stepping from "
                          "the m = 8 seed until it settles, then Newton-GMRES to 1e-10) on "
@@ -785,7 +787,7 @@ def resolution_study(torch, RotatingShell):
 
 
 def c5_run(torch, RotatingShell, nsteps=1000, krylov=100, precisions=("mixed", "fp64"),
-           wave=False, tuning=None):
+           wave=False, tuning=None, wave_krylov=1000):
     """The large single instance (Ek = 3e-6, Pr = 1, r_in/r_out = 0.35, L = 255, M_s = 8,
     N_r = 96, dt = 2e-6, Ra = 1.1 Ra_c of m = 8): from the m = 8 seed, `nsteps` IMEX Euler
     steps timed with CUDA events, then one Newton iteration (FP64 residual at dt = 200, GMRES
@@ -793,7 +795,8 @@ def c5_run(torch, RotatingShell, nsteps=1000, krylov=100, precisions=("mixed", "
     mixed and the FP64 path, each autotuned; and the per-kernel time of one traced Newton
     iteration.  wave: the m = 8 rotating wave converged on the mixed path (time stepping at
     dt = 2e-5 from the seed until the m = 8 temperature amplitude settles, then Newton-GMRES
-    to a residual of 1e-10), with the time of each part.  tuning: fixed launch shapes (JSON)
+    to a residual of 1e-10 with GMRES of at most wave_krylov actions per Newton iteration),
+    with the time of each part.  tuning: fixed launch shapes (JSON)
     instead of autotuning, so that a profiled run holds only the measured work."""
     c = si.config("C5")
     out = {"config": f"C5: Ek=3e-6, L=255, Ms=8, Nr=96, dt=2e-6, Ra={c['Ra']:.4f} "
@@ -853,7 +856,8 @@ def c5_run(torch, RotatingShell, nsteps=1000, krylov=100, precisions=("mixed", "
         U = guess.clone()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        C, rep, st = sh.newton_rw(U, C0, J, tol=1e-10, max_newton=12, kmax=400, gmres_tol=1e-10)
+        C, rep, st = sh.newton_rw(U, C0, J, tol=1e-10, max_newton=16, kmax=wave_krylov,
+                                  gmres_tol=1e-10)
         torch.cuda.synchronize()
         t_newton = time.perf_counter() - t0
         ke, nui, nuo = sh.diagnostics(U)
@@ -861,6 +865,8 @@ def c5_run(torch, RotatingShell, nsteps=1000, krylov=100, precisions=("mixed", "
                        "newton_s": t_newton, "status": st, "C": C, "KE": ke, "Nu_in": nui,
                        "Nu_out": nuo, "newton_iterations": rep["iterations"],
                        "jacobian_actions": rep["gmres_total"], "residual": rep["residual"],
+                       "residual_history": rep["residual_history"],
+                       "gmres_per_newton": rep["gmres_history"], "krylov_cap": wave_krylov,
                        "time_to_wave_s": t_seed + t_newton}
         sh.close()
         print(json.dumps({"c5_wave": out["wave"]}), flush=True)
@@ -1014,7 +1020,8 @@ def run_gpu(args):
         if rank == 0:
             precs = ("mixed", "fp64") if args.c5_precision == "both" else (args.c5_precision,)
             print(json.dumps({"c5": c5_run(torch, RotatingShell, args.c5_steps, args.c5_krylov,
-                                           precs, wave=args.c5_wave, tuning=args.tuning)}),
+                                           precs, wave=args.c5_wave, tuning=args.tuning,
+                                           wave_krylov=args.c5_wave_krylov)}),
                   flush=True)
         return 0
     if args.implicit_solves:
