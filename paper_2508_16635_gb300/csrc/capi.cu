@@ -953,10 +953,10 @@ rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
     const bool pipe = ctx->synth_pipe != 0;
     const size_t smem = tc_synth_smem(ctx->tc_kmax, pipe);
     if (pipe)
-      k_synth_tc<true><<<grid, 128, smem, ctx->s>>>(g, tt, reinterpret_cast<const float2*>(ctx->SR),
+      k_synth_tc<true><<<grid, kTcThreads, smem, ctx->s>>>(g, tt, reinterpret_cast<const float2*>(ctx->SR),
                                                     reinterpret_cast<float2*>(FCout));
     else
-      k_synth_tc<false><<<grid, 128, smem, ctx->s>>>(g, tt, reinterpret_cast<const float2*>(ctx->SR),
+      k_synth_tc<false><<<grid, kTcThreads, smem, ctx->s>>>(g, tt, reinterpret_cast<const float2*>(ctx->SR),
                                                      reinterpret_cast<float2*>(FCout));
     CK(cudaGetLastError());
   } else {
@@ -1036,7 +1036,7 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
   const int TC = ctx->atc[sizeof(R) == 4 ? 1 : 0];
   if (sizeof(R) == 4 && ctx->anal_tc) {
     TaTables ta{ctx->ta_tiles, ctx->ta_off, ctx->ta_nchunk, ctx->d_status};
-    k_analysis_tc<<<dim3(d.nm, (d.Nd + kTaRadii - 1) / kTaRadii), 128, ta_smem(), ctx->s>>>(
+    k_analysis_tc<<<dim3(d.nm, (d.Nd + kTaRadii - 1) / kTaRadii), kTaThreads, ta_smem(), ctx->s>>>(
         g, ta, reinterpret_cast<const float2*>(ctx->FA), reinterpret_cast<float2*>(ctx->AR));
   } else {
     k_analysis<R><<<dim3(d.nm, (d.Nd + RTa - 1) / RTa), dim3(round32(d.L + 1), RTa),

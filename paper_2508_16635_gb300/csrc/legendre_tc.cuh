@@ -16,7 +16,7 @@
 // epilogue reads tensor memory (tcgen05.ld) and forms the nine grid fields
 // exactly as the CUDA-core synthesis does.
 //
-// One CTA = (m, RT = 8 radii, one 128-latitude tile); 128 threads (4 warps).
+// One CTA = (m, RT = 8 radii, one 128-latitude tile); kTcThreads = 256 threads (8 warps).
 // All waits are bounded; a timeout sets *status and the CTA still frees its
 // tensor memory before returning.
 #pragma once
@@ -30,6 +30,9 @@ constexpr int kTcNP = 48;                 // 6 columns per radius (3 fields x re
 constexpr int kTcNV = 80;                 // 10 columns per radius (5 fields x re/im)
 constexpr int kTcCols = 2 * kTcNP + 4 * kTcNV;   // 416 accumulator columns
 constexpr int kTcAlloc = 512;             // tensor-memory columns allocated
+constexpr int kTcThreads = 256;           // two warpgroups: both gather the B operands; in
+                                          // the epilogue each reads its warp quadrant's
+                                          // tensor-memory lanes for half of the radii
 
 struct TcTables {
   const float* tiles;        // all A tiles
@@ -104,11 +107,11 @@ __device__ __forceinline__ void tc_gather_b(const float2* __restrict__ SR, int p
   const int NC = (w == 0) ? 3 : 5;          // components of this table type
   const int NW = (w == 0) ? kTcNP : kTcNV;  // N of the GEMM (padded)
   const int total = NW * Kp;
-  for (int base = tid; base < total; base += 128 * 8) {
+  for (int base = tid; base < total; base += kTcThreads * 8) {
     float vals[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int idx = base + 128 * u;
+      const int idx = base + kTcThreads * u;
       const int k = idx / NW;
       const int n = idx - k * NW;
       const int q = s + 2 * k;
@@ -127,7 +130,7 @@ __device__ __forceinline__ void tc_gather_b(const float2* __restrict__ SR, int p
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int idx = base + 128 * u;
+      const int idx = base + kTcThreads * u;
       if (idx < total) {
         const int k = idx / NW;
         const int n = idx - k * NW;
@@ -194,9 +197,9 @@ __host__ __device__ constexpr size_t tc_synth_smem(int kmax, bool pipe) {
 // waits for them before the next phase starts.  PIPE = true: the A tile and B operand of
 // phase p + 1 are staged (second A stage, the other B buffer) while the MMAs of phase p run;
 // a buffer is refilled only after the MMAs that read it have completed.
-// grid = (nm, ceil(Nd / 8), nmt); block = 128; dynamic smem tc_synth_smem(kmax, PIPE).
+// grid = (nm, ceil(Nd / 8), nmt); block = kTcThreads; dynamic smem tc_synth_smem(kmax, PIPE).
 template <bool PIPE>
-__global__ void __launch_bounds__(128) k_synth_tc(DevGeom g, TcTables tt, const float2* __restrict__ SR,
+__global__ void __launch_bounds__(kTcThreads) k_synth_tc(DevGeom g, TcTables tt, const float2* __restrict__ SR,
                                                   float2* __restrict__ FC) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   const int a = blockIdx.x;
@@ -331,13 +334,16 @@ __global__ void __launch_bounds__(128) k_synth_tc(DevGeom g, TcTables tt, const 
   }
   if (!ok && tid == 0) atomicExch(tt.status, 7);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // (4) epilogue: warp w owns latitudes (TMEM lanes) 32 w .. 32 w + 31 of this tile
-  const int t = mt * 128 + warp * 32 + lane;
+  // (4) epilogue: warp w owns latitudes (TMEM lanes) 32 (w % 4) .. 32 (w % 4) + 31 of this
+  // tile (its quadrant) for the radii of its warpgroup w / 4
+  const int quad = warp & 3, grp = warp >> 2;
+  const int t = mt * 128 + quad * 32 + lane;
   const bool live = ok && t < g.nlat2;
-  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
   const float mm = (float)m;
   const int K1 = g.K + 1, nlat = g.nlat;
-  for (int rr = 0; rr < kTcRadii; ++rr) {
+  constexpr int kRadGrp = kTcRadii / (kTcThreads / 128);
+  for (int rr = grp * kRadGrp; rr < (grp + 1) * kRadGrp; ++rr) {
     const int i = i0 + rr;
     float Pe[6], Po[6], De[10], Do[10], Se[10], So[10];
     // the loads are warp-collective: every lane takes part

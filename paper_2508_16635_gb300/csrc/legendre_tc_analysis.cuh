@@ -13,8 +13,8 @@
 // memory.  The epilogue reads tensor memory (tcgen05.ld) and forms Q, S, T, N of the
 // CUDA-core analysis (k_analysis) for its degree (one TMEM lane per degree).
 //
-// One CTA = (m, 8 radii); 128 threads.  All waits are bounded; a timeout sets *status and
-// the CTA still frees its tensor memory.
+// One CTA = (m, 8 radii); kTaThreads = 256 threads.  All waits are bounded; a timeout sets
+// *status and the CTA still frees its tensor memory.
 #pragma once
 
 namespace rsc {
@@ -23,6 +23,8 @@ constexpr int kTaRadii = 8;     // radii per CTA
 constexpr int kTaKc = 48;       // latitudes per staged chunk (multiple of 8)
 constexpr int kTaN = 32;        // columns of each GEMM
 constexpr int kTaAlloc = 256;   // tensor-memory columns: 2 parities x 3 tables x 32
+constexpr int kTaThreads = 256; // two warpgroups: both gather B; in the epilogue warpgroup g
+                                // reads parity class g from its warp quadrant's lanes
 
 struct TaTables {
   const float* tiles;   // A tiles, hi then lo, K-major core-matrix layout
@@ -52,8 +54,8 @@ inline size_t ta_smem() {
   return (3 * 2 * 128 * (size_t)kTaKc + 2 * 2 * 64 * (size_t)kTaKc) * sizeof(float) + 64;
 }
 
-// grid = (nm, ceil(Nd / 8)); block = 128.
-__global__ void __launch_bounds__(128) k_analysis_tc(DevGeom g, TaTables tt,
+// grid = (nm, ceil(Nd / 8)); block = kTaThreads.
+__global__ void __launch_bounds__(kTaThreads) k_analysis_tc(DevGeom g, TaTables tt,
                                                      const float2* __restrict__ FA,
                                                      float2* __restrict__ AR) {
   extern __shared__ __align__(1024) unsigned char ta_raw[];
@@ -94,11 +96,11 @@ __global__ void __launch_bounds__(128) k_analysis_tc(DevGeom g, TaTables tt,
     // (1) B: sym / ant of the 4 fields of 8 radii at latitudes c kTaKc + k; column
     // n = f * 16 + rr * 2 + re/im, K-major core-matrix layout; eight pairs of gathers in flight
     const int total = 4 * kTaRadii * kTaKc;
-    for (int base = tid; base < total; base += 128 * 8) {
+    for (int base = tid; base < total; base += kTaThreads * 8) {
       float2 nv[8], sv[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int idx = base + 128 * u;
+        const int idx = base + kTaThreads * u;
         const int f = idx / (kTaRadii * kTaKc);
         const int rem = idx - f * kTaRadii * kTaKc;
         const int rr = rem / kTaKc, k = rem - rr * kTaKc;
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(128) k_analysis_tc(DevGeom g, TaTables tt,
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int idx = base + 128 * u;
+        const int idx = base + kTaThreads * u;
         if (idx >= total) continue;
         const int f = idx / (kTaRadii * kTaKc);
         const int rem = idx - f * kTaRadii * kTaKc;
@@ -190,11 +192,13 @@ __global__ void __launch_bounds__(128) k_analysis_tc(DevGeom g, TaTables tt,
   }
   if (!ok && tid == 0) atomicExch(tt.status, 7);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // (4) epilogue: TMEM lane = degree index k of the class; warp w owns lanes 32 w .. 32 w + 31
-  const int row = warp * 32 + lane;
-  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+  // (4) epilogue: TMEM lane = degree index k of the class; warp w owns lanes 32 (w % 4) ..
+  // 32 (w % 4) + 31 (its quadrant), for the parity class w / 4
+  const int quad = warp & 3;
+  const int row = quad * 32 + lane;
+  const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
   const float mm = (float)m;
-  for (int s = 0; s < 2; ++s) {
+  for (int s = warp >> 2; s < 2; s += kTaThreads / 128) {
     float Pv[32], Xv[32], Yv[32];
     {
       float v[16];
