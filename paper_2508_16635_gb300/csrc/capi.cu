@@ -26,6 +26,7 @@
 #include "krylov_split.cuh"
 #include "chain_df.cuh"
 #include "chain_cr.cuh"
+#include "products_lin.cuh"
 #include "cr_factor_gpu.cuh"
 #include "factor_gpu.cuh"
 #include "rsc_internal.h"
@@ -1016,7 +1017,26 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
   KSpan sp(ctx, RSC_K_PRODUCTS,
            (double)(nft + 4) * d.Nd * K1 * d.nlat * sizeof(V) + (ug ? 9.0 * npts * sizeof(R) : 0.0),
            npts * (4.0 * nft * d.K + (lin ? 60.0 : 30.0) + 16.0 * K1));
-  if (lin)
+  bool done = false;
+  if constexpr (sizeof(R) == 4) {
+    // Jacobian actions on the small transforms of the wave workloads
+    // (the kernel's gather offsets are 32-bit: 9 Nd (K + 1) nlat coefficients per field set)
+    if (lin && ug && d.nphi <= 32 && K1 <= 16 && WPB <= kPlMaxWarps &&
+        9.0 * d.Nd * K1 * d.nlat < 2147483647.0) {
+      const float2* fc = reinterpret_cast<const float2*>(ctx->FC);
+      float2* fa = reinterpret_cast<float2*>(ctx->FA);
+      const float* ugp = reinterpret_cast<const float*>(ctx->UG);
+      if (K1 <= 8)
+        k_products_lin<8><<<grid, 32 * WPB, 0, ctx->s>>>(g, L.view(), (float)ctx->p.Ek, fc, fa, LPW, ugp);
+      else if (K1 <= 12)
+        k_products_lin<12><<<grid, 32 * WPB, 0, ctx->s>>>(g, L.view(), (float)ctx->p.Ek, fc, fa, LPW, ugp);
+      else
+        k_products_lin<16><<<grid, 32 * WPB, 0, ctx->s>>>(g, L.view(), (float)ctx->p.Ek, fc, fa, LPW, ugp);
+      done = true;
+    }
+  }
+  if (done) {
+  } else if (lin)
     k_products<R, true><<<grid, 32 * WPB, smem, ctx->s>>>(
         g, L.view(), (R)ctx->p.Ek, reinterpret_cast<const V*>(ctx->FC),
         reinterpret_cast<const V*>(ctx->FCU), reinterpret_cast<V*>(ctx->FA), LPW,

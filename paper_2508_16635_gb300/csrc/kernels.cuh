@@ -592,6 +592,58 @@ __global__ void k_rhs(DevGeom g, RhsParams rp, const typename C2<R>::T* __restri
       dSx += w1 * s.x; dSy += w1 * s.y;
     }
   }
+  if constexpr (sizeof(R) == 4) {
+    if (low && !coriolis_rhs) {
+      // Jacobian action of the mixed path: every term is FP32-accurate (FP32 transforms and
+      // mass products), so the combination runs in FP32 too (the FP64 pipe of GB300 issues
+      // at 1/64 of the FP32 rate); only the stores widen to FP64.
+      const float lamf = (float)(l * (l + 1));
+      const float irf = 1.0f / (float)g.rc[j], ir2f = irf * irf;
+      const float Ekf = (float)rp.Ek, Raf = (float)rp.Ra, rof = (float)rp.r_out;
+      auto mass_f = [&](const float2* vf, float2& me, float2& mf, float2& mt) {
+        float e0x = 0, e0y = 0, f0x = 0, f0y = 0, f2x = 0, f2y = 0, t0x = 0, t0y = 0;
+        for (int k = 0; k < Nr; ++k) {
+          const float c0 = g.EcT0f[k * Nr + j], c2 = g.EcT2f[k * Nr + j];
+          const float2 e = vf[k], f = vf[Nr + k], t = vf[2 * Nr + k];
+          e0x += c0 * e.x; e0y += c0 * e.y;
+          f0x += c0 * f.x; f0y += c0 * f.y;
+          f2x += c2 * f.x; f2y += c2 * f.y;
+          t0x += c0 * t.x; t0y += c0 * t.y;
+        }
+        const float ce = lamf * Ekf * ir2f, cl = lamf * ir2f;
+        me = make_float2(ce * e0x, ce * e0y);
+        mf = make_float2(-ce * (f2x - cl * f0x), -ce * (f2y - cl * f0y));
+        mt = make_float2(t0x, t0y);
+      };
+      float2 Me, Mf, MT;
+      mass_f(xf, Me, Mf, MT);
+      const float cb = lamf * Raf * irf / rof;
+      const float2 Ne = make_float2(lamf * irf * Tcx, lamf * irf * Tcy);
+      const float2 Nf = make_float2(lamf * ir2f * (Qcx - dSx) + cb * MT.x, lamf * ir2f * (Qcy - dSy) + cb * MT.y);
+      const float2 NT = make_float2(-Ncx, -Ncy);
+      const float fr = (float)rp.inv_dt, fi = (float)(rp.C * m);  // (1/dt + i C m)
+      auto cm = [&](float2 v, float2 n) {
+        return make_float2(fr * v.x - fi * v.y + n.x, fr * v.y + fi * v.x + n.y);
+      };
+      float2 o[3] = {cm(Me, Ne), cm(Mf, Nf), cm(MT, NT)};
+      if (has_c) {
+        float2 ue, uf_, ut;
+        mass_f(uf, ue, uf_, ut);
+        const float cmv = (float)u_orig[rp.J] * (float)m;  // c * i m * v = (-cm v.y, cm v.x)
+        o[0].x -= cmv * ue.y; o[0].y += cmv * ue.x;
+        o[1].x -= cmv * uf_.y; o[1].y += cmv * uf_.x;
+        o[2].x -= cmv * ut.y; o[2].y += cmv * ut.x;
+      }
+      // boundary rows (Sec. 3.1) and identity rows of e_00, f_00
+      if (j == 0 || j == Nr - 1) { o[0] = make_float2(0, 0); o[2] = make_float2(0, 0); }
+      if (j == 0 || j == 1 || j == Nr - 2 || j == Nr - 1) o[1] = make_float2(0, 0);
+      if (l == 0) { o[0] = make_float2(0, 0); o[1] = make_float2(0, 0); }
+      if (m == 0) { o[0].y = 0; o[1].y = 0; o[2].y = 0; }
+#pragma unroll
+      for (int f = 0; f < 3; ++f) rhs[((long)f * P + p) * Nr + j] = make_double2(o[f].x, o[f].y);
+      return;
+    }
+  }
   const double2 Tc = make_double2(Tcx, Tcy), Qc = make_double2(Qcx, Qcy);
   const double2 dS = make_double2(dSx, dSy), Nc = make_double2(Ncx, Ncy);
   // M x at the collocation radius r_j.  FP64 except in Jacobian actions of the
