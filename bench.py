@@ -302,12 +302,12 @@ def dtype_label(precision, tuning):
     """What the path computes in, from the tuning the run used."""
     if precision != "mixed":
         return "f64"
-    parts = ["f32 transforms (tcgen05 3xTF32 Legendre sums)"]
+    parts = ["f32 transforms (tcgen05 3xTF32 Legendre sums) and Jacobian-action RHS"]
     parts.append("double-float e/f chain solve" if tuning.get("chain_df", 0)
                  else "f64 e/f chain solve")
     parts.append("double-float Krylov basis" if tuning.get("krylov_split", 0)
                  else "f64 Krylov basis")
-    parts.append("f64 RHS, temperature solve, residual and update")
+    parts.append("f64 step / residual RHS, temperature solve and update")
     return " + ".join(parts)
 
 

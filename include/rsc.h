@@ -64,8 +64,10 @@ typedef enum {
 typedef enum {
   RSC_FP64 = 0,        /* every stage in FP64                                 */
   RSC_MIXED = 1        /* transforms and products in FP32 (Legendre sums on
-                          tcgen05 tensor cores, 3xTF32); right-hand side,
-                          temperature solve, Newton residual and update in FP64;
+                          tcgen05 tensor cores, 3xTF32), and so the right-hand
+                          side of Jacobian actions; the right-hand side of steps
+                          and residuals, the temperature solve, Newton residual
+                          and update in FP64;
                           the e/f chain solve of Jacobian actions and steps
                           and the GMRES orthogonalisation in double-float
                           arithmetic (FP32 hi + lo pairs, 48-bit significand)
