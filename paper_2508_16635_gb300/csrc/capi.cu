@@ -1919,7 +1919,7 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
   {
     KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 1.0 * n);
     if (split)
-      k_scale_split<<<nb, 256, 0, ctx->s>>>(b, V, Vs, n, nullptr, 1.0 / beta);
+      k_scale_split<<<nb, 256, 0, ctx->s>>>(b, V, Vs, n, nullptr, 0, nullptr, 1.0 / beta);
     else
       k_axpby<<<nb, 256, 0, ctx->s>>>(1.0 / beta, b, 0.0, V, n);
     CK(cudaGetLastError());
@@ -1986,11 +1986,19 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
     const double* tv = h_in + k + 2;
     double* Lk = Lr(k);
     for (int j = 0; j < k; ++j) Lk[j] = tv[j];
+    // (the GPU waits for this solve: each row's sum runs in four independent chains)
     for (int i = 0; i <= k; ++i) {
-      double a = sv[i];
       const double* Li = Lr(i);
-      for (int j = 0; j < i; ++j) a -= Li[j] * h_out[j];
-      h_out[i] = a;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int j = 0;
+      for (; j + 4 <= i; j += 4) {
+        a0 += Li[j] * h_out[j];
+        a1 += Li[j + 1] * h_out[j + 1];
+        a2 += Li[j + 2] * h_out[j + 2];
+        a3 += Li[j + 3] * h_out[j + 3];
+      }
+      for (; j < i; ++j) a0 += Li[j] * h_out[j];
+      h_out[i] = sv[i] - ((a0 + a1) + (a2 + a3));
     }
     if (!std::isfinite(h_out[k])) {
       ctx->err = "non-finite Krylov vector";
@@ -2013,15 +2021,16 @@ rsc_status gmres(rsc_ctx* ctx, const double* U, double C, long J, const double* 
         k_axpy_norm<<<nb, 256, 0, ctx->s>>>(V, ld, k + 1, d_h, w, n, ctx->partial);
       CK(cudaGetLastError());
     }
-    {
+    if (!split) {
       KSpan sp(ctx, RSC_K_BLAS, 8.0 * nb, 1.0 * nb);
       k_reduce_rows<<<1, 256, 0, ctx->s>>>(ctx->partial, nb, dbuf);
       CK(cudaGetLastError());
     }
     {
-      KSpan sp(ctx, RSC_K_BLAS, 16.0 * n, 1.0 * n);
-      if (split)
-        k_scale_split<<<nb, 256, 0, ctx->s>>>(w, w, Vs + (long)(k + 1) * ld, n, dbuf, 1.0);
+      KSpan sp(ctx, RSC_K_BLAS, 16.0 * n + 8.0 * nb, 1.0 * n);
+      if (split)   // the norm's block shares are summed inside (|w|^2 to dbuf[0])
+        k_scale_split<<<nb, 256, 0, ctx->s>>>(w, w, Vs + (long)(k + 1) * ld, n, ctx->partial, nb,
+                                              dbuf, 1.0);
       else
         k_scale_inv_sqrt<<<nb, 256, 0, ctx->s>>>(w, n, dbuf);
       CK(cudaGetLastError());

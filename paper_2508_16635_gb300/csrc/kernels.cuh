@@ -1330,9 +1330,13 @@ __global__ void __launch_bounds__(256) k_axpy_norm(const double* __restrict__ V,
 
 // w <- w / sqrt(nrm2[0]) (left unchanged when nrm2[0] is zero: a breakdown the host sees).
 __global__ void k_scale_inv_sqrt(double* __restrict__ w, long n, const double* __restrict__ nrm2) {
+  // one FP64 square root and division per block (the FP64 pipe is narrow)
+  __shared__ double sinv;
   const double s2 = nrm2[0];
   if (!(s2 > 0.0)) return;
-  const double inv = 1.0 / sqrt(s2);
+  if (threadIdx.x == 0) sinv = 1.0 / sqrt(s2);
+  __syncthreads();
+  const double inv = sinv;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (long)gridDim.x * blockDim.x)
     w[idx] *= inv;

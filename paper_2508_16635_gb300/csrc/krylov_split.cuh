@@ -25,13 +25,36 @@ __device__ __forceinline__ void ks_prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// out = s * in and outs = split48(out); s = 1 / sqrt(nrm2[0]) when nrm2 is given (1 when
-// nrm2[0] <= 0, a breakdown the host detects), else the argument.  in may equal out.
-__global__ void k_scale_split(const double* in, double* out, float2* __restrict__ outs, long n,
-                              const double* __restrict__ nrm2, double s) {
-  if (nrm2) {
-    const double s2 = nrm2[0];
-    s = (s2 > 0.0) ? 1.0 / sqrt(s2) : 1.0;
+// out = s * in and outs = split48(out).  With part given, |in|^2 = the sum of part[0, np)
+// (the blocks' shares of k_axpy_norm_s), summed by every block in the same order (threads
+// strided, then the warp and block trees), written to nrm2_out[0] by block 0, and
+// s = 1 / sqrt(|in|^2) (1 when |in|^2 <= 0, a breakdown the host detects); else s is the
+// argument.  One thread per block evaluates the FP64 square root and division.  in may
+// equal out.  block = 256.
+__global__ void __launch_bounds__(256) k_scale_split(const double* in, double* out,
+                                                     float2* __restrict__ outs, long n,
+                                                     const double* __restrict__ part, int np,
+                                                     double* __restrict__ nrm2_out, double s) {
+  if (part) {
+    __shared__ double red[8];
+    __shared__ double sc;
+    double t = 0.0;
+    for (int b = threadIdx.x; b < np; b += blockDim.x) t += part[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (threadIdx.x == 0) {
+        sc = (t > 0.0) ? 1.0 / sqrt(t) : 1.0;
+        if (blockIdx.x == 0) nrm2_out[0] = t;
+      }
+    }
+    __syncthreads();
+    s = sc;
   }
   const long n2 = n >> 1;
   const double2* in2 = reinterpret_cast<const double2*>(in);
