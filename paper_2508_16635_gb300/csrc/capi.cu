@@ -27,6 +27,7 @@
 #include "chain_df.cuh"
 #include "chain_cr.cuh"
 #include "products_lin.cuh"
+#include "radial_rhs_f32.cuh"
 #include "cr_factor_gpu.cuh"
 #include "factor_gpu.cuh"
 #include "rsc_internal.h"
@@ -156,6 +157,7 @@ struct rsc_ctx {
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int rt_synth[2] = {1, 1}, rt_anal[2] = {1, 1};  // radii per block, [fp64, fp32]
+  int radial_f32_grid = 0, rhs_lin_grid = 0;     // persistent FP32 radial kernels (0: not used)
   int wpb[2] = {0, 0};     // warps per block of the products kernel (0: largest that fits)
   int ppb[2] = {0, 0};     // pairs per block of the right-hand-side kernel (0: 256 / Nr)
   int atc[2] = {16, 16};   // latitudes per staged chunk of the analysis tables
@@ -487,6 +489,29 @@ rsc_status set_smem_limits(rsc_ctx* ctx) {
   CK(cudaFuncSetAttribute(k_products<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_radial<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   CK(cudaFuncSetAttribute(k_radial<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  {
+    // the persistent FP32 radial kernels: one or two blocks per SM with the tables staged
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const Dims& d = ctx->d;
+    const size_t lim = 227 * 1024;
+    auto grid_for = [&](const void* fn, int thr, size_t smem, bool fits) -> int {
+      if (!fits || thr > 1024 || smem > lim) return 0;
+      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, thr, smem) != cudaSuccess || nb < 1)
+        return 0;
+      return (int)std::min<long>((long)nb * nsm, d.P);
+    };
+    const int tr = 4 * ((d.Nd + 7) / 8 * 8), th = 4 * ((d.Nr + 7) / 8 * 8);
+    ctx->radial_f32_grid = grid_for((const void*)k_radial_f32, tr, radial_f32_smem(d.Nr, d.Nd),
+                                    tr >= 3 * d.Nr);
+    ctx->rhs_lin_grid = grid_for((const void*)k_rhs_lin, th, rhs_lin_smem(d.Nr, d.Nd),
+                                 th <= 512 && th >= 3 * d.Nr && 2 * th >= 4 * d.Nd);
+    cudaGetLastError();   // a refused attribute leaves the kernels unused, not an error
+  }
   // radii per block of the Legendre kernels: as many as the register file allows (<= 4)
   auto rt_for = [&](const void* fn, int threads_x) {
     cudaFuncAttributes at{};
@@ -938,8 +963,12 @@ rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
   {
   KSpan sp(ctx, RSC_K_RADIAL, 48.0 * d.P * d.Nr + 8.0 * d.P * d.Nd * sizeof(V),
            28.0 * d.P * d.Nd * d.Nr);
-  k_radial<R><<<d.P, round32(std::max(d.Nd, 32)), 3 * d.Nr * sizeof(V), ctx->s>>>(
-      g, reinterpret_cast<const double2*>(x), reinterpret_cast<V*>(ctx->SR));
+  if (sizeof(R) == 4 && ctx->radial_f32_grid > 0)   // FP32: persistent, tables staged once
+    k_radial_f32<<<ctx->radial_f32_grid, 4 * ((d.Nd + 7) / 8 * 8), radial_f32_smem(d.Nr, d.Nd), ctx->s>>>(
+        g, reinterpret_cast<const double2*>(x), reinterpret_cast<float2*>(ctx->SR));
+  else
+    k_radial<R><<<d.P, round32(std::max(d.Nd, 32)), 3 * d.Nr * sizeof(V), ctx->s>>>(
+        g, reinterpret_cast<const double2*>(x), reinterpret_cast<V*>(ctx->SR));
   CK(cudaGetLastError());
   }
   const LegDev<R>& L = leg<R>(ctx);
@@ -1079,6 +1108,16 @@ rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const d
   KSpan sp(ctx, RSC_K_RHS,
            4.0 * d.P * d.Nd * sizeof(V) + (rp.J >= 0 ? 144.0 : 96.0) * d.P * d.Nr,
            d.P * (double)d.Nr * (16.0 * d.Nd + 32.0 * d.Nr));
+  if constexpr (sizeof(R) == 4) {
+    // Jacobian actions of the mixed path: persistent, tables staged once (k_rhs_lin)
+    if (rp.mode == 1 && !rp.explicit_coriolis && ctx->rhs_lin_grid > 0) {
+      k_rhs_lin<<<ctx->rhs_lin_grid, 4 * ((d.Nr + 7) / 8 * 8), rhs_lin_smem(d.Nr, d.Nd), ctx->s>>>(
+          ctx->geom(), rp, reinterpret_cast<const float2*>(ctx->AR),
+          reinterpret_cast<const double2*>(x), reinterpret_cast<const double2*>(U), u_orig, out);
+      CK(cudaGetLastError());
+      return RSC_OK;
+    }
+  }
   k_rhs<R><<<(d.P + PPB - 1) / PPB, dim3(round32(d.Nr), PPB), smem, ctx->s>>>(
       ctx->geom(), rp, reinterpret_cast<const V*>(ctx->AR), reinterpret_cast<const double2*>(x),
       reinterpret_cast<const double2*>(U), u_orig,
