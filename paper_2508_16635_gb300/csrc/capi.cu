@@ -481,6 +481,12 @@ bool threads_fit(const void* fn, int threads) {
          threads <= at.maxThreadsPerBlock;
 }
 
+// Radial sizes with a compile-time instantiation of the FP32 radial kernels: 1 for
+// (N_r, N_d) = (64, 96), 2 for (96, 144), else 0 (sizes read at run time).
+int radial_fixed(const Dims& d) {
+  return (d.Nr == 64 && d.Nd == 96) ? 1 : (d.Nr == 96 && d.Nd == 144) ? 2 : 0;
+}
+
 rsc_status set_smem_limits(rsc_ctx* ctx) {
   const int big = 200 * 1024;
   CK(cudaFuncSetAttribute(k_products<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -506,9 +512,13 @@ rsc_status set_smem_limits(rsc_ctx* ctx) {
       return (int)std::min<long>((long)nb * nsm, d.P);
     };
     const int tr = 4 * ((d.Nd + 7) / 8 * 8), th = 4 * ((d.Nr + 7) / 8 * 8);
-    ctx->radial_f32_grid = grid_for((const void*)k_radial_f32, tr, radial_f32_smem(d.Nr, d.Nd),
-                                    tr >= 3 * d.Nr);
-    ctx->rhs_lin_grid = grid_for((const void*)k_rhs_lin, th, rhs_lin_smem(d.Nr, d.Nd),
+    const int fix = radial_fixed(d);
+    const void* fr = fix == 1 ? (const void*)k_radial_f32<64, 96>
+                   : fix == 2 ? (const void*)k_radial_f32<96, 144> : (const void*)k_radial_f32<0, 0>;
+    const void* fh = fix == 1 ? (const void*)k_rhs_lin<64, 96>
+                   : fix == 2 ? (const void*)k_rhs_lin<96, 144> : (const void*)k_rhs_lin<0, 0>;
+    ctx->radial_f32_grid = grid_for(fr, tr, radial_f32_smem(d.Nr, d.Nd), tr >= 3 * d.Nr);
+    ctx->rhs_lin_grid = grid_for(fh, th, rhs_lin_smem(d.Nr, d.Nd),
                                  th <= 512 && th >= 3 * d.Nr && 2 * th >= 4 * d.Nd);
     cudaGetLastError();   // a refused attribute leaves the kernels unused, not an error
   }
@@ -963,12 +973,20 @@ rsc_status stage_synth(rsc_ctx* ctx, const double* x, void* FCout) {
   {
   KSpan sp(ctx, RSC_K_RADIAL, 48.0 * d.P * d.Nr + 8.0 * d.P * d.Nd * sizeof(V),
            28.0 * d.P * d.Nd * d.Nr);
-  if (sizeof(R) == 4 && ctx->radial_f32_grid > 0)   // FP32: persistent, tables staged once
-    k_radial_f32<<<ctx->radial_f32_grid, 4 * ((d.Nd + 7) / 8 * 8), radial_f32_smem(d.Nr, d.Nd), ctx->s>>>(
-        g, reinterpret_cast<const double2*>(x), reinterpret_cast<float2*>(ctx->SR));
-  else
+  if (sizeof(R) == 4 && ctx->radial_f32_grid > 0) {   // FP32: persistent, tables staged once
+    const dim3 gr(ctx->radial_f32_grid), bl(4 * ((d.Nd + 7) / 8 * 8));
+    const size_t sm = radial_f32_smem(d.Nr, d.Nd);
+    const double2* xx = reinterpret_cast<const double2*>(x);
+    float2* sr = reinterpret_cast<float2*>(ctx->SR);
+    switch (radial_fixed(d)) {
+      case 1: k_radial_f32<64, 96><<<gr, bl, sm, ctx->s>>>(g, xx, sr); break;
+      case 2: k_radial_f32<96, 144><<<gr, bl, sm, ctx->s>>>(g, xx, sr); break;
+      default: k_radial_f32<0, 0><<<gr, bl, sm, ctx->s>>>(g, xx, sr); break;
+    }
+  } else {
     k_radial<R><<<d.P, round32(std::max(d.Nd, 32)), 3 * d.Nr * sizeof(V), ctx->s>>>(
         g, reinterpret_cast<const double2*>(x), reinterpret_cast<V*>(ctx->SR));
+  }
   CK(cudaGetLastError());
   }
   const LegDev<R>& L = leg<R>(ctx);
@@ -1111,9 +1129,17 @@ rsc_status stage_rhs(rsc_ctx* ctx, const RhsParams& rp, const double* x, const d
   if constexpr (sizeof(R) == 4) {
     // Jacobian actions of the mixed path: persistent, tables staged once (k_rhs_lin)
     if (rp.mode == 1 && !rp.explicit_coriolis && ctx->rhs_lin_grid > 0) {
-      k_rhs_lin<<<ctx->rhs_lin_grid, 4 * ((d.Nr + 7) / 8 * 8), rhs_lin_smem(d.Nr, d.Nd), ctx->s>>>(
-          ctx->geom(), rp, reinterpret_cast<const float2*>(ctx->AR),
-          reinterpret_cast<const double2*>(x), reinterpret_cast<const double2*>(U), u_orig, out);
+      const dim3 gr(ctx->rhs_lin_grid), bl(4 * ((d.Nr + 7) / 8 * 8));
+      const size_t sm = rhs_lin_smem(d.Nr, d.Nd);
+      const DevGeom g = ctx->geom();
+      const float2* arp = reinterpret_cast<const float2*>(ctx->AR);
+      const double2* xx = reinterpret_cast<const double2*>(x);
+      const double2* uu = reinterpret_cast<const double2*>(U);
+      switch (radial_fixed(d)) {
+        case 1: k_rhs_lin<64, 96><<<gr, bl, sm, ctx->s>>>(g, rp, arp, xx, uu, u_orig, out); break;
+        case 2: k_rhs_lin<96, 144><<<gr, bl, sm, ctx->s>>>(g, rp, arp, xx, uu, u_orig, out); break;
+        default: k_rhs_lin<0, 0><<<gr, bl, sm, ctx->s>>>(g, rp, arp, xx, uu, u_orig, out); break;
+      }
       CK(cudaGetLastError());
       return RSC_OK;
     }

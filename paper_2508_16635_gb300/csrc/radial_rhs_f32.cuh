@@ -67,10 +67,15 @@ __host__ __forceinline__ size_t rhs_lin_smem(int Nr, int Nd) {
 
 // grid <= P blocks, block = 4 * round8(Nd) threads (>= 3 Nr), dynamic shared memory
 // radial_f32_smem.  SR[(p * Nd + i) * 8 + q], q = u_r, S_u, T_u, omega_r, S_w, T_w, d_r T, S_T.
+// NR_, ND_ > 0 fix N_r, N_d at compile time (both multiples of 4: the four-lane loops unroll
+// fully); 0, 0 reads them from g.
+template <int NR_, int ND_>
 __global__ void __launch_bounds__(1024) k_radial_f32(DevGeom g, const double2* __restrict__ x,
                                                      float2* __restrict__ SR) {
   extern __shared__ __align__(16) float rr_sh[];
-  const int Nr = g.Nr, Nd = g.Nd, P = g.P;
+  constexpr bool FIX = NR_ > 0;
+  static_assert(!FIX || (NR_ % 4 == 0 && ND_ % 4 == 0), "fixed sizes are multiples of 4");
+  const int Nr = FIX ? NR_ : g.Nr, Nd = FIX ? ND_ : g.Nd, P = g.P;
   const int SI = rr_stride(Nd);
   float* E0 = rr_sh;                 // [k][i], stride SI
   float* E1 = E0 + Nr * SI;
@@ -97,7 +102,7 @@ __global__ void __launch_bounds__(1024) k_radial_f32(DevGeom g, const double2* _
     if (ld && p + gridDim.x < P) nx = x[((long)tf * P + p + gridDim.x) * Nr + tk];
     float fvx = 0, fvy = 0, f1x = 0, f1y = 0, f2x = 0, f2y = 0, evx = 0, evy = 0, e1x = 0, e1y = 0;
     float Tvx = 0, Tvy = 0, T1x = 0, T1y = 0;
-    for (int k = s; k < Nr; k += 4) {
+    auto step = [&](int k) {
       const float a0 = E0[k * SI + i], a1 = E1[k * SI + i], a2 = E2[k * SI + i];
       const float2 e = xs[k], f = xs[Nr + k], T = xs[2 * Nr + k];
       fvx += a0 * f.x; fvy += a0 * f.y;
@@ -107,6 +112,12 @@ __global__ void __launch_bounds__(1024) k_radial_f32(DevGeom g, const double2* _
       e1x += a1 * e.x; e1y += a1 * e.y;
       Tvx += a0 * T.x; Tvy += a0 * T.y;
       T1x += a1 * T.x; T1y += a1 * T.y;
+    };
+    if constexpr (FIX) {
+#pragma unroll
+      for (int u = 0; u < NR_ / 4; ++u) step(4 * u + s);
+    } else {
+      for (int k = s; k < Nr; k += 4) step(k);
     }
     fvx = rl_sum4(fvx); fvy = rl_sum4(fvy); f1x = rl_sum4(f1x); f1y = rl_sum4(f1y);
     f2x = rl_sum4(f2x); f2y = rl_sum4(f2y); evx = rl_sum4(evx); evy = rl_sum4(evy);
@@ -135,6 +146,8 @@ __global__ void __launch_bounds__(1024) k_radial_f32(DevGeom g, const double2* _
 
 // grid <= P blocks, block = 4 * round8(Nr) threads (>= 3 Nr, >= 2 Nd, <= 512), dynamic shared memory
 // rhs_lin_smem.  rhs[(f * P + p) * Nr + j], f = e, f, T.
+// NR_, ND_ as for k_radial_f32.
+template <int NR_, int ND_>
 __global__ void __launch_bounds__(512) k_rhs_lin(DevGeom g, RhsParams rp,
                                                   const float2* __restrict__ AR,
                                                   const double2* __restrict__ x,
@@ -142,7 +155,9 @@ __global__ void __launch_bounds__(512) k_rhs_lin(DevGeom g, RhsParams rp,
                                                   const double* __restrict__ u_orig,
                                                   double2* __restrict__ rhs) {
   extern __shared__ __align__(16) float rl_sh[];
-  const int Nr = g.Nr, Nd = g.Nd, P = g.P;
+  constexpr bool FIX = NR_ > 0;
+  static_assert(!FIX || (NR_ % 4 == 0 && ND_ % 4 == 0), "fixed sizes are multiples of 4");
+  const int Nr = FIX ? NR_ : g.Nr, Nd = FIX ? ND_ : g.Nd, P = g.P;
   const int SJ = rr_stride(Nr);
   const bool has_c = rp.J >= 0;
   float* W0 = rl_sh;                 // [i][j] projection onto T_j's row j
@@ -197,24 +212,36 @@ __global__ void __launch_bounds__(512) k_rhs_lin(DevGeom g, RhsParams rp,
     if (p + gridDim.x < P) fetch(p + gridDim.x);
     // radial projection of the analysed products
     float Qx = 0, Qy = 0, Tx = 0, Ty = 0, Nx = 0, Ny = 0, Sx = 0, Sy = 0;
-    for (int i = s; i < Nd; i += 4) {
+    auto pstep = [&](int i) {
       const float w0 = W0[i * SJ + j], w1 = W1[i * SJ + j];
       const float2 q = ar[i * 4 + 0], sv = ar[i * 4 + 1], tt = ar[i * 4 + 2], n = ar[i * 4 + 3];
       Qx += w0 * q.x; Qy += w0 * q.y;
       Tx += w0 * tt.x; Ty += w0 * tt.y;
       Nx += w0 * n.x; Ny += w0 * n.y;
       Sx += w1 * sv.x; Sy += w1 * sv.y;
+    };
+    if constexpr (FIX) {
+#pragma unroll
+      for (int u = 0; u < ND_ / 4; ++u) pstep(4 * u + s);
+    } else {
+      for (int i = s; i < Nd; i += 4) pstep(i);
     }
     // mass products: e0 = sum_k T_k(r_j) e_k, f0, f2 = sum_k T_k''(r_j) f_k, t0
     auto mass = [&](const float2* vf, float* o) {
       float e0x = 0, e0y = 0, f0x = 0, f0y = 0, f2x = 0, f2y = 0, t0x = 0, t0y = 0;
-      for (int k = s; k < Nr; k += 4) {
+      auto mstep = [&](int k) {
         const float c0 = C0[k * SJ + j], c2 = C2[k * SJ + j];
         const float2 e = vf[k], f = vf[Nr + k], T = vf[2 * Nr + k];
         e0x += c0 * e.x; e0y += c0 * e.y;
         f0x += c0 * f.x; f0y += c0 * f.y;
         f2x += c2 * f.x; f2y += c2 * f.y;
         t0x += c0 * T.x; t0y += c0 * T.y;
+      };
+      if constexpr (FIX) {
+#pragma unroll
+        for (int u = 0; u < NR_ / 4; ++u) mstep(4 * u + s);
+      } else {
+        for (int k = s; k < Nr; k += 4) mstep(k);
       }
       o[0] = rl_sum4(e0x); o[1] = rl_sum4(e0y); o[2] = rl_sum4(f0x); o[3] = rl_sum4(f0y);
       o[4] = rl_sum4(f2x); o[5] = rl_sum4(f2y); o[6] = rl_sum4(t0x); o[7] = rl_sum4(t0y);
