@@ -1068,17 +1068,16 @@ rsc_status stage_products_analysis(rsc_ctx* ctx, bool lin) {
   if constexpr (sizeof(R) == 4) {
     // Jacobian actions on the small transforms of the wave workloads
     // (the kernel's gather offsets are 32-bit: 9 Nd (K + 1) nlat coefficients per field set)
-    if (lin && ug && d.nphi <= 32 && K1 <= 16 && WPB <= kPlMaxWarps &&
+    if (lin && ug && d.nphi <= 32 && K1 <= 12 && WPB <= kPlMaxWarps &&
         9.0 * d.Nd * K1 * d.nlat < 2147483647.0) {
       const float2* fc = reinterpret_cast<const float2*>(ctx->FC);
       float2* fa = reinterpret_cast<float2*>(ctx->FA);
       const float* ugp = reinterpret_cast<const float*>(ctx->UG);
+      // (nphi >= 3 K + 1, so nphi <= 32 keeps K + 1 <= 11)
       if (K1 <= 8)
         k_products_lin<8><<<grid, 32 * WPB, 0, ctx->s>>>(g, L.view(), (float)ctx->p.Ek, fc, fa, LPW, ugp);
-      else if (K1 <= 12)
-        k_products_lin<12><<<grid, 32 * WPB, 0, ctx->s>>>(g, L.view(), (float)ctx->p.Ek, fc, fa, LPW, ugp);
       else
-        k_products_lin<16><<<grid, 32 * WPB, 0, ctx->s>>>(g, L.view(), (float)ctx->p.Ek, fc, fa, LPW, ugp);
+        k_products_lin<12><<<grid, 32 * WPB, 0, ctx->s>>>(g, L.view(), (float)ctx->p.Ek, fc, fa, LPW, ugp);
       done = true;
     }
   }

@@ -3,7 +3,7 @@
 // values, and the forward DFT of the four products (Sec. 3.1, Eqs. advec / curl terms,
 // linearised about the wave as in Sec. 3.3), in FP32.  The same arithmetic as
 // k_products<float, true> with the base state read from UG (k_base_grid), arranged for
-// the small transforms of the wave workloads (K + 1 <= KM wavenumbers, nphi <= 32
+// the small transforms of the wave workloads (K + 1 <= KM <= 16 wavenumbers, nphi <= 32
 // longitudes):
 //  - a warp per latitude, lane j = longitude j for the inverse DFT: its twiddles
 //    cos / sin(2 pi a j / nphi) sit in registers for every latitude the warp takes, and

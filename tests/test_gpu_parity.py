@@ -142,6 +142,30 @@ def test_jacobian_parity(torch, name, L, Ms, Nr, Ek, Ra, with_drift):
     gpu.close()
 
 
+# N_r = 96 reaches the compile-time (96, 144) instantiation of the FP32 radial kernels
+CASES_MIXED_JVP = CASES_C3 + [("Nr96", 15, 4, 96, 1e-3, 80.0)]
+
+
+@pytest.mark.parametrize("name,L,Ms,Nr,Ek,Ra", CASES_MIXED_JVP)
+@pytest.mark.parametrize("with_drift", [False, True])
+def test_mixed_jacobian_parity(torch, name, L, Ms, Nr, Ek, Ra, with_drift):
+    """Mixed path: the Jacobian action (FP32 radial evaluation, transforms, products and
+    right-hand side; double-float chain solve) against the FP64 oracle, field by field.
+    The bound is FP32-level: sums of O(100) terms rounded to FP32 (unit roundoff 6e-8) and
+    3xTF32 Legendre products, about 1e-6 of the field magnitudes (measured on a GB300: at
+    most 1.6e-6 over these cases); a missing or wrong term (a boundary row, the drift term,
+    a Coriolis coupling) is O(1)."""
+    from paper_2508_16635_gb300 import RotatingShell
+    C, dt = -1.1, 200.0
+    U, u, J, want = _oracle_jvp(L, Ms, Nr, Ek, Ra, 29, with_drift, C, dt)
+    gpu = RotatingShell(L, Ms, Nr, Ek, Ra, precision="mixed")
+    got = gpu.apply_jacobian(torch.tensor(U, device="cuda"), C, J,
+                             torch.tensor(u, device="cuda"), dt).cpu().numpy()
+    errs = _maxabs_fields(_shell(L, Ms, Nr, Ek, Ra), got, want)
+    assert max(errs) < 1e-5, errs
+    gpu.close()
+
+
 def test_jacobian_batch_of_directions(torch):
     from paper_2508_16635_gb300 import RotatingShell
     L, Ms, Nr = 15, 4, 16
