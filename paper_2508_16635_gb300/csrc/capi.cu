@@ -502,10 +502,33 @@ rsc_status set_smem_limits(rsc_ctx* ctx) {
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const Dims& d = ctx->d;
     const size_t lim = 227 * 1024;
+    // The attribute belongs to the kernel on this device, not to this context: it only ever
+    // grows (the largest need of any context so far), so that a context of smaller sizes
+    // created later never lowers it under an earlier one.
+    struct AttrSet {
+      const void* fn;
+      int dev;
+      size_t smem;
+    };
+    static std::mutex attr_mu;
+    static std::vector<AttrSet> attr_set;
     auto grid_for = [&](const void* fn, int thr, size_t smem, bool fits) -> int {
       if (!fits || thr > 1024 || smem > lim) return 0;
-      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 0;
+      {
+        std::lock_guard<std::mutex> lk(attr_mu);
+        size_t* have = nullptr;
+        for (auto& e : attr_set)
+          if (e.fn == fn && e.dev == dev) have = &e.smem;
+        if (!have) {
+          attr_set.push_back(AttrSet{fn, dev, 0});
+          have = &attr_set.back().smem;
+        }
+        if (smem > *have) {
+          if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return 0;
+          *have = smem;
+        }
+      }
       int nb = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, thr, smem) != cudaSuccess || nb < 1)
         return 0;
