@@ -13,8 +13,10 @@ tol * ||b|| (Sec. 3.3 accepts at relative 1e-10).
 Pins: tests/test_oracle_krylov.py (GMRES against a dense LU solve of the
 assembled Jacobian with the drift unknown; the converged rotating wave is the
 same at pseudo-timesteps 200 and 20 (Eq. finalrhs); quadratic convergence of
-Newton onto the wave) and tests/test_oracle_paper_values.py (the drift speeds
-of Table 1).
+Newton onto the wave; the converged wave balances the heat flux through the two
+walls and the buoyancy work against the viscous dissipation, as a steady state
+of the continuous equations does) and tests/test_oracle_paper_values.py (the
+drift speeds of Table 1).
 """
 import numpy as np
 

@@ -5,12 +5,20 @@
 * The rotating wave does not depend on the Newton pseudo-timestep: B(U) - U = P(dt) A(U)
   with P(dt) invertible (Eq. finalrhs), so the roots at dt = 200 and dt = 20 coincide.
 * Newton converges quadratically once close to the wave (Eq. precond, Eq. twNewton).
+* The converged wave is steady in its drifting frame, so two balances of the continuous
+  equations hold on it to spectral accuracy (and fail on a state that is still evolving):
+  the heat flux through the inner and outer walls is the same (Nu_in = Nu_out), and the
+  buoyancy work equals the viscous dissipation.  With the momentum equation of the model,
+  Ek dU/dt = Ek lap U - 2 e_z x U + Ek U x omega + Ra T r / r_out - grad p (Sec. 2), and
+  no-slip walls, Coriolis and U x omega do no work and int U . lap U dV = -int |omega|^2 dV,
+  so on the wave Ek int |omega|^2 dV = (Ra / r_out) int T r u_r dV.  The integrals are
+  computed here by synthesis at Gauss-Legendre radii, independently of the time step.
 """
 import numpy as np
 import pytest
 
 import seeded_inputs as si
-from oracle import krylov
+from oracle import basis, krylov
 from oracle.shell import Shell
 
 
@@ -77,3 +85,76 @@ def test_newton_converges_quadratically(rw4):
     k = next(i for i, v in enumerate(r) if v < 1e-4)
     assert k + 1 < len(r)
     assert np.log10(r[k + 1]) < 1.8 * np.log10(r[k])
+
+
+def _dissipation_and_work(s, vec):
+    """(Ek int |omega|^2 dV, (Ra / r_out) int T r u_r dV) of a state: omega = curl U has
+    poloidal potential e and toroidal potential -L_l f (Sec. 2.1); the fields are synthesised
+    on the transform grid at 2 N_r + 16 Gauss-Legendre radii and integrated with the
+    latitude weights, over the sector, and in r."""
+    x = s.to_complex(vec)
+    xq, wq = np.polynomial.legendre.leggauss(2 * s.Nr + 16)
+    rq = basis.x_to_r(xq, s.r_in, s.r_out)
+    E0, E1, E2 = (basis.cheb_matrix(xq, s.Nr, o, s.r_in, s.r_out) for o in range(3))
+    e, f, T = x[0], x[1], x[2]
+    r = rq[None, :]
+    lam = s.lam[:, None]
+    fv, f2, ev = f @ E0.T, f @ E2.T, e @ E0.T
+    sp = s.sph
+
+    def scalar(a):
+        return sp.fourier_to_grid(sp.synth_scalar(s.split_m(a)))
+
+    w_r = scalar(lam * ev / r ** 2)
+    w_t, w_p = sp.synth_vector(s.split_m((e @ E1.T) / r), s.split_m(-(f2 - lam * fv / r ** 2) / r))
+    w_t, w_p = sp.fourier_to_grid(w_t), sp.fourier_to_grid(w_p)
+    u_r = scalar(lam * fv / r ** 2)
+    Tg = scalar(T @ E0.T)
+    wlat = sp.w[None, :, None]
+    dphi = 2.0 * np.pi / sp.nphi
+    rad = 0.5 * (s.r_out - s.r_in) * wq * rq ** 2
+
+    def integral(g):
+        return float((rad * (g * wlat).sum(axis=(0, 1)) * dphi).sum())
+
+    D = integral(w_r ** 2 + w_t ** 2 + w_p ** 2)
+    W = integral(Tg * u_r * rq[None, None, :])
+    return s.Ek * D, s.Ra / s.r_out * W
+
+
+@pytest.fixture(scope="module")
+def rw4_fine():
+    """The RW4 wave at L = 23, N_r = 20 (resolved to about 1e-4 in the balances below)."""
+    s, U0, C0, J = _rw4_guess(23, 4, 20)
+    U, C, hist = krylov.newton(s, U0, C0, J, dt=200.0, tol=1e-12, max_newton=12, kmax=300)
+    assert hist[-1]["residual"] < 1e-12
+    return s, U0, U
+
+
+def _power_imbalance(s, vec):
+    D, W = _dissipation_and_work(s, vec)
+    return abs(D - W) / D
+
+
+def _heat_imbalance(s, vec):
+    nin, nout = s.nusselt(vec)
+    return abs(nin - nout) / abs(nin - 1.0)
+
+
+def test_rotating_wave_balances_heat_flux_and_power(rw4_fine):
+    s, U0, U = rw4_fine
+    assert _heat_imbalance(s, U) < 2e-3          # measured 2.4e-4
+    assert _power_imbalance(s, U) < 5e-4         # measured 4.1e-5
+    # the time-stepped guess is still evolving: neither balance holds
+    assert _heat_imbalance(s, U0) > 0.1          # measured 0.34
+    assert _power_imbalance(s, U0) > 1e-2        # measured 0.040
+
+
+def test_balance_defects_are_truncation_errors(rw4, rw4_fine):
+    """The imbalance of the converged wave falls by orders of magnitude from L = 15, N_r = 16
+    to L = 23, N_r = 20 (a wrong factor in the model would leave an O(1) defect)."""
+    s_c, sols = rw4
+    s_f, _, U_f = rw4_fine
+    coarse = _power_imbalance(s_c, sols[200.0][0])   # measured 1.4e-2
+    fine = _power_imbalance(s_f, U_f)
+    assert fine < coarse / 30.0
