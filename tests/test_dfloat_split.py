@@ -21,7 +21,7 @@ import pytest
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_2508_16635_gb300", "csrc")
 
-DRIVER = r"""
+HARNESS = r"""
 #include <cstdio>
 #include <vector>
 #include "dfloat.h"
@@ -51,7 +51,7 @@ def split_exe(tmp_path_factory):
         pytest.skip("no host C++ compiler")
     d = tmp_path_factory.mktemp("split48")
     src = d / "drv.cpp"
-    src.write_text(DRIVER)
+    src.write_text(HARNESS)
     exe = d / "drv"
     subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
     return d, exe

@@ -23,7 +23,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_2508_16635_gb300", "csrc")
 
-DRIVER = r"""
+HARNESS = r"""
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -91,7 +91,7 @@ def solve_exe(tmp_path_factory):
         pytest.skip("no host C++ compiler or CUDA headers")
     d = tmp_path_factory.mktemp("hostfactor")
     src = d / "solve.cpp"
-    src.write_text(DRIVER)
+    src.write_text(HARNESS)
     exe = d / "solve"
     subprocess.run([cxx, "-std=c++17", "-O2", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
                     "-I", inc, str(src), os.path.join(CSRC, "tables.cpp"), "-o", str(exe),

@@ -33,12 +33,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_2508_16635_gb300", "csrc")
 
-# The driver writes the factors' products with the right-hand side: the test supplies the
-# couplings (from the oracle) applied to the neighbours, so that the driver needs only the
+# The C harness writes the factors' products with the right-hand side: the test supplies the
+# couplings (from the oracle) applied to the neighbours, so that the harness needs only the
 # factors.  Protocol: phase 1 reads b and writes u = D^-1 b on the odd blocks; the test forms
 # b' = b - A u - C u on the even blocks; phase 2 reads b' and writes the reduced solution;
 # the test forms r = b - A x - C x on the odd blocks; phase 3 reads r and writes D^-1 r.
-DRIVER = r"""
+HARNESS = r"""
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -97,7 +97,7 @@ def cr_exe(tmp_path_factory):
         pytest.skip("no host C++ compiler or CUDA headers")
     d = tmp_path_factory.mktemp("hostfactor_cr")
     src = d / "cr.cpp"
-    src.write_text(DRIVER)
+    src.write_text(HARNESS)
     exe = d / "cr"
     subprocess.run([cxx, "-std=c++17", "-O2", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
                     "-I", inc, str(src), os.path.join(CSRC, "tables.cpp"), "-o", str(exe),

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_2508_16635_gb300", "csrc")
 
-DRIVER = r"""
+HARNESS = r"""
 // CPU check of the partitioned chain factorisation: solve random right-hand sides on every
 // chain with the unpartitioned twisted factors and with the partitioned ones (part solves,
 // reduced system, correction; the data flow of the GPU kernels) and compare.
@@ -137,7 +137,7 @@ def check_exe(tmp_path_factory):
         pytest.skip("no host C++ compiler or CUDA headers")
     d = tmp_path_factory.mktemp("partition")
     src = d / "check.cpp"
-    src.write_text(DRIVER)
+    src.write_text(HARNESS)
     exe = d / "check"
     subprocess.run([cxx, "-std=c++17", "-O2", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
                     "-I", inc, str(src), os.path.join(CSRC, "tables.cpp"), "-o", str(exe),

@@ -49,7 +49,7 @@ def test_norm2_noalloc_matches_context_norm_on_two_calls(torch):
         assert st == 0
         torch.cuda.synchronize()
         assert abs(out.item() - ref) <= 1e-12 * ref
-    # the calls allocated no device memory (driver free bytes and torch's allocator)
+    # the calls allocated no device memory (the CUDA driver's free bytes and torch's allocator)
     assert torch.cuda.mem_get_info()[0] == free0
     assert torch.cuda.memory_allocated() == alloc0
     v = vs[0]
