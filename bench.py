@@ -981,6 +981,19 @@ def configs_study(torch, RotatingShell, Batch):
     return out
 
 
+def replica_throughput(torch, dist, units, seconds, device):
+    """Whole-job throughput of independent replicas: the units every rank processed, summed,
+    over the slowest rank's time (seconds).  dist = None on a single rank.  The two
+    reductions run on tensors on `device` (the rank's GPU under NCCL, the CPU under gloo)."""
+    if dist is None:
+        return units / seconds, units, seconds
+    u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()) / float(t.item()), float(u.item()), float(t.item())
+
+
 def run_gpu(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -1097,10 +1110,10 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    # JVPs per second of all ranks: the actions every rank ran over the slowest rank's time
+    value, _, slowest_s = replica_throughput(torch, dist, gmres_total / args.steps, ms * 1e-3,
+                                             torch.device("cuda", local))
+    ms = slowest_s * 1e3
     # traced passes over the same iteration (individual launches, CUDA events on the
     # context stream): one with every kernel for the breakdown, then one timing only
     # the dominant kernel for the roofline
@@ -1118,7 +1131,6 @@ def run_gpu(args):
     prof = sh.profile_report()
     sh.profile(False)
     jvps_per_step = gmres_total / args.steps
-    value = world * jvps_per_step / (ms * 1e-3)
 
     # per-kernel cost of one Jacobian action and of one FP64 residual step
     ub = torch.tensor(si.random_vector(w["L"], w["Ms"], w["Nr"], seed=3002), device="cuda")
@@ -1157,8 +1169,9 @@ def run_gpu(args):
         t0 = time.perf_counter()
         _, rep2, _ = sh.newton_rw_host(h, 0.5, J, tol=0.0, max_newton=1, kmax=K, gmres_tol=0.0)
         e2e_times.append((time.perf_counter() - t0, rep2["gmres_total"]))
-    e2e_t = sum(t for t, _ in e2e_times) / len(e2e_times)
-    e2e_v = world * sum(g for _, g in e2e_times) / len(e2e_times) / e2e_t
+    e2e_v, _, e2e_t = replica_throughput(torch, dist, sum(g for _, g in e2e_times) / len(e2e_times),
+                                         sum(t for t, _ in e2e_times) / len(e2e_times),
+                                         torch.device("cuda", local))
 
     if rank == 0:
         line = {

@@ -73,3 +73,40 @@ def test_dtype_label_says_what_ran():
     assert "double-float e/f chain solve" in lab and "double-float Krylov basis" in lab
     lab = bench.dtype_label("mixed", {"chain_df": 0, "krylov_split": 0})
     assert "f64 e/f chain solve" in lab and "f64 Krylov basis" in lab
+
+
+def _replica_rank(rank, world, port, out):
+    """One gloo rank on the CPU: rank r ran r + 1 units in 0.5 + r seconds."""
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        v, units, secs = bench.replica_throughput(torch, dist, rank + 1, 0.5 + rank,
+                                                  torch.device("cpu"))
+        out[rank] = (v, units, secs)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_throughput_sums_units_over_the_slowest_rank():
+    """bench.py with N > 1: the whole-job value is the units of all ranks over the slowest
+    rank's time (world_size 2 over gloo on the CPU); a single rank reduces to units / time."""
+    import socket
+    import torch
+    import torch.multiprocessing as mp
+    assert bench.replica_throughput(torch, None, 200, 0.08, None) == (2500.0, 200, 0.08)
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        mp.start_processes(_replica_rank, args=(2, port, out), nprocs=2, join=True,
+                           start_method="spawn")
+        res = dict(out)
+    for r in (0, 1):
+        v, units, secs = res[r]
+        assert units == 3.0 and secs == 1.5
+        assert v == pytest.approx(2.0)
